@@ -1,0 +1,464 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test compares the oracle with something other than itself: a published
+identity between two independent coefficient tables, a closed form, a second
+published form of the same quantity, a symmetry, or a library routine on a
+special case.  A dropped term, wrong sign or transposed index in the oracle
+fails at least one of them.  No GPU is needed.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import gwcat
+import oracle
+from tests.helpers import (OMEGA_E, R_EARTH, C_SI, amp0, geom_grid, jks, oracle_catalog,
+                           psd_eval)
+
+RNG = np.random.default_rng(7)
+
+
+def richardson(fun, x, h, levels=4):
+    """Richardson-extrapolated central difference of a scalar function (test-side)."""
+    R = []
+    for m in range(levels):
+        d = h / 2 ** m
+        R.append([(fun(x + d) - fun(x - d)) / (2 * d)])
+    for j in range(1, levels):
+        for m in range(j, levels):
+            R[m].append(R[m][j - 1] + (R[m][j - 1] - R[m - 1][j - 1]) / (4 ** j - 1))
+    return R[-1][-1]
+
+
+# ---------------------------------------------------------------- waveform tables
+@pytest.mark.parametrize("Mc,eta", [(1.2, 0.2499), (1.5, 0.23), (30.0, 0.2), (8.0, 0.1)])
+def test_phase_and_tau_tables_agree(Mc, eta):
+    """dPsi/df = -2 pi tau*(f) for the non-spinning 3.5PN tables (stationary phase:
+    the time-frequency relation of Buonanno et al. 2009, cited in Sec. 2.2)."""
+    fisco = 1 / (6 ** 1.5 * math.pi * Mc * eta ** -0.6 * 4.925490947641267e-6)
+    for f in np.geomspace(3.0, 0.8 * fisco, 6):
+        dpsi = richardson(lambda x: oracle.psi_pn(Mc, eta, 0, 0, 0, 0, x), f, 1e-3 * f)
+        tau = oracle.tau_star(Mc, eta, f)
+        assert abs(dpsi + 2 * math.pi * tau) <= 1e-9 * abs(2 * math.pi * tau)
+
+
+def test_chirp_mass_scaling():
+    """At fixed eta, Psi depends on Mc f only and tau* = Mc x function(Mc f)."""
+    for _ in range(5):
+        Mc, eta, lam = RNG.uniform(1, 40), RNG.uniform(0.1, 0.25), RNG.uniform(0.5, 2)
+        f = 5.0
+        a = oracle.psi_pn(lam * Mc, eta, 0.3, -0.2, 0, 0, f)
+        b = oracle.psi_pn(Mc, eta, 0.3, -0.2, 0, 0, lam * f)
+        assert abs(a - b) <= 1e-13 * abs(a)
+        ta, tb = oracle.tau_star(lam * Mc, eta, f), lam * oracle.tau_star(Mc, eta, lam * f)
+        assert abs(ta - tb) <= 1e-13 * abs(ta)
+
+
+def _v(Mc, eta, f):
+    return (math.pi * Mc * 4.925490947641267e-6 * eta ** -0.6 * f) ** (1 / 3)
+
+
+def test_spin_terms_match_chis_chia_form():
+    """The spin-orbit coefficient written per body equals the (chi_s, chi_a) form
+    (Eq. (2.1) of the paper defines chi_s, chi_a), with spin-spin 79/8 eta chi1 chi2."""
+    for _ in range(6):
+        Mc, eta = RNG.uniform(2, 30), RNG.uniform(0.1, 0.249)
+        c1, c2 = RNG.uniform(-0.9, 0.9, 2)
+        f = RNG.uniform(3, 20)
+        d = math.sqrt(1 - 4 * eta)
+        cs, ca = (c1 + c2) / 2, (c1 - c2) / 2
+        beta = 113 / 12 * (cs + d * ca - 76 / 113 * eta * cs)
+        sigma = 79 / 8 * eta * c1 * c2
+        v = _v(Mc, eta, f)
+        expect = 3 / (128 * eta * v ** 5) * (4 * beta * v ** 3 - 10 * sigma * v ** 4)
+        got = oracle.psi_pn(Mc, eta, c1, c2, 0, 0, f) - oracle.psi_pn(Mc, eta, 0, 0, 0, 0, f)
+        assert abs(got - expect) <= 1e-7 * abs(expect) + 1e-9
+
+
+def test_tidal_phase_matches_per_body_form():
+    """Lambda-tilde / delta-Lambda-tilde from Eq. (2.2) inserted in the 5PN+6PN
+    tidal phase equal the per-body tidal phase (Flanagan-Hinderer 5PN,
+    Vines-Flanagan-Hinderer 6PN)."""
+    n = 8
+    m1, m2 = RNG.uniform(1.0, 2.2, n), RNG.uniform(1.0, 2.2, n)
+    L1, L2 = RNG.uniform(0, 2000, n), RNG.uniform(0, 2000, n)
+    z = np.zeros(n)
+    p = oracle.prepare(m1, m2, z, z, L1, L2, np.full(n, 100.0), np.zeros(n, np.uint8), z)
+    for e in range(n):
+        a, b, la, lb = m1[e], m2[e], L1[e], L2[e]
+        if b > a:
+            a, b, la, lb = b, a, lb, la
+        M = a + b
+        X = (a / M, b / M)
+        Lam = (la, lb)
+        eta = p["eta"][e]
+        f = RNG.uniform(20, 300)
+        v = _v(p["Mc"][e], eta, f)
+        s5 = sum(24 * (1 + 11 * X[1 - i]) * X[i] ** 4 * Lam[i] for i in range(2))
+        s6 = sum((15895 / 28 - 4595 / 28 * X[i] - 5715 / 14 * X[i] ** 2 + 325 / 7 * X[i] ** 3)
+                 * X[i] ** 4 * Lam[i] for i in range(2))
+        expect = 3 / (128 * eta) * (-s5 * v ** 5 - s6 * v ** 7)
+        got = (oracle.psi_pn(p["Mc"][e], eta, 0, 0, p["LamT"][e], p["dLamT"][e], f)
+               - oracle.psi_pn(p["Mc"][e], eta, 0, 0, 0, 0, f))
+        assert abs(got - expect) <= 1e-8 * abs(expect)
+
+
+def test_lambda_tilde_special_cases():
+    """Eq. (2.2): equal masses and equal Lambda give LambdaT = Lambda, dLambdaT = 0;
+    LambdaT equals the mass-weighted definition (16/13) sum (X_a + 12 X_b) X_a^4 L_a."""
+    one = np.ones(1)
+    p = oracle.prepare(1.4 * one, 1.4 * one, 0 * one, 0 * one, 400 * one, 400 * one,
+                       100 * one, np.zeros(1, np.uint8), 0 * one)
+    assert abs(p["LamT"][0] - 400) < 1e-10 and abs(p["dLamT"][0]) < 1e-10
+    assert abs(p["eta"][0] - 0.25) < 1e-15
+    m1, m2, L1, L2 = 1.9, 1.2, 200.0, 900.0
+    p = oracle.prepare(np.array([m2]), np.array([m1]), one * 0, one * 0, np.array([L2]),
+                       np.array([L1]), one * 100, np.zeros(1, np.uint8), one * 0)
+    M = m1 + m2
+    X1, X2 = m1 / M, m2 / M
+    lt = 16 / 13 * ((X1 + 12 * X2) * X1 ** 4 * L1 + (X2 + 12 * X1) * X2 ** 4 * L2)
+    assert abs(p["LamT"][0] - lt) < 1e-10 * lt
+
+
+def test_prepare_masses_and_redshift():
+    """Sec. 2.1: detector-frame chirp mass and eta from (1+z) m with z = H0 dL / c;
+    f_ISCO of the Sec. 2.2 footnote; tcoal in sidereal days."""
+    m1, m2, dl = np.array([30.0]), np.array([20.0]), np.array([3000.0])
+    p = oracle.prepare(m1, m2, np.array([0.5]), np.array([-0.2]), None, None, dl,
+                       np.ones(1, np.uint8), np.array([0.25]))
+    z = 70.0 * 3000.0 / 299792.458
+    M = 50.0 * (1 + z)
+    eta = 600.0 / 2500.0
+    assert abs(p["eta"][0] - eta) < 1e-15
+    assert abs(p["Mc"][0] - M * eta ** 0.6) < 1e-12 * M
+    assert abs(p["dL"][0] - 3.0) < 1e-15
+    assert abs(p["tc"][0] - 0.25 * 86164.0905) < 1e-9
+    fisco = 1 / (6 ** 1.5 * math.pi * M * 4.925490947641267e-6)
+    assert abs(p["fisco"][0] - fisco) < 1e-12 * fisco
+    # m2 > m1 is reordered with its spin
+    p = oracle.prepare(m2, m1, np.array([0.5]), np.array([-0.2]), None, None, dl,
+                       np.zeros(1, np.uint8), np.array([0.0]))
+    assert p["chi1z"][0] == -0.2 and p["chi2z"][0] == 0.5
+
+
+def test_grid_rule():
+    n = oracle.grid_npts(np.array([2.0, 2.0, 2.0]), np.array([10.0, 2.0e4, 2.1]), 40.0, 200, 20000)
+    assert list(n) == [200, math.ceil(40 * math.log(1e4)), 200]
+
+
+# ---------------------------------------------------------------- antenna patterns
+def test_antenna_tensor_equals_jks():
+    """Pattern functions by tensor contraction equal the JKS closed form."""
+    for _ in range(50):
+        lat, L, gam = RNG.uniform(-1.5, 1.5), RNG.uniform(0, 6.3), RNG.uniform(0, 6.3)
+        th, ph, ps = RNG.uniform(0, math.pi), RNG.uniform(0, 6.3), RNG.uniform(0, math.pi)
+        zeta = RNG.choice([math.pi / 2, math.pi / 3])
+        a = oracle.antenna(lat, L, gam, zeta, th, ph, ps)
+        b = jks(lat, gam, zeta, th, ph, ps, L)
+        assert abs(a[0] - b[0]) < 1e-14 and abs(a[1] - b[1]) < 1e-14
+
+
+def test_triangle_arms_sum_to_zero_and_zenith_norm():
+    """Closed triangle: the three arms' patterns sum to zero (Sec. 3.3).
+    Source at the zenith of an L detector: F+^2 + Fx^2 = sin^2 zeta."""
+    for _ in range(20):
+        lat, L, gT = RNG.uniform(-1.5, 1.5), RNG.uniform(0, 6.3), RNG.uniform(0, 6.3)
+        th, ph, ps = RNG.uniform(0, math.pi), RNG.uniform(0, 6.3), RNG.uniform(0, math.pi)
+        arms = [oracle.antenna(lat, L, gT + math.pi / 6 + 2 * math.pi * k / 3, math.pi / 3,
+                               th, ph, ps) for k in range(3)]
+        assert abs(sum(a[0] for a in arms)) < 1e-15 and abs(sum(a[1] for a in arms)) < 1e-15
+        fp, fx = oracle.antenna(lat, L, gT, math.pi / 2, math.pi / 2 - lat, L, ps)
+        assert abs(fp * fp + fx * fx - 1.0) < 1e-14
+        assert abs(oracle.antenna(lat, L, gT, math.pi / 2, th, ph, ps + math.pi / 2)[0]
+                   + oracle.antenna(lat, L, gT, math.pi / 2, th, ph, ps)[0]) < 1e-14
+
+
+# ---------------------------------------------------------------- strain: rotation and Doppler
+def _one_event(cfg="c1", seed=11, zero_spin=False):
+    cat, d, p = oracle_catalog(cfg, 1, seed=seed)
+    ev = cat.ev[0].copy()
+    if zero_spin:
+        ev[9:13] = 0
+    return ev, cat
+
+
+def test_strain_rotation_follows_t_of_f():
+    """|h(f)| = A(f) |F+(g) c+ + i Fx(g) cx| with Earth angle g = Omega_E (tc - tau*(f))."""
+    ev, cat = _one_event("c1")
+    det, psd, rot = gwcat.network("c1")
+    f, h = oracle.strain(ev, 2.0, cat.fmax[0], 40, det[:1], 1)
+    Mc, eta, dL, th, ph, io, ps, tc = ev[:8]
+    row = det[0]
+    for k in range(0, 40, 7):
+        g = OMEGA_E * (tc - oracle.tau_star(Mc, eta, f[k]))
+        A = amp0(Mc, dL) * f[k] ** (-7 / 6)
+        for a in range(3):
+            fp, fx = jks(row[0], row[2] + math.pi / 6 + 2 * math.pi * a / 3, math.pi / 3,
+                         th, ph, ps, row[1] + g)
+            q = A * abs(fp * (1 + math.cos(io) ** 2) / 2 + 1j * fx * math.cos(io))
+            assert abs(abs(h[a, k]) - q) <= 1e-12 * q
+
+
+def test_doppler_delay_between_sites():
+    """Without rotation, arg(h1/h2) is linear in f with slope 2 pi (r1 - r2).n R_E / c."""
+    ev, cat = _one_event("c0", zero_spin=True)
+    d1 = [0.7, 0.2, 0.3, math.pi / 2, 0, 0]
+    d2 = [-0.4, 2.1, 1.1, math.pi / 2, 0, 0]
+    f, h1 = oracle.strain(ev, 10.0, 400.0, 64, np.array([d1]), 0)
+    _, h2 = oracle.strain(ev, 10.0, 400.0, 64, np.array([d2]), 0)
+    ph = np.unwrap(np.angle(h1[0] / h2[0]))
+    slope = np.polyfit(f, ph, 1)[0]
+    th, phi, tc = ev[3], ev[4], ev[7]
+    g = OMEGA_E * tc
+    n = np.array([math.sin(th) * math.cos(phi), math.sin(th) * math.sin(phi), math.cos(th)])
+
+    def r(lat, lon):
+        L = lon + g
+        return np.array([math.cos(lat) * math.cos(L), math.cos(lat) * math.sin(L), math.sin(lat)])
+
+    expect = 2 * math.pi * (r(d1[0], d1[1]) - r(d2[0], d2[1])) @ n * R_EARTH / C_SI
+    assert abs(slope - expect) < 1e-9 * abs(expect)
+
+
+# ---------------------------------------------------------------- SNR quadrature
+@pytest.mark.parametrize("p_exp", [0.0, -4.0, 2.0])
+def test_snr_geometric_series_closed_form(p_exp):
+    """Power-law PSD, leading-order amplitude, fixed antennas: the trapezoid sum on
+    the geometric grid is a geometric series with a closed form; it also converges
+    to the continuum integral (Sec. 3.2, SNR definition)."""
+    ev, _ = _one_event("c0", zero_spin=True)
+    det = np.array([[0.75, 0.17, 0.35, math.pi / 2, 0, 0]])
+    psd = np.array([[10.0, 1e-49, 1, 1.0, 0, 0, 0, p_exp, 0, 0, 0]])
+    fmin, fmax = 10.0, 900.0
+    Mc, eta, dL, th, ph, io, ps, tc = ev[:8]
+    fp, fx = jks(det[0, 0], det[0, 2], det[0, 3], th, ph, ps, det[0, 1] + OMEGA_E * tc)
+    pol2 = abs(fp * (1 + math.cos(io) ** 2) / 2 + 1j * fx * math.cos(io)) ** 2
+    K = 4 * amp0(Mc, dL) ** 2 * pol2 / (1e-49 * 10.0 ** (-p_exp))
+    q = -7 / 3 - p_exp + 1            # exponent of f in w_k |h|^2 / S
+    for n in (2, 7, 300):
+        cat = oracle.Catalog(ev, 0, fmin, fmax, n)
+        s, st = oracle.snr(cat, det, psd, 0)
+        r = (fmax / fmin) ** (1 / (n - 1))
+        rq = r ** q
+        geo = sum(rq ** k for k in range(1, n - 1))
+        total = fmin ** q * ((r - 1) / 2 + (r - 1 / r) / 2 * geo + (1 - 1 / r) / 2 * rq ** (n - 1))
+        assert abs(s[0] ** 2 - K * total) <= 1e-13 * K * total
+    cat = oracle.Catalog(ev, 0, fmin, fmax, 20000)
+    s, _ = oracle.snr(cat, det, psd, 0)
+    integral = K * (fmax ** q - fmin ** q) / q
+    assert abs(s[0] ** 2 - integral) <= 2e-7 * integral
+
+
+# ---------------------------------------------------------------- Fisher closed forms
+def _fisher1(ev, pset, fmin, fmax, n, det, psd, rot, P):
+    cat = oracle.Catalog(ev, pset, fmin, fmax, n)
+    F, s, err, st = oracle.fisher(cat, det, psd, rot, P)
+    assert st[0] == 0
+    return F[0], s[0]
+
+
+@pytest.mark.parametrize("rot", [0, 1])
+def test_fisher_extrinsic_closed_forms(rot):
+    """d h / d ln dL = -h gives dL^2 G_dLdL = SNR^2; d h/d Phic = -i h gives
+    G_PhicPhic = SNR^2 and G_dL,Phic = 0.  Without rotation d h/d tc = 2 pi i f h
+    gives G_tctc and G_tc,Phic in closed form."""
+    ev, cat = _one_event("c1")
+    det, psd, _ = gwcat.network("c1")
+    n = 120
+    F, s = _fisher1(ev, 1, 2.0, cat.fmax[0], n, det, psd, rot, 11)
+    dL = ev[2]
+    assert abs(dL ** 2 * F[2, 2] - s ** 2) < 1e-9 * s ** 2
+    assert abs(F[8, 8] - s ** 2) < 1e-9 * s ** 2
+    assert abs(F[2, 8]) < 1e-9 * math.sqrt(F[2, 2] * F[8, 8])
+    if rot == 0:
+        f, h = oracle.strain(ev, 2.0, cat.fmax[0], n, det, 0)
+        fg, w = geom_grid(2.0, cat.fmax[0], n)
+        W = 4 * w / psd_eval(psd[0], fg)
+        m2 = (np.abs(h) ** 2).sum(axis=0)
+        gtt = np.sum(W * (2 * math.pi * fg) ** 2 * m2)
+        gtp = -np.sum(W * 2 * math.pi * fg * m2)
+        assert abs(F[7, 7] - gtt) < 1e-9 * gtt
+        assert abs(F[7, 8] - gtp) < 1e-9 * math.sqrt(F[7, 7] * F[8, 8])
+
+
+def test_fisher_chirp_mass_closed_form():
+    """Without spins, tides or rotation, Mc dPsi/dMc = f dPsi/df = -2 pi f tau*(f),
+    so d h/d Mc = h (5/(6 Mc) - 2 pi i f tau*/Mc) and G_McMc, G_Mc,Phic follow."""
+    ev, cat = _one_event("c0", zero_spin=True)
+    det, psd, _ = gwcat.network("c0")
+    n = 150
+    F, s = _fisher1(ev, 0, 10.0, cat.fmax[0], n, det, psd, 0, 9)
+    f, h = oracle.strain(ev, 10.0, cat.fmax[0], n, det, 0)
+    fg, w = geom_grid(10.0, cat.fmax[0], n)
+    W = 4 * w / psd_eval(psd[0], fg) * np.abs(h[0]) ** 2
+    Mc, eta = ev[0], ev[1]
+    tau = np.array([oracle.tau_star(Mc, eta, x) for x in fg])
+    a = 5 / (6 * Mc)
+    b = 2 * math.pi * fg * tau / Mc
+    gmm = np.sum(W * (a ** 2 + b ** 2))
+    gmp = np.sum(W * b)
+    assert abs(F[0, 0] - gmm) < 1e-8 * gmm
+    assert abs(F[0, 8] - gmp) < 1e-8 * math.sqrt(F[0, 0] * F[8, 8])
+    assert abs(F[0, 2] - np.sum(W * a * (-1 / ev[2]))) < 1e-8 * math.sqrt(F[0, 0] * F[2, 2])
+
+
+def test_fisher_iota_psi_closed_forms():
+    """Without rotation the pattern functions are constant: d h/d iota and
+    d h/d psi have closed forms through the JKS patterns."""
+    ev, cat = _one_event("c0", zero_spin=True)
+    det, psd, _ = gwcat.network("c0")
+    n = 100
+    F, s = _fisher1(ev, 0, 10.0, cat.fmax[0], n, det, psd, 0, 9)
+    Mc, eta, dL, th, ph, io, ps, tc = ev[:8]
+    row = det[0]
+    fp, fx = jks(row[0], row[2], row[3], th, ph, ps, row[1] + OMEGA_E * tc)
+    ci, si = math.cos(io), math.sin(io)
+    cp = (1 + ci * ci) / 2
+    fg, w = geom_grid(10.0, cat.fmax[0], n)
+    K = np.sum(4 * w / psd_eval(psd[0], fg) * (amp0(Mc, dL) * fg ** (-7 / 6)) ** 2)
+    d_io = fp * (-ci * si) + 1j * fx * (-si)
+    d_ps = 2 * fx * cp - 2j * fp * ci
+    q = fp * cp + 1j * fx * ci
+    assert abs(s ** 2 - K * abs(q) ** 2) < 1e-12 * s ** 2
+    assert abs(F[5, 5] - K * abs(d_io) ** 2) < 1e-9 * F[5, 5]
+    assert abs(F[6, 6] - K * abs(d_ps) ** 2) < 1e-9 * F[6, 6]
+    assert abs(F[5, 6] - K * (np.conj(d_io) * d_ps).real) < 1e-9 * math.sqrt(F[5, 5] * F[6, 6])
+
+
+def test_fisher_symmetries():
+    """SNR and Gamma are invariant under psi -> psi + pi and under a Phic shift;
+    with rotation they are invariant under (tc, phi) -> (tc + D, phi + Omega_E D)."""
+    ev, cat = _one_event("c1")
+    det, psd, _ = gwcat.network("c1")
+    n = 80
+    F0, s0 = _fisher1(ev, 1, 2.0, cat.fmax[0], n, det, psd, 1, 11)
+    scale = np.sqrt(np.outer(np.diag(F0), np.diag(F0)))
+    for mod in ("psi", "phic", "tc"):
+        e2 = ev.copy()
+        if mod == "psi":
+            e2[6] += math.pi
+        elif mod == "phic":
+            e2[8] += 1.3
+        else:
+            D = 5000.0
+            e2[7] += D
+            e2[4] += OMEGA_E * D
+        F1, s1 = _fisher1(e2, 1, 2.0, cat.fmax[0], n, det, psd, 1, 11)
+        assert abs(s1 - s0) < 1e-11 * s0
+        assert np.max(np.abs(F1 - F0) / scale) < 1e-8
+
+
+def test_fisher_step_insensitive():
+    """The Richardson result does not depend on the first step (0.05-0.2 rad)."""
+    cat, _, _ = oracle_catalog("c2", 2, max_npts=150)
+    det, psd, rot = gwcat.network("c2")
+    res = []
+    for t in (0.05, 0.2):
+        oracle.set_fd_target(t)
+        F, s, err, st = oracle.fisher(cat, det, psd, rot, 11)
+        res.append(F)
+    oracle.set_fd_target(0.1)
+    dg = np.sqrt(np.einsum("eii->ei", res[0]))
+    rel = np.abs(res[1] - res[0]) / (dg[:, :, None] * dg[:, None, :])
+    assert rel.max() < 5e-9
+
+
+def test_config0_fisher_is_rank_five():
+    """One detector with fixed patterns: dL, theta, phi, iota, psi, Phic enter
+    through one complex amplitude, so the 9x9 Fisher has rank 5; the inversion
+    flags every event (Sec. 4: condition number beyond the inverse precision)."""
+    cat, _, _ = oracle_catalog("c0", 3, max_npts=120)
+    det, psd, rot = gwcat.network("c0")
+    F, s, err, st = oracle.fisher(cat, det, psd, rot, 9)
+    for e in range(3):
+        d = np.sqrt(np.diag(F[e]))
+        lam = np.linalg.eigvalsh(F[e] / np.outer(d, d))
+        assert np.sum(lam < 1e-9 * lam.max()) == 4
+    C, k, eps, sti = oracle.invert(F)
+    assert np.all((sti & (oracle.ST_ILL_COND | oracle.ST_NOT_PD)) != 0)
+
+
+# ---------------------------------------------------------------- inversion
+def test_invert_against_numpy():
+    P = 11
+    mats = []
+    for _ in range(6):
+        A = RNG.normal(size=(P, P))
+        G = A @ A.T + P * np.eye(P)
+        s = np.exp(RNG.uniform(-8, 8, P))
+        mats.append(G * np.outer(s, s))
+    F = np.array(mats)
+    C, k, eps, st = oracle.invert(F)
+    for e in range(len(F)):
+        ref = np.linalg.inv(F[e])
+        sc = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+        assert np.max(np.abs(C[e] - ref) / sc) < 1e-12
+        d = np.sqrt(np.diag(F[e]))
+        lam = np.linalg.eigvalsh(F[e] / np.outer(d, d))
+        assert abs(k[e] - lam.max() / lam.min()) < 1e-10 * k[e]
+        assert st[e] == 0 and eps[e] < 1e-8
+    bad = F[:3].copy()
+    bad[0, 0, 1] = bad[0, 1, 0] = 10 * math.sqrt(bad[0, 0, 0] * bad[0, 1, 1])
+    bad[1, 2, 2] = np.nan
+    C, k, eps, st = oracle.invert(bad, cond_max=1e50)
+    assert st[0] & oracle.ST_NOT_PD and np.isnan(C[0]).all()
+    assert st[1] & oracle.ST_NONFINITE
+    C, k, eps, st = oracle.invert(F[:1], cond_max=1.0)
+    assert st[0] & oracle.ST_COND_GT_MAX and np.isnan(C[0]).all()
+
+
+# ---------------------------------------------------------------- VJP references
+def test_snr_grad_pins():
+    """d SNR/d Phic = 0, d SNR/d dL = -SNR/dL; without rotation d SNR/d iota and
+    d SNR/d psi follow from the JKS patterns."""
+    ev, cat = _one_event("c0", zero_spin=True)
+    det, psd, _ = gwcat.network("c0")
+    n = 100
+    c = oracle.Catalog(ev, 0, 10.0, cat.fmax[0], n)
+    g = oracle.snr_grad(c, det, psd, 0, 9)[0]
+    s, _ = oracle.snr(c, det, psd, 0)
+    assert abs(g[8]) < 1e-10 * s[0]
+    assert abs(g[2] + s[0] / ev[2]) < 1e-10 * abs(g[2])
+    Mc, eta, dL, th, ph, io, ps, tc = ev[:8]
+    row = det[0]
+    fg, w = geom_grid(10.0, cat.fmax[0], n)
+    K = math.sqrt(np.sum(4 * w / psd_eval(psd[0], fg) * (amp0(Mc, dL) * fg ** (-7 / 6)) ** 2))
+
+    def snr_of(io_, ps_):
+        fp, fx = jks(row[0], row[2], row[3], th, ph, ps_, row[1] + OMEGA_E * tc)
+        return K * abs(fp * (1 + math.cos(io_) ** 2) / 2 + 1j * fx * math.cos(io_))
+
+    fp, fx = jks(row[0], row[2], row[3], th, ph, ps, row[1] + OMEGA_E * tc)
+    ci, si = math.cos(io), math.sin(io)
+    q = fp * (1 + ci * ci) / 2 + 1j * fx * ci
+    dq_io = fp * (-ci * si) + 1j * fx * (-si)
+    dq_ps = 2 * fx * (1 + ci * ci) / 2 - 2j * fp * ci
+    assert abs(snr_of(io, ps) - s[0]) < 1e-12 * s[0]
+    assert abs(g[5] - K * (np.conj(q) * dq_io).real / abs(q)) < 1e-9 * s[0]
+    assert abs(g[6] - K * (np.conj(q) * dq_ps).real / abs(q)) < 1e-9 * s[0]
+
+
+def test_logdet_grad_gamma_matches_jacobi_formula():
+    """d log det Gamma / d gamma = tr(Gamma^-1 d Gamma/d gamma) (Jacobi's formula),
+    with d Gamma/d gamma from differences of whole Fisher matrices; the oracle
+    differences log det itself.  Tidal BNS on the five-interferometer network
+    (well conditioned enough for an elementwise difference of Gamma)."""
+    cat, _, _ = oracle_catalog("c2", 1, max_npts=60)
+    det, psd, rot = gwcat.network("c4")
+    gg, ldet = oracle.logdet_grad_gamma(cat, det, psd, rot, 11, [1, 2])
+    F0, s0, _, _ = oracle.fisher(cat, det, psd, rot, 11)
+    Finv = np.linalg.inv(F0[0])
+    d = np.sqrt(np.diag(F0[0]))
+    sign, v = np.linalg.slogdet(F0[0] / np.outer(d, d))
+    assert sign > 0 and abs(v + 2 * np.sum(np.log(d)) - ldet[0]) < 1e-8 * abs(ldet[0])
+    for q, di in enumerate([1, 2]):
+        def fisher_at(gam):
+            d2 = det.copy()
+            d2[di, 2] = gam
+            return oracle.fisher(cat, d2, psd, rot, 11)[0][0]
+        h = 0.02
+        dG = (8 * (fisher_at(det[di, 2] + h) - fisher_at(det[di, 2] - h))
+              - (fisher_at(det[di, 2] + 2 * h) - fisher_at(det[di, 2] - 2 * h))) / (12 * h)
+        jac = np.trace(Finv @ dG)
+        assert abs(gg[q] - jac) < 1e-4 * (abs(jac) + 1)
