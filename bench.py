@@ -1,0 +1,402 @@
+"""Benchmark of the Fisher-forecast hot path on GB300.
+
+One step = one pass of the whole hot path over the 1e5-event uneven catalog
+(70 % BBH / 30 % tidal BNS, rotating triangle, per-event log grid from 2 Hz to
+f_ISCO): catalog preparation, network SNR + 11x11 Fisher matrix (mixed
+precision by default), batched FP64 Cholesky inversion with conditioning
+check, and the VJP of the network SNR with respect to all 11 source
+parameters.  Inputs are resident in HBM before the timed region; L2 is
+flushed (256 MiB write) before every timed step.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision mixed|fp64]
+                  [--grid literal|stress] [--impl ours|reference]
+
+--impl reference times the CPU oracle (oracle/) on a bounded sample of the same
+workload on the host cores (the paper's method has no GPU implementation).
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+import gwcat
+
+METRIC = "events/s (SNR + 11x11 Fisher), mixed vs FP64 path at stated error; % FP peak"
+WORKLOAD = "c3: 1e5 events, 70% BBH (5-80 Msun, spins) + 30% tidal BNS, ET-like triangle, " \
+           "Earth rotation, per-event log grid 2 Hz..f_ISCO"
+N_PAR = 11
+SM_COUNT = 152
+DFMA_PER_CLK_SM = 2          # measured on GB300: 2 FP64 FMA / clock / SM (1.26 TFLOP/s)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--grid", choices=["literal", "stress"], default="literal")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--events", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ oracle leg
+def _oracle_event_step(args):
+    """Every row of the step for one event, on the CPU oracle."""
+    import oracle
+    raw, rule, det, psd, rot = args
+    p = oracle.prepare(raw["m1"], raw["m2"], raw["chi1"], raw["chi2"], raw["lam1"], raw["lam2"],
+                       raw["dL_Mpc"], raw["zflag"], raw["tcoal"])
+    if rule[0] == "efold":
+        npts = oracle.grid_npts(raw["fmin"], p["fisco"], *rule[1:])
+    else:
+        npts = raw["npts"]
+    ev = np.stack([p["Mc"], p["eta"], p["dL"], raw["theta"], raw["phi"], raw["iota"], raw["psi"],
+                   p["tc"], raw["Phic"], p["chi1z"], p["chi2z"], p["LamT"], p["dLamT"]], 1)
+    cat = oracle.Catalog(ev, raw["pset"], raw["fmin"], p["fisco"], npts)
+    F, s, err, st = oracle.fisher(cat, det, psd, rot, N_PAR)
+    oracle.invert(F)
+    oracle.snr_grad(cat, det, psd, rot, N_PAR)
+    return 1
+
+
+def _sample(raw, idx):
+    out = {}
+    for k, v in raw.items():
+        if isinstance(v, np.ndarray) and v.shape[:1] == (len(raw["m1"]),):
+            out[k] = v[idx]
+    return out
+
+
+def oracle_timing(raw, n_events, cores, budget_s=20.0):
+    """Time the oracle on a bounded sample of the workload (spawn pool)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    det, psd, rot = gwcat.network("c3")
+    rule = raw["npts_rule"]
+    ctx = mp.get_context("spawn")
+    rng = np.random.default_rng(1)
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_event_step, [(_sample(raw, [0]), rule, det, psd, rot)])   # warm
+        done, t0 = 0, time.time()
+        while True:
+            idx = rng.choice(len(raw["m1"]), cores, replace=False)
+            tasks = [(_sample(raw, [i]), rule, det, psd, rot) for i in idx]
+            done += sum(pool.map(_oracle_event_step, tasks))
+            el = time.time() - t0
+            if el >= budget_s or done >= n_events:
+                return done / el, done, el
+
+
+def run_reference(a):
+    raw = gwcat.draw("c3", a.events, grid=a.grid)
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    det, psd, rot = gwcat.network("c3")
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(2)
+    times = []
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for i in range(a.warmup + a.steps):
+            idx = rng.choice(len(raw["m1"]), cores, replace=False)
+            tasks = [(_sample(raw, [j]), raw["npts_rule"], det, psd, rot) for j in idx]
+            t0 = time.time()
+            pool.map(_oracle_event_step, tasks)
+            if i >= a.warmup:
+                times.append(time.time() - t0)
+    per_step = float(np.mean(times))
+    value = cores / per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64/long double",
+        "data": "synthetic (seeded, gwcat)",
+        "config": {"workload": WORKLOAD, "grid": a.grid, "sample_events_per_step": cores},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} random events of the catalog per step, one per process"},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def fp64_flops_per_point(n_ifo_virtual: int, n_site: int, mode: str, precision: str) -> float:
+    """Algorithmic FP64 work per grid point of the fused kernel, counted from its
+    straight-line formulas (one FMA = 2 flops, one multiply or add = 1 flop).
+    Shared per point: basis powers of v (8 mul), d Psi/d Mc and d Psi/d eta
+    (2 x 10 FMA), slots 9/10 (2 x 4 FMA), tau* and two derivatives (3 x 8 FMA +
+    3 mul), f (2 mul), recurrences (4).  FP64 path only, per site: Earth-angle
+    sincos (~20 FMA), JKS and Doppler (30 FMA); per virtual interferometer:
+    patterns (12 FMA + 12 mul), tangents (30), weights and the 66-pair
+    Gram update (22 mul + 132 FMA) or 11-term SNR tangent sums (22 FMA)."""
+    shared = 8 + 2 * 10 * 2 + 2 * 4 * 2 + 3 * 8 * 2 + 3 + 2 + 4
+    if precision == "mixed":
+        return shared + 4          # + Earth angle reduction
+    site = 20 * 2 + 30 * 2
+    if mode == "fisher":
+        ifo = 12 * 2 + 12 + 30 * 1.5 + 22 + 132 * 2
+    else:
+        ifo = 12 * 2 + 12 + 30 * 1.5 + 22 * 2
+    return shared + 15 + n_site * site + n_ifo_virtual * ifo
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    import paper_2207_06910_gb300 as gw
+
+    prec = gw.GW_MIXED if a.precision == "mixed" else gw.GW_FP64
+    # weak scaling: every rank owns its own 1e5-event shard (seed offset by rank)
+    raw = gwcat.draw("c3", a.events, seed=gwcat.SEED_BASE + 3 + 1000 * rank, grid=a.grid)
+    n = len(raw["m1"])
+    rule = raw["npts_rule"]
+    det, psd, rot = gwcat.network("c3")
+    net = gw.Network(det, psd, rot)
+    keys = ("m1", "m2", "chi1", "chi2", "lam1", "lam2", "dL_Mpc", "tcoal", "fmin",
+            "theta", "phi", "iota", "psi", "Phic")
+    host = {k: torch.as_tensor(np.ascontiguousarray(raw[k], np.float64)).pin_memory() for k in keys}
+    host["zflag"] = torch.as_tensor(np.ascontiguousarray(raw["zflag"], np.uint8)).pin_memory()
+    host["pset"] = torch.as_tensor(np.ascontiguousarray(raw["pset"], np.int8)).pin_memory()
+    if rule[0] == "given":
+        host["npts"] = torch.as_tensor(np.ascontiguousarray(raw["npts"], np.int32)).pin_memory()
+    dev = {k: v.cuda() for k, v in host.items()}
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    grad_up = torch.ones(n, dtype=torch.float64, device="cuda")
+    ctx = gw.context()
+    lib = gw.load_library()
+
+    def prepare(d):
+        return gw_prepare_dev(gw, d, rule, n)
+
+    def step(d):
+        cat = prepare(d)
+        F, snr, st = gw.gw_fisher(cat, net, N_PAR, prec)
+        cov, cond, err, sti = gw.gw_fisher_inverse(F, N_PAR)
+        g = gw.gw_snr_vjp(cat, net, N_PAR, grad_up, prec)
+        return cat, F, snr, cov, cond, g, st
+
+    launches_per_step = 1 + 6 + 1 + 6
+    for _ in range(a.warmup):
+        step(dev)
+    torch.cuda.synchronize()
+    # sanity of the timed configuration: no event flagged by the point loop
+    cat, F, snr, cov, cond, g, st = step(dev)
+    torch.cuda.synchronize()
+    assert int((st != 0).sum()) == 0, "events flagged in the benchmark catalog"
+    n_points = int(cat.npts.to(torch.int64).sum().item())
+
+    # ---- device-resident timed loop
+    clk = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    fisher_ms = []
+    gw.gw_set_profiling(True)
+    for i in range(a.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        cat = prepare(dev)
+        F, snr, st = gw.gw_fisher(cat, net, N_PAR, prec)
+        fisher_ms.append(gw.gw_point_kernel_ms())
+        gw.gw_fisher_inverse(F, N_PAR)
+        gw.gw_snr_vjp(cat, net, N_PAR, grad_up, prec)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    gw.gw_set_profiling(False)
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_ms = float(sum(step_ms))
+
+    # ---- end to end: host (pinned) -> device, step, device -> host
+    outs_host = {"snr": torch.empty(n, dtype=torch.float64).pin_memory(),
+                 "F": torch.empty((N_PAR * (N_PAR + 1) // 2, n), dtype=torch.float64).pin_memory(),
+                 "cov": torch.empty((N_PAR * (N_PAR + 1) // 2, n), dtype=torch.float64).pin_memory(),
+                 "g": torch.empty((N_PAR, n), dtype=torch.float64).pin_memory()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in outs_host.values())
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(a.steps)]
+    for i in range(a.steps):
+        flush.zero_()
+        e2e_ev[i][0].record(stream)
+        d = {k: v.cuda(non_blocking=True) for k, v in host.items()}
+        cat, F, snr, cov, cond, g, st = step(d)
+        outs_host["snr"].copy_(snr, non_blocking=True)
+        outs_host["F"].copy_(F, non_blocking=True)
+        outs_host["cov"].copy_(cov, non_blocking=True)
+        outs_host["g"].copy_(g, non_blocking=True)
+        e2e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = float(sum(s.elapsed_time(e) for s, e in e2e_ev))
+
+    t = torch.tensor([total_ms, e2e_ms, float(np.mean(fisher_ms))], dtype=torch.float64,
+                     device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms, kern_ms = t.tolist()
+    value = world * n * a.steps / (total_ms * 1e-3)
+    e2e_value = world * n * a.steps / (e2e_ms * 1e-3)
+
+    if rank == 0:
+        n_site = net.n_det
+        n_ifo = sum(1 if int(r[4]) == 0 else 2 for r in det)
+        flops = fp64_flops_per_point(n_ifo, n_site, "fisher", a.precision) * n_points
+        sm_mhz = clocks.get("sm_mhz") or 2070.0
+        peak = SM_COUNT * DFMA_PER_CLK_SM * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s at the sampled clock
+        achieved = flops / (kern_ms * 1e-3) / 1e12
+        cpu = None
+        if not a.no_cpu_baseline:
+            cores = os.cpu_count() or 1
+            v, done, el = oracle_timing(raw, 10 ** 9, cores, budget_s=20.0)
+            cpu = {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{done} random events of this catalog in {el:.1f} s "
+                             f"(prepare + SNR + Fisher + inversion + SNR gradient), "
+                             f"one event per process on {cores} host cores"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
+            "data": "synthetic (seeded, gwcat)",
+            "config": {"workload": WORKLOAD, "n_events_per_gpu": n, "grid": a.grid,
+                       "points_per_step": n_points, "precision": a.precision, "n_par": N_PAR,
+                       "step": "prepare + SNR/Fisher + Cholesky inversion + SNR VJP",
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "parallelism": f"event shards, {world} GPU(s), no collective"},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * a.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"k_points_{'mixed' if a.precision == 'mixed' else 'fp64'} (Fisher)",
+                         "kernel_ms": kern_ms,
+                         "peak_basis": f"FP64 pipe: {SM_COUNT} SMs x {DFMA_PER_CLK_SM} DFMA/clk x 2 "
+                                       f"flops x {sm_mhz:.0f} MHz (median sampled SM clock)"},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def gw_prepare_dev(gw, d, rule, n):
+    """gw_prepare_catalog on device-resident raw arrays (no host transfer)."""
+    import ctypes
+    import torch
+    lib = gw.load_library()
+    ctx = gw.context()
+    dev = d["m1"].device
+    out = {k: torch.empty(n, dtype=torch.float64, device=dev) for k in
+           ("Mc", "eta", "dL", "chi1z", "chi2z", "LamT", "dLamT", "tc", "fmax")}
+    npts = torch.empty(n, dtype=torch.int32, device=dev)
+    fixed, per, lo, hi, given = 0, 0.0, 0, 0, None
+    if rule[0] == "fixed":
+        fixed = int(rule[1])
+    elif rule[0] == "efold":
+        per, lo, hi = float(rule[1]), int(rule[2]), int(rule[3])
+    else:
+        given = d["npts"]
+    P = gw._ptr
+    st = lib.gw_prepare_catalog(ctx, n, P(d["m1"]), P(d["m2"]), P(d["chi1"]), P(d["chi2"]),
+                                P(d["lam1"]), P(d["lam2"]), P(d["dL_Mpc"]), P(d["zflag"]),
+                                P(d["tcoal"]), P(d["fmin"]), P(given), fixed, per, lo, hi,
+                                P(out["Mc"]), P(out["eta"]), P(out["dL"]), P(out["chi1z"]),
+                                P(out["chi2z"]), P(out["LamT"]), P(out["dLamT"]), P(out["tc"]),
+                                P(out["fmax"]), P(npts), gw._stream())
+    gw._check(st, ctx)
+    t = dict(out)
+    for k in ("theta", "phi", "iota", "psi", "Phic"):
+        t[k] = d[k]
+    return gw.Catalog(t, d["pset"], d["fmin"], out["fmax"], npts)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,370 @@
+"""Python binding of libgwfish, the GB300 Fisher-forecast library.
+
+Argument marshalling only: every step of SNR, Fisher, inversion and the VJPs
+runs in the CUDA kernels of ``libgwfish.so`` (C ABI in ``include/gwfish.h``).
+PyTorch provides device memory and streams.  The functions keep the C names:
+``gw_prepare_catalog``, ``gw_snr``, ``gw_fisher``, ``gw_fisher_inverse``,
+``gw_snr_vjp``, ``gw_logdet_vjp_detangles``.  ``SNR`` wraps ``gw_snr`` and
+``gw_snr_vjp`` as a ``torch.autograd.Function``.
+
+The library must be built (``paper_2207_06910_gb300.build.build()`` or
+``__graft_entry__.build()``); importing this module fails loudly otherwise,
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+GW_FP64, GW_MIXED = 0, 1
+ST_NOT_PD, ST_COND_GT_MAX, ST_NONFINITE, ST_EMPTY_GRID, ST_BAD_PARAM, ST_ILL_COND = 1, 2, 4, 8, 16, 32
+FISHER_PARAMS_9 = ("Mc", "eta", "dL", "theta", "phi", "iota", "psi", "tc", "Phic")
+
+_P = ctypes.c_void_p
+
+
+class gw_catalog(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64)] + [(k, _P) for k in (
+        "Mc", "eta", "dL", "theta", "phi", "iota", "psi", "tc", "Phic",
+        "chi1z", "chi2z", "LamT", "dLamT", "pset", "fmin", "fmax", "npts")]
+
+
+class gw_detector(ctypes.Structure):
+    _fields_ = [("lat", ctypes.c_double), ("lon", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("zeta", ctypes.c_double), ("shape", ctypes.c_int32), ("psd", ctypes.c_int32)]
+
+
+class gw_psd(ctypes.Structure):
+    _fields_ = [("f0", ctypes.c_double), ("scale", ctypes.c_double), ("nterm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("coef", ctypes.c_double * 4),
+                ("pw", ctypes.c_double * 4)]
+
+
+class gw_network(ctypes.Structure):
+    _fields_ = [("n_det", ctypes.c_int32), ("earth_rotation", ctypes.c_int32),
+                ("det", ctypes.POINTER(gw_detector)), ("n_psd", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("psd", ctypes.POINTER(gw_psd))]
+
+
+EXPORTS = ("gw_create", "gw_destroy", "gw_last_error", "gw_abi_version", "gw_prepare_catalog",
+           "gw_snr", "gw_fisher", "gw_fisher_inverse", "gw_snr_vjp", "gw_logdet_vjp_detangles",
+           "gw_set_profiling", "gw_point_kernel_ms")
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(path: str | None = None):
+    """Load libgwfish.so and declare its signatures (no GPU needed)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"libgwfish.so is not built ({p}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    i32, i64, d = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    C, N = ctypes.POINTER(gw_catalog), ctypes.POINTER(gw_network)
+    lib.gw_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int]
+    lib.gw_destroy.argtypes = [_P]
+    lib.gw_last_error.argtypes = [_P]
+    lib.gw_last_error.restype = ctypes.c_char_p
+    lib.gw_abi_version.restype = ctypes.c_int
+    lib.gw_prepare_catalog.argtypes = [_P, i64] + [_P] * 11 + [i32, d, i32, i32] + [_P] * 10 + [_P]
+    lib.gw_snr.argtypes = [_P, C, N, ctypes.c_int, _P, _P, _P, _P]
+    lib.gw_fisher.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
+    lib.gw_fisher_inverse.argtypes = [_P, _P, i64, ctypes.c_int, d, _P, _P, _P, _P, _P]
+    lib.gw_snr_vjp.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+    lib.gw_logdet_vjp_detangles.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+    for name in EXPORTS:
+        if name not in ("gw_last_error", "gw_abi_version", "gw_destroy", "gw_point_kernel_ms"):
+            getattr(lib, name).restype = ctypes.c_int
+    lib.gw_destroy.restype = ctypes.c_int
+    lib.gw_set_profiling.argtypes = [_P, ctypes.c_int]
+    lib.gw_point_kernel_ms.argtypes = [_P]
+    lib.gw_point_kernel_ms.restype = ctypes.c_double
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class GWError(RuntimeError):
+    pass
+
+
+_ctx_by_dev: dict[int, _P] = {}
+
+
+def context(device: int | None = None) -> _P:
+    """The library context of a CUDA device (created on first use)."""
+    if device is None:
+        device = torch.cuda.current_device()
+    if device not in _ctx_by_dev:
+        lib = load_library()
+        h = _P()
+        st = lib.gw_create(ctypes.byref(h), int(device))
+        if st != 0:
+            raise GWError(f"gw_create failed with status {st}")
+        _ctx_by_dev[device] = h
+    return _ctx_by_dev[device]
+
+
+def gw_set_profiling(enable: bool = True) -> None:
+    """Record CUDA events around every point-loop kernel launch."""
+    ctx = context()
+    _check(load_library().gw_set_profiling(ctx, int(enable)), ctx)
+
+
+def gw_point_kernel_ms() -> float:
+    """Duration of the last point-loop kernel (ms), -1 if none recorded."""
+    return load_library().gw_point_kernel_ms(context())
+
+
+def _check(st: int, ctx) -> None:
+    if st != 0:
+        msg = load_library().gw_last_error(ctx).decode(errors="replace")
+        raise GWError(f"libgwfish status {st}: {msg}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise TypeError("device arrays must be contiguous CUDA tensors")
+    return _P(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _P(s.cuda_stream)
+
+
+class Catalog:
+    """Device-resident catalog (structure of arrays, float64 / int8 / int32)."""
+
+    FIELDS = ("Mc", "eta", "dL", "theta", "phi", "iota", "psi", "tc", "Phic",
+              "chi1z", "chi2z", "LamT", "dLamT")
+
+    def __init__(self, tensors: dict, pset, fmin, fmax, npts):
+        self.t = {k: tensors.get(k) for k in self.FIELDS}
+        self.pset, self.fmin, self.fmax, self.npts = pset, fmin, fmax, npts
+        self.n = int(self.t["Mc"].numel())
+
+    @classmethod
+    def from_numpy(cls, ev: np.ndarray, pset, fmin, fmax, npts, device="cuda"):
+        """From oracle-style event rows [n, 13] (order of ``FIELDS``)."""
+        ev = np.asarray(ev, dtype=np.float64).reshape(-1, 13)
+        n = ev.shape[0]
+        t = {k: torch.as_tensor(np.ascontiguousarray(ev[:, i]), device=device)
+             for i, k in enumerate(cls.FIELDS)}
+        col = lambda a, dt: torch.as_tensor(np.array(np.broadcast_to(a, (n,)), dtype=dt), device=device)
+        return cls(t, col(pset, np.int8), col(fmin, np.float64), col(fmax, np.float64),
+                   col(npts, np.int32))
+
+    def struct(self) -> gw_catalog:
+        c = gw_catalog()
+        c.n = self.n
+        for k in self.FIELDS:
+            setattr(c, k, _ptr(self.t[k]))
+        c.pset, c.fmin, c.fmax, c.npts = (_ptr(self.pset), _ptr(self.fmin), _ptr(self.fmax),
+                                          _ptr(self.npts))
+        return c
+
+    def with_field(self, name, tensor):
+        t = dict(self.t)
+        t[name] = tensor
+        return Catalog(t, self.pset, self.fmin, self.fmax, self.npts)
+
+
+class Network:
+    """Host-side detector network (see gw_network in include/gwfish.h)."""
+
+    def __init__(self, det, psd, rotation: int):
+        det = np.asarray(det, dtype=np.float64).reshape(-1, 6)
+        psd = np.asarray(psd, dtype=np.float64).reshape(-1, 11)
+        self.det_rows, self.psd_rows, self.rotation = det, psd, int(rotation)
+        self._dets = (gw_detector * len(det))()
+        for i, r in enumerate(det):
+            self._dets[i] = gw_detector(r[0], r[1], r[2], r[3], int(r[4]), int(r[5]))
+        self._psds = (gw_psd * len(psd))()
+        for i, r in enumerate(psd):
+            p = gw_psd()
+            p.f0, p.scale, p.nterm = r[0], r[1], int(r[2])
+            for j in range(4):
+                p.coef[j] = r[3 + j]
+                p.pw[j] = r[7 + j]
+            self._psds[i] = p
+        self.net = gw_network(len(det), self.rotation, self._dets, len(psd), 0, self._psds)
+
+    @property
+    def n_det(self) -> int:
+        return len(self.det_rows)
+
+    def with_gamma(self, d: int, gamma: float) -> "Network":
+        det = self.det_rows.copy()
+        det[d, 2] = gamma
+        return Network(det, self.psd_rows, self.rotation)
+
+
+def n_packed(n_par: int) -> int:
+    return n_par * (n_par + 1) // 2
+
+
+def unpack(packed: torch.Tensor, n_par: int) -> torch.Tensor:
+    """[P(P+1)/2, n] packed upper, event-minor  ->  [n, P, P] (a view copy)."""
+    n = packed.shape[1]
+    out = torch.empty((n, n_par, n_par), dtype=packed.dtype, device=packed.device)
+    k = 0
+    for i in range(n_par):
+        for j in range(i, n_par):
+            out[:, i, j] = packed[k]
+            out[:, j, i] = packed[k]
+            k += 1
+    return out
+
+
+# ---------------------------------------------------------------- entry points
+def gw_prepare_catalog(raw: dict, npts_rule, device="cuda", stream=None) -> Catalog:
+    """Raw seeded draws (m1, m2, chi1, chi2, lam1, lam2, dL_Mpc, zflag, tcoal,
+    theta, phi, iota, psi, Phic, pset, fmin, optional npts) -> device Catalog."""
+    ctx = context()
+    f64 = lambda k: torch.as_tensor(np.ascontiguousarray(raw[k], np.float64), device=device)
+    n = len(raw["m1"])
+    ins = {k: f64(k) for k in ("m1", "m2", "chi1", "chi2", "lam1", "lam2", "dL_Mpc", "tcoal", "fmin")}
+    zflag = torch.as_tensor(np.ascontiguousarray(raw["zflag"], np.uint8), device=device)
+    given = None
+    fixed, per, lo, hi = 0, 0.0, 0, 0
+    if npts_rule[0] == "fixed":
+        fixed = int(npts_rule[1])
+    elif npts_rule[0] == "efold":
+        per, lo, hi = float(npts_rule[1]), int(npts_rule[2]), int(npts_rule[3])
+    else:
+        given = torch.as_tensor(np.ascontiguousarray(raw["npts"], np.int32), device=device)
+    out = {k: torch.empty(n, dtype=torch.float64, device=device) for k in
+           ("Mc", "eta", "dL", "chi1z", "chi2z", "LamT", "dLamT", "tc", "fmax")}
+    npts = torch.empty(n, dtype=torch.int32, device=device)
+    st = load_library().gw_prepare_catalog(
+        ctx, n, _ptr(ins["m1"]), _ptr(ins["m2"]), _ptr(ins["chi1"]), _ptr(ins["chi2"]),
+        _ptr(ins["lam1"]), _ptr(ins["lam2"]), _ptr(ins["dL_Mpc"]), _ptr(zflag), _ptr(ins["tcoal"]),
+        _ptr(ins["fmin"]), _ptr(given), fixed, per, lo, hi,
+        _ptr(out["Mc"]), _ptr(out["eta"]), _ptr(out["dL"]), _ptr(out["chi1z"]), _ptr(out["chi2z"]),
+        _ptr(out["LamT"]), _ptr(out["dLamT"]), _ptr(out["tc"]), _ptr(out["fmax"]), _ptr(npts),
+        _stream(stream))
+    _check(st, ctx)
+    t = dict(out)
+    for k in ("theta", "phi", "iota", "psi", "Phic"):
+        t[k] = f64(k)
+    pset = torch.as_tensor(np.ascontiguousarray(raw["pset"], np.int8), device=device)
+    return Catalog(t, pset, ins["fmin"], out["fmax"], npts)
+
+
+def gw_snr(cat: Catalog, net: Network, prec=GW_FP64, per_detector=False, stream=None):
+    ctx = context()
+    dev = cat.t["Mc"].device
+    snr = torch.empty(cat.n, dtype=torch.float64, device=dev)
+    sdet = torch.empty((net.n_det, cat.n), dtype=torch.float64, device=dev) if per_detector else None
+    status = torch.empty(cat.n, dtype=torch.int32, device=dev)
+    c = cat.struct()
+    st = load_library().gw_snr(ctx, ctypes.byref(c), ctypes.byref(net.net), int(prec), _ptr(snr),
+                               _ptr(sdet), _ptr(status), _stream(stream))
+    _check(st, ctx)
+    return (snr, sdet, status) if per_detector else (snr, status)
+
+
+def gw_fisher(cat: Catalog, net: Network, n_par: int, prec=GW_FP64, stream=None, out=None):
+    """Returns (fisher [P(P+1)/2, n] packed upper event-minor, snr [n], status [n])."""
+    ctx = context()
+    dev = cat.t["Mc"].device
+    if out is None:
+        fisher = torch.empty((n_packed(n_par), cat.n), dtype=torch.float64, device=dev)
+        snr = torch.empty(cat.n, dtype=torch.float64, device=dev)
+        status = torch.empty(cat.n, dtype=torch.int32, device=dev)
+    else:
+        fisher, snr, status = out
+    c = cat.struct()
+    st = load_library().gw_fisher(ctx, ctypes.byref(c), ctypes.byref(net.net), int(prec), n_par,
+                                  _ptr(fisher), _ptr(snr), _ptr(status), _stream(stream))
+    _check(st, ctx)
+    return fisher, snr, status
+
+
+def gw_fisher_inverse(fisher: torch.Tensor, n_par: int, cond_max=1e50, stream=None, out=None):
+    """Returns (cov packed like fisher, cond [n], inv_err [n], status [n])."""
+    ctx = context()
+    n = fisher.shape[1]
+    if out is None:
+        cov = torch.empty_like(fisher)
+        cond = torch.empty(n, dtype=torch.float64, device=fisher.device)
+        err = torch.empty(n, dtype=torch.float64, device=fisher.device)
+        status = torch.empty(n, dtype=torch.int32, device=fisher.device)
+    else:
+        cov, cond, err, status = out
+    st = load_library().gw_fisher_inverse(ctx, _ptr(fisher), n, n_par, float(cond_max), _ptr(cov),
+                                          _ptr(cond), _ptr(err), _ptr(status), _stream(stream))
+    _check(st, ctx)
+    return cov, cond, err, status
+
+
+def gw_snr_vjp(cat: Catalog, net: Network, n_par: int, grad_snr: torch.Tensor, prec=GW_FP64,
+               stream=None, out=None):
+    """grad_params [n_par, n] = grad_snr * d SNR / d theta."""
+    ctx = context()
+    g = out if out is not None else torch.empty((n_par, cat.n), dtype=torch.float64,
+                                                device=grad_snr.device)
+    c = cat.struct()
+    st = load_library().gw_snr_vjp(ctx, ctypes.byref(c), ctypes.byref(net.net), int(prec), n_par,
+                                   _ptr(grad_snr.contiguous()), _ptr(g), _stream(stream))
+    _check(st, ctx)
+    return g
+
+
+def gw_logdet_vjp_detangles(cat: Catalog, net: Network, n_par: int, cov: torch.Tensor,
+                            prec=GW_FP64, stream=None, out=None):
+    """d(sum_e log det Gamma_e)/d gamma_d for every detector d -> [n_det]."""
+    ctx = context()
+    g = out if out is not None else torch.empty(net.n_det, dtype=torch.float64, device=cov.device)
+    c = cat.struct()
+    st = load_library().gw_logdet_vjp_detangles(ctx, ctypes.byref(c), ctypes.byref(net.net),
+                                                int(prec), n_par, _ptr(cov), _ptr(g),
+                                                _stream(stream))
+    _check(st, ctx)
+    return g
+
+
+class SNR(torch.autograd.Function):
+    """Network SNR as a differentiable function of the catalog's Fisher
+    parameters: forward = gw_snr, backward = gw_snr_vjp."""
+
+    @staticmethod
+    def forward(ctx_, params: torch.Tensor, base: Catalog, net: Network, n_par: int, prec: int):
+        # params [n_par, n] float64 on the device, order of the Fisher slots;
+        # slots 9, 10 are (chi1z, chi2z) for pset 1 events, (LamT, dLamT) for pset 2
+        cat = base
+        for i, k in enumerate(FISHER_PARAMS_9):
+            cat = cat.with_field(k, params[i].contiguous())
+        if n_par == 11:
+            spin = base.pset == 1
+            tide = base.pset == 2
+            for i, (ks, kt) in enumerate((("chi1z", "LamT"), ("chi2z", "dLamT"))):
+                row = params[9 + i]
+                zs = base.t[ks] if base.t[ks] is not None else torch.zeros_like(row)
+                zt = base.t[kt] if base.t[kt] is not None else torch.zeros_like(row)
+                cat = cat.with_field(ks, torch.where(spin, row, zs).contiguous())
+                cat = cat.with_field(kt, torch.where(tide, row, zt).contiguous())
+        ctx_.cat, ctx_.net, ctx_.n_par, ctx_.prec = cat, net, n_par, prec
+        snr, status = gw_snr(cat, net, prec)
+        return snr
+
+    @staticmethod
+    def backward(ctx_, grad):
+        g = gw_snr_vjp(ctx_.cat, ctx_.net, ctx_.n_par, grad.to(torch.float64).contiguous(),
+                       ctx_.prec)
+        return g, None, None, None, None

@@ -1,0 +1,386 @@
+// gw_api.cu -- the C ABI of libgwfish (declared in include/gwfish.h):
+// argument validation, network expansion, workspace management and the
+// launch sequence  event setup -> work-item scan -> point loop -> reduction.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/gwfish.h"
+#include "gw_kernels.cuh"
+
+using namespace gw;
+
+struct gw_ctx {
+    int device = 0;
+    char err[512] = {0};
+    double *evc = nullptr;      size_t evc_cap = 0;
+    double *sitec = nullptr;    size_t sitec_cap = 0;
+    float *sitec_f = nullptr;   size_t sitec_f_cap = 0;
+    int32_t *status = nullptr;  size_t status_cap = 0;
+    int64_t *counts = nullptr;  size_t counts_cap = 0;
+    int64_t *off = nullptr;     size_t off_cap = 0;
+    int64_t *scan = nullptr;    size_t scan_cap = 0;
+    double *partial = nullptr;  size_t partial_cap = 0;
+    int64_t *h_total = nullptr;   // pinned
+    int profiling = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool ev_recorded = false;
+};
+
+namespace {
+
+gw_status fail(gw_ctx *c, gw_status st, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof c->err, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ctx, GW_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                        __FILE__, __LINE__);                                             \
+    } while (0)
+
+template <typename T>
+gw_status ensure(gw_ctx *ctx, T *&p, size_t &cap, size_t need)
+{
+    if (need <= cap) return GW_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t n = need + need / 4 + 64;
+    if (cudaMalloc((void **)&p, n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GW_ENOMEM, "workspace allocation of %zu bytes failed", n * sizeof(T));
+    }
+    cap = n;
+    return GW_OK;
+}
+
+bool is_int(double x) { return std::isfinite(x) && std::fabs(x - std::nearbyint(x)) < 1e-12; }
+
+gw_status build_net(gw_ctx *ctx, const gw_network *net, DevNet &d)
+{
+    if (!net || !net->det || !net->psd) return fail(ctx, GW_EINVAL, "network: null pointer");
+    if (net->n_det < 1 || net->n_det > MAX_DET)
+        return fail(ctx, GW_EINVAL, "network: n_det=%d outside [1,%d]", net->n_det, MAX_DET);
+    if (net->n_psd < 1 || net->n_psd > MAX_PSD)
+        return fail(ctx, GW_EINVAL, "network: n_psd=%d outside [1,%d]", net->n_psd, MAX_PSD);
+    memset(&d, 0, sizeof d);
+    d.n_psd = net->n_psd;
+    d.rotation = net->earth_rotation ? 1 : 0;
+    d.n_det = net->n_det;
+    for (int p = 0; p < net->n_psd; p++) {
+        const gw_psd &P = net->psd[p];
+        if (!(P.f0 > 0) || !std::isfinite(P.scale) || P.scale <= 0 || P.nterm < 1 ||
+            P.nterm > MAX_TERM)
+            return fail(ctx, GW_EINVAL, "psd %d: need f0 > 0, scale > 0, 1 <= nterm <= 4", p);
+        d.psd_f0[p] = P.f0;
+        d.psd_inv_f0[p] = 1.0 / P.f0;
+        d.psd_nterm[p] = P.nterm;
+        for (int j = 0; j < P.nterm; j++) {
+            if (!is_int(P.pw[j]) || std::fabs(P.pw[j]) > 15)
+                return fail(ctx, GW_EUNSUPPORTED,
+                            "psd %d term %d: power %g (only integer powers |p| <= 15)", p, j,
+                            P.pw[j]);
+            if (!std::isfinite(P.coef[j]) || P.coef[j] < 0)
+                return fail(ctx, GW_EINVAL, "psd %d term %d: coefficient must be >= 0", p, j);
+            d.psd_coef[p][j] = P.scale * P.coef[j];
+            d.psd_coef_f[p][j] = (float)(P.scale / net->psd[0].scale * P.coef[j]);
+            d.psd_pow[p][j] = (int)std::nearbyint(P.pw[j]);
+        }
+        d.psd_inv_f0_f[p] = (float)(1.0 / P.f0);
+    }
+    d.inv_sqrt_scale_ref = 1.0 / std::sqrt(net->psd[0].scale);
+    int ni = 0;
+    for (int s = 0; s < net->n_det; s++) {
+        const gw_detector &D = net->det[s];
+        if (!std::isfinite(D.lat) || !std::isfinite(D.lon) || !std::isfinite(D.gamma) ||
+            !std::isfinite(D.zeta))
+            return fail(ctx, GW_EINVAL, "detector %d: non-finite angle", s);
+        if (D.shape != 0 && D.shape != 1)
+            return fail(ctx, GW_EINVAL, "detector %d: shape %d (0 = L, 1 = triangle)", s, D.shape);
+        if (D.psd < 0 || D.psd >= net->n_psd)
+            return fail(ctx, GW_EINVAL, "detector %d: psd index %d", s, D.psd);
+        d.site_slat[s] = std::sin(D.lat);
+        d.site_clat[s] = std::cos(D.lat);
+        d.site_lon[s] = D.lon;
+        d.site_ifo0[s] = ni;
+        const int nv = D.shape == 0 ? 1 : 2;
+        for (int v = 0; v < nv; v++) {
+            // a triangle is two virtual 90-degree interferometers at gamma_T and
+            // gamma_T + 45 deg with amplitude sqrt(3/2) sin(60 deg) = 3/(2 sqrt 2)
+            const double g = D.gamma + (v ? 0.25 * M_PI : 0.0);
+            d.ifo_s2g[ni] = std::sin(2.0 * g);
+            d.ifo_c2g[ni] = std::cos(2.0 * g);
+            d.ifo_amp[ni] = D.shape == 0 ? std::sin(D.zeta) : 1.5 / std::sqrt(2.0);
+            d.ifo_site[ni] = s;
+            d.ifo_psd[ni] = D.psd;
+            d.ifo_det[ni] = s;
+            ni++;
+        }
+        d.site_ifo1[s] = ni;
+    }
+    d.n_site = net->n_det;
+    d.n_ifo = ni;
+    return GW_OK;
+}
+
+gw_status check_cat(gw_ctx *ctx, const gw_catalog *c, int np)
+{
+    if (!c) return fail(ctx, GW_EINVAL, "catalog: null");
+    if (c->n < 0) return fail(ctx, GW_EINVAL, "catalog: n < 0");
+    if (c->n == 0) return GW_OK;
+    if (!c->Mc || !c->eta || !c->dL || !c->theta || !c->phi || !c->iota || !c->psi || !c->tc ||
+        !c->Phic || !c->fmin || !c->fmax || !c->npts)
+        return fail(ctx, GW_EINVAL, "catalog: a required array is null");
+    if (np == 11 && !c->pset) return fail(ctx, GW_EINVAL, "catalog: n_par 11 needs pset");
+    return GW_OK;
+}
+
+DevCat dev_cat(const gw_catalog *c)
+{
+    DevCat d;
+    d.n = c->n;
+    d.Mc = c->Mc; d.eta = c->eta; d.dL = c->dL; d.theta = c->theta; d.phi = c->phi;
+    d.iota = c->iota; d.psi = c->psi; d.tc = c->tc; d.Phic = c->Phic;
+    d.chi1 = c->chi1z; d.chi2 = c->chi2z; d.LamT = c->LamT; d.dLamT = c->dLamT;
+    d.pset = c->pset; d.fmin = c->fmin; d.fmax = c->fmax; d.npts = c->npts;
+    return d;
+}
+
+// event setup -> scan -> point loop -> reduction
+gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_precision prec,
+                     int mode, int np, int32_t *status_out, double *snr, double *snr_det,
+                     double *fisher, const double *grad_snr, double *grad_params,
+                     const double *cov, double *grad_gamma, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    gw_status st = check_cat(ctx, cat, np);
+    if (st) return st;
+    if (np != 9 && np != 11) return fail(ctx, GW_EINVAL, "n_par must be 9 or 11 (got %d)", np);
+    if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_EINVAL, "bad precision");
+    DevNet dn;
+    if ((st = build_net(ctx, net, dn))) return st;
+    const int64_t n = cat->n;
+    const int nacc = n_acc(mode, np, dn.n_det);
+    if (n == 0) {
+        if (mode == MODE_LOGDET) CK(cudaMemsetAsync(grad_gamma, 0, sizeof(double) * dn.n_det, s));
+        return GW_OK;
+    }
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure(ctx, ctx->evc, ctx->evc_cap, (size_t)n * EVC))) return st;
+    if ((st = ensure(ctx, ctx->sitec, ctx->sitec_cap, (size_t)n * dn.n_site * SC_N))) return st;
+    const bool mixed = prec == GW_MIXED && (mode == MODE_FISHER || mode == MODE_SNR ||
+                                            mode == MODE_SNRGRAD);
+    if (mixed && (st = ensure(ctx, ctx->sitec_f, ctx->sitec_f_cap, (size_t)n * dn.n_site * SC_N)))
+        return st;
+    if ((st = ensure(ctx, ctx->counts, ctx->counts_cap, (size_t)n))) return st;
+    if ((st = ensure(ctx, ctx->off, ctx->off_cap, (size_t)n + 1))) return st;
+    if ((st = ensure(ctx, ctx->scan, ctx->scan_cap, scan_tmp_size(n)))) return st;
+    int32_t *status = status_out;
+    if (!status) {
+        if ((st = ensure(ctx, ctx->status, ctx->status_cap, (size_t)n))) return st;
+        status = ctx->status;
+    }
+    const DevCat dc = dev_cat(cat);
+    CK(launch_event_setup(dc, dn, np, ctx->evc, ctx->sitec, mixed ? ctx->sitec_f : nullptr, status,
+                          ctx->counts, s));
+    CK(launch_scan(ctx->counts, n, ctx->off, ctx->scan, s));
+    CK(cudaMemcpyAsync(ctx->h_total, ctx->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t n_items = *ctx->h_total;
+    if ((st = ensure(ctx, ctx->partial, ctx->partial_cap, (size_t)(n_items > 0 ? n_items : 1) * nacc)))
+        return st;
+    PointArgs pa;
+    pa.net = dn;
+    pa.evc = ctx->evc;
+    pa.sitec = ctx->sitec;
+    pa.sitec_f = ctx->sitec_f;
+    pa.item_off = ctx->off;
+    pa.n_ev = n;
+    pa.n_items = n_items;
+    pa.partial = ctx->partial;
+    pa.nacc = nacc;
+    pa.cov = cov;
+    if (ctx->profiling) CK(cudaEventRecord(ctx->ev0, s));
+    if (mixed) CK(launch_points_mixed(mode, np, dn.rotation, pa, s));
+    else CK(launch_points_fp64(mode, np, dn.rotation, pa, s));
+    if (ctx->profiling) {
+        CK(cudaEventRecord(ctx->ev1, s));
+        ctx->ev_recorded = true;
+    }
+    if (mode == MODE_LOGDET && n_items == 0) {
+        CK(cudaMemsetAsync(grad_gamma, 0, sizeof(double) * dn.n_det, s));
+        return GW_OK;
+    }
+    CK(launch_finish(mode, np, dn.n_det, pa, status, snr, snr_det, fisher, grad_snr, grad_params,
+                     grad_gamma, s));
+    return GW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gw_abi_version(void) { return 1; }
+
+gw_status gw_create(gw_ctx **out, int device)
+{
+    if (!out) return GW_EINVAL;
+    *out = nullptr;
+    gw_ctx *ctx = new (std::nothrow) gw_ctx();
+    if (!ctx) return GW_ENOMEM;
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaMallocHost((void **)&ctx->h_total, sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return GW_ECUDA;
+    }
+    *out = ctx;
+    return GW_OK;
+}
+
+gw_status gw_destroy(gw_ctx *ctx)
+{
+    if (!ctx) return GW_OK;
+    cudaSetDevice(ctx->device);
+    cudaFree(ctx->evc);
+    cudaFree(ctx->sitec);
+    cudaFree(ctx->sitec_f);
+    cudaFree(ctx->status);
+    cudaFree(ctx->counts);
+    cudaFree(ctx->off);
+    cudaFree(ctx->scan);
+    cudaFree(ctx->partial);
+    cudaFreeHost(ctx->h_total);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+    return GW_OK;
+}
+
+const char *gw_last_error(const gw_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+gw_status gw_set_profiling(gw_ctx *ctx, int enable)
+{
+    if (!ctx) return GW_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    if (enable && !ctx->ev0) {
+        CK(cudaEventCreate(&ctx->ev0));
+        CK(cudaEventCreate(&ctx->ev1));
+    }
+    ctx->profiling = enable ? 1 : 0;
+    ctx->ev_recorded = false;
+    return GW_OK;
+}
+
+double gw_point_kernel_ms(gw_ctx *ctx)
+{
+    if (!ctx || !ctx->ev_recorded) return -1.0;
+    float ms = -1.0f;
+    if (cudaEventSynchronize(ctx->ev1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0;
+    }
+    return (double)ms;
+}
+
+gw_status gw_prepare_catalog(gw_ctx *ctx, int64_t n, const double *m1, const double *m2,
+                             const double *chi1, const double *chi2, const double *lam1,
+                             const double *lam2, const double *dL_Mpc, const uint8_t *zflag,
+                             const double *tcoal, const double *fmin, const int32_t *npts_given,
+                             int32_t npts_fixed, double per_efold, int32_t npts_lo,
+                             int32_t npts_hi, double *Mc, double *eta, double *dL_Gpc,
+                             double *chi1o, double *chi2o, double *LamT, double *dLamT,
+                             double *tc_s, double *fmax, int32_t *npts, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (n < 0) return fail(ctx, GW_EINVAL, "n < 0");
+    if (n == 0) return GW_OK;
+    if (!m1 || !m2 || !chi1 || !chi2 || !dL_Mpc || !zflag || !tcoal || !fmin || !Mc || !eta ||
+        !dL_Gpc || !chi1o || !chi2o || !LamT || !dLamT || !tc_s || !fmax || !npts)
+        return fail(ctx, GW_EINVAL, "prepare: a required array is null");
+    if (!npts_given && npts_fixed <= 0 && !(per_efold > 0 && npts_lo >= 2 && npts_hi >= npts_lo))
+        return fail(ctx, GW_EINVAL, "prepare: no valid grid-length rule");
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_prepare(n, m1, m2, chi1, chi2, lam1, lam2, dL_Mpc, zflag, tcoal, fmin, npts_given,
+                      npts_fixed, per_efold, npts_lo, npts_hi, Mc, eta, dL_Gpc, chi1o, chi2o, LamT,
+                      dLamT, tc_s, fmax, npts, (cudaStream_t)stream));
+    return GW_OK;
+}
+
+gw_status gw_snr(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_precision prec,
+                 double *snr, double *snr_det, int32_t *status, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (!snr) return fail(ctx, GW_EINVAL, "snr: output is null");
+    // the parameter set does not matter for the SNR: run as 9-parameter events
+    // with a catalog view whose pset is ignored
+    gw_catalog c9 = *cat;
+    c9.pset = nullptr;
+    return run_points(ctx, &c9, net, prec, MODE_SNR, 9, status, snr, snr_det, nullptr, nullptr,
+                      nullptr, nullptr, nullptr, stream);
+}
+
+gw_status gw_fisher(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_precision prec,
+                    int n_par, double *fisher, double *snr, int32_t *status, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (!fisher) return fail(ctx, GW_EINVAL, "fisher: output is null");
+    return run_points(ctx, cat, net, prec, MODE_FISHER, n_par, status, snr, nullptr, fisher,
+                      nullptr, nullptr, nullptr, nullptr, stream);
+}
+
+gw_status gw_fisher_inverse(gw_ctx *ctx, const double *fisher, int64_t n, int n_par,
+                            double cond_max, double *cov, double *cond, double *inv_err,
+                            int32_t *status, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (n < 0 || (n > 0 && (!fisher || !cov)))
+        return fail(ctx, GW_EINVAL, "fisher_inverse: bad arguments");
+    if (n_par != 9 && n_par != 11) return fail(ctx, GW_EINVAL, "n_par must be 9 or 11");
+    if (n == 0) return GW_OK;
+    CK(cudaSetDevice(ctx->device));
+    int32_t *st = status;
+    if (!st) {
+        gw_status e = ensure(ctx, ctx->status, ctx->status_cap, (size_t)n);
+        if (e) return e;
+        st = ctx->status;
+    }
+    CK(launch_invert(fisher, n, n_par, cond_max, cov, cond, inv_err, st, (cudaStream_t)stream));
+    return GW_OK;
+}
+
+gw_status gw_snr_vjp(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_precision prec,
+                     int n_par, const double *grad_snr, double *grad_params, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (!grad_snr || !grad_params) return fail(ctx, GW_EINVAL, "snr_vjp: null array");
+    return run_points(ctx, cat, net, prec, MODE_SNRGRAD, n_par, nullptr, nullptr, nullptr,
+                      nullptr, grad_snr, grad_params, nullptr, nullptr, stream);
+}
+
+gw_status gw_logdet_vjp_detangles(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
+                                  gw_precision prec, int n_par, const double *cov,
+                                  double *grad_gamma, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (!cov || !grad_gamma) return fail(ctx, GW_EINVAL, "logdet_vjp: null array");
+    return run_points(ctx, cat, net, prec, MODE_LOGDET, n_par, nullptr, nullptr, nullptr,
+                      nullptr, nullptr, nullptr, cov, grad_gamma, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// gw_internal.cuh -- device-side data layout shared by the kernels of libgwfish.
+//
+// Per call, the host turns the caller's network into a DevNet passed by value
+// as a kernel argument (it lives in the constant bank; every thread reads the
+// same entries).  A triangle becomes two virtual 90-degree interferometers at
+// bisectors gamma_T and gamma_T + 45 deg with amplitude 3/(2 sqrt 2): the three
+// 60-degree arms (bisectors gamma_T + 30 + 120 k deg) have detector tensors
+// that sum to zero, and the sum of the three arms' outer products of any
+// quantity linear in the detector tensor (strain, its parameter derivatives)
+// equals that of the two virtual interferometers.  This is exact, and replaces
+// the paper's "third arm from the other two" saving (Sec. 3.3) by a two-term
+// form: 2 of 3 projections and 2 of 3 rank-2 updates per point.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gw {
+
+constexpr int MAX_SITE = 8;
+constexpr int MAX_IFO = 16;
+constexpr int MAX_DET = 8;
+constexpr int MAX_PSD = 4;
+constexpr int MAX_TERM = 4;
+
+// physical constants (SI; masses as G M / c^3 in seconds)
+constexpr double PI = 3.141592653589793238462643383279502884;
+constexpr double TWO_PI = 6.283185307179586476925286766559005768;
+constexpr double EULER_GAMMA = 0.577215664901532860606512090082402431;
+constexpr double T_SUN = 4.925490947641267e-6;
+constexpr double C_SI = 299792458.0;
+constexpr double MPC_M = 3.085677581491367e22;
+constexpr double GPC_S = 1.0e3 * MPC_M / C_SI;
+constexpr double R_EARTH_S = 6.371e6 / C_SI;       // Earth radius in light-seconds
+constexpr double T_SIDEREAL = 86164.0905;
+constexpr double OMEGA_E = TWO_PI / T_SIDEREAL;
+constexpr double H0_KMS_MPC = 70.0;
+constexpr double C_KMS = 299792.458;
+
+struct DevNet {
+    int n_site, n_ifo, n_psd, rotation, n_det;
+    int pad_;
+    double site_slat[MAX_SITE], site_clat[MAX_SITE], site_lon[MAX_SITE];
+    int site_ifo0[MAX_SITE], site_ifo1[MAX_SITE];   // IFOs of site s: [ifo0, ifo1)
+    int ifo_site[MAX_IFO], ifo_psd[MAX_IFO], ifo_det[MAX_IFO];
+    double ifo_s2g[MAX_IFO], ifo_c2g[MAX_IFO], ifo_amp[MAX_IFO];
+    double psd_inv_f0[MAX_PSD], psd_f0[MAX_PSD];
+    int psd_nterm[MAX_PSD];
+    double psd_coef[MAX_PSD][MAX_TERM];   // scale * coef
+    int psd_pow[MAX_PSD][MAX_TERM];       // integer powers, |p| <= 15
+    // FP32 path: PSDs divided by a reference scale (S_n ~ 1e-49 is below the
+    // FP32 range) and the amplitude divided by sqrt(reference scale)
+    float psd_coef_f[MAX_PSD][MAX_TERM];
+    float psd_inv_f0_f[MAX_PSD];
+    double inv_sqrt_scale_ref;
+};
+
+// ---- per-event constants (FP64), row of EVC doubles per event ----------
+enum EvSlot : int {
+    EV_MC = 0, EV_ETA, EV_DL, EV_NPTS, EV_LNR,
+    EV_WC0, EV_WCM, EV_WCN,            // trapezoid weight / f at first, interior, last point
+    EV_LNF0,                            // ln fmin
+    EV_LNPIM,                           // ln(pi M_s)
+    EV_INV_PIM,                         // 1/(pi M_s)  (f = v^3 / (pi M_s))
+    EV_PIM,                             // pi M_s      (1/f = pi M_s v^-3)
+    EV_RHO32, EV_RHOI32, EV_LNRHO32,    // v, 1/v, ln v advance per 32 points
+    EV_A0,                              // A = A0 f^(-7/6)
+    EV_RA32,                            // A advance per 32 points
+    EV_CP, EV_CX, EV_DCP, EV_DCX,       // (1+cos^2 i)/2, cos i and their iota derivatives
+    EV_C2PSI, EV_S2PSI,
+    EV_AMC,                             // 5 / (6 Mc)
+    EV_INVDL,
+    EV_PM,                              // 11: d Psi / d Mc            (basis B11)
+    EV_PE = EV_PM + 11,                 // 11: d Psi / d eta | Mc      (basis B11)
+    EV_P9 = EV_PE + 11,                 // 4: slot 9  (v^-2, v^-1, v^5, v^7)
+    EV_P10 = EV_P9 + 4,                 // 4: slot 10
+    EV_T0 = EV_P10 + 4,                 // 8: tau*                (basis B8, times v^-3)
+    EV_TM = EV_T0 + 8,                  // 8: d tau*/d Mc
+    EV_TE = EV_TM + 8,                  // 8: d tau*/d eta | Mc
+    EVC = EV_TE + 8
+};
+// B11 = (v^-5, v^-3, v^-2, v^-1, 1, v, v^2, v^5, v^7, ln v, v ln v)
+// B8  = (v^-5, v^-3, v^-2, v^-1, 1, v, v^2, v ln v)
+
+// ---- per (event, site) constants -----------------------------------------
+enum SiteSlot : int {
+    SC_X0 = 0,                    // phi - lon - Omega_E tc, reduced to [-pi, pi]
+    SC_A1, SC_A2, SC_A3, SC_A4, SC_A5, SC_B1, SC_B2, SC_B3, SC_B4,
+    SC_A1T, SC_A2T, SC_A3T, SC_A4T, SC_A5T, SC_B1T, SC_B2T, SC_B3T, SC_B4T,
+    SC_D1, SC_D2, SC_D1T, SC_D2T, // Doppler: R/c [cos lat sin th, sin lat cos th] and d/d theta
+    SC_N
+};
+
+// accumulator layouts
+template <int NP> struct Acc {
+    static constexpr int NPAIR = NP * (NP + 1) / 2;
+};
+
+enum Mode : int { MODE_SNR = 0, MODE_FISHER = 1, MODE_SNRGRAD = 2, MODE_LOGDET = 3 };
+
+constexpr int PPL_MAX = 16;              // points per lane per work item (max)
+constexpr int CHUNK_MAX = 32 * PPL_MAX;  // points per work item (max)
+
+}  // namespace gw

@@ -1,0 +1,75 @@
+// gw_kernels.cuh -- launch interfaces between the host API (gw_api.cu) and the
+// kernels (gw_setup.cu, gw_points_fp64.cu, gw_points_mixed.cu).
+#pragma once
+
+#include "gw_internal.cuh"
+
+namespace gw {
+
+// catalog in device memory (pointers may be null where the ABI allows)
+struct DevCat {
+    int64_t n;
+    const double *Mc, *eta, *dL, *theta, *phi, *iota, *psi, *tc, *Phic;
+    const double *chi1, *chi2, *LamT, *dLamT;
+    const int8_t *pset;
+    const double *fmin, *fmax;
+    const int32_t *npts;
+};
+
+struct PointArgs {
+    DevNet net;
+    const double *evc;        // [n][EVC]
+    const double *sitec;      // [n][n_site][SC_N]
+    const float *sitec_f;     // [n][n_site][SC_N], FP32 copy for the mixed path
+    const int64_t *item_off;  // [n+1] exclusive prefix of work items per event
+    int64_t n_ev, n_items;
+    double *partial;          // [n_items][nacc]
+    int nacc;
+    const double *cov;        // logdet mode: covariance, packed, event-minor
+};
+
+// number of accumulators per work item
+inline int n_acc(int mode, int np, int n_det)
+{
+    switch (mode) {
+    case MODE_SNR: return 1 + n_det;
+    case MODE_FISHER: return 1 + np * (np + 1) / 2;
+    case MODE_SNRGRAD: return 1 + np;
+    default: return n_det;
+    }
+}
+
+cudaError_t launch_prepare(int64_t n, const double *m1, const double *m2, const double *chi1,
+                           const double *chi2, const double *lam1, const double *lam2,
+                           const double *dL_Mpc, const uint8_t *zflag, const double *tcoal,
+                           const double *fmin, const int32_t *npts_given, int32_t npts_fixed,
+                           double per_efold, int32_t lo, int32_t hi, double *Mc, double *eta,
+                           double *dL_Gpc, double *chi1o, double *chi2o, double *LamT,
+                           double *dLamT, double *tc_s, double *fmax, int32_t *npts,
+                           cudaStream_t s);
+
+// event constants, status, and work items per event
+cudaError_t launch_event_setup(const DevCat &cat, const DevNet &net, int np, double *evc,
+                               double *sitec, float *sitec_f, int32_t *status, int64_t *counts,
+                               cudaStream_t s);
+
+// exclusive scan of counts[0..n) into off[0..n], off[n] = total; tmp needs
+// scan_tmp_size(n) int64 elements
+size_t scan_tmp_size(int64_t n);
+cudaError_t launch_scan(const int64_t *counts, int64_t n, int64_t *off, int64_t *tmp,
+                        cudaStream_t s);
+
+cudaError_t launch_points_fp64(int mode, int np, int rot, const PointArgs &a, cudaStream_t s);
+cudaError_t launch_points_mixed(int mode, int np, int rot, const PointArgs &a, cudaStream_t s);
+
+// partial sums of the items of each event -> outputs
+cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const int32_t *status,
+                          double *snr, double *snr_det, double *fisher, const double *grad_snr,
+                          double *grad_params, double *grad_gamma, cudaStream_t s);
+
+cudaError_t launch_invert(const double *fisher, int64_t n, int np, double cond_max, double *cov,
+                          double *cond, double *inv_err, int32_t *status, cudaStream_t s);
+
+int points_grid_size();   // persistent grid (blocks) for the point kernels
+
+}  // namespace gw

@@ -1,0 +1,457 @@
+// gw_points_fp64.cu -- the fused point loop, every operation in FP64.
+//
+// One warp per work item (a contiguous run of at most CHUNK_MAX grid points of
+// one event); lane l takes points k0 + l, k0 + l + 32, ...  For each point it
+// forms the TaylorF2 phase derivatives, tau*(f) and its derivatives (Sec. 2.2),
+// the pattern functions and Doppler phase at the Earth angle of t(f)
+// (Sec. 3.1), the tangents g_i = dQ/dtheta_i + i Q dPhi/dtheta_i of every
+// (virtual) interferometer and accumulates
+//     SNR^2 += W |Q|^2,   Gamma_ij += W Re(g_i^* g_j),   W = 4 w_k / S_n(f_k)
+// (Sec. 3.2, Eqs. 3.1-3.3, trapezoid weights w_k on the log grid).  The strain
+// phase Phi itself is never formed: with h = Q e^{i Phi} the factor e^{i Phi}
+// cancels in |h|^2 and in Re(d_i h^* d_j h), so only its derivatives enter.
+// Tangents never leave registers; each warp writes one row of partial sums.
+#include <cmath>
+
+#include "gw_kernels.cuh"
+
+namespace gw {
+
+namespace {
+
+// reciprocal: hardware estimate refined by two Newton-Raphson steps
+// y <- y (2 - x y) (Newton's method for f(y) = 1/y - x)
+__device__ __forceinline__ double rcp64(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    return y;
+}
+
+__device__ __forceinline__ double ipow(double x, int p)
+{
+    double r = 1.0;
+    while (p) {
+        if (p & 1) r *= x;
+        x *= x;
+        p >>= 1;
+    }
+    return r;
+}
+
+__device__ __forceinline__ int64_t find_event(const int64_t *off, int64_t n, int64_t it)
+{
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= it) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int MODE, int NP>
+struct NAccOf {
+    static constexpr int value = MODE == MODE_FISHER ? 1 + NP * (NP + 1) / 2
+                               : MODE == MODE_SNRGRAD ? 1 + NP
+                               : MODE == MODE_SNR ? 1 + MAX_DET
+                               : MAX_DET;
+};
+
+// per-IFO pattern values at one point
+struct Pat {
+    double fp, fx, fpT, fxT, fpX, fxX;
+};
+
+__device__ __forceinline__ Pat patterns(double s2g, double c2g, double P1, double P2,
+                                        const double (&J)[12])
+{
+    // J = a_s, a_c, b_c, b_s, then theta- and x-derivatives of each
+    Pat p;
+    double a = s2g * J[0] + c2g * J[1], b = c2g * J[2] + s2g * J[3];
+    double aT = s2g * J[4] + c2g * J[5], bT = c2g * J[6] + s2g * J[7];
+    double aX = s2g * J[8] + c2g * J[9], bX = c2g * J[10] + s2g * J[11];
+    p.fp = P1 * a + P2 * b;
+    p.fx = P1 * b - P2 * a;
+    p.fpT = P1 * aT + P2 * bT;
+    p.fxT = P1 * bT - P2 * aT;
+    p.fpX = P1 * aX + P2 * bX;
+    p.fxX = P1 * bX - P2 * aX;
+    return p;
+}
+
+// phase-derivative values common to all IFOs of one site at one point
+struct Phase {
+    double Mc, eta, th, ph, tc, p9, p10;   // d Phi / d theta_i
+    double tMc, teta;                      // Omega_E d tau*/d Mc, Omega_E d tau*/d eta
+};
+
+// tangents of one IFO: real and imaginary parts
+template <int NP, bool ROT>
+__device__ __forceinline__ void tangents(const Pat &p, double Acp, double Acx, double Adcp,
+                                         double Adcx, double aMc, double invdL, const Phase &ph,
+                                         double (&gr)[NP], double (&gi)[NP], double &qr,
+                                         double &qi)
+{
+    qr = Acp * p.fp;
+    qi = Acx * p.fx;
+    const double xr = Acp * p.fpX, xi = Acx * p.fxX;   // dQ/dx
+    const double tr = Acp * p.fpT, ti = Acx * p.fxT;   // dQ/dtheta
+    // Mc
+    gr[0] = aMc * qr - qi * ph.Mc;
+    gi[0] = aMc * qi + qr * ph.Mc;
+    if (ROT) {
+        gr[0] = fma(ph.tMc, xr, gr[0]);
+        gi[0] = fma(ph.tMc, xi, gi[0]);
+    }
+    // eta
+    gr[1] = -qi * ph.eta;
+    gi[1] = qr * ph.eta;
+    if (ROT) {
+        gr[1] = fma(ph.teta, xr, gr[1]);
+        gi[1] = fma(ph.teta, xi, gi[1]);
+    }
+    // dL
+    gr[2] = -qr * invdL;
+    gi[2] = -qi * invdL;
+    // theta
+    gr[3] = tr - qi * ph.th;
+    gi[3] = ti + qr * ph.th;
+    // phi (x = phi - lon - Omega_E t)
+    gr[4] = xr - qi * ph.ph;
+    gi[4] = xi + qr * ph.ph;
+    // iota
+    gr[5] = Adcp * p.fp;
+    gi[5] = Adcx * p.fx;
+    // psi: dF+/dpsi = 2 Fx, dFx/dpsi = -2 F+
+    gr[6] = 2.0 * Acp * p.fx;
+    gi[6] = -2.0 * Acx * p.fp;
+    // tc: dx/dtc = -Omega_E
+    gr[7] = -qi * ph.tc;
+    gi[7] = qr * ph.tc;
+    if (ROT) {
+        gr[7] = fma(-OMEGA_E, xr, gr[7]);
+        gi[7] = fma(-OMEGA_E, xi, gi[7]);
+    }
+    // Phic: dPhi/dPhic = -1
+    gr[8] = qi;
+    gi[8] = -qr;
+    if (NP == 11) {
+        gr[NP - 2] = -qi * ph.p9;
+        gi[NP - 2] = qr * ph.p9;
+        gr[NP - 1] = -qi * ph.p10;
+        gi[NP - 1] = qr * ph.p10;
+    }
+}
+
+template <int MODE, int NP, bool ROT>
+__global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
+{
+    constexpr int NACC = NAccOf<MODE, NP>::value;
+    extern __shared__ double red_smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    double *red = red_smem + wib * (NACC * 33);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const DevNet &net = A.net;
+
+    for (int64_t it = blockIdx.x * (int64_t)(blockDim.x >> 5) + wib; it < A.n_items;
+         it += nwarps) {
+        const int64_t e = find_event(A.item_off, A.n_ev, it);
+        const int64_t j = it - A.item_off[e];
+        const int64_t nj = A.item_off[e + 1] - A.item_off[e];
+        const double *E = A.evc + e * (int64_t)EVC;
+        const int N = (int)E[EV_NPTS];
+        const int kb = (int)((int64_t)N * j / nj), ke = (int)((int64_t)N * (j + 1) / nj);
+
+        double acc[NACC];
+#pragma unroll
+        for (int a = 0; a < NACC; a++) acc[a] = 0.0;
+
+        // covariance of the event (logdet mode), packed upper
+        double Cv[MODE == MODE_LOGDET ? NP * (NP + 1) / 2 : 1];
+        bool skip = false;
+        if (MODE == MODE_LOGDET) {
+#pragma unroll
+            for (int q = 0; q < NP * (NP + 1) / 2; q++) Cv[q] = A.cov[(int64_t)q * A.n_ev + e];
+            skip = !isfinite(Cv[0]);
+        }
+
+        int k = kb + lane;
+        if (k < ke && !skip) {
+            const double lnr = E[EV_LNR];
+            const double lnf = fma((double)k, lnr, E[EV_LNF0]);
+            double lnv = (lnf + E[EV_LNPIM]) * (1.0 / 3.0);
+            double v = exp(lnv), vinv = exp(-lnv);
+            double Aamp = E[EV_A0] * exp(-7.0 / 6.0 * lnf);
+            const double rho = E[EV_RHO32], rhoi = E[EV_RHOI32], dlnv = E[EV_LNRHO32];
+            const double rA = E[EV_RA32];
+            const double inv_pim = E[EV_INV_PIM], pim = E[EV_PIM];
+            const double wc0 = E[EV_WC0], wcm = E[EV_WCM], wcn = E[EV_WCN];
+            const double cp = E[EV_CP], cx = E[EV_CX], dcp = E[EV_DCP], dcx = E[EV_DCX];
+            const double c2p = E[EV_C2PSI], s2p = E[EV_S2PSI];
+            const double aMc = E[EV_AMC], invdL = E[EV_INVDL];
+
+            for (; k < ke; k += 32) {
+                // ---- grid point, weight, basis
+                const double vi2 = vinv * vinv, vi3 = vi2 * vinv, vi5 = vi3 * vi2;
+                const double v2 = v * v, v5 = v2 * v2 * v, v7 = v5 * v2, vl = v * lnv;
+                const double f = v2 * v * inv_pim;
+                const double w = f * (k == 0 ? wc0 : (k == N - 1 ? wcn : wcm));
+                const double twopif = TWO_PI * f;
+                // ---- phase derivatives of the PN phase (basis B11 dot products)
+                const double *PM = E + EV_PM, *PE = E + EV_PE;
+                double dMc = PM[8] * v7;
+                dMc = fma(PM[7], v5, dMc);
+                dMc = fma(PM[10], vl, dMc);
+                dMc = fma(PM[6], v2, dMc);
+                dMc = fma(PM[5], v, dMc);
+                dMc = fma(PM[4], 1.0, dMc);
+                dMc = fma(PM[3], vinv, dMc);
+                dMc = fma(PM[2], vi2, dMc);
+                dMc = fma(PM[1], vi3, dMc);
+                dMc = fma(PM[0], vi5, dMc);
+                double dEt = PE[8] * v7;
+                dEt = fma(PE[7], v5, dEt);
+                dEt = fma(PE[10], vl, dEt);
+                dEt = fma(PE[9], lnv, dEt);
+                dEt = fma(PE[6], v2, dEt);
+                dEt = fma(PE[5], v, dEt);
+                dEt = PE[4] + dEt;
+                dEt = fma(PE[3], vinv, dEt);
+                dEt = fma(PE[2], vi2, dEt);
+                dEt = fma(PE[1], vi3, dEt);
+                dEt = fma(PE[0], vi5, dEt);
+                double d9 = 0.0, d10 = 0.0;
+                if (NP == 11) {
+                    const double *P9 = E + EV_P9, *P10 = E + EV_P10;
+                    d9 = fma(P9[0], vi2, fma(P9[1], vinv, fma(P9[2], v5, P9[3] * v7)));
+                    d10 = fma(P10[0], vi2, fma(P10[1], vinv, fma(P10[2], v5, P10[3] * v7)));
+                }
+                // ---- tau*(f) and its derivatives (rotation only)
+                double tau = 0.0, tMc = 0.0, tEt = 0.0;
+                if (ROT) {
+                    const double *T0 = E + EV_T0, *TM = E + EV_TM, *TE = E + EV_TE;
+                    double b[8] = {vi5, vi3, vi2, vinv, 1.0, v, v2, vl};
+                    double s0 = T0[7] * b[7], s1 = TM[7] * b[7], s2 = TE[7] * b[7];
+#pragma unroll
+                    for (int q = 6; q >= 0; q--) {
+                        s0 = fma(T0[q], b[q], s0);
+                        s1 = fma(TM[q], b[q], s1);
+                        s2 = fma(TE[q], b[q], s2);
+                    }
+                    tau = s0 * vi3;
+                    tMc = s1 * vi3;
+                    tEt = s2 * vi3;
+                }
+                // ---- noise weights per PSD: W = 4 w / S_n(f)
+                double Wp[MAX_PSD];
+#pragma unroll
+                for (int p = 0; p < MAX_PSD; p++) {
+                    if (p < net.n_psd) {
+                        const double x = f * net.psd_inv_f0[p];
+                        const double xi = net.psd_f0[p] * pim * vi3;
+                        double S = 0.0;
+                        for (int q = 0; q < net.psd_nterm[p]; q++) {
+                            const int pw = net.psd_pow[p][q];
+                            S = fma(net.psd_coef[p][q], pw >= 0 ? ipow(x, pw) : ipow(xi, -pw), S);
+                        }
+                        Wp[p] = 4.0 * w * rcp64(S);
+                    } else {
+                        Wp[p] = 0.0;
+                    }
+                }
+                const double Acp = Aamp * cp, Acx = Aamp * cx, Adcp = Aamp * dcp,
+                             Adcx = Aamp * dcx;
+
+                // ---- sites
+                for (int s = 0; s < net.n_site; s++) {
+                    const double *S = A.sitec + (e * net.n_site + s) * (int64_t)SC_N;
+                    const double x = ROT ? fma(OMEGA_E, tau, S[SC_X0]) : S[SC_X0];
+                    double sx, cxx;
+                    sincos(x, &sx, &cxx);
+                    const double c2x = fma(2.0 * cxx, cxx, -1.0), s2x = 2.0 * sx * cxx;
+                    double J[12];
+                    J[0] = fma(S[SC_A1], c2x, fma(S[SC_A2], cxx, S[SC_A3]));
+                    J[1] = fma(S[SC_A4], s2x, S[SC_A5] * sx);
+                    J[2] = fma(S[SC_B1], c2x, S[SC_B2] * cxx);
+                    J[3] = fma(S[SC_B3], s2x, S[SC_B4] * sx);
+                    J[4] = fma(S[SC_A1T], c2x, fma(S[SC_A2T], cxx, S[SC_A3T]));
+                    J[5] = fma(S[SC_A4T], s2x, S[SC_A5T] * sx);
+                    J[6] = fma(S[SC_B1T], c2x, S[SC_B2T] * cxx);
+                    J[7] = fma(S[SC_B3T], s2x, S[SC_B4T] * sx);
+                    J[8] = fma(-2.0 * S[SC_A1], s2x, -S[SC_A2] * sx);
+                    J[9] = fma(2.0 * S[SC_A4], c2x, S[SC_A5] * cxx);
+                    J[10] = fma(-2.0 * S[SC_B1], s2x, -S[SC_B2] * sx);
+                    J[11] = fma(2.0 * S[SC_B3], c2x, S[SC_B4] * cxx);
+                    Phase ph;
+                    const double dxPD = -twopif * S[SC_D1] * sx;
+                    ph.th = twopif * fma(S[SC_D1T], cxx, S[SC_D2T]);
+                    ph.ph = dxPD;
+                    ph.Mc = dMc;
+                    ph.eta = dEt;
+                    ph.tc = twopif;
+                    ph.p9 = d9;
+                    ph.p10 = d10;
+                    ph.tMc = 0.0;
+                    ph.teta = 0.0;
+                    if (ROT) {
+                        // dx/dMc = Omega_E dtau*/dMc, dx/deta likewise, dx/dtc = -Omega_E
+                        ph.tMc = OMEGA_E * tMc;
+                        ph.teta = OMEGA_E * tEt;
+                        ph.Mc = fma(dxPD, ph.tMc, dMc);
+                        ph.eta = fma(dxPD, ph.teta, dEt);
+                        ph.tc = fma(-OMEGA_E, dxPD, twopif);
+                    }
+                    if (MODE == MODE_SNRGRAD) {
+                        ph.Mc = ph.eta = ph.th = ph.ph = ph.tc = ph.p9 = ph.p10 = 0.0;
+                    }
+                    for (int q = net.site_ifo0[s]; q < net.site_ifo1[s]; q++) {
+                        const double amp = net.ifo_amp[q];
+                        const Pat pt = patterns(net.ifo_s2g[q], net.ifo_c2g[q], amp * c2p,
+                                                amp * s2p, J);
+                        const double W = Wp[net.ifo_psd[q]];
+                        double gr[NP], gi[NP], qr, qi;
+                        tangents<NP, ROT>(pt, Acp, Acx, Adcp, Adcx, aMc, invdL, ph, gr, gi, qr,
+                                          qi);
+                        const double q2 = fma(qr, qr, qi * qi);
+                        if (MODE == MODE_FISHER) {
+                            acc[0] = fma(W, q2, acc[0]);
+                            double wr[NP], wi[NP];
+#pragma unroll
+                            for (int i = 0; i < NP; i++) {
+                                wr[i] = W * gr[i];
+                                wi[i] = W * gi[i];
+                            }
+                            int a = 1;
+#pragma unroll
+                            for (int i = 0; i < NP; i++)
+#pragma unroll
+                                for (int jj = i; jj < NP; jj++) {
+                                    acc[a] = fma(wr[i], gr[jj], fma(wi[i], gi[jj], acc[a]));
+                                    a++;
+                                }
+                        } else if (MODE == MODE_SNR) {
+                            acc[0] = fma(W, q2, acc[0]);
+                            const int dd = net.ifo_det[q];
+#pragma unroll
+                            for (int d = 0; d < MAX_DET; d++)
+                                if (d == dd) acc[1 + d] = fma(W, q2, acc[1 + d]);
+                        } else if (MODE == MODE_SNRGRAD) {
+                            // Re(Q^* g_i) = Re(Q^* dQ/dtheta_i): the phase part i Q dPhi
+                            // contributes exactly zero, so it is left out (it would only
+                            // add rounding), and Phic / slots 9, 10 stay exactly 0.
+                            acc[0] = fma(W, q2, acc[0]);
+                            const double wqr = W * qr, wqi = W * qi;
+#pragma unroll
+                            for (int i = 0; i < 8; i++)
+                                acc[1 + i] = fma(wqr, gr[i], fma(wqi, gi[i], acc[1 + i]));
+                        } else {   // MODE_LOGDET
+                            // y = C g
+                            double yr[NP], yi[NP];
+#pragma unroll
+                            for (int i = 0; i < NP; i++) {
+                                double sr = 0.0, si = 0.0;
+#pragma unroll
+                                for (int m = 0; m < NP; m++) {
+                                    const int lo = i < m ? i : m, hi = i < m ? m : i;
+                                    const double c = Cv[lo * NP - lo * (lo - 1) / 2 + (hi - lo)];
+                                    sr = fma(c, gr[m], sr);
+                                    si = fma(c, gi[m], si);
+                                }
+                                yr[i] = sr;
+                                yi[i] = si;
+                            }
+                            // g' = d g / d gamma: the same tangents with (sin2g, cos2g)
+                            // replaced by (2 cos2g, -2 sin2g)
+                            const Pat pd = patterns(2.0 * net.ifo_c2g[q], -2.0 * net.ifo_s2g[q],
+                                                    amp * c2p, amp * s2p, J);
+                            double hr[NP], hi_[NP], dqr, dqi;
+                            tangents<NP, ROT>(pd, Acp, Acx, Adcp, Adcx, aMc, invdL, ph, hr, hi_,
+                                              dqr, dqi);
+                            double t = 0.0;
+#pragma unroll
+                            for (int i = 0; i < NP; i++) t = fma(hr[i], yr[i], fma(hi_[i], yi[i], t));
+                            const int dd = net.ifo_det[q];
+#pragma unroll
+                            for (int d = 0; d < MAX_DET; d++)
+                                if (d == dd) acc[d] = fma(2.0 * W, t, acc[d]);
+                        }
+                    }
+                }
+                // ---- advance to the lane's next point (k + 32)
+                v *= rho;
+                vinv *= rhoi;
+                lnv += dlnv;
+                Aamp *= rA;
+            }
+        }
+        // ---- warp reduction through shared memory, fixed order
+#pragma unroll
+        for (int a = 0; a < NACC; a++) red[a * 33 + lane] = acc[a];
+        __syncwarp();
+        double *out = A.partial + it * (int64_t)A.nacc;
+        for (int a = lane; a < A.nacc; a += 32) {
+            double s = 0.0;
+#pragma unroll 8
+            for (int l = 0; l < 32; l++) s += red[a * 33 + l];
+            out[a] = s;
+        }
+        __syncwarp();
+    }
+}
+
+template <int MODE, int NP, bool ROT>
+cudaError_t launch_one(const PointArgs &a, cudaStream_t s)
+{
+    constexpr int NACC = NAccOf<MODE, NP>::value;
+    const size_t smem = 4 * NACC * 33 * sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t err = cudaFuncSetAttribute(k_points_fp64<MODE, NP, ROT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+        if (err != cudaSuccess) return err;
+        attr_set = true;
+    }
+    if (a.n_items <= 0) return cudaSuccess;
+    k_points_fp64<MODE, NP, ROT><<<points_grid_size(), 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_mode(int np, int rot, const PointArgs &a, cudaStream_t s)
+{
+    if (np == 9) return rot ? launch_one<MODE, 9, true>(a, s) : launch_one<MODE, 9, false>(a, s);
+    return rot ? launch_one<MODE, 11, true>(a, s) : launch_one<MODE, 11, false>(a, s);
+}
+
+}  // namespace
+
+int points_grid_size()
+{
+    static int g = 0;
+    if (!g) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g = 2 * (sms > 0 ? sms : 148);
+    }
+    return g;
+}
+
+cudaError_t launch_points_fp64(int mode, int np, int rot, const PointArgs &a, cudaStream_t s)
+{
+    switch (mode) {
+    case MODE_SNR: return launch_mode<MODE_SNR>(np, rot, a, s);
+    case MODE_FISHER: return launch_mode<MODE_FISHER>(np, rot, a, s);
+    case MODE_SNRGRAD: return launch_mode<MODE_SNRGRAD>(np, rot, a, s);
+    default: return launch_mode<MODE_LOGDET>(np, rot, a, s);
+    }
+}
+
+}  // namespace gw

@@ -1,0 +1,584 @@
+// gw_setup.cu -- per-event kernels around the point loop:
+//   catalog preparation (Sec. 2.1, Eq. 2.2, f_ISCO of the Sec. 2.2 footnote),
+//   per-event waveform / geometry constants, work-item scan, reduction of the
+//   per-item partial sums into SNR / Fisher / VJP outputs, and the batched
+//   Cholesky inversion with conditioning check (Sec. 4.1).
+#include <cfloat>
+#include <cmath>
+
+#include "gw_kernels.cuh"
+
+namespace gw {
+
+// ------------------------------------------------------------------------
+// catalog preparation: one thread per event
+__global__ void k_prepare(int64_t n, const double *m1, const double *m2, const double *chi1,
+                          const double *chi2, const double *lam1, const double *lam2,
+                          const double *dL_Mpc, const uint8_t *zflag, const double *tcoal,
+                          const double *fmin, const int32_t *npts_given, int32_t npts_fixed,
+                          double per_efold, int32_t lo, int32_t hi, double *Mc, double *eta,
+                          double *dL_Gpc, double *chi1o, double *chi2o, double *LamT,
+                          double *dLamT, double *tc_s, double *fmax_o, int32_t *npts)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double a = m1[e], b = m2[e], ca = chi1[e], cb = chi2[e];
+    double la = lam1 ? lam1[e] : 0.0, lb = lam2 ? lam2[e] : 0.0;
+    if (b > a) {   // m1 >= m2, spins and deformabilities follow their body
+        double t = a; a = b; b = t;
+        t = ca; ca = cb; cb = t;
+        t = la; la = lb; lb = t;
+    }
+    double z = zflag[e] ? H0_KMS_MPC * dL_Mpc[e] / C_KMS : 0.0;
+    a *= 1.0 + z;
+    b *= 1.0 + z;
+    double M = a + b;
+    double et = a * b / (M * M);
+    double d = sqrt(fmax(0.0, 1.0 - 4.0 * et));
+    double sL = la + lb, dLam = la - lb;
+    double lt = 8.0 / 13.0 * ((1.0 + 7.0 * et - 31.0 * et * et) * sL
+                              + d * (1.0 + 9.0 * et - 11.0 * et * et) * dLam);
+    double dlt = 0.5 * (d * (1.0 - 13272.0 / 1319.0 * et + 8944.0 / 1319.0 * et * et) * sL
+                        + (1.0 - 15910.0 / 1319.0 * et + 32850.0 / 1319.0 * et * et
+                           + 3380.0 / 1319.0 * et * et * et) * dLam);
+    Mc[e] = M * pow(et, 0.6);
+    eta[e] = et;
+    dL_Gpc[e] = dL_Mpc[e] * 1.0e-3;
+    chi1o[e] = ca;
+    chi2o[e] = cb;
+    LamT[e] = lt;
+    dLamT[e] = dlt;
+    tc_s[e] = tcoal[e] * T_SIDEREAL;
+    double fi = 1.0 / (pow(6.0, 1.5) * PI * M * T_SUN);
+    fmax_o[e] = fi;
+    int32_t np;
+    if (npts_given) {
+        np = npts_given[e];
+    } else if (npts_fixed > 0) {
+        np = npts_fixed;
+    } else {
+        double x = ceil(per_efold * log(fi / fmin[e]));
+        if (!(x >= (double)lo)) x = lo;   // also catches NaN
+        if (x > hi) x = hi;
+        np = (int32_t)x;
+    }
+    npts[e] = np;
+}
+
+cudaError_t launch_prepare(int64_t n, const double *m1, const double *m2, const double *chi1,
+                           const double *chi2, const double *lam1, const double *lam2,
+                           const double *dL_Mpc, const uint8_t *zflag, const double *tcoal,
+                           const double *fmin, const int32_t *npts_given, int32_t npts_fixed,
+                           double per_efold, int32_t lo, int32_t hi, double *Mc, double *eta,
+                           double *dL_Gpc, double *chi1o, double *chi2o, double *LamT,
+                           double *dLamT, double *tc_s, double *fmax, int32_t *npts,
+                           cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int bs = 256;
+    int64_t nb = (n + bs - 1) / bs;
+    k_prepare<<<(unsigned)nb, bs, 0, s>>>(n, m1, m2, chi1, chi2, lam1, lam2, dL_Mpc, zflag,
+                                          tcoal, fmin, npts_given, npts_fixed, per_efold, lo, hi,
+                                          Mc, eta, dL_Gpc, chi1o, chi2o, LamT, dLamT, tc_s, fmax,
+                                          npts);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// per-event constants.  TaylorF2 phase and tau* are written in the basis
+//   B11 = (v^-5, v^-3, v^-2, v^-1, 1, v, v^2, v^5, v^7, ln v, v ln v)
+// at fixed f, so that every parameter derivative is one dot product with the
+// point's basis values.  At fixed f:  Mc d/dMc = (1/3) v d/dv  and
+// d/deta|Mc = d/deta|v - (1/(5 eta)) v d/dv  (v = (pi M f)^(1/3), M = Mc eta^-3/5).
+__global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec,
+                              float *sitec_f, int32_t *status, int64_t *counts)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= cat.n) return;
+    const double Mc = cat.Mc[e], eta = cat.eta[e], dL = cat.dL[e];
+    const double th = cat.theta[e], ph = cat.phi[e], io = cat.iota[e], ps = cat.psi[e];
+    const double tc = cat.tc[e];
+    const double c1 = cat.chi1 ? cat.chi1[e] : 0.0, c2 = cat.chi2 ? cat.chi2[e] : 0.0;
+    const double LT = cat.LamT ? cat.LamT[e] : 0.0, dLT = cat.dLamT ? cat.dLamT[e] : 0.0;
+    const int pset = cat.pset ? (int)cat.pset[e] : 0;
+    const double fmin = cat.fmin[e], fmx = cat.fmax[e];
+    const int N = cat.npts[e];
+    int st = 0;
+    if (!(Mc > 0.0) || !(eta > 0.0) || !(eta <= 0.25) || !(dL > 0.0)) st |= 16;
+    if (pset < 0 || pset > 2 || ((np == 9) != (pset == 0))) st |= 16;
+    if (!isfinite(th) || !isfinite(ph) || !isfinite(io) || !isfinite(ps) || !isfinite(tc) ||
+        !isfinite(c1) || !isfinite(c2) || !isfinite(LT) || !isfinite(dLT) ||
+        !isfinite(cat.Phic[e]))
+        st |= 16;
+    if (!(fmin > 0.0) || !(fmx > fmin) || !isfinite(fmx) || N < 2) st |= 8;
+    status[e] = st;
+    counts[e] = st ? 0 : (int64_t)((N + CHUNK_MAX - 1) / CHUNK_MAX);
+    if (st) return;
+
+    double *E = evc + e * (int64_t)EVC;
+    const double Mcs = Mc * T_SUN;
+    const double Ms = Mcs * pow(eta, -0.6);
+    const double pim = PI * Ms;
+    const double lnr = log(fmx / fmin) / (double)(N - 1);
+    E[EV_MC] = Mc;
+    E[EV_ETA] = eta;
+    E[EV_DL] = dL;
+    E[EV_NPTS] = (double)N;
+    E[EV_LNR] = lnr;
+    E[EV_WC0] = 0.5 * expm1(lnr);
+    E[EV_WCM] = sinh(lnr);
+    E[EV_WCN] = -0.5 * expm1(-lnr);
+    E[EV_LNF0] = log(fmin);
+    E[EV_LNPIM] = log(pim);
+    E[EV_INV_PIM] = 1.0 / pim;
+    E[EV_PIM] = pim;
+    E[EV_RHO32] = exp(32.0 * lnr / 3.0);
+    E[EV_RHOI32] = exp(-32.0 * lnr / 3.0);
+    E[EV_LNRHO32] = 32.0 * lnr / 3.0;
+    E[EV_A0] = sqrt(5.0 / 24.0) * pow(PI, -2.0 / 3.0) * pow(Mcs, 5.0 / 6.0) / (dL * GPC_S);
+    E[EV_RA32] = exp(-7.0 / 6.0 * 32.0 * lnr);
+    double si, ci, s2p, c2p;
+    sincos(io, &si, &ci);
+    sincos(2.0 * ps, &s2p, &c2p);
+    E[EV_CP] = 0.5 * (1.0 + ci * ci);
+    E[EV_CX] = ci;
+    E[EV_DCP] = -ci * si;
+    E[EV_DCX] = -si;
+    E[EV_C2PSI] = c2p;
+    E[EV_S2PSI] = s2p;
+    E[EV_AMC] = 5.0 / (6.0 * Mc);
+    E[EV_INVDL] = 1.0 / dL;
+
+    // ---- TaylorF2 3.5PN phase coefficients (restricted PN)
+    const double pi2 = PI * PI;
+    const double d = sqrt(fmax(0.0, 1.0 - 4.0 * eta));
+    const double X1 = 0.5 * (1.0 + d), X2 = 0.5 * (1.0 - d);
+    const double b1 = 113.0 / 12.0 * X1 * X1 + 25.0 * eta / 4.0;
+    const double b2 = 113.0 / 12.0 * X2 * X2 + 25.0 * eta / 4.0;
+    const double beta = b1 * c1 + b2 * c2;
+    const double sigma = 79.0 / 8.0 * eta * c1 * c2;
+    const double dbeta = 113.0 / 6.0 * (X2 * c2 - X1 * c1) / d + 25.0 / 4.0 * (c1 + c2);
+    const double dsigma = 79.0 / 8.0 * c1 * c2;
+    const double ln6h = 1.0 + 1.5 * log(6.0);                 // 1 - 3 ln v_lso
+    const double L6 = -6848.0 / 21.0;
+    const double p2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
+    const double p3 = -16.0 * PI + 4.0 * beta;
+    const double p4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta
+                      - 10.0 * sigma;
+    const double p5a = PI * (38645.0 / 756.0 - 65.0 / 9.0 * eta);
+    const double p5c = p5a * ln6h;
+    const double p6c = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi2
+                       - 6848.0 / 21.0 * EULER_GAMMA
+                       + (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2) * eta
+                       + 76055.0 / 1728.0 * eta * eta - 127825.0 / 1296.0 * eta * eta * eta;
+    const double p6 = p6c + L6 * log(4.0);
+    const double p7 = PI * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta
+                            - 74045.0 / 756.0 * eta * eta);
+    const double t10 = -39.0 / 2.0 * LT;
+    const double t12 = -3115.0 / 64.0 * LT + 6595.0 / 364.0 * d * dLT;
+    const double dp4 = 27145.0 / 504.0 + 2.0 * 3085.0 / 72.0 * eta - 10.0 * dsigma;
+    const double dp5a = -65.0 * PI / 9.0;
+    const double dp6 = -15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2
+                       + 2.0 * 76055.0 / 1728.0 * eta - 3.0 * 127825.0 / 1296.0 * eta * eta;
+    const double dp7 = PI * (378515.0 / 1512.0 - 2.0 * 74045.0 / 756.0 * eta);
+    const double dt12 = 6595.0 / 364.0 * (-2.0 / d) * dLT;
+    const double pre = 3.0 / (128.0 * eta);
+    const double ie = 1.0 / eta;
+    // v dPsi/dv
+    const double V[11] = {-5.0, -3.0 * p2, -2.0 * p3, -p4, 3.0 * p5a, p6 + L6, 2.0 * p7,
+                          5.0 * t10, 7.0 * t12, 0.0, L6};
+    // dPsi/deta at fixed v (before the prefactor)
+    const double De[11] = {-ie, 55.0 / 9.0 - p2 * ie, 4.0 * dbeta - p3 * ie, dp4 - p4 * ie,
+                           dp5a * ln6h - p5c * ie, dp6 - p6 * ie, dp7 - p7 * ie, -t10 * ie,
+                           dt12 - t12 * ie, 3.0 * (dp5a - p5a * ie), -L6 * ie};
+    for (int k = 0; k < 11; k++) {
+        E[EV_PM + k] = pre * V[k] / (3.0 * Mc);
+        E[EV_PE + k] = pre * (De[k] - V[k] / (5.0 * eta));
+    }
+    double q9[4] = {0, 0, 0, 0}, q10[4] = {0, 0, 0, 0};
+    if (pset == 1) {
+        q9[0] = 4.0 * b1;
+        q9[1] = -10.0 * 79.0 / 8.0 * eta * c2;
+        q10[0] = 4.0 * b2;
+        q10[1] = -10.0 * 79.0 / 8.0 * eta * c1;
+    } else if (pset == 2) {
+        q9[2] = -39.0 / 2.0;
+        q9[3] = -3115.0 / 64.0;
+        q10[3] = 6595.0 / 364.0 * d;
+    }
+    for (int k = 0; k < 4; k++) {
+        E[EV_P9 + k] = pre * q9[k];
+        E[EV_P10 + k] = pre * q10[k];
+    }
+    // ---- tau*(f), 3.5PN (Buonanno et al. 2009 Eq. 3.8b), basis B8 times v^-3
+    const double Kt = 5.0 * Ms / (256.0 * eta);
+    const double t2 = 743.0 / 252.0 + 11.0 / 3.0 * eta;
+    const double t3 = -32.0 / 5.0 * PI;
+    const double t4 = 3058673.0 / 508032.0 + 5429.0 / 504.0 * eta + 617.0 / 72.0 * eta * eta;
+    const double t5 = (-7729.0 / 252.0 + 13.0 / 3.0 * eta) * PI;
+    const double t6 = -10052469856691.0 / 23471078400.0 + 128.0 / 3.0 * pi2
+                      + 6848.0 / 105.0 * EULER_GAMMA
+                      + (3147553127.0 / 3048192.0 - 451.0 / 12.0 * pi2) * eta
+                      - 15211.0 / 1728.0 * eta * eta + 25565.0 / 1296.0 * eta * eta * eta
+                      + 3424.0 / 105.0 * log(16.0);
+    const double t6L = 6848.0 / 105.0;
+    const double t7 = (-15419335.0 / 127008.0 - 75703.0 / 756.0 * eta
+                       + 14809.0 / 378.0 * eta * eta) * PI;
+    const double dt4 = 5429.0 / 504.0 + 2.0 * 617.0 / 72.0 * eta;
+    const double dt5 = 13.0 / 3.0 * PI;
+    const double dt6 = 3147553127.0 / 3048192.0 - 451.0 / 12.0 * pi2
+                       - 2.0 * 15211.0 / 1728.0 * eta + 3.0 * 25565.0 / 1296.0 * eta * eta;
+    const double dt7 = PI * (-75703.0 / 756.0 + 2.0 * 14809.0 / 378.0 * eta);
+    const double T0[8] = {1.0, t2, t3, t4, t5, t6, t7, t6L};
+    const double Tv[8] = {-5.0, -3.0 * t2, -2.0 * t3, -t4, 0.0, t6 + t6L, 2.0 * t7, t6L};
+    const double Te[8] = {-ie, 11.0 / 3.0 - t2 * ie, -t3 * ie, dt4 - t4 * ie, dt5 - t5 * ie,
+                          dt6 - t6 * ie, dt7 - t7 * ie, -t6L * ie};
+    for (int k = 0; k < 8; k++) {
+        E[EV_T0 + k] = Kt * T0[k];
+        E[EV_TM + k] = Kt * Tv[k] / (3.0 * Mc);
+        E[EV_TE + k] = Kt * (Te[k] - Tv[k] / (5.0 * eta));
+    }
+
+    // ---- per-site JKS coefficients (pattern functions as functions of the
+    // hour-angle-like x = phi - lon - g) and Doppler factors.
+    double sth, cth;
+    sincos(th, &sth, &cth);
+    const double sd = cth, cd = sth;                  // delta = pi/2 - theta
+    const double s2d = 2.0 * sth * cth, c2d = sth * sth - cth * cth;
+    for (int s = 0; s < net.n_site; s++) {
+        double *S = sitec + (e * net.n_site + s) * (int64_t)SC_N;
+        const double sl = net.site_slat[s], cl = net.site_clat[s];
+        const double c2l = 1.0 - 2.0 * sl * sl, s2l = 2.0 * sl * cl;
+        double x0 = ph - net.site_lon[s] - OMEGA_E * tc;
+        x0 = remainder(x0, TWO_PI);
+        S[SC_X0] = x0;
+        S[SC_A1] = (3.0 - c2l) * (3.0 - c2d) / 16.0;
+        S[SC_A2] = s2l * s2d / 4.0;
+        S[SC_A3] = 0.75 * cl * cl * cd * cd;
+        S[SC_A4] = -sl * (3.0 - c2d) / 4.0;
+        S[SC_A5] = -cl * s2d / 2.0;
+        S[SC_B1] = sl * sd;
+        S[SC_B2] = cl * cd;
+        S[SC_B3] = (3.0 - c2l) * sd / 4.0;
+        S[SC_B4] = s2l * cd / 2.0;
+        // d/dtheta = -d/ddelta
+        S[SC_A1T] = -(3.0 - c2l) * s2d / 8.0;
+        S[SC_A2T] = -s2l * c2d / 2.0;
+        S[SC_A3T] = 0.75 * cl * cl * s2d;
+        S[SC_A4T] = sl * s2d / 2.0;
+        S[SC_A5T] = cl * c2d;
+        S[SC_B1T] = -sl * cd;
+        S[SC_B2T] = cl * sd;
+        S[SC_B3T] = -(3.0 - c2l) * cd / 4.0;
+        S[SC_B4T] = s2l * sd / 2.0;
+        S[SC_D1] = R_EARTH_S * cl * sth;
+        S[SC_D2] = R_EARTH_S * sl * cth;
+        S[SC_D1T] = R_EARTH_S * cl * cth;
+        S[SC_D2T] = -R_EARTH_S * sl * sth;
+        if (sitec_f) {
+            float *Sf = sitec_f + (e * net.n_site + s) * (int64_t)SC_N;
+            for (int q = 0; q < SC_N; q++) Sf[q] = (float)S[q];
+        }
+    }
+}
+
+cudaError_t launch_event_setup(const DevCat &cat, const DevNet &net, int np, double *evc,
+                               double *sitec, float *sitec_f, int32_t *status, int64_t *counts,
+                               cudaStream_t s)
+{
+    if (cat.n <= 0) return cudaSuccess;
+    int bs = 128;
+    int64_t nb = (cat.n + bs - 1) / bs;
+    k_event_setup<<<(unsigned)nb, bs, 0, s>>>(cat, net, np, evc, sitec, sitec_f, status, counts);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// exclusive scan (int64), three passes: block sums, scan of block sums in one
+// block, then per-block offsets.  SCAN_BS elements per block.
+constexpr int SCAN_BS = 1024;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// block-wide exclusive scan of one value per thread; returns the block total
+__device__ int64_t block_excl_scan(int64_t v, int64_t &excl)
+{
+    __shared__ int64_t wsum[SCAN_BS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t inc = warp_incl_scan(v);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int64_t x = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
+        x = warp_incl_scan(x);
+        if (lane < (int)(blockDim.x >> 5)) wsum[lane] = x;
+    }
+    __syncthreads();
+    int64_t base = (w > 0) ? wsum[w - 1] : 0;
+    excl = base + inc - v;
+    int64_t total = wsum[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return total;
+}
+
+__global__ void k_scan_blocks(const int64_t *counts, int64_t n, int64_t *off, int64_t *bsum)
+{
+    int64_t i = blockIdx.x * (int64_t)SCAN_BS + threadIdx.x;
+    int64_t v = (i < n) ? counts[i] : 0;
+    int64_t ex;
+    int64_t tot = block_excl_scan(v, ex);
+    if (i < n) off[i] = ex;
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int64_t *bsum, int64_t nb, int64_t *off_total)
+{
+    // single block; loops over chunks of SCAN_BS block sums
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += SCAN_BS) {
+        int64_t i = b0 + threadIdx.x;
+        int64_t v = (i < nb) ? bsum[i] : 0;
+        int64_t ex;
+        int64_t tot = block_excl_scan(v, ex);
+        if (i < nb) bsum[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *off_total = carry;
+}
+
+__global__ void k_scan_add(int64_t *off, int64_t n, const int64_t *bsum)
+{
+    int64_t i = blockIdx.x * (int64_t)SCAN_BS + threadIdx.x;
+    if (i < n) off[i] += bsum[blockIdx.x];
+}
+
+size_t scan_tmp_size(int64_t n) { return (size_t)((n + SCAN_BS - 1) / SCAN_BS + 1); }
+
+cudaError_t launch_scan(const int64_t *counts, int64_t n, int64_t *off, int64_t *tmp,
+                        cudaStream_t s)
+{
+    int64_t nb = (n + SCAN_BS - 1) / SCAN_BS;
+    if (nb < 1) nb = 1;
+    k_scan_blocks<<<(unsigned)nb, SCAN_BS, 0, s>>>(counts, n, off, tmp);
+    k_scan_sums<<<1, SCAN_BS, 0, s>>>(tmp, nb, off + n);
+    k_scan_add<<<(unsigned)nb, SCAN_BS, 0, s>>>(off, n, tmp);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// reduction of item partials: one thread per (event, accumulator), items of an
+// event summed in item order (deterministic).
+__global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc,
+                         const int64_t *item_off, const double *partial, const int32_t *status,
+                         double *snr, double *snr_det, double *fisher, const double *grad_snr,
+                         double *grad_params)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t e = t / nacc;
+    int a = (int)(t - e * nacc);
+    if (e >= n) return;
+    const bool bad = status[e] != 0;
+    const int64_t i0 = item_off[e], i1 = item_off[e + 1];
+    double s = 0.0;
+    for (int64_t it = i0; it < i1; it++) s += partial[it * nacc + a];
+    if (mode == MODE_FISHER) {
+        if (a == 0) {
+            if (snr) snr[e] = bad ? NAN : sqrt(s);
+        } else {
+            fisher[(int64_t)(a - 1) * n + e] = bad ? NAN : s;
+        }
+    } else if (mode == MODE_SNR) {
+        if (a == 0) snr[e] = bad ? NAN : sqrt(s);
+        else if (snr_det) snr_det[(int64_t)(a - 1) * n + e] = bad ? NAN : sqrt(s);
+    } else if (mode == MODE_SNRGRAD) {
+        if (a > 0) {
+            double s0 = 0.0;
+            for (int64_t it = i0; it < i1; it++) s0 += partial[it * nacc];
+            // d SNR / d theta = sum W Re(Q* g) / SNR
+            grad_params[(int64_t)(a - 1) * n + e] = bad ? NAN : grad_snr[e] * s / sqrt(s0);
+        }
+    }
+}
+
+// logdet mode: total over all items of each detector accumulator, fixed order
+__global__ void k_finish_total(int64_t n_items, int nacc, const double *partial, double *out)
+{
+    __shared__ double sh[256];
+    int a = blockIdx.x;
+    double s = 0.0;
+    for (int64_t it = threadIdx.x; it < n_items; it += blockDim.x) s += partial[it * nacc + a];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[a] = sh[0];
+}
+
+cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const int32_t *status,
+                          double *snr, double *snr_det, double *fisher, const double *grad_snr,
+                          double *grad_params, double *grad_gamma, cudaStream_t s)
+{
+    if (mode == MODE_LOGDET) {
+        k_finish_total<<<a.nacc, 256, 0, s>>>(a.n_items, a.nacc, a.partial, grad_gamma);
+        return cudaGetLastError();
+    }
+    int64_t tot = a.n_ev * a.nacc;
+    if (tot <= 0) return cudaSuccess;
+    int bs = 256;
+    k_finish<<<(unsigned)((tot + bs - 1) / bs), bs, 0, s>>>(mode, np, n_det, a.n_ev, a.nacc,
+                                                           a.item_off, a.partial, status, snr,
+                                                           snr_det, fisher, grad_snr,
+                                                           grad_params);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// Batched inversion (Sec. 4.1): normalise by sqrt(diag), Cholesky, triangular
+// inverse, C = L^-T L^-1 rescaled; 1-norm condition number of the normalised
+// matrix and eps = max |Gamma C - 1|.  One thread per event, FP64.
+template <int NP>
+__global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, double cond_max,
+                                                double *cov, double *cond, double *inv_err,
+                                                int32_t *status)
+{
+    constexpr int NK = NP * (NP + 1) / 2;
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double G[NP][NP];
+    int st = 0;
+    {
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i < NP; i++)
+#pragma unroll
+            for (int j = i; j < NP; j++) {
+                double v = F[(int64_t)k * n + e];
+                k++;
+                if (!isfinite(v)) st |= 4;
+                G[i][j] = v;
+                G[j][i] = v;
+            }
+    }
+    double d[NP];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+        if (!(G[i][i] > 0.0)) st |= 1;
+        d[i] = sqrt(G[i][i]);
+    }
+    double kappa = NAN, eps = NAN;
+    double C[NP][NP];
+    if (!st) {
+        double H[NP][NP], L[NP][NP];
+#pragma unroll
+        for (int i = 0; i < NP; i++)
+#pragma unroll
+            for (int j = 0; j < NP; j++) {
+                H[i][j] = G[i][j] / (d[i] * d[j]);
+                L[i][j] = 0.0;
+            }
+        // Cholesky H = L L^T
+#pragma unroll
+        for (int j = 0; j < NP; j++) {
+            double sjj = H[j][j];
+#pragma unroll
+            for (int k = 0; k < j; k++) sjj -= L[j][k] * L[j][k];
+            if (!(sjj > 0.0)) st |= 1;
+            const double ljj = sqrt(sjj);
+            L[j][j] = ljj;
+            const double il = 1.0 / ljj;
+#pragma unroll
+            for (int i = j + 1; i < NP; i++) {
+                double t = H[i][j];
+#pragma unroll
+                for (int k = 0; k < j; k++) t -= L[i][k] * L[j][k];
+                L[i][j] = t * il;
+            }
+        }
+        if (!st) {
+            // M = L^-1 (lower), forward substitution column by column
+            double M[NP][NP];
+#pragma unroll
+            for (int c = 0; c < NP; c++) {
+#pragma unroll
+                for (int i = 0; i < NP; i++) {
+                    if (i < c) { M[i][c] = 0.0; continue; }
+                    double t = (i == c) ? 1.0 : 0.0;
+#pragma unroll
+                    for (int k = c; k < i; k++) t -= L[i][k] * M[k][c];
+                    M[i][c] = t / L[i][i];
+                }
+            }
+            // Hinv = M^T M
+            double hn1 = 0.0, in1 = 0.0;
+#pragma unroll
+            for (int j = 0; j < NP; j++) {
+                double colh = 0.0, coli = 0.0;
+#pragma unroll
+                for (int i = 0; i < NP; i++) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int k = (i > j ? i : j); k < NP; k++) t += M[k][i] * M[k][j];
+                    C[i][j] = t / (d[i] * d[j]);
+                    coli += fabs(t);
+                    colh += fabs(H[i][j]);
+                }
+                hn1 = fmax(hn1, colh);
+                in1 = fmax(in1, coli);
+            }
+            kappa = hn1 * in1;
+            if (kappa > 1.0 / DBL_EPSILON) st |= 32;
+            if (kappa > cond_max) st |= 2;
+            eps = 0.0;
+#pragma unroll
+            for (int i = 0; i < NP; i++)
+#pragma unroll
+                for (int j = 0; j < NP; j++) {
+                    double t = (i == j) ? -1.0 : 0.0;
+#pragma unroll
+                    for (int k = 0; k < NP; k++) t += G[i][k] * C[k][j];
+                    eps = fmax(eps, fabs(t));
+                }
+        }
+    }
+    const bool ok = !(st & (1 | 2 | 4));
+    {
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i < NP; i++)
+#pragma unroll
+            for (int j = i; j < NP; j++) {
+                cov[(int64_t)k * n + e] = ok ? C[i][j] : NAN;
+                k++;
+            }
+    }
+    if (cond) cond[e] = (st & (1 | 4)) ? NAN : kappa;
+    if (inv_err) inv_err[e] = ok ? eps : NAN;
+    status[e] = st;
+    (void)NK;
+}
+
+cudaError_t launch_invert(const double *fisher, int64_t n, int np, double cond_max, double *cov,
+                          double *cond, double *inv_err, int32_t *status, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int bs = 64;
+    unsigned nb = (unsigned)((n + bs - 1) / bs);
+    if (np == 9)
+        k_invert<9><<<nb, bs, 0, s>>>(fisher, n, cond_max, cov, cond, inv_err, status);
+    else
+        k_invert<11><<<nb, bs, 0, s>>>(fisher, n, cond_max, cov, cond, inv_err, status);
+    return cudaGetLastError();
+}
+
+}  // namespace gw
