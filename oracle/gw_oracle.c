@@ -835,8 +835,10 @@ int or_abi_version(void) { return 1; }
 int or_grid_npts(int64_t n, const double *fmin, const double *fmax, double per_efold,
                  int lo, int hi, int32_t *npts)
 {
+    /* an integer decided by floating point: taken in double precision, the
+     * precision in which the library takes it */
     for (int64_t e = 0; e < n; e++) {
-        ld x = ceill((ld)per_efold * logl((ld)fmax[e] / (ld)fmin[e]));
+        double x = ceil(per_efold * log(fmax[e] / fmin[e]));
         if (!(x == x) || x < lo) x = lo;
         if (x > hi) x = hi;
         npts[e] = (int32_t)x;
