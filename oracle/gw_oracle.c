@@ -287,7 +287,7 @@ int or_prepare(int64_t n, const double *m1, const double *m2, const double *chi1
         ld M = a + b;
         ld et = a * b / (M * M);
         ld mc = M * powl(et, 0.6L);
-        ld d = sqrtl(fmaxl(0.0L, 1.0L - 4.0L * et));
+        ld d = (a - b) / M;   /* sqrt(1 - 4 eta) for m1 >= m2 */
         ld lt = 8.0L / 13.0L * ((1.0L + 7.0L * et - 31.0L * et * et) * (la + lb)
                 + d * (1.0L + 9.0L * et - 11.0L * et * et) * (la - lb));
         ld dlt = 0.5L * (d * (1.0L - 13272.0L / 1319.0L * et + 8944.0L / 1319.0L * et * et) * (la + lb)
