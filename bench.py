@@ -244,12 +244,11 @@ def run_ours(a):
 
     def step(d):
         cat = prepare(d)
-        F, snr, st = gw.gw_fisher(cat, net, N_PAR, prec)
+        F, snr, st, g = gw.gw_fisher(cat, net, N_PAR, prec, grad_snr=grad_up)
         cov, cond, err, sti = gw.gw_fisher_inverse(F, N_PAR)
-        g = gw.gw_snr_vjp(cat, net, N_PAR, grad_up, prec)
         return cat, F, snr, cov, cond, g, st
 
-    launches_per_step = 1 + 6 + 1 + 6
+    launches_per_step = 1 + 7 + 1
     for _ in range(a.warmup):
         step(dev)
     torch.cuda.synchronize()
@@ -273,10 +272,9 @@ def run_ours(a):
         flush.zero_()
         ev[i][0].record(stream)
         cat = prepare(dev)
-        F, snr, st = gw.gw_fisher(cat, net, N_PAR, prec)
+        F, snr, st, g = gw.gw_fisher(cat, net, N_PAR, prec, grad_snr=grad_up)
         fisher_ms.append(gw.gw_point_kernel_ms())
         gw.gw_fisher_inverse(F, N_PAR)
-        gw.gw_snr_vjp(cat, net, N_PAR, grad_up, prec)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     gw.gw_set_profiling(False)
@@ -339,7 +337,7 @@ def run_ours(a):
             "data": "synthetic (seeded, gwcat)",
             "config": {"workload": WORKLOAD, "n_events_per_gpu": n, "grid": a.grid,
                        "points_per_step": n_points, "precision": a.precision, "n_par": N_PAR,
-                       "step": "prepare + SNR/Fisher + Cholesky inversion + SNR VJP",
+                       "step": "prepare + SNR/Fisher with fused SNR VJP + Cholesky inversion",
                        "l2": "flushed before every timed step (256 MiB write)",
                        "parallelism": f"event shards, {world} GPU(s), no collective"},
             "clocks": clocks,

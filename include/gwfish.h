@@ -113,7 +113,7 @@ gw_status gw_create(gw_ctx **ctx, int device);
 gw_status gw_destroy(gw_ctx *ctx);
 /* Text of the last error on this context (static storage, never NULL). */
 const char *gw_last_error(const gw_ctx *ctx);
-/* ABI version of this header (incremented on any signature change). */
+/* ABI version of this header (incremented on any signature change): 2. */
 int gw_abi_version(void);
 
 /* Measurement hook (no counterpart in the paper): when enabled, the context
@@ -154,10 +154,16 @@ gw_status gw_snr(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
  *   fisher [n_par(n_par+1)/2][n]: packed upper triangle, row-major over
  *          (i <= j), event-minor (element (i,j) of event e at
  *          fisher[k(i,j) * n + e]), like the paper's (P, P, N) layout;
- *   snr [n] (or NULL); status [n] (or NULL). */
+ *   snr [n] (or NULL); status [n] (or NULL);
+ *   grad_params [n_par][n] (or NULL): the SNR vector-Jacobian product of
+ *          gw_snr_vjp for the upstream gradient grad_snr [n] (DEVICE), formed
+ *          in the same pass.  In the FP64 path it is the exact identity
+ *          d SNR/d theta_i = -dL Gamma_{i,dL} / SNR (d h/d dL = -h/dL); the
+ *          mixed path accumulates the phase-free sums Re(Q^* dQ/d theta_i). */
 gw_status gw_fisher(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
                     gw_precision prec, int n_par, double *fisher, double *snr,
-                    int32_t *status, void *stream);
+                    int32_t *status, const double *grad_snr, double *grad_params,
+                    void *stream);
 
 /* Covariance by Cholesky inversion of the normalised Fisher (Sec. 4.1):
  * Gh = Gamma_ij / sqrt(Gamma_ii Gamma_jj), Gh = L L^T, C = Gh^-1 rescaled.

@@ -80,7 +80,7 @@ def load_library(path: str | None = None):
     lib.gw_abi_version.restype = ctypes.c_int
     lib.gw_prepare_catalog.argtypes = [_P, i64] + [_P] * 11 + [i32, d, i32, i32] + [_P] * 10 + [_P]
     lib.gw_snr.argtypes = [_P, C, N, ctypes.c_int, _P, _P, _P, _P]
-    lib.gw_fisher.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
+    lib.gw_fisher.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P]
     lib.gw_fisher_inverse.argtypes = [_P, _P, i64, ctypes.c_int, d, _P, _P, _P, _P, _P]
     lib.gw_snr_vjp.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P]
     lib.gw_logdet_vjp_detangles.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P]
@@ -279,21 +279,28 @@ def gw_snr(cat: Catalog, net: Network, prec=GW_FP64, per_detector=False, stream=
     return (snr, sdet, status) if per_detector else (snr, status)
 
 
-def gw_fisher(cat: Catalog, net: Network, n_par: int, prec=GW_FP64, stream=None, out=None):
-    """Returns (fisher [P(P+1)/2, n] packed upper event-minor, snr [n], status [n])."""
+def gw_fisher(cat: Catalog, net: Network, n_par: int, prec=GW_FP64, stream=None, out=None,
+              grad_snr: torch.Tensor | None = None):
+    """Returns (fisher [P(P+1)/2, n] packed upper event-minor, snr [n], status [n]);
+    with ``grad_snr`` [n] also the fused SNR VJP grad_params [P, n] (4th item)."""
     ctx = context()
     dev = cat.t["Mc"].device
     if out is None:
         fisher = torch.empty((n_packed(n_par), cat.n), dtype=torch.float64, device=dev)
         snr = torch.empty(cat.n, dtype=torch.float64, device=dev)
         status = torch.empty(cat.n, dtype=torch.int32, device=dev)
+        gp = (torch.empty((n_par, cat.n), dtype=torch.float64, device=dev)
+              if grad_snr is not None else None)
     else:
-        fisher, snr, status = out
+        fisher, snr, status = out[:3]
+        gp = out[3] if len(out) > 3 else None
     c = cat.struct()
     st = load_library().gw_fisher(ctx, ctypes.byref(c), ctypes.byref(net.net), int(prec), n_par,
-                                  _ptr(fisher), _ptr(snr), _ptr(status), _stream(stream))
+                                  _ptr(fisher), _ptr(snr), _ptr(status),
+                                  _ptr(grad_snr.contiguous() if grad_snr is not None else None),
+                                  _ptr(gp), _stream(stream))
     _check(st, ctx)
-    return fisher, snr, status
+    return (fisher, snr, status, gp) if grad_snr is not None else (fisher, snr, status)
 
 
 def gw_fisher_inverse(fisher: torch.Tensor, n_par: int, cond_max=1e50, stream=None, out=None):

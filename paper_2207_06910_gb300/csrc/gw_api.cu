@@ -19,11 +19,14 @@ struct gw_ctx {
     double *evc = nullptr;      size_t evc_cap = 0;
     double *sitec = nullptr;    size_t sitec_cap = 0;
     float *sitec_f = nullptr;   size_t sitec_f_cap = 0;
+    float2 *evc_f = nullptr;    size_t evc_f_cap = 0;
     int32_t *status = nullptr;  size_t status_cap = 0;
     int64_t *counts = nullptr;  size_t counts_cap = 0;
     int64_t *off = nullptr;     size_t off_cap = 0;
     int64_t *scan = nullptr;    size_t scan_cap = 0;
     double *partial = nullptr;  size_t partial_cap = 0;
+    double *xsums = nullptr;    size_t xsums_cap = 0;   // mixed SNR-gradient sums [6][n]
+    double *snr_tmp = nullptr;  size_t snr_tmp_cap = 0;
     int64_t *h_total = nullptr;   // pinned
     int profiling = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -173,7 +176,11 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     DevNet dn;
     if ((st = build_net(ctx, net, dn))) return st;
     const int64_t n = cat->n;
-    const int nacc = n_acc(mode, np, dn.n_det);
+    const bool mixed = prec == GW_MIXED && (mode == MODE_FISHER || mode == MODE_SNR ||
+                                            mode == MODE_SNRGRAD);
+    const int nacc = n_acc(mode, np, dn.n_det, mixed);
+    // fused SNR vector-Jacobian product of a Fisher pass
+    const bool fused_grad = mode == MODE_FISHER && grad_params != nullptr;
     if (n == 0) {
         if (mode == MODE_LOGDET) CK(cudaMemsetAsync(grad_gamma, 0, sizeof(double) * dn.n_det, s));
         return GW_OK;
@@ -181,10 +188,21 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     CK(cudaSetDevice(ctx->device));
     if ((st = ensure(ctx, ctx->evc, ctx->evc_cap, (size_t)n * EVC))) return st;
     if ((st = ensure(ctx, ctx->sitec, ctx->sitec_cap, (size_t)n * dn.n_site * SC_N))) return st;
-    const bool mixed = prec == GW_MIXED && (mode == MODE_FISHER || mode == MODE_SNR ||
-                                            mode == MODE_SNRGRAD);
+    double *xs = nullptr;
+    if (fused_grad) {
+        if (!grad_snr) return fail(ctx, GW_EINVAL, "fisher: grad_params needs grad_snr");
+        if (mixed) {
+            if ((st = ensure(ctx, ctx->xsums, ctx->xsums_cap, (size_t)N_SNRGRAD_X * n))) return st;
+            xs = ctx->xsums;
+        }
+        if (!snr) {
+            if ((st = ensure(ctx, ctx->snr_tmp, ctx->snr_tmp_cap, (size_t)n))) return st;
+            snr = ctx->snr_tmp;
+        }
+    }
     if (mixed && (st = ensure(ctx, ctx->sitec_f, ctx->sitec_f_cap, (size_t)n * dn.n_site * SC_N)))
         return st;
+    if (mixed && (st = ensure(ctx, ctx->evc_f, ctx->evc_f_cap, (size_t)n * EVC))) return st;
     if ((st = ensure(ctx, ctx->counts, ctx->counts_cap, (size_t)n))) return st;
     if ((st = ensure(ctx, ctx->off, ctx->off_cap, (size_t)n + 1))) return st;
     if ((st = ensure(ctx, ctx->scan, ctx->scan_cap, scan_tmp_size(n)))) return st;
@@ -194,8 +212,8 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
         status = ctx->status;
     }
     const DevCat dc = dev_cat(cat);
-    CK(launch_event_setup(dc, dn, np, ctx->evc, ctx->sitec, mixed ? ctx->sitec_f : nullptr, status,
-                          ctx->counts, s));
+    CK(launch_event_setup(dc, dn, np, ctx->evc, ctx->sitec, mixed ? ctx->sitec_f : nullptr,
+                          mixed ? ctx->evc_f : nullptr, status, ctx->counts, s));
     CK(launch_scan(ctx->counts, n, ctx->off, ctx->scan, s));
     CK(cudaMemcpyAsync(ctx->h_total, ctx->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -207,6 +225,7 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     pa.evc = ctx->evc;
     pa.sitec = ctx->sitec;
     pa.sitec_f = ctx->sitec_f;
+    pa.evc_f = ctx->evc_f;
     pa.item_off = ctx->off;
     pa.n_ev = n;
     pa.n_items = n_items;
@@ -225,7 +244,10 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
         return GW_OK;
     }
     CK(launch_finish(mode, np, dn.n_det, pa, status, snr, snr_det, fisher, grad_snr, grad_params,
-                     grad_gamma, s));
+                     grad_gamma, xs, s));
+    if (fused_grad)
+        CK(launch_snr_grad_from_fisher(n, np, mixed, dn.rotation, fisher, snr, xs, cat->Mc,
+                                       cat->dL, status, grad_snr, grad_params, s));
     return GW_OK;
 }
 
@@ -233,7 +255,7 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
 
 extern "C" {
 
-int gw_abi_version(void) { return 1; }
+int gw_abi_version(void) { return 2; }
 
 gw_status gw_create(gw_ctx **out, int device)
 {
@@ -259,11 +281,14 @@ gw_status gw_destroy(gw_ctx *ctx)
     cudaFree(ctx->evc);
     cudaFree(ctx->sitec);
     cudaFree(ctx->sitec_f);
+    cudaFree(ctx->evc_f);
     cudaFree(ctx->status);
     cudaFree(ctx->counts);
     cudaFree(ctx->off);
     cudaFree(ctx->scan);
     cudaFree(ctx->partial);
+    cudaFree(ctx->xsums);
+    cudaFree(ctx->snr_tmp);
     cudaFreeHost(ctx->h_total);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -326,7 +351,8 @@ gw_status gw_snr(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_p
                  double *snr, double *snr_det, int32_t *status, void *stream)
 {
     if (!ctx) return GW_EINVAL;
-    if (!snr) return fail(ctx, GW_EINVAL, "snr: output is null");
+    if (!cat) return fail(ctx, GW_EINVAL, "catalog: null");
+    if (!snr && cat->n > 0) return fail(ctx, GW_EINVAL, "snr: output is null");
     // the parameter set does not matter for the SNR: run as 9-parameter events
     // with a catalog view whose pset is ignored
     gw_catalog c9 = *cat;
@@ -336,12 +362,14 @@ gw_status gw_snr(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_p
 }
 
 gw_status gw_fisher(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_precision prec,
-                    int n_par, double *fisher, double *snr, int32_t *status, void *stream)
+                    int n_par, double *fisher, double *snr, int32_t *status,
+                    const double *grad_snr, double *grad_params, void *stream)
 {
     if (!ctx) return GW_EINVAL;
-    if (!fisher) return fail(ctx, GW_EINVAL, "fisher: output is null");
+    if (!cat) return fail(ctx, GW_EINVAL, "catalog: null");
+    if (!fisher && cat->n > 0) return fail(ctx, GW_EINVAL, "fisher: output is null");
     return run_points(ctx, cat, net, prec, MODE_FISHER, n_par, status, snr, nullptr, fisher,
-                      nullptr, nullptr, nullptr, nullptr, stream);
+                      grad_snr, grad_params, nullptr, nullptr, stream);
 }
 
 gw_status gw_fisher_inverse(gw_ctx *ctx, const double *fisher, int64_t n, int n_par,
@@ -368,7 +396,9 @@ gw_status gw_snr_vjp(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
                      int n_par, const double *grad_snr, double *grad_params, void *stream)
 {
     if (!ctx) return GW_EINVAL;
-    if (!grad_snr || !grad_params) return fail(ctx, GW_EINVAL, "snr_vjp: null array");
+    if (!cat) return fail(ctx, GW_EINVAL, "catalog: null");
+    if ((!grad_snr || !grad_params) && cat->n > 0)
+        return fail(ctx, GW_EINVAL, "snr_vjp: null array");
     return run_points(ctx, cat, net, prec, MODE_SNRGRAD, n_par, nullptr, nullptr, nullptr,
                       nullptr, grad_snr, grad_params, nullptr, nullptr, stream);
 }
@@ -378,7 +408,8 @@ gw_status gw_logdet_vjp_detangles(gw_ctx *ctx, const gw_catalog *cat, const gw_n
                                   double *grad_gamma, void *stream)
 {
     if (!ctx) return GW_EINVAL;
-    if (!cov || !grad_gamma) return fail(ctx, GW_EINVAL, "logdet_vjp: null array");
+    if (!cat) return fail(ctx, GW_EINVAL, "catalog: null");
+    if (!grad_gamma || (!cov && cat->n > 0)) return fail(ctx, GW_EINVAL, "logdet_vjp: null array");
     return run_points(ctx, cat, net, prec, MODE_LOGDET, n_par, nullptr, nullptr, nullptr,
                       nullptr, nullptr, nullptr, cov, grad_gamma, stream);
 }

@@ -63,9 +63,9 @@ enum EvSlot : int {
     EV_LNPIM,                           // ln(pi M_s)
     EV_INV_PIM,                         // 1/(pi M_s)  (f = v^3 / (pi M_s))
     EV_PIM,                             // pi M_s      (1/f = pi M_s v^-3)
-    EV_RHO32, EV_RHOI32, EV_LNRHO32,    // v, 1/v, ln v advance per 32 points
+    EV_RHOG, EV_RHOIG, EV_LNRHOG,       // v, 1/v, ln v advance per GROUP points
     EV_A0,                              // A = A0 f^(-7/6)
-    EV_RA32,                            // A advance per 32 points
+    EV_RAG,                             // A advance per GROUP points
     EV_CP, EV_CX, EV_DCP, EV_DCX,       // (1+cos^2 i)/2, cos i and their iota derivatives
     EV_C2PSI, EV_S2PSI,
     EV_AMC,                             // 5 / (6 Mc)
@@ -88,6 +88,7 @@ enum SiteSlot : int {
     SC_A1, SC_A2, SC_A3, SC_A4, SC_A5, SC_B1, SC_B2, SC_B3, SC_B4,
     SC_A1T, SC_A2T, SC_A3T, SC_A4T, SC_A5T, SC_B1T, SC_B2T, SC_B3T, SC_B4T,
     SC_D1, SC_D2, SC_D1T, SC_D2T, // Doppler: R/c [cos lat sin th, sin lat cos th] and d/d theta
+    SC_X0LO,                      // FP32 table only: x0 - (float)x0 (double-float x0)
     SC_N
 };
 
@@ -98,7 +99,14 @@ template <int NP> struct Acc {
 
 enum Mode : int { MODE_SNR = 0, MODE_FISHER = 1, MODE_SNRGRAD = 2, MODE_LOGDET = 3 };
 
-constexpr int PPL_MAX = 16;              // points per lane per work item (max)
-constexpr int CHUNK_MAX = 32 * PPL_MAX;  // points per work item (max)
+// A work item is a contiguous run of at most CHUNK_MAX grid points of one
+// event, processed by a group of GROUP lanes (lane l takes points k0 + l,
+// k0 + l + GROUP, ...); a warp runs 32 / GROUP items at once.  Short items
+// (the 200-300-point grids of light catalogs) then give every lane ~30
+// points, which amortises the per-lane start and the per-item reduction.
+constexpr int GROUP = 8;
+constexpr int GROUPS_PER_WARP = 32 / GROUP;
+constexpr int PPL_MAX = 32;                   // points per lane per work item (max)
+constexpr int CHUNK_MAX = GROUP * PPL_MAX;    // points per work item (max)
 
 }  // namespace gw

@@ -21,6 +21,7 @@ struct PointArgs {
     const double *evc;        // [n][EVC]
     const double *sitec;      // [n][n_site][SC_N]
     const float *sitec_f;     // [n][n_site][SC_N], FP32 copy for the mixed path
+    const float2 *evc_f;      // [n][EVC], double-float copy for the mixed path
     const int64_t *item_off;  // [n+1] exclusive prefix of work items per event
     int64_t n_ev, n_items;
     double *partial;          // [n_items][nacc]
@@ -28,12 +29,17 @@ struct PointArgs {
     const double *cov;        // logdet mode: covariance, packed, event-minor
 };
 
+// extra accumulators of the mixed Fisher kernel: phase-free SNR-gradient sums
+//   Re(Q* dQ/dx), Omega tau*_Mc Re(Q* dQ/dx), Omega tau*_eta Re(Q* dQ/dx),
+//   Re(Q* dQ/dtheta), Re(Q* dQ/diota), Re(Q* dQ/dpsi)
+constexpr int N_SNRGRAD_X = 6;
+
 // number of accumulators per work item
-inline int n_acc(int mode, int np, int n_det)
+inline int n_acc(int mode, int np, int n_det, bool mixed = false)
 {
     switch (mode) {
     case MODE_SNR: return 1 + n_det;
-    case MODE_FISHER: return 1 + np * (np + 1) / 2;
+    case MODE_FISHER: return 1 + np * (np + 1) / 2 + (mixed ? N_SNRGRAD_X : 0);
     case MODE_SNRGRAD: return 1 + np;
     default: return n_det;
     }
@@ -50,8 +56,8 @@ cudaError_t launch_prepare(int64_t n, const double *m1, const double *m2, const 
 
 // event constants, status, and work items per event
 cudaError_t launch_event_setup(const DevCat &cat, const DevNet &net, int np, double *evc,
-                               double *sitec, float *sitec_f, int32_t *status, int64_t *counts,
-                               cudaStream_t s);
+                               double *sitec, float *sitec_f, float2 *evc_f, int32_t *status,
+                               int64_t *counts, cudaStream_t s);
 
 // exclusive scan of counts[0..n) into off[0..n], off[n] = total; tmp needs
 // scan_tmp_size(n) int64 elements
@@ -65,11 +71,18 @@ cudaError_t launch_points_mixed(int mode, int np, int rot, const PointArgs &a, c
 // partial sums of the items of each event -> outputs
 cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const int32_t *status,
                           double *snr, double *snr_det, double *fisher, const double *grad_snr,
-                          double *grad_params, double *grad_gamma, cudaStream_t s);
+                          double *grad_params, double *grad_gamma, double *xsums, cudaStream_t s);
+
+// SNR vector-Jacobian product from a Fisher pass (see gw_fisher)
+cudaError_t launch_snr_grad_from_fisher(int64_t n, int np, bool mixed, int rot,
+                                        const double *fisher, const double *snr,
+                                        const double *xsums, const double *Mc, const double *dL,
+                                        const int32_t *status, const double *grad_snr,
+                                        double *grad_params, cudaStream_t s);
 
 cudaError_t launch_invert(const double *fisher, int64_t n, int np, double cond_max, double *cov,
                           double *cond, double *inv_err, int32_t *status, cudaStream_t s);
 
-int points_grid_size();   // persistent grid (blocks) for the point kernels
+int points_grid_size(int blocks_per_sm);   // persistent grid (blocks) for the point kernels
 
 }  // namespace gw

@@ -1,7 +1,8 @@
 // gw_points_fp64.cu -- the fused point loop, every operation in FP64.
 //
-// One warp per work item (a contiguous run of at most CHUNK_MAX grid points of
-// one event); lane l takes points k0 + l, k0 + l + 32, ...  For each point it
+// One group of GROUP lanes per work item (a contiguous run of at most CHUNK_MAX
+// grid points of one event); lane l of the group takes points k0 + l,
+// k0 + l + GROUP, ...  For each point it
 // forms the TaylorF2 phase derivatives, tau*(f) and its derivatives (Sec. 2.2),
 // the pattern functions and Doppler phase at the Earth angle of t(f)
 // (Sec. 3.1), the tangents g_i = dQ/dtheta_i + i Q dPhi/dtheta_i of every
@@ -10,7 +11,7 @@
 // (Sec. 3.2, Eqs. 3.1-3.3, trapezoid weights w_k on the log grid).  The strain
 // phase Phi itself is never formed: with h = Q e^{i Phi} the factor e^{i Phi}
 // cancels in |h|^2 and in Re(d_i h^* d_j h), so only its derivatives enter.
-// Tangents never leave registers; each warp writes one row of partial sums.
+// Tangents never leave registers; each group writes one row of partial sums.
 #include <cmath>
 
 #include "gw_kernels.cuh"
@@ -152,19 +153,28 @@ template <int MODE, int NP, bool ROT>
 __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
 {
     constexpr int NACC = NAccOf<MODE, NP>::value;
+    constexpr int RS = GROUP + 1;
     extern __shared__ double red_smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    double *red = red_smem + wib * (NACC * 33);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int gid = lane / GROUP, gl = lane % GROUP;
+    const unsigned gmask = ((1u << GROUP) - 1u) << (gid * GROUP);
+    double *red = red_smem + (wib * GROUPS_PER_WARP + gid) * (NACC * RS);
+    // per-group copy of the item's event constants (read every point from
+    // shared memory instead of being held in registers across the loop)
+    double *cs = red_smem + 4 * GROUPS_PER_WARP * NACC * RS + (wib * GROUPS_PER_WARP + gid) * EVC;
+    const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GROUPS_PER_WARP;
     const DevNet &net = A.net;
 
-    for (int64_t it = blockIdx.x * (int64_t)(blockDim.x >> 5) + wib; it < A.n_items;
-         it += nwarps) {
+    for (int64_t it = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GROUPS_PER_WARP + gid;
+         it < A.n_items; it += ngroups) {
         const int64_t e = find_event(A.item_off, A.n_ev, it);
         const int64_t j = it - A.item_off[e];
         const int64_t nj = A.item_off[e + 1] - A.item_off[e];
-        const double *E = A.evc + e * (int64_t)EVC;
+        const double *Eg = A.evc + e * (int64_t)EVC;
+        for (int q = gl; q < EVC; q += GROUP) cs[q] = Eg[q];
+        __syncwarp(gmask);
+        const double *E = cs;
         const int N = (int)E[EV_NPTS];
         const int kb = (int)((int64_t)N * j / nj), ke = (int)((int64_t)N * (j + 1) / nj);
 
@@ -181,22 +191,23 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
             skip = !isfinite(Cv[0]);
         }
 
-        int k = kb + lane;
+        int k = kb + gl;
         if (k < ke && !skip) {
             const double lnr = E[EV_LNR];
             const double lnf = fma((double)k, lnr, E[EV_LNF0]);
             double lnv = (lnf + E[EV_LNPIM]) * (1.0 / 3.0);
             double v = exp(lnv), vinv = exp(-lnv);
             double Aamp = E[EV_A0] * exp(-7.0 / 6.0 * lnf);
-            const double rho = E[EV_RHO32], rhoi = E[EV_RHOI32], dlnv = E[EV_LNRHO32];
-            const double rA = E[EV_RA32];
+            const double rho = E[EV_RHOG], rhoi = E[EV_RHOIG], dlnv = E[EV_LNRHOG];
+            const double rA = E[EV_RAG];
             const double inv_pim = E[EV_INV_PIM], pim = E[EV_PIM];
             const double wc0 = E[EV_WC0], wcm = E[EV_WCM], wcn = E[EV_WCN];
             const double cp = E[EV_CP], cx = E[EV_CX], dcp = E[EV_DCP], dcx = E[EV_DCX];
             const double c2p = E[EV_C2PSI], s2p = E[EV_S2PSI];
             const double aMc = E[EV_AMC], invdL = E[EV_INVDL];
 
-            for (; k < ke; k += 32) {
+#pragma unroll 1
+            for (; k < ke; k += GROUP) {
                 // ---- grid point, weight, basis
                 const double vi2 = vinv * vinv, vi3 = vi2 * vinv, vi5 = vi3 * vi2;
                 const double v2 = v * v, v5 = v2 * v2 * v, v7 = v5 * v2, vl = v * lnv;
@@ -215,6 +226,7 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
                 dMc = fma(PM[2], vi2, dMc);
                 dMc = fma(PM[1], vi3, dMc);
                 dMc = fma(PM[0], vi5, dMc);
+                asm volatile("" ::: "memory");   // keep coefficient loads local (register pressure)
                 double dEt = PE[8] * v7;
                 dEt = fma(PE[7], v5, dEt);
                 dEt = fma(PE[10], vl, dEt);
@@ -226,6 +238,7 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
                 dEt = fma(PE[2], vi2, dEt);
                 dEt = fma(PE[1], vi3, dEt);
                 dEt = fma(PE[0], vi5, dEt);
+                asm volatile("" ::: "memory");
                 double d9 = 0.0, d10 = 0.0;
                 if (NP == 11) {
                     const double *P9 = E + EV_P9, *P10 = E + EV_P10;
@@ -247,8 +260,10 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
                     tau = s0 * vi3;
                     tMc = s1 * vi3;
                     tEt = s2 * vi3;
+                    asm volatile("" ::: "memory");
                 }
-                // ---- noise weights per PSD: W = 4 w / S_n(f)
+                // ---- amplitude times sqrt of the noise weight per PSD:
+                //      sigma = A sqrt(W), W = 4 w / S_n(f); tangents are scaled by it
                 double Wp[MAX_PSD];
 #pragma unroll
                 for (int p = 0; p < MAX_PSD; p++) {
@@ -260,15 +275,14 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
                             const int pw = net.psd_pow[p][q];
                             S = fma(net.psd_coef[p][q], pw >= 0 ? ipow(x, pw) : ipow(xi, -pw), S);
                         }
-                        Wp[p] = 4.0 * w * rcp64(S);
+                        Wp[p] = Aamp * sqrt(4.0 * w * rcp64(S));
                     } else {
                         Wp[p] = 0.0;
                     }
                 }
-                const double Acp = Aamp * cp, Acx = Aamp * cx, Adcp = Aamp * dcp,
-                             Adcx = Aamp * dcx;
 
                 // ---- sites
+#pragma unroll 1
                 for (int s = 0; s < net.n_site; s++) {
                     const double *S = A.sitec + (e * net.n_site + s) * (int64_t)SC_N;
                     const double x = ROT ? fma(OMEGA_E, tau, S[SC_X0]) : S[SC_X0];
@@ -310,46 +324,40 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
                     if (MODE == MODE_SNRGRAD) {
                         ph.Mc = ph.eta = ph.th = ph.ph = ph.tc = ph.p9 = ph.p10 = 0.0;
                     }
+#pragma unroll 1
                     for (int q = net.site_ifo0[s]; q < net.site_ifo1[s]; q++) {
                         const double amp = net.ifo_amp[q];
                         const Pat pt = patterns(net.ifo_s2g[q], net.ifo_c2g[q], amp * c2p,
                                                 amp * s2p, J);
-                        const double W = Wp[net.ifo_psd[q]];
+                        const double sg = Wp[net.ifo_psd[q]];
                         double gr[NP], gi[NP], qr, qi;
-                        tangents<NP, ROT>(pt, Acp, Acx, Adcp, Adcx, aMc, invdL, ph, gr, gi, qr,
-                                          qi);
+                        tangents<NP, ROT>(pt, sg * cp, sg * cx, sg * dcp, sg * dcx, aMc, invdL, ph,
+                                          gr, gi, qr, qi);
                         const double q2 = fma(qr, qr, qi * qi);
                         if (MODE == MODE_FISHER) {
-                            acc[0] = fma(W, q2, acc[0]);
-                            double wr[NP], wi[NP];
-#pragma unroll
-                            for (int i = 0; i < NP; i++) {
-                                wr[i] = W * gr[i];
-                                wi[i] = W * gi[i];
-                            }
+                            acc[0] += q2;
                             int a = 1;
 #pragma unroll
                             for (int i = 0; i < NP; i++)
 #pragma unroll
                                 for (int jj = i; jj < NP; jj++) {
-                                    acc[a] = fma(wr[i], gr[jj], fma(wi[i], gi[jj], acc[a]));
+                                    acc[a] = fma(gr[i], gr[jj], fma(gi[i], gi[jj], acc[a]));
                                     a++;
                                 }
                         } else if (MODE == MODE_SNR) {
-                            acc[0] = fma(W, q2, acc[0]);
+                            acc[0] += q2;
                             const int dd = net.ifo_det[q];
 #pragma unroll
                             for (int d = 0; d < MAX_DET; d++)
-                                if (d == dd) acc[1 + d] = fma(W, q2, acc[1 + d]);
+                                if (d == dd) acc[1 + d] += q2;
                         } else if (MODE == MODE_SNRGRAD) {
                             // Re(Q^* g_i) = Re(Q^* dQ/dtheta_i): the phase part i Q dPhi
                             // contributes exactly zero, so it is left out (it would only
                             // add rounding), and Phic / slots 9, 10 stay exactly 0.
-                            acc[0] = fma(W, q2, acc[0]);
-                            const double wqr = W * qr, wqi = W * qi;
+                            acc[0] += q2;
 #pragma unroll
                             for (int i = 0; i < 8; i++)
-                                acc[1 + i] = fma(wqr, gr[i], fma(wqi, gi[i], acc[1 + i]));
+                                acc[1 + i] = fma(qr, gr[i], fma(qi, gi[i], acc[1 + i]));
                         } else {   // MODE_LOGDET
                             // y = C g
                             double yr[NP], yi[NP];
@@ -371,37 +379,37 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
                             const Pat pd = patterns(2.0 * net.ifo_c2g[q], -2.0 * net.ifo_s2g[q],
                                                     amp * c2p, amp * s2p, J);
                             double hr[NP], hi_[NP], dqr, dqi;
-                            tangents<NP, ROT>(pd, Acp, Acx, Adcp, Adcx, aMc, invdL, ph, hr, hi_,
-                                              dqr, dqi);
+                            tangents<NP, ROT>(pd, sg * cp, sg * cx, sg * dcp, sg * dcx, aMc, invdL,
+                                              ph, hr, hi_, dqr, dqi);
                             double t = 0.0;
 #pragma unroll
                             for (int i = 0; i < NP; i++) t = fma(hr[i], yr[i], fma(hi_[i], yi[i], t));
                             const int dd = net.ifo_det[q];
 #pragma unroll
                             for (int d = 0; d < MAX_DET; d++)
-                                if (d == dd) acc[d] = fma(2.0 * W, t, acc[d]);
+                                if (d == dd) acc[d] = fma(2.0, t, acc[d]);
                         }
                     }
                 }
-                // ---- advance to the lane's next point (k + 32)
+                // ---- advance to the lane's next point (k + GROUP)
                 v *= rho;
                 vinv *= rhoi;
                 lnv += dlnv;
                 Aamp *= rA;
             }
         }
-        // ---- warp reduction through shared memory, fixed order
+        // ---- group reduction through shared memory, fixed order
 #pragma unroll
-        for (int a = 0; a < NACC; a++) red[a * 33 + lane] = acc[a];
-        __syncwarp();
+        for (int a = 0; a < NACC; a++) red[a * RS + gl] = acc[a];
+        __syncwarp(gmask);
         double *out = A.partial + it * (int64_t)A.nacc;
-        for (int a = lane; a < A.nacc; a += 32) {
+        for (int a = gl; a < A.nacc; a += GROUP) {
             double s = 0.0;
-#pragma unroll 8
-            for (int l = 0; l < 32; l++) s += red[a * 33 + l];
+#pragma unroll
+            for (int l = 0; l < GROUP; l++) s += red[a * RS + l];
             out[a] = s;
         }
-        __syncwarp();
+        __syncwarp(gmask);
     }
 }
 
@@ -409,7 +417,8 @@ template <int MODE, int NP, bool ROT>
 cudaError_t launch_one(const PointArgs &a, cudaStream_t s)
 {
     constexpr int NACC = NAccOf<MODE, NP>::value;
-    const size_t smem = 4 * NACC * 33 * sizeof(double);
+    const size_t smem = ((size_t)4 * GROUPS_PER_WARP * NACC * (GROUP + 1) +
+                         (size_t)4 * GROUPS_PER_WARP * EVC) * sizeof(double);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t err = cudaFuncSetAttribute(k_points_fp64<MODE, NP, ROT>,
@@ -419,7 +428,7 @@ cudaError_t launch_one(const PointArgs &a, cudaStream_t s)
         attr_set = true;
     }
     if (a.n_items <= 0) return cudaSuccess;
-    k_points_fp64<MODE, NP, ROT><<<points_grid_size(), 128, smem, s>>>(a);
+    k_points_fp64<MODE, NP, ROT><<<points_grid_size(2), 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -432,16 +441,16 @@ cudaError_t launch_mode(int np, int rot, const PointArgs &a, cudaStream_t s)
 
 }  // namespace
 
-int points_grid_size()
+int points_grid_size(int blocks_per_sm)
 {
-    static int g = 0;
-    if (!g) {
-        int dev = 0, sms = 0;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        g = 2 * (sms > 0 ? sms : 148);
+        if (sms <= 0) sms = 148;
     }
-    return g;
+    return blocks_per_sm * sms;
 }
 
 cudaError_t launch_points_fp64(int mode, int np, int rot, const PointArgs &a, cudaStream_t s)

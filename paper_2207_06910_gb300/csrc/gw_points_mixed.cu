@@ -1,21 +1,25 @@
 // gw_points_mixed.cu -- the fused point loop in mixed precision.
 //
-// FP64: the log grid (v = (pi M f)^(1/3) and 1/v by recurrence, ln v), the
-//       TaylorF2 phase derivatives d Psi/d theta_i, tau*(f) and its
-//       derivatives, the Earth angle x = x0 + Omega_E tau* reduced to
-//       [-pi, pi], and f itself.
-// FP32: noise weight, amplitude, pattern functions, Doppler derivatives,
-//       tangents g_i, and the products Re(g_i^* g_j).
-// Sums: every product is split exactly (p = a b, e = fma(a, b, -p)) and added
-//       to a double-float accumulator (hi, lo) with an error-free two-sum
-//       (Knuth), so the accumulated Gamma_ij equals the exact sum of the FP32
-//       products to ~1e-13 relative.  The only FP32 rounding left is that of the
-//       tangents themselves, which perturbs Gamma like a slightly different
-//       set of tangent vectors (a Gram matrix of perturbed vectors), not
-//       element by element.
-// The tangents are pre-scaled by sigma = A sqrt(4 w / S_n), so the weight is
-// inside the products; a rounding of sigma is a common factor of all tangents
-// of a point, i.e. a perturbation of the noise weight.
+// GB300 runs FP32 at ~58x its FP64 rate (FFMA 117 vs DFMA 2 per clock and SM),
+// so this kernel keeps the FP64 pipe almost idle:
+//  * high precision without FP64: the log grid (v = (pi M f)^(1/3), 1/v, ln v
+//    by recurrence), the TaylorF2 phase derivatives d Psi/d theta_i, tau*(f)
+//    and its derivatives, and the Earth angle x = x0 + Omega_E tau* are
+//    evaluated in double-float arithmetic (value = hi + lo, two FP32 numbers,
+//    ~2^-48 relative; error-free transforms of Knuth (two-sum) and Dekker
+//    (product with an FMA)), then rounded once to FP32;
+//  * FP32: noise weight, amplitude, pattern functions, Doppler derivatives,
+//    tangents g_i and the products Re(g_i^* g_j);
+//  * sums: every product is split exactly (p = a b, e = fma(a, b, -p)) and
+//    added to a double-float accumulator with a two-sum, so Gamma_ij is the
+//    exact sum of the FP32 products to ~1e-13 relative.  The rounding left is
+//    that of each tangent once per point: it perturbs Gamma as a Gram matrix of
+//    slightly perturbed vectors, not element by element.
+// Tangents are pre-scaled by sigma = A sqrt(4 w / S_n), so the weight sits in
+// the products; a rounding of sigma is a common factor of a point's tangents,
+// i.e. a perturbation of the noise weight.
+// FP64 is used only once per lane and work item (start of the recurrences)
+// and in the final per-item sum.
 #include <cmath>
 
 #include "gw_kernels.cuh"
@@ -23,6 +27,71 @@
 namespace gw {
 
 namespace {
+
+// ---------------------------------------------------------------- double-float
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return DF{s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ DF fast_two_sum(float a, float b)   // |a| >= |b|
+{
+    const float s = a + b;
+    return DF{s, b - (s - a)};
+}
+
+__device__ __forceinline__ DF df_mul(DF x, DF y)
+{
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_add(DF x, DF y)
+{
+    DF s = two_sum(x.hi, y.hi);
+    s.lo += x.lo + y.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ DF df_of(float2 c) { return DF{c.x, c.y}; }
+
+__device__ __forceinline__ DF df_from_double(double x)
+{
+    const float hi = (float)x;
+    return DF{hi, (float)(x - (double)hi)};
+}
+
+__device__ __forceinline__ float df_round(DF x) { return x.hi + x.lo; }
+
+// sum_q c[q] b[q] in double-float
+template <int N>
+__device__ __forceinline__ DF df_dot(const float2 *c, const DF (&b)[N])
+{
+    DF s = df_mul(df_of(c[N - 1]), b[N - 1]);
+#pragma unroll
+    for (int q = N - 2; q >= 0; q--) s = df_add(s, df_mul(df_of(c[q]), b[q]));
+    return s;
+}
+
+// accumulate a + b (two FP32 products with their exact rounding errors) into
+// the pair (hi, *lo); hi lives in a register, the compensation in shared memory
+__device__ __forceinline__ void acc_add2(float &hi, float *lo, float a, float ea, float b,
+                                         float eb)
+{
+    const DF p = two_sum(a, b);
+    const DF t = two_sum(hi, p.hi);
+    hi = t.hi;
+    *lo += (ea + eb) + (p.lo + t.lo);
+}
 
 __device__ __forceinline__ int64_t find_event_m(const int64_t *off, int64_t n, int64_t it)
 {
@@ -46,29 +115,9 @@ __device__ __forceinline__ float ipowf(float x, int p)
     return r;
 }
 
-// double-float accumulator: value = hi + lo
-struct DF {
-    float hi, lo;
-};
-
-// add a + b (two FP32 products given with their exact rounding errors ea, eb)
-__device__ __forceinline__ void df_add2(DF &s, float a, float ea, float b, float eb)
-{
-    // p = a + b exactly as (p, ep)
-    const float p = a + b;
-    const float bb = p - a;
-    const float ep = (a - (p - bb)) + (b - bb);
-    // s.hi + p exactly as (t, et)
-    const float t = s.hi + p;
-    const float bq = t - s.hi;
-    const float et = (s.hi - (t - bq)) + (p - bq);
-    s.hi = t;
-    s.lo += (ea + eb) + (ep + et);
-}
-
 template <int MODE, int NP>
 struct NAccM {
-    static constexpr int value = MODE == MODE_FISHER ? 1 + NP * (NP + 1) / 2
+    static constexpr int value = MODE == MODE_FISHER ? 1 + NP * (NP + 1) / 2 + N_SNRGRAD_X
                                : MODE == MODE_SNRGRAD ? 1 + NP
                                : 1 + MAX_DET;
 };
@@ -100,13 +149,16 @@ struct PhaseF {
 template <int NP, bool ROT>
 __device__ __forceinline__ void tangents_f(const PatF &p, float Acp, float Acx, float Adcp,
                                            float Adcx, float aMc, float invdL, const PhaseF &ph,
-                                           float (&gr)[NP], float (&gi)[NP], float &qr, float &qi)
+                                           float (&gr)[NP], float (&gi)[NP], float &qr, float &qi,
+                                           float &xr, float &xi, float &tr, float &ti)
 {
     const float omega = (float)OMEGA_E;
     qr = Acp * p.fp;
     qi = Acx * p.fx;
-    const float xr = Acp * p.fpX, xi = Acx * p.fxX;
-    const float tr = Acp * p.fpT, ti = Acx * p.fxT;
+    xr = Acp * p.fpX;      // dQ/dx
+    xi = Acx * p.fxX;
+    tr = Acp * p.fpT;      // dQ/dtheta
+    ti = Acx * p.fxT;
     gr[0] = aMc * qr - qi * ph.Mc;
     gi[0] = aMc * qi + qr * ph.Mc;
     if (ROT) {
@@ -146,99 +198,105 @@ __device__ __forceinline__ void tangents_f(const PatF &p, float Acp, float Acx, 
 }
 
 template <int MODE, int NP, bool ROT>
-__global__ void __launch_bounds__(128) k_points_mixed(PointArgs A)
+__global__ void __launch_bounds__(128, 3) k_points_mixed(PointArgs A)
 {
     constexpr int NACC = NAccM<MODE, NP>::value;
-    extern __shared__ double red_smem[];
+    constexpr int NT = 128;         // threads per block
+    extern __shared__ float red_f[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    double *red = red_smem + wib * (NACC * 33);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int gid = lane / GROUP, gl = lane % GROUP;
+    const unsigned gmask = ((1u << GROUP) - 1u) << (gid * GROUP);
+    // compensation terms of the accumulators: lo[a * NT + thread]
+    float *lo = red_f;
+    float *mylo = lo + threadIdx.x;
+    // per-group copy of the item's event constants (read every point from
+    // shared memory instead of being held in registers across the loop)
+    float2 *cs = reinterpret_cast<float2 *>(red_f + NACC * NT) +
+                 (wib * GROUPS_PER_WARP + gid) * EVC;
+    const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GROUPS_PER_WARP;
     const DevNet &net = A.net;
+    const DF two_pi = DF{6.28318548f, -1.74845553e-7f};          // 2 pi = hi + lo
+    const DF omega_e = df_from_double(OMEGA_E);
 
-    for (int64_t it = blockIdx.x * (int64_t)(blockDim.x >> 5) + wib; it < A.n_items;
-         it += nwarps) {
+    for (int64_t it = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GROUPS_PER_WARP + gid;
+         it < A.n_items; it += ngroups) {
         const int64_t e = find_event_m(A.item_off, A.n_ev, it);
         const int64_t j = it - A.item_off[e];
         const int64_t nj = A.item_off[e + 1] - A.item_off[e];
         const double *E = A.evc + e * (int64_t)EVC;
+        const float2 *Eg = A.evc_f + e * (int64_t)EVC;
+        for (int q = gl; q < EVC; q += GROUP) cs[q] = Eg[q];
+        __syncwarp(gmask);
+        const float2 *Ef = cs;
         const int N = (int)E[EV_NPTS];
         const int kb = (int)((int64_t)N * j / nj), ke = (int)((int64_t)N * (j + 1) / nj);
 
-        DF acc[NACC];
+        float acc[NACC];
 #pragma unroll
-        for (int a = 0; a < NACC; a++) acc[a] = DF{0.0f, 0.0f};
+        for (int a = 0; a < NACC; a++) {
+            acc[a] = 0.0f;
+            mylo[a * NT] = 0.0f;
+        }
 
-        int k = kb + lane;
+        int k = kb + gl;
         if (k < ke) {
-            const double lnr = E[EV_LNR];
-            const double lnf = fma((double)k, lnr, E[EV_LNF0]);
-            double lnv = (lnf + E[EV_LNPIM]) * (1.0 / 3.0);
-            double v = exp(lnv), vinv = exp(-lnv);
-            float Aamp = (float)(E[EV_A0] * net.inv_sqrt_scale_ref * exp(-7.0 / 6.0 * lnf));
-            const double rho = E[EV_RHO32], rhoi = E[EV_RHOI32], dlnv = E[EV_LNRHO32];
-            const float rA = (float)E[EV_RA32];
-            const double inv_pim = E[EV_INV_PIM];
-            const float wc0 = (float)E[EV_WC0], wcm = (float)E[EV_WCM], wcn = (float)E[EV_WCN];
-            const float cp = (float)E[EV_CP], cx = (float)E[EV_CX];
-            const float dcp = (float)E[EV_DCP], dcx = (float)E[EV_DCX];
-            const float c2p = (float)E[EV_C2PSI], s2p = (float)E[EV_S2PSI];
-            const float aMc = (float)E[EV_AMC], invdL = (float)E[EV_INVDL];
+            // start of the lane's recurrences (FP64, once per lane and item)
+            const double lnf = fma((double)k, E[EV_LNR], E[EV_LNF0]);
+            const double lnv_d = (lnf + E[EV_LNPIM]) * (1.0 / 3.0);
+            DF v = df_from_double(exp(lnv_d));
+            DF vinv = df_from_double(exp(-lnv_d));
+            DF lnv = df_from_double(lnv_d);
+            float Aamp = (float)(E[EV_A0] * net.inv_sqrt_scale_ref) *
+                         expf((float)(-7.0 / 6.0 * lnf));
+            const DF rho = df_of(Ef[EV_RHOG]), rhoi = df_of(Ef[EV_RHOIG]);
+            const DF dlnv = df_of(Ef[EV_LNRHOG]);
+            const DF inv_pim = df_of(Ef[EV_INV_PIM]);
+            const float rA = Ef[EV_RAG].x;
+            const float wc0 = Ef[EV_WC0].x, wcm = Ef[EV_WCM].x, wcn = Ef[EV_WCN].x;
+            const float cp = Ef[EV_CP].x, cx = Ef[EV_CX].x;
+            const float dcp = Ef[EV_DCP].x, dcx = Ef[EV_DCX].x;
+            const float c2p = Ef[EV_C2PSI].x, s2p = Ef[EV_S2PSI].x;
+            const float aMc = Ef[EV_AMC].x, invdL = Ef[EV_INVDL].x;
 
-            for (; k < ke; k += 32) {
-                // ---------------- FP64 part
-                const double vi2 = vinv * vinv, vi3 = vi2 * vinv, vi5 = vi3 * vi2;
-                const double v2 = v * v, v5 = v2 * v2 * v, v7 = v5 * v2, vl = v * lnv;
-                const double f = v2 * v * inv_pim;
-                const double *PM = E + EV_PM, *PE = E + EV_PE;
-                double dMc = PM[8] * v7;
-                dMc = fma(PM[7], v5, dMc);
-                dMc = fma(PM[10], vl, dMc);
-                dMc = fma(PM[6], v2, dMc);
-                dMc = fma(PM[5], v, dMc);
-                dMc = PM[4] + dMc;
-                dMc = fma(PM[3], vinv, dMc);
-                dMc = fma(PM[2], vi2, dMc);
-                dMc = fma(PM[1], vi3, dMc);
-                dMc = fma(PM[0], vi5, dMc);
-                double dEt = PE[8] * v7;
-                dEt = fma(PE[7], v5, dEt);
-                dEt = fma(PE[10], vl, dEt);
-                dEt = fma(PE[9], lnv, dEt);
-                dEt = fma(PE[6], v2, dEt);
-                dEt = fma(PE[5], v, dEt);
-                dEt = PE[4] + dEt;
-                dEt = fma(PE[3], vinv, dEt);
-                dEt = fma(PE[2], vi2, dEt);
-                dEt = fma(PE[1], vi3, dEt);
-                dEt = fma(PE[0], vi5, dEt);
+#pragma unroll 1
+            for (; k < ke; k += GROUP) {
+                // ---------------- double-float part
+                const DF vi2 = df_mul(vinv, vinv), vi3 = df_mul(vi2, vinv);
+                const DF vi5 = df_mul(vi3, vi2);
+                const DF v2 = df_mul(v, v), v3 = df_mul(v2, v), v5 = df_mul(v3, v2);
+                const DF v7 = df_mul(v5, v2), vl = df_mul(v, lnv);
+                const DF one = DF{1.0f, 0.0f};
+                const DF b11[11] = {vi5, vi3, vi2, vinv, one, v, v2, v5, v7, lnv, vl};
+                // (the empty asm statements keep the compiler from loading every
+                // coefficient of every polynomial at once, which spills registers)
+                const float dMcf = df_round(df_dot<11>(Ef + EV_PM, b11));
+                asm volatile("" ::: "memory");
+                const float dEtf = df_round(df_dot<11>(Ef + EV_PE, b11));
+                asm volatile("" ::: "memory");
                 float d9 = 0.0f, d10 = 0.0f;
                 if (NP == 11) {
-                    const double *P9 = E + EV_P9, *P10 = E + EV_P10;
-                    d9 = (float)fma(P9[0], vi2, fma(P9[1], vinv, fma(P9[2], v5, P9[3] * v7)));
-                    d10 = (float)fma(P10[0], vi2, fma(P10[1], vinv, fma(P10[2], v5, P10[3] * v7)));
+                    const DF b4[4] = {vi2, vinv, v5, v7};
+                    d9 = df_round(df_dot<4>(Ef + EV_P9, b4));
+                    d10 = df_round(df_dot<4>(Ef + EV_P10, b4));
+                    asm volatile("" ::: "memory");
                 }
-                double tau = 0.0;
+                DF tau = DF{0.0f, 0.0f};
                 float tMc = 0.0f, tEt = 0.0f;
                 if (ROT) {
-                    const double *T0 = E + EV_T0, *TM = E + EV_TM, *TE = E + EV_TE;
-                    const double b[8] = {vi5, vi3, vi2, vinv, 1.0, v, v2, vl};
-                    double s0 = T0[7] * b[7], s1 = TM[7] * b[7], s2 = TE[7] * b[7];
-#pragma unroll
-                    for (int q = 6; q >= 0; q--) {
-                        s0 = fma(T0[q], b[q], s0);
-                        s1 = fma(TM[q], b[q], s1);
-                        s2 = fma(TE[q], b[q], s2);
-                    }
-                    tau = s0 * vi3;
-                    tMc = (float)(OMEGA_E * s1 * vi3);
-                    tEt = (float)(OMEGA_E * s2 * vi3);
+                    const DF b8[8] = {vi5, vi3, vi2, vinv, one, v, v2, vl};
+                    tau = df_mul(df_dot<8>(Ef + EV_T0, b8), vi3);
+                    asm volatile("" ::: "memory");
+                    tMc = (float)OMEGA_E * df_round(df_mul(df_dot<8>(Ef + EV_TM, b8), vi3));
+                    asm volatile("" ::: "memory");
+                    tEt = (float)OMEGA_E * df_round(df_mul(df_dot<8>(Ef + EV_TE, b8), vi3));
+                    asm volatile("" ::: "memory");
                 }
-                const float ff = (float)f;
-                const float twopif = (float)(TWO_PI * f);
-                const float dMcf = (float)dMc, dEtf = (float)dEt;
+                const DF fdf = df_mul(v3, inv_pim);
+                const float ff = df_round(fdf);
+                const float twopif = (float)TWO_PI * ff;
 
-                // ---------------- FP32 part: weights and amplitude per PSD
+                // ---------------- FP32: noise weight and amplitude per PSD
                 const float w = ff * (k == 0 ? wc0 : (k == N - 1 ? wcn : wcm));
                 float sig[MAX_PSD];
 #pragma unroll
@@ -257,14 +315,16 @@ __global__ void __launch_bounds__(128) k_points_mixed(PointArgs A)
                     }
                 }
 
+#pragma unroll 1
                 for (int s = 0; s < net.n_site; s++) {
                     const float *S = A.sitec_f + (e * net.n_site + s) * (int64_t)SC_N;
                     float xs;
                     if (ROT) {
-                        double x = A.sitec[(e * net.n_site + s) * (int64_t)SC_N + SC_X0] +
-                                   OMEGA_E * tau;
-                        x -= TWO_PI * rint(x * (1.0 / TWO_PI));
-                        xs = (float)x;
+                        // x = x0 + Omega_E tau* in double-float, reduced to about [-pi, pi]
+                        DF x = df_add(DF{S[SC_X0], S[SC_X0LO]}, df_mul(omega_e, tau));
+                        const float kq = rintf(x.hi * 0.159154943f);
+                        x = df_add(x, df_mul(two_pi, DF{-kq, 0.0f}));
+                        xs = df_round(x);
                     } else {
                         xs = S[SC_X0];
                     }
@@ -301,68 +361,94 @@ __global__ void __launch_bounds__(128) k_points_mixed(PointArgs A)
                         ph.tc = fmaf(-(float)OMEGA_E, dxPD, twopif);
                     }
                     if (MODE == MODE_SNRGRAD) {
+                        // Re(Q^* i Q dPhi) = 0: phase parts left out of the SNR gradient
                         ph.Mc = ph.eta = ph.th = ph.ph = ph.tc = ph.p9 = ph.p10 = 0.0f;
                     }
+#pragma unroll 1
                     for (int q = net.site_ifo0[s]; q < net.site_ifo1[s]; q++) {
                         const float amp = (float)net.ifo_amp[q];
                         const PatF pt = patterns_f((float)net.ifo_s2g[q], (float)net.ifo_c2g[q],
                                                    amp * c2p, amp * s2p, J);
                         const float sg = sig[net.ifo_psd[q]];
-                        float gr[NP], gi[NP], qr, qi;
+                        float gr[NP], gi[NP], qr, qi, xr, xi, tr, ti;
                         tangents_f<NP, ROT>(pt, sg * cp, sg * cx, sg * dcp, sg * dcx, aMc, invdL,
-                                            ph, gr, gi, qr, qi);
+                                            ph, gr, gi, qr, qi, xr, xi, tr, ti);
                         {
                             const float p1 = qr * qr, p2 = qi * qi;
-                            df_add2(acc[0], p1, fmaf(qr, qr, -p1), p2, fmaf(qi, qi, -p2));
+                            acc_add2(acc[0], mylo, p1, fmaf(qr, qr, -p1), p2, fmaf(qi, qi, -p2));
                         }
                         if (MODE == MODE_FISHER) {
                             int a = 1;
 #pragma unroll
-                            for (int i = 0; i < NP; i++)
+                            for (int i = 0; i < NP; i++) {
 #pragma unroll
                                 for (int jj = i; jj < NP; jj++) {
                                     const float p1 = gr[i] * gr[jj], p2 = gi[i] * gi[jj];
-                                    df_add2(acc[a], p1, fmaf(gr[i], gr[jj], -p1), p2,
-                                            fmaf(gi[i], gi[jj], -p2));
+                                    acc_add2(acc[a], mylo + a * NT, p1, fmaf(gr[i], gr[jj], -p1),
+                                             p2, fmaf(gi[i], gi[jj], -p2));
                                     a++;
                                 }
+                                if (i & 1) asm volatile("" ::: "memory");
+                            }
+                            // phase-free SNR-gradient sums (see N_SNRGRAD_X)
+                            constexpr int X0 = 1 + NP * (NP + 1) / 2;
+                            const float rx[N_SNRGRAD_X][4] = {
+                                {qr, xr, qi, xi},
+                                {ph.tMc * qr, xr, ph.tMc * qi, xi},
+                                {ph.teta * qr, xr, ph.teta * qi, xi},
+                                {qr, tr, qi, ti},
+                                {qr, gr[5], qi, gi[5]},
+                                {qr, gr[6], qi, gi[6]}};
+#pragma unroll
+                            for (int m = 0; m < N_SNRGRAD_X; m++) {
+                                const float p1 = rx[m][0] * rx[m][1], p2 = rx[m][2] * rx[m][3];
+                                acc_add2(acc[X0 + m], mylo + (X0 + m) * NT, p1,
+                                         fmaf(rx[m][0], rx[m][1], -p1), p2,
+                                         fmaf(rx[m][2], rx[m][3], -p2));
+                            }
                         } else if (MODE == MODE_SNR) {
                             const int dd = net.ifo_det[q];
                             const float p1 = qr * qr, p2 = qi * qi;
 #pragma unroll
                             for (int d = 0; d < MAX_DET; d++)
                                 if (d == dd)
-                                    df_add2(acc[1 + d], p1, fmaf(qr, qr, -p1), p2,
-                                            fmaf(qi, qi, -p2));
-                        } else {   // MODE_SNRGRAD: phase parts left out (see FP64 kernel)
+                                    acc_add2(acc[1 + d], mylo + (1 + d) * NT, p1,
+                                             fmaf(qr, qr, -p1), p2, fmaf(qi, qi, -p2));
+                        } else {   // MODE_SNRGRAD
 #pragma unroll
                             for (int i = 0; i < 8; i++) {
                                 const float p1 = qr * gr[i], p2 = qi * gi[i];
-                                df_add2(acc[1 + i], p1, fmaf(qr, gr[i], -p1), p2,
-                                        fmaf(qi, gi[i], -p2));
+                                acc_add2(acc[1 + i], mylo + (1 + i) * NT, p1, fmaf(qr, gr[i], -p1),
+                                         p2, fmaf(qi, gi[i], -p2));
                             }
                         }
                     }
                 }
-                v *= rho;
-                vinv *= rhoi;
-                lnv += dlnv;
+                v = df_mul(v, rho);
+                vinv = df_mul(vinv, rhoi);
+                lnv = df_add(lnv, dlnv);
                 Aamp *= rA;
             }
         }
-        // warp reduction in FP64 (hi + lo of every lane, fixed order); the PSD
-        // reference scale cancels between sigma^2 and 1/S_n
-#pragma unroll
-        for (int a = 0; a < NACC; a++) red[a * 33 + lane] = (double)acc[a].hi + (double)acc[a].lo;
-        __syncwarp();
+        // ---- group reduction: butterfly over the GROUP lanes in double-float
+        // (error-free two-sum of the high parts, compensations added), then
+        // every lane writes the accumulators a = gl (mod GROUP) in FP64
         double *out = A.partial + it * (int64_t)A.nacc;
-        for (int a = lane; a < A.nacc; a += 32) {
-            double s = 0.0;
-#pragma unroll 8
-            for (int l = 0; l < 32; l++) s += red[a * 33 + l];
-            out[a] = s;
+#pragma unroll
+        for (int a = 0; a < NACC; a++) {
+            DF s = DF{acc[a], mylo[a * NT]};
+#pragma unroll
+            for (int o = 1; o < GROUP; o <<= 1) {
+                const float oh = __shfl_xor_sync(gmask, s.hi, o);
+                const float ol = __shfl_xor_sync(gmask, s.lo, o);
+                // identical operands on both lanes of a pair: same result on both
+                const DF t = (gl & o) ? two_sum(oh, s.hi) : two_sum(s.hi, oh);
+                s.hi = t.hi;
+                s.lo = ((gl & o) ? (ol + s.lo) : (s.lo + ol)) + t.lo;
+            }
+            if ((a % GROUP) == gl && a < A.nacc) out[a] = (double)s.hi + (double)s.lo;
         }
-        __syncwarp();
+        __syncwarp(gmask);
     }
 }
 
@@ -370,7 +456,7 @@ template <int MODE, int NP, bool ROT>
 cudaError_t launch_one_m(const PointArgs &a, cudaStream_t s)
 {
     constexpr int NACC = NAccM<MODE, NP>::value;
-    const size_t smem = 4 * NACC * 33 * sizeof(double);
+    const size_t smem = ((size_t)NACC * 128 + (size_t)4 * GROUPS_PER_WARP * EVC * 2) * sizeof(float);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t err = cudaFuncSetAttribute(k_points_mixed<MODE, NP, ROT>,
@@ -380,7 +466,7 @@ cudaError_t launch_one_m(const PointArgs &a, cudaStream_t s)
         attr_set = true;
     }
     if (a.n_items <= 0) return cudaSuccess;
-    k_points_mixed<MODE, NP, ROT><<<points_grid_size(), 128, smem, s>>>(a);
+    k_points_mixed<MODE, NP, ROT><<<points_grid_size(3), 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ __global__ void k_prepare(int64_t n, const double *m1, const double *m2, const d
     b *= 1.0 + z;
     double M = a + b;
     double et = a * b / (M * M);
-    double d = sqrt(fmax(0.0, 1.0 - 4.0 * et));
+    double d = (a - b) / M;   // = sqrt(1 - 4 eta) for m1 >= m2, without the cancellation
     double sL = la + lb, dLam = la - lb;
     double lt = 8.0 / 13.0 * ((1.0 + 7.0 * et - 31.0 * et * et) * sL
                               + d * (1.0 + 9.0 * et - 11.0 * et * et) * dLam);
@@ -91,7 +91,7 @@ cudaError_t launch_prepare(int64_t n, const double *m1, const double *m2, const 
 // point's basis values.  At fixed f:  Mc d/dMc = (1/3) v d/dv  and
 // d/deta|Mc = d/deta|v - (1/(5 eta)) v d/dv  (v = (pi M f)^(1/3), M = Mc eta^-3/5).
 __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec,
-                              float *sitec_f, int32_t *status, int64_t *counts)
+                              float *sitec_f, float2 *evc_f, int32_t *status, int64_t *counts)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= cat.n) return;
@@ -132,11 +132,11 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
     E[EV_LNPIM] = log(pim);
     E[EV_INV_PIM] = 1.0 / pim;
     E[EV_PIM] = pim;
-    E[EV_RHO32] = exp(32.0 * lnr / 3.0);
-    E[EV_RHOI32] = exp(-32.0 * lnr / 3.0);
-    E[EV_LNRHO32] = 32.0 * lnr / 3.0;
+    E[EV_RHOG] = exp(GROUP * lnr / 3.0);
+    E[EV_RHOIG] = exp(-GROUP * lnr / 3.0);
+    E[EV_LNRHOG] = GROUP * lnr / 3.0;
     E[EV_A0] = sqrt(5.0 / 24.0) * pow(PI, -2.0 / 3.0) * pow(Mcs, 5.0 / 6.0) / (dL * GPC_S);
-    E[EV_RA32] = exp(-7.0 / 6.0 * 32.0 * lnr);
+    E[EV_RAG] = exp(-7.0 / 6.0 * GROUP * lnr);
     double si, ci, s2p, c2p;
     sincos(io, &si, &ci);
     sincos(2.0 * ps, &s2p, &c2p);
@@ -239,6 +239,15 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
         E[EV_TE + k] = Kt * (Te[k] - Tv[k] / (5.0 * eta));
     }
 
+    // double-float (hi, lo) copy of every constant for the mixed path
+    if (evc_f) {
+        float2 *Ef = evc_f + e * (int64_t)EVC;
+        for (int q = 0; q < EVC; q++) {
+            const float hi = (float)E[q];
+            Ef[q] = make_float2(hi, (float)(E[q] - (double)hi));
+        }
+    }
+
     // ---- per-site JKS coefficients (pattern functions as functions of the
     // hour-angle-like x = phi - lon - g) and Doppler factors.
     double sth, cth;
@@ -275,21 +284,24 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
         S[SC_D2] = R_EARTH_S * sl * cth;
         S[SC_D1T] = R_EARTH_S * cl * cth;
         S[SC_D2T] = -R_EARTH_S * sl * sth;
+        S[SC_X0LO] = 0.0;
         if (sitec_f) {
             float *Sf = sitec_f + (e * net.n_site + s) * (int64_t)SC_N;
             for (int q = 0; q < SC_N; q++) Sf[q] = (float)S[q];
+            Sf[SC_X0LO] = (float)(x0 - (double)(float)x0);
         }
     }
 }
 
 cudaError_t launch_event_setup(const DevCat &cat, const DevNet &net, int np, double *evc,
-                               double *sitec, float *sitec_f, int32_t *status, int64_t *counts,
-                               cudaStream_t s)
+                               double *sitec, float *sitec_f, float2 *evc_f, int32_t *status,
+                               int64_t *counts, cudaStream_t s)
 {
     if (cat.n <= 0) return cudaSuccess;
     int bs = 128;
     int64_t nb = (cat.n + bs - 1) / bs;
-    k_event_setup<<<(unsigned)nb, bs, 0, s>>>(cat, net, np, evc, sitec, sitec_f, status, counts);
+    k_event_setup<<<(unsigned)nb, bs, 0, s>>>(cat, net, np, evc, sitec, sitec_f, evc_f, status,
+                                              counts);
     return cudaGetLastError();
 }
 
@@ -380,7 +392,7 @@ cudaError_t launch_scan(const int64_t *counts, int64_t n, int64_t *off, int64_t 
 __global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc,
                          const int64_t *item_off, const double *partial, const int32_t *status,
                          double *snr, double *snr_det, double *fisher, const double *grad_snr,
-                         double *grad_params)
+                         double *grad_params, double *xsums)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t e = t / nacc;
@@ -391,10 +403,13 @@ __global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc,
     double s = 0.0;
     for (int64_t it = i0; it < i1; it++) s += partial[it * nacc + a];
     if (mode == MODE_FISHER) {
+        const int npair = np * (np + 1) / 2;
         if (a == 0) {
             if (snr) snr[e] = bad ? NAN : sqrt(s);
-        } else {
+        } else if (a <= npair) {
             fisher[(int64_t)(a - 1) * n + e] = bad ? NAN : s;
+        } else if (xsums) {
+            xsums[(int64_t)(a - 1 - npair) * n + e] = bad ? NAN : s;
         }
     } else if (mode == MODE_SNR) {
         if (a == 0) snr[e] = bad ? NAN : sqrt(s);
@@ -425,9 +440,61 @@ __global__ void k_finish_total(int64_t n_items, int nacc, const double *partial,
     if (threadIdx.x == 0) out[a] = sh[0];
 }
 
+// SNR vector-Jacobian product after a Fisher pass, one thread per event.
+//  FP64 path: d SNR/d theta_i = -dL Gamma_{i,dL} / SNR, because d h/d dL = -h/dL
+//             makes Re(h^* d_i h) = -dL Re(d_dL h^* d_i h) (Sec. 3.2 definitions).
+//  mixed path: phase-free sums (the phase part of Re(h^* d_i h) is zero):
+//             Mc: 5/(6 Mc) SNR^2 + X1, eta: X2, dL: -SNR^2/dL, theta: X3, phi: X0,
+//             iota: X4, psi: X5, tc: -Omega_E X0, Phic and slots 9, 10: 0.
+__global__ void k_snr_grad(int64_t n, int np, int mixed, int rot, const double *F,
+                           const double *snr, const double *X, const double *Mc, const double *dL,
+                           const int32_t *status, const double *grad_snr, double *grad)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const bool bad = status[e] != 0;
+    const double s = snr[e], up = grad_snr[e], d = dL[e];
+    for (int i = 0; i < np; i++) {
+        double g;
+        if (!mixed) {
+            const int lo = i < 2 ? i : 2, hi = i < 2 ? 2 : i;
+            const int k = lo * np - lo * (lo - 1) / 2 + (hi - lo);
+            g = -d * F[(int64_t)k * n + e] / s;
+        } else {
+            const double s2 = s * s;
+            switch (i) {
+            case 0: g = (5.0 / (6.0 * Mc[e]) * s2 + X[1 * n + e]) / s; break;
+            case 1: g = X[2 * n + e] / s; break;
+            case 2: g = -s2 / (d * s); break;
+            case 3: g = X[3 * n + e] / s; break;
+            case 4: g = X[0 * n + e] / s; break;
+            case 5: g = X[4 * n + e] / s; break;
+            case 6: g = X[5 * n + e] / s; break;
+            case 7: g = rot ? -OMEGA_E * X[0 * n + e] / s : 0.0; break;   // tc moves x only with rotation
+            default: g = 0.0;
+            }
+        }
+        grad[(int64_t)i * n + e] = bad ? NAN : up * g;
+    }
+}
+
+cudaError_t launch_snr_grad_from_fisher(int64_t n, int np, bool mixed, int rot,
+                                        const double *fisher, const double *snr,
+                                        const double *xsums, const double *Mc, const double *dL,
+                                        const int32_t *status, const double *grad_snr,
+                                        double *grad_params, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int bs = 256;
+    k_snr_grad<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(n, np, mixed ? 1 : 0, rot, fisher, snr,
+                                                            xsums, Mc, dL, status, grad_snr,
+                                                            grad_params);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const int32_t *status,
                           double *snr, double *snr_det, double *fisher, const double *grad_snr,
-                          double *grad_params, double *grad_gamma, cudaStream_t s)
+                          double *grad_params, double *grad_gamma, double *xsums, cudaStream_t s)
 {
     if (mode == MODE_LOGDET) {
         k_finish_total<<<a.nacc, 256, 0, s>>>(a.n_items, a.nacc, a.partial, grad_gamma);
@@ -439,7 +506,7 @@ cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const
     k_finish<<<(unsigned)((tot + bs - 1) / bs), bs, 0, s>>>(mode, np, n_det, a.n_ev, a.nacc,
                                                            a.item_off, a.partial, status, snr,
                                                            snr_det, fisher, grad_snr,
-                                                           grad_params);
+                                                           grad_params, xsums);
     return cudaGetLastError();
 }
 

@@ -179,6 +179,10 @@ def test_snr_vjp(name, prec):
     rtol = 1e-7 if prec == 0 else 2e-5
     tol = rtol * (np.abs(want) + np.abs(up.cpu().numpy())[:, None] * s_or[:, None] / scale * 1e-3)
     assert np.all(np.abs(g - want) <= tol), np.max(np.abs(g - want) / tol)
+    # the same VJP fused into the Fisher pass
+    F, snr, st, gf = gw.gw_fisher(gcat, net, P, prec, grad_snr=up)
+    gf = gf.cpu().numpy().T
+    assert np.all(np.abs(gf - want) <= tol), np.max(np.abs(gf - want) / tol)
 
 
 def test_snr_autograd_matches_vjp():
@@ -201,12 +205,19 @@ def test_logdet_vjp_detangles():
     cat, d, p = oracle_catalog("c4", 2, max_npts=100)
     det, psd, rot = gwcat.network("c4")
     g_or, ld_or = oracle_pool.logdet_grad(cat, det, psd, rot, 11, [0, 1, 2])
+    F_or, _, _, _ = oracle_pool.fisher(cat, det, psd, rot, 11)
+    kappa = oracle.invert(F_or)[1].max()
     gcat = _gpu_cat(cat)
     net = gw.Network(det, psd, rot)
     F, snr, st = gw.gw_fisher(gcat, net, 11, gw.GW_FP64)
     C, cond, err, sti = gw.gw_fisher_inverse(F, 11)
     g = gw.gw_logdet_vjp_detangles(gcat, net, 11, C, gw.GW_FP64).cpu().numpy()
-    assert np.all(np.abs(g - g_or) < 1e-5 * (np.abs(g_or) + 1.0)), (g, g_or)
+    # tr(Gamma^-1 dGamma): an elementwise FP64 rounding u of the accumulated
+    # Gamma moves it by ~u kappa; 2e-15 kappa covers sqrt(n) growth of u
+    tol = 1e-6 + 2e-15 * kappa
+    assert np.all(np.abs(g - g_or) < tol * (np.abs(g_or) + 1.0)), (g, g_or, kappa)
+    # a closed triangle is invariant under rotation in its plane: d/d gamma_T = 0
+    assert abs(g_or[0]) < 1e-12 and abs(g[0]) < tol
 
 
 # ---------------------------------------------------------------- edges
@@ -280,7 +291,8 @@ def test_prepare_matches_oracle_full_c3():
                        d["dL_Mpc"], d["zflag"], d["tcoal"])
     for k in ("Mc", "eta", "dL", "chi1z", "chi2z", "LamT", "dLamT", "tc"):
         got = cat.t[k].cpu().numpy()
-        assert np.allclose(got, p[k], rtol=1e-13, atol=1e-12 * np.max(np.abs(p[k]))), k
+        # FP64 against long double over a few operations: a few ulp
+        assert np.allclose(got, p[k], rtol=4e-15, atol=4e-15 * np.max(np.abs(p[k]))), k
     assert np.allclose(cat.fmax.cpu().numpy(), p["fisco"], rtol=1e-13, atol=0)
     npts_or = oracle.grid_npts(d["fmin"], cat.fmax.cpu().numpy(), *d["npts_rule"][1:])
     assert np.array_equal(cat.npts.cpu().numpy(), npts_or)
