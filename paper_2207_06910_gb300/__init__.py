@@ -53,7 +53,7 @@ class gw_network(ctypes.Structure):
 
 EXPORTS = ("gw_create", "gw_destroy", "gw_last_error", "gw_abi_version", "gw_prepare_catalog",
            "gw_snr", "gw_fisher", "gw_fisher_inverse", "gw_snr_vjp", "gw_logdet_vjp_detangles",
-           "gw_set_profiling", "gw_point_kernel_ms")
+           "gw_set_profiling", "gw_point_kernel_ms", "gw_fisher_noalloc")
 
 _lib = None
 
@@ -88,6 +88,7 @@ def load_library(path: str | None = None):
         if name not in ("gw_last_error", "gw_abi_version", "gw_destroy", "gw_point_kernel_ms"):
             getattr(lib, name).restype = ctypes.c_int
     lib.gw_destroy.restype = ctypes.c_int
+    lib.gw_fisher_noalloc.argtypes = [C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
     lib.gw_set_profiling.argtypes = [_P, ctypes.c_int]
     lib.gw_point_kernel_ms.argtypes = [_P]
     lib.gw_point_kernel_ms.restype = ctypes.c_double
@@ -301,6 +302,20 @@ def gw_fisher(cat: Catalog, net: Network, n_par: int, prec=GW_FP64, stream=None,
                                   _ptr(gp), _stream(stream))
     _check(st, ctx)
     return (fisher, snr, status, gp) if grad_snr is not None else (fisher, snr, status)
+
+
+GW_ETOOLARGE = 5
+
+
+def gw_fisher_noalloc(cat: Catalog, net: Network, n_par: int, fisher: torch.Tensor,
+                      snr: torch.Tensor | None, status: torch.Tensor, prec=GW_FP64,
+                      stream=None) -> int:
+    """Allocation-free Fisher pass into caller-provided tensors; returns the C
+    status (0 ok, GW_ETOOLARGE when the request exceeds the static workspace)."""
+    c = cat.struct()
+    return load_library().gw_fisher_noalloc(ctypes.byref(c), ctypes.byref(net.net), int(prec),
+                                            n_par, _ptr(fisher), _ptr(snr), _ptr(status),
+                                            _stream(stream))
 
 
 def gw_fisher_inverse(fisher: torch.Tensor, n_par: int, cond_max=1e50, stream=None, out=None):

@@ -72,7 +72,11 @@ gw_status ensure(gw_ctx *ctx, T *&p, size_t &cap, size_t need)
 
 bool is_int(double x) { return std::isfinite(x) && std::fabs(x - std::nearbyint(x)) < 1e-12; }
 
-gw_status build_net(gw_ctx *ctx, const gw_network *net, DevNet &d)
+}  // namespace
+
+// network expansion and catalog checks, shared with the allocation-free entry
+// point (gw_noalloc.cu); errors go to ctx when it is non-null
+gw_status gwi_build_net(gw_ctx *ctx, const gw_network *net, DevNet &d)
 {
     if (!net || !net->det || !net->psd) return fail(ctx, GW_EINVAL, "network: null pointer");
     if (net->n_det < 1 || net->n_det > MAX_DET)
@@ -139,7 +143,7 @@ gw_status build_net(gw_ctx *ctx, const gw_network *net, DevNet &d)
     return GW_OK;
 }
 
-gw_status check_cat(gw_ctx *ctx, const gw_catalog *c, int np)
+gw_status gwi_check_cat(gw_ctx *ctx, const gw_catalog *c, int np)
 {
     if (!c) return fail(ctx, GW_EINVAL, "catalog: null");
     if (c->n < 0) return fail(ctx, GW_EINVAL, "catalog: n < 0");
@@ -151,7 +155,7 @@ gw_status check_cat(gw_ctx *ctx, const gw_catalog *c, int np)
     return GW_OK;
 }
 
-DevCat dev_cat(const gw_catalog *c)
+DevCat gwi_dev_cat(const gw_catalog *c)
 {
     DevCat d;
     d.n = c->n;
@@ -162,6 +166,8 @@ DevCat dev_cat(const gw_catalog *c)
     return d;
 }
 
+namespace {
+
 // event setup -> scan -> point loop -> reduction
 gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_precision prec,
                      int mode, int np, int32_t *status_out, double *snr, double *snr_det,
@@ -169,12 +175,12 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
                      const double *cov, double *grad_gamma, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    gw_status st = check_cat(ctx, cat, np);
+    gw_status st = gwi_check_cat(ctx, cat, np);
     if (st) return st;
     if (np != 9 && np != 11) return fail(ctx, GW_EINVAL, "n_par must be 9 or 11 (got %d)", np);
     if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_EINVAL, "bad precision");
     DevNet dn;
-    if ((st = build_net(ctx, net, dn))) return st;
+    if ((st = gwi_build_net(ctx, net, dn))) return st;
     const int64_t n = cat->n;
     const bool mixed = prec == GW_MIXED && (mode == MODE_FISHER || mode == MODE_SNR ||
                                             mode == MODE_SNRGRAD);
@@ -211,7 +217,7 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
         if ((st = ensure(ctx, ctx->status, ctx->status_cap, (size_t)n))) return st;
         status = ctx->status;
     }
-    const DevCat dc = dev_cat(cat);
+    const DevCat dc = gwi_dev_cat(cat);
     CK(launch_event_setup(dc, dn, np, ctx->evc, ctx->sitec, mixed ? ctx->sitec_f : nullptr,
                           mixed ? ctx->evc_f : nullptr, status, ctx->counts, s));
     CK(launch_scan(ctx->counts, n, ctx->off, ctx->scan, s));
