@@ -40,6 +40,7 @@ WORKLOAD = "c3: 1e5 events, 70% BBH (5-80 Msun, spins) + 30% tidal BNS, ET-like 
 N_PAR = 11
 SM_COUNT = 152
 DFMA_PER_CLK_SM = 2          # measured on GB300: 2 FP64 FMA / clock / SM (1.26 TFLOP/s)
+FFMA_PER_CLK_SM = 128        # FP32 FMA lanes per SM (measured 117 / clock with a plain FFMA loop)
 
 
 def parse():
@@ -186,24 +187,26 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def fp64_flops_per_point(n_ifo_virtual: int, n_site: int, mode: str, precision: str) -> float:
-    """Algorithmic FP64 work per grid point of the fused kernel, counted from its
-    straight-line formulas (one FMA = 2 flops, one multiply or add = 1 flop).
-    Shared per point: basis powers of v (8 mul), d Psi/d Mc and d Psi/d eta
-    (2 x 10 FMA), slots 9/10 (2 x 4 FMA), tau* and two derivatives (3 x 8 FMA +
-    3 mul), f (2 mul), recurrences (4).  FP64 path only, per site: Earth-angle
-    sincos (~20 FMA), JKS and Doppler (30 FMA); per virtual interferometer:
-    patterns (12 FMA + 12 mul), tangents (30), weights and the 66-pair
-    Gram update (22 mul + 132 FMA) or 11-term SNR tangent sums (22 FMA)."""
-    shared = 8 + 2 * 10 * 2 + 2 * 4 * 2 + 3 * 8 * 2 + 3 + 2 + 4
+def flops_per_point(n_site: int, n_ifo: int, precision: str) -> float:
+    """Arithmetic of the fused Fisher kernel per grid point (P = 11, rotation on),
+    counted from its straight-line formulas, one FMA = 2 flops.
+
+    FP64 path (all FP64): basis powers 8, f/w 4, d Psi/d Mc 19, d Psi/d eta 20,
+    slots 9/10 14, tau* and two derivatives 48, PSD weight with reciprocal and
+    square root 35, recurrences 4; per site: Earth-angle sincos ~40, double
+    angle 5, JKS/Doppler/phase combinations ~95; per virtual interferometer:
+    patterns 38, tangents 46, sigma scaling 4, |Q|^2 3, 66-pair Gram update 265.
+    Mixed path (FP32 pipe): double-float basis 80, phase dot products 586 (two
+    11-term 220 each, two 4-term 73 each), tau* dot products 501, f 10,
+    roundings 8, recurrences 32, PSD weight 20; per site 122 (double-float
+    Earth angle 44, sincosf ~20, JKS/Doppler ~58); per virtual interferometer
+    1711 (patterns 38, tangents 60, scaling 4, 73 compensated accumulations of
+    22 flops: two products, two exact product errors, two two-sums, compensation)."""
     if precision == "mixed":
-        return shared + 4          # + Earth angle reduction
-    site = 20 * 2 + 30 * 2
-    if mode == "fisher":
-        ifo = 12 * 2 + 12 + 30 * 1.5 + 22 + 132 * 2
-    else:
-        ifo = 12 * 2 + 12 + 30 * 1.5 + 22 * 2
-    return shared + 15 + n_site * site + n_ifo_virtual * ifo
+        shared = 80 + 586 + 501 + 10 + 8 + 32 + 20
+        return shared + 122 * n_site + 1711 * n_ifo
+    shared = 8 + 4 + 19 + 20 + 14 + 48 + 35 + 4
+    return shared + 140 * n_site + 356 * n_ifo
 
 
 def run_ours(a):
@@ -317,9 +320,10 @@ def run_ours(a):
     if rank == 0:
         n_site = net.n_det
         n_ifo = sum(1 if int(r[4]) == 0 else 2 for r in det)
-        flops = fp64_flops_per_point(n_ifo, n_site, "fisher", a.precision) * n_points
+        flops = flops_per_point(n_site, n_ifo, a.precision) * n_points
         sm_mhz = clocks.get("sm_mhz") or 2070.0
-        peak = SM_COUNT * DFMA_PER_CLK_SM * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s at the sampled clock
+        per_clk = FFMA_PER_CLK_SM if a.precision == "mixed" else DFMA_PER_CLK_SM
+        peak = SM_COUNT * per_clk * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s at the sampled clock
         achieved = flops / (kern_ms * 1e-3) / 1e12
         cpu = None
         if not a.no_cpu_baseline:
@@ -348,8 +352,10 @@ def run_ours(a):
                          "frac": achieved / peak, "traffic": None,
                          "kernel": f"k_points_{'mixed' if a.precision == 'mixed' else 'fp64'} (Fisher)",
                          "kernel_ms": kern_ms,
-                         "peak_basis": f"FP64 pipe: {SM_COUNT} SMs x {DFMA_PER_CLK_SM} DFMA/clk x 2 "
-                                       f"flops x {sm_mhz:.0f} MHz (median sampled SM clock)"},
+                         "flops_per_point": flops_per_point(n_site, n_ifo, a.precision),
+                         "peak_basis": (f"{'FP32' if a.precision == 'mixed' else 'FP64'} pipe: "
+                                        f"{SM_COUNT} SMs x {per_clk} FMA/clk x 2 flops x "
+                                        f"{sm_mhz:.0f} MHz (median sampled SM clock)")},
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -82,15 +82,30 @@ __device__ __forceinline__ DF df_dot(const float2 *c, const DF (&b)[N])
     return s;
 }
 
-// accumulate a + b (two FP32 products with their exact rounding errors) into
-// the pair (hi, *lo); hi lives in a register, the compensation in shared memory
-__device__ __forceinline__ void acc_add2(float &hi, float *lo, float a, float ea, float b,
-                                         float eb)
+// packed FP32x2 subtraction (sm_100+)
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b)
 {
-    const DF p = two_sum(a, b);
-    const DF t = two_sum(hi, p.hi);
-    hi = t.hi;
-    *lo += (ea + eb) + (p.lo + t.lo);
+    unsigned long long ra = *reinterpret_cast<unsigned long long *>(&a);
+    unsigned long long rb = *reinterpret_cast<unsigned long long *>(&b);
+    unsigned long long rd;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    return *reinterpret_cast<float2 *>(&rd);
+}
+
+// Exact accumulation of the elementwise product a * b (two lanes: real and
+// imaginary parts) into a packed double-float accumulator that holds the
+// NEGATED sum: hn (register) + *ln (shared memory).  nb = -b.  With p = fl(a b)
+// and q = fl(a nb) = -p, e = fma(a, b, q) is the exact error of p; the two-sum
+// of hn + q is exact; so hn + ln = -(sum of a b) up to the FP32 rounding of ln.
+__device__ __forceinline__ void acc_pk(float2 &hn, float2 *ln, float2 a, float2 b, float2 nb)
+{
+    const float2 q = __fmul2_rn(a, nb);
+    const float2 e = __ffma2_rn(a, b, q);
+    const float2 s = __fadd2_rn(hn, q);
+    const float2 bb = f2sub(s, hn);
+    const float2 tn = __fadd2_rn(f2sub(hn, f2sub(s, bb)), f2sub(q, bb));
+    hn = s;
+    *ln = __fadd2_rn(*ln, f2sub(tn, e));
 }
 
 __device__ __forceinline__ int64_t find_event_m(const int64_t *off, int64_t n, int64_t it)
@@ -198,7 +213,7 @@ __device__ __forceinline__ void tangents_f(const PatF &p, float Acp, float Acx, 
 }
 
 template <int MODE, int NP, bool ROT>
-__global__ void __launch_bounds__(128, 3) k_points_mixed(PointArgs A)
+__global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
 {
     constexpr int NACC = NAccM<MODE, NP>::value;
     constexpr int NT = 128;         // threads per block
@@ -207,13 +222,11 @@ __global__ void __launch_bounds__(128, 3) k_points_mixed(PointArgs A)
     const int wib = threadIdx.x >> 5;
     const int gid = lane / GROUP, gl = lane % GROUP;
     const unsigned gmask = ((1u << GROUP) - 1u) << (gid * GROUP);
-    // compensation terms of the accumulators: lo[a * NT + thread]
-    float *lo = red_f;
-    float *mylo = lo + threadIdx.x;
+    // compensation terms of the packed accumulators: lo[a * NT + thread]
+    float2 *mylo = reinterpret_cast<float2 *>(red_f) + threadIdx.x;
     // per-group copy of the item's event constants (read every point from
     // shared memory instead of being held in registers across the loop)
-    float2 *cs = reinterpret_cast<float2 *>(red_f + NACC * NT) +
-                 (wib * GROUPS_PER_WARP + gid) * EVC;
+    float2 *cs = reinterpret_cast<float2 *>(red_f) + NACC * NT + (wib * GROUPS_PER_WARP + gid) * EVC;
     const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GROUPS_PER_WARP;
     const DevNet &net = A.net;
     const DF two_pi = DF{6.28318548f, -1.74845553e-7f};          // 2 pi = hi + lo
@@ -232,11 +245,12 @@ __global__ void __launch_bounds__(128, 3) k_points_mixed(PointArgs A)
         const int N = (int)E[EV_NPTS];
         const int kb = (int)((int64_t)N * j / nj), ke = (int)((int64_t)N * (j + 1) / nj);
 
-        float acc[NACC];
+        // accumulators: negated (real-part sum, imaginary-part sum) per entry
+        float2 acc[NACC];
 #pragma unroll
         for (int a = 0; a < NACC; a++) {
-            acc[a] = 0.0f;
-            mylo[a * NT] = 0.0f;
+            acc[a] = make_float2(0.0f, 0.0f);
+            mylo[a * NT] = make_float2(0.0f, 0.0f);
         }
 
         int k = kb + gl;
@@ -373,54 +387,52 @@ __global__ void __launch_bounds__(128, 3) k_points_mixed(PointArgs A)
                         float gr[NP], gi[NP], qr, qi, xr, xi, tr, ti;
                         tangents_f<NP, ROT>(pt, sg * cp, sg * cx, sg * dcp, sg * dcx, aMc, invdL,
                                             ph, gr, gi, qr, qi, xr, xi, tr, ti);
-                        {
-                            const float p1 = qr * qr, p2 = qi * qi;
-                            acc_add2(acc[0], mylo, p1, fmaf(qr, qr, -p1), p2, fmaf(qi, qi, -p2));
+                        // tangents as (real, imaginary) pairs and their negations
+                        float2 G[NP], NG[NP];
+#pragma unroll
+                        for (int i = 0; i < NP; i++) {
+                            G[i] = make_float2(gr[i], gi[i]);
+                            NG[i] = make_float2(-gr[i], -gi[i]);
                         }
+                        const float2 Q = make_float2(qr, qi);
                         if (MODE == MODE_FISHER) {
+                            // Gamma_ij: real and imaginary products summed separately
+                            // (|Q|^2 = the (Phic, Phic) entry, copied at the end)
                             int a = 1;
 #pragma unroll
                             for (int i = 0; i < NP; i++) {
 #pragma unroll
                                 for (int jj = i; jj < NP; jj++) {
-                                    const float p1 = gr[i] * gr[jj], p2 = gi[i] * gi[jj];
-                                    acc_add2(acc[a], mylo + a * NT, p1, fmaf(gr[i], gr[jj], -p1),
-                                             p2, fmaf(gi[i], gi[jj], -p2));
+                                    acc_pk(acc[a], mylo + a * NT, G[i], G[jj], NG[jj]);
                                     a++;
                                 }
                                 if (i & 1) asm volatile("" ::: "memory");
                             }
                             // phase-free SNR-gradient sums (see N_SNRGRAD_X)
                             constexpr int X0 = 1 + NP * (NP + 1) / 2;
-                            const float rx[N_SNRGRAD_X][4] = {
-                                {qr, xr, qi, xi},
-                                {ph.tMc * qr, xr, ph.tMc * qi, xi},
-                                {ph.teta * qr, xr, ph.teta * qi, xi},
-                                {qr, tr, qi, ti},
-                                {qr, gr[5], qi, gi[5]},
-                                {qr, gr[6], qi, gi[6]}};
-#pragma unroll
-                            for (int m = 0; m < N_SNRGRAD_X; m++) {
-                                const float p1 = rx[m][0] * rx[m][1], p2 = rx[m][2] * rx[m][3];
-                                acc_add2(acc[X0 + m], mylo + (X0 + m) * NT, p1,
-                                         fmaf(rx[m][0], rx[m][1], -p1), p2,
-                                         fmaf(rx[m][2], rx[m][3], -p2));
-                            }
+                            const float2 X = make_float2(xr, xi), NX = make_float2(-xr, -xi);
+                            const float2 T = make_float2(tr, ti), NT2 = make_float2(-tr, -ti);
+                            acc_pk(acc[X0 + 0], mylo + (X0 + 0) * NT, Q, X, NX);
+                            acc_pk(acc[X0 + 1], mylo + (X0 + 1) * NT,
+                                   make_float2(ph.tMc * qr, ph.tMc * qi), X, NX);
+                            acc_pk(acc[X0 + 2], mylo + (X0 + 2) * NT,
+                                   make_float2(ph.teta * qr, ph.teta * qi), X, NX);
+                            acc_pk(acc[X0 + 3], mylo + (X0 + 3) * NT, Q, T, NT2);
+                            acc_pk(acc[X0 + 4], mylo + (X0 + 4) * NT, Q, G[5], NG[5]);
+                            acc_pk(acc[X0 + 5], mylo + (X0 + 5) * NT, Q, G[6], NG[6]);
                         } else if (MODE == MODE_SNR) {
+                            const float2 NQ = make_float2(-qr, -qi);
+                            acc_pk(acc[0], mylo, Q, Q, NQ);
                             const int dd = net.ifo_det[q];
-                            const float p1 = qr * qr, p2 = qi * qi;
 #pragma unroll
                             for (int d = 0; d < MAX_DET; d++)
-                                if (d == dd)
-                                    acc_add2(acc[1 + d], mylo + (1 + d) * NT, p1,
-                                             fmaf(qr, qr, -p1), p2, fmaf(qi, qi, -p2));
+                                if (d == dd) acc_pk(acc[1 + d], mylo + (1 + d) * NT, Q, Q, NQ);
                         } else {   // MODE_SNRGRAD
+                            const float2 NQ = make_float2(-qr, -qi);
+                            acc_pk(acc[0], mylo, Q, Q, NQ);
 #pragma unroll
-                            for (int i = 0; i < 8; i++) {
-                                const float p1 = qr * gr[i], p2 = qi * gi[i];
-                                acc_add2(acc[1 + i], mylo + (1 + i) * NT, p1, fmaf(qr, gr[i], -p1),
-                                         p2, fmaf(qi, gi[i], -p2));
-                            }
+                            for (int i = 0; i < 8; i++)
+                                acc_pk(acc[1 + i], mylo + (1 + i) * NT, Q, G[i], NG[i]);
                         }
                     }
                 }
@@ -434,9 +446,18 @@ __global__ void __launch_bounds__(128, 3) k_points_mixed(PointArgs A)
         // (error-free two-sum of the high parts, compensations added), then
         // every lane writes the accumulators a = gl (mod GROUP) in FP64
         double *out = A.partial + it * (int64_t)A.nacc;
+        if (MODE == MODE_FISHER) {
+            // SNR^2 = sum |Q|^2 = the (Phic, Phic) entry
+            constexpr int k88 = 1 + 8 * NP - 8 * 7 / 2;
+            acc[0] = acc[k88];
+            mylo[0] = mylo[k88 * NT];
+        }
 #pragma unroll
         for (int a = 0; a < NACC; a++) {
-            DF s = DF{acc[a], mylo[a * NT]};
+            // collapse (real, imaginary) parts: value = -(hn.x + hn.y + ln.x + ln.y)
+            const float2 l2 = mylo[a * NT];
+            const DF h = two_sum(acc[a].x, acc[a].y);
+            DF s = DF{-h.hi, -((l2.x + l2.y) + h.lo)};
 #pragma unroll
             for (int o = 1; o < GROUP; o <<= 1) {
                 const float oh = __shfl_xor_sync(gmask, s.hi, o);
@@ -456,7 +477,7 @@ template <int MODE, int NP, bool ROT>
 cudaError_t launch_one_m(const PointArgs &a, cudaStream_t s)
 {
     constexpr int NACC = NAccM<MODE, NP>::value;
-    const size_t smem = ((size_t)NACC * 128 + (size_t)4 * GROUPS_PER_WARP * EVC * 2) * sizeof(float);
+    const size_t smem = ((size_t)NACC * 128 + (size_t)4 * GROUPS_PER_WARP * EVC) * sizeof(float2);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t err = cudaFuncSetAttribute(k_points_mixed<MODE, NP, ROT>,
@@ -466,7 +487,7 @@ cudaError_t launch_one_m(const PointArgs &a, cudaStream_t s)
         attr_set = true;
     }
     if (a.n_items <= 0) return cudaSuccess;
-    k_points_mixed<MODE, NP, ROT><<<points_grid_size(3), 128, smem, s>>>(a);
+    k_points_mixed<MODE, NP, ROT><<<points_grid_size(2), 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 
