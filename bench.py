@@ -37,10 +37,16 @@ import gwcat
 METRIC = "events/s (SNR + 11x11 Fisher), mixed vs FP64 path at stated error; % FP peak"
 WORKLOAD = "c3: 1e5 events, 70% BBH (5-80 Msun, spins) + 30% tidal BNS, ET-like triangle, " \
            "Earth rotation, per-event log grid 2 Hz..f_ISCO"
+WORKLOAD_C4 = "c4: 1e6 events drawn as c3 on five interferometers (triangle + two L)"
 N_PAR = 11
 SM_COUNT = 152
 DFMA_PER_CLK_SM = 2          # measured on GB300: 2 FP64 FMA / clock / SM (1.26 TFLOP/s)
 FFMA_PER_CLK_SM = 128        # FP32 FMA lanes per SM (measured 117 / clock with a plain FFMA loop)
+# DRAM bytes (read + write) per grid point of the Fisher point kernel, from one
+# ncu capture of the 2e4-event c3 catalog (4,376,070 points) of the current
+# kernels (profiles/k_points_*_fisher_c3.md); scaled by points to a full launch
+DRAM_BYTES_PER_POINT = {"mixed": (19.328768e6 + 80.128e3) / 4376070,
+                        "fp64": (16.705792e6 + 59.648e3) / 4376070}
 
 
 def parse():
@@ -52,7 +58,13 @@ def parse():
     ap.add_argument("--grid", choices=["literal", "stress"], default="literal")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--events", type=int, default=None)
+    ap.add_argument("--workload", choices=["c3", "c4"], default="c3",
+                    help="c3: 1e5 events on the triangle (headline); c4: 1e6 events on five "
+                         "interferometers, the step adding the log-det VJP over the "
+                         "detector orientations")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch the step call by call instead of replaying a CUDA graph")
     return ap.parse_args()
 
 
@@ -209,6 +221,24 @@ def flops_per_point(n_site: int, n_ifo: int, precision: str) -> float:
     return shared + 140 * n_site + 356 * n_ifo
 
 
+def shard_seed(rank: int) -> int:
+    """Seed of rank's catalog shard: every rank owns its own full-size shard
+    (weak scaling; events are independent, nothing is exchanged)."""
+    return gwcat.SEED_BASE + 3 + 1000 * rank
+
+
+def aggregate(times_ms, n_events: int, steps: int, world: int, dist=None, device="cpu"):
+    """Max over ranks of each timed quantity (ms) and the whole-job rates:
+    events/s = world * n_events * steps / max_time."""
+    import torch
+    t = torch.tensor([float(x) for x in times_ms], dtype=torch.float64, device=device)
+    if world > 1 and dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t = t.tolist()
+    rates = [world * n_events * steps / (x * 1e-3) for x in t]
+    return t, rates
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -223,10 +253,10 @@ def run_ours(a):
 
     prec = gw.GW_MIXED if a.precision == "mixed" else gw.GW_FP64
     # weak scaling: every rank owns its own 1e5-event shard (seed offset by rank)
-    raw = gwcat.draw("c3", a.events, seed=gwcat.SEED_BASE + 3 + 1000 * rank, grid=a.grid)
+    raw = gwcat.draw(a.workload, a.events, seed=shard_seed(rank), grid=a.grid)
     n = len(raw["m1"])
     rule = raw["npts_rule"]
-    det, psd, rot = gwcat.network("c3")
+    det, psd, rot = gwcat.network(a.workload)
     net = gw.Network(det, psd, rot)
     keys = ("m1", "m2", "chi1", "chi2", "lam1", "lam2", "dL_Mpc", "tcoal", "fmin",
             "theta", "phi", "iota", "psi", "Phic")
@@ -245,13 +275,17 @@ def run_ours(a):
     def prepare(d):
         return gw_prepare_dev(gw, d, rule, n)
 
+    with_logdet = a.workload == "c4"
+
     def step(d):
         cat = prepare(d)
         F, snr, st, g = gw.gw_fisher(cat, net, N_PAR, prec, grad_snr=grad_up)
         cov, cond, err, sti = gw.gw_fisher_inverse(F, N_PAR)
+        if with_logdet:
+            gw.gw_logdet_vjp_detangles(cat, net, N_PAR, cov, gw.GW_FP64)
         return cat, F, snr, cov, cond, g, st
 
-    launches_per_step = 1 + 7 + 1
+    launches_per_step = 1 + 7 + 1 + (6 if with_logdet else 0)
     for _ in range(a.warmup):
         step(dev)
     torch.cuda.synchronize()
@@ -261,6 +295,38 @@ def run_ours(a):
     assert int((st != 0).sum()) == 0, "events flagged in the benchmark catalog"
     n_points = int(cat.npts.to(torch.int64).sum().item())
 
+    # ---- reserve the workspace (asynchronous calls) and capture the step
+    gw.gw_reserve(n, gw.work_items(cat.npts), net.n_det)
+    for _ in range(2):
+        step(dev)
+    torch.cuda.synchronize()
+    graph, gout = None, None
+    if not a.eager:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            gout = step(dev)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert int((gout[6] != 0).sum()) == 0 and torch.allclose(gout[2], snr, rtol=1e-12)
+
+    def run_step():
+        if graph is not None:
+            graph.replay()
+            return gout
+        return step(dev)
+
+    # Fisher point-kernel duration: a few eager Fisher calls with the library's
+    # event hooks (read before any later point kernel of the step)
+    fisher_ms = []
+    gw.gw_set_profiling(True)
+    for _ in range(5):
+        flush.zero_()
+        cat_p = prepare(dev)
+        gw.gw_fisher(cat_p, net, N_PAR, prec, grad_snr=grad_up)
+        fisher_ms.append(gw.gw_point_kernel_ms())
+    gw.gw_set_profiling(False)
+    torch.cuda.synchronize()
+
     # ---- device-resident timed loop
     clk = Clocks(local)
     if world > 1:
@@ -269,18 +335,12 @@ def run_ours(a):
     clk.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(a.steps)]
-    fisher_ms = []
-    gw.gw_set_profiling(True)
     for i in range(a.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        cat = prepare(dev)
-        F, snr, st, g = gw.gw_fisher(cat, net, N_PAR, prec, grad_snr=grad_up)
-        fisher_ms.append(gw.gw_point_kernel_ms())
-        gw.gw_fisher_inverse(F, N_PAR)
+        run_step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
-    gw.gw_set_profiling(False)
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
@@ -299,8 +359,9 @@ def run_ours(a):
     for i in range(a.steps):
         flush.zero_()
         e2e_ev[i][0].record(stream)
-        d = {k: v.cuda(non_blocking=True) for k, v in host.items()}
-        cat, F, snr, cov, cond, g, st = step(d)
+        for k, v in host.items():
+            dev[k].copy_(v, non_blocking=True)
+        cat, F, snr, cov, cond, g, st = run_step()
         outs_host["snr"].copy_(snr, non_blocking=True)
         outs_host["F"].copy_(F, non_blocking=True)
         outs_host["cov"].copy_(cov, non_blocking=True)
@@ -308,14 +369,11 @@ def run_ours(a):
         e2e_ev[i][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = float(sum(s.elapsed_time(e) for s, e in e2e_ev))
+    gw.gw_reserve(0, 0, 0)
 
-    t = torch.tensor([total_ms, e2e_ms, float(np.mean(fisher_ms))], dtype=torch.float64,
-                     device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms, kern_ms = t.tolist()
-    value = world * n * a.steps / (total_ms * 1e-3)
-    e2e_value = world * n * a.steps / (e2e_ms * 1e-3)
+    (total_ms, e2e_ms, kern_ms), (value, e2e_value, _) = aggregate(
+        [total_ms, e2e_ms, float(np.mean(fisher_ms))], n, a.steps, world,
+        dist if world > 1 else None, device="cuda")
 
     if rank == 0:
         n_site = net.n_det
@@ -339,17 +397,23 @@ def run_ours(a):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
             "data": "synthetic (seeded, gwcat)",
-            "config": {"workload": WORKLOAD, "n_events_per_gpu": n, "grid": a.grid,
+            "config": {"workload": WORKLOAD if a.workload == "c3" else WORKLOAD_C4,
+                       "n_events_per_gpu": n, "grid": a.grid,
                        "points_per_step": n_points, "precision": a.precision, "n_par": N_PAR,
-                       "step": "prepare + SNR/Fisher with fused SNR VJP + Cholesky inversion",
+                       "step": "prepare + SNR/Fisher with fused SNR VJP + Cholesky inversion"
+                               + (" + log-det VJP (FP64) over detector orientations"
+                                  if with_logdet else ""),
                        "l2": "flushed before every timed step (256 MiB write)",
+                       "launch": "eager calls" if a.eager else "one CUDA graph replay per step",
                        "parallelism": f"event shards, {world} GPU(s), no collective"},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * a.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": DRAM_BYTES_PER_POINT[a.precision] * n_points
+                         if a.grid == "literal" else None,
                          "kernel": f"k_points_{'mixed' if a.precision == 'mixed' else 'fp64'} (Fisher)",
                          "kernel_ms": kern_ms,
                          "flops_per_point": flops_per_point(n_site, n_ifo, a.precision),

@@ -56,9 +56,14 @@ enum {
     GW_ST_EMPTY_GRID = 8,   /* fmax <= fmin or npts < 2                        */
     GW_ST_BAD_PARAM = 16,   /* Mc <= 0, eta outside (0, 1/4], dL <= 0, wrong
                                parameter set for n_par                         */
-    GW_ST_ILL_COND = 32     /* condition number above 1/DBL_EPSILON (Sec. 4:
+    GW_ST_ILL_COND = 32,    /* condition number above 1/DBL_EPSILON (Sec. 4:
                                inversion unreliable beyond inverse precision)  */
+    GW_ST_OVERFLOW = 64     /* work items beyond the gw_reserve capacity       */
 };
+
+/* A work item is a run of at most GW_ITEM_POINTS consecutive grid points of one
+ * event: an event of npts points has ceil(npts / GW_ITEM_POINTS) items. */
+#define GW_ITEM_POINTS 256
 
 /* Fisher parameter order (the fixed order of Sec. 3.2): slot 0..8 =
  *   Mc [Msun, detector frame], eta, dL [Gpc], theta, phi, iota, psi [rad],
@@ -116,6 +121,18 @@ gw_status gw_destroy(gw_ctx *ctx);
 const char *gw_last_error(const gw_ctx *ctx);
 /* ABI version of this header (incremented on any signature change): 2. */
 int gw_abi_version(void);
+
+/* Reserve workspace for up to max_events events on up to max_sites detector
+ * sites and max_items work items, and switch the context to asynchronous mode:
+ * gw_snr, gw_fisher, gw_snr_vjp and gw_logdet_vjp_detangles then neither read
+ * the work count back (no synchronisation) nor allocate while a call fits the
+ * reservation, so a sequence of calls can be captured in a CUDA graph and
+ * replayed.  The kernels take the work count from device memory; events whose
+ * work items fall beyond max_items get GW_ST_OVERFLOW and NaN outputs.  A call
+ * that needs more events or sites than reserved grows the workspace (which is
+ * not allowed during capture and then fails with GW_ECUDA).  max_items = 0
+ * returns to the synchronous default.  No counterpart in the paper. */
+gw_status gw_reserve(gw_ctx *ctx, int64_t max_events, int64_t max_items, int max_sites);
 
 /* Measurement hook (no counterpart in the paper): when enabled, the context
  * records CUDA events on the call's stream around every point-loop kernel

@@ -23,6 +23,8 @@ from . import build as _build
 
 GW_FP64, GW_MIXED = 0, 1
 ST_NOT_PD, ST_COND_GT_MAX, ST_NONFINITE, ST_EMPTY_GRID, ST_BAD_PARAM, ST_ILL_COND = 1, 2, 4, 8, 16, 32
+ST_OVERFLOW = 64
+ITEM_POINTS = 256          # grid points per work item (GW_ITEM_POINTS)
 FISHER_PARAMS_9 = ("Mc", "eta", "dL", "theta", "phi", "iota", "psi", "tc", "Phic")
 
 _P = ctypes.c_void_p
@@ -53,7 +55,7 @@ class gw_network(ctypes.Structure):
 
 EXPORTS = ("gw_create", "gw_destroy", "gw_last_error", "gw_abi_version", "gw_prepare_catalog",
            "gw_snr", "gw_fisher", "gw_fisher_inverse", "gw_snr_vjp", "gw_logdet_vjp_detangles",
-           "gw_set_profiling", "gw_point_kernel_ms", "gw_fisher_noalloc")
+           "gw_set_profiling", "gw_point_kernel_ms", "gw_fisher_noalloc", "gw_reserve")
 
 _lib = None
 
@@ -88,6 +90,7 @@ def load_library(path: str | None = None):
         if name not in ("gw_last_error", "gw_abi_version", "gw_destroy", "gw_point_kernel_ms"):
             getattr(lib, name).restype = ctypes.c_int
     lib.gw_destroy.restype = ctypes.c_int
+    lib.gw_reserve.argtypes = [_P, i64, i64, ctypes.c_int]
     lib.gw_fisher_noalloc.argtypes = [C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
     lib.gw_set_profiling.argtypes = [_P, ctypes.c_int]
     lib.gw_point_kernel_ms.argtypes = [_P]
@@ -116,6 +119,19 @@ def context(device: int | None = None) -> _P:
             raise GWError(f"gw_create failed with status {st}")
         _ctx_by_dev[device] = h
     return _ctx_by_dev[device]
+
+
+def gw_reserve(max_events: int, max_items: int, max_sites: int = 1) -> None:
+    """Pre-size the workspace and switch to asynchronous (graph-capturable) mode;
+    max_items = 0 returns to the synchronous default."""
+    ctx = context()
+    _check(load_library().gw_reserve(ctx, int(max_events), int(max_items), int(max_sites)), ctx)
+
+
+def work_items(npts) -> int:
+    """Number of work items of a catalog with these grid lengths."""
+    n = torch.as_tensor(npts).to(torch.int64)
+    return int(((n + ITEM_POINTS - 1) // ITEM_POINTS).sum().item())
 
 
 def gw_set_profiling(enable: bool = True) -> None:

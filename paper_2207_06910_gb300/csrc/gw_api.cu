@@ -28,6 +28,7 @@ struct gw_ctx {
     double *xsums = nullptr;    size_t xsums_cap = 0;   // mixed SNR-gradient sums [6][n]
     double *snr_tmp = nullptr;  size_t snr_tmp_cap = 0;
     int64_t *h_total = nullptr;   // pinned
+    int64_t item_cap = 0;       // > 0: asynchronous mode with this many work items
     int profiling = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool ev_recorded = false;
@@ -221,11 +222,19 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     CK(launch_event_setup(dc, dn, np, ctx->evc, ctx->sitec, mixed ? ctx->sitec_f : nullptr,
                           mixed ? ctx->evc_f : nullptr, status, ctx->counts, s));
     CK(launch_scan(ctx->counts, n, ctx->off, ctx->scan, s));
-    CK(cudaMemcpyAsync(ctx->h_total, ctx->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const int64_t n_items = *ctx->h_total;
-    if ((st = ensure(ctx, ctx->partial, ctx->partial_cap, (size_t)(n_items > 0 ? n_items : 1) * nacc)))
-        return st;
+    int64_t n_items;
+    if (ctx->item_cap > 0) {
+        // asynchronous: the kernels take the work count from device memory
+        n_items = ctx->item_cap;
+        if ((st = ensure(ctx, ctx->partial, ctx->partial_cap, (size_t)n_items * nacc))) return st;
+    } else {
+        CK(cudaMemcpyAsync(ctx->h_total, ctx->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        n_items = *ctx->h_total;
+        if ((st = ensure(ctx, ctx->partial, ctx->partial_cap,
+                         (size_t)(n_items > 0 ? n_items : 1) * nacc)))
+            return st;
+    }
     PointArgs pa;
     pa.net = dn;
     pa.evc = ctx->evc;
@@ -303,6 +312,33 @@ gw_status gw_destroy(gw_ctx *ctx)
 }
 
 const char *gw_last_error(const gw_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+gw_status gw_reserve(gw_ctx *ctx, int64_t max_events, int64_t max_items, int max_sites)
+{
+    if (!ctx) return GW_EINVAL;
+    if (max_events < 0 || max_items < 0 || max_sites < 0 || max_sites > MAX_SITE)
+        return fail(ctx, GW_EINVAL, "reserve: bad sizes");
+    CK(cudaSetDevice(ctx->device));
+    ctx->item_cap = 0;
+    if (max_items == 0) return GW_OK;
+    const size_t n = (size_t)(max_events > 0 ? max_events : 1);
+    const size_t sites = (size_t)(max_sites > 0 ? max_sites : 1);
+    const size_t nacc_max = 1 + 11 * 12 / 2 + N_SNRGRAD_X;
+    gw_status st;
+    if ((st = ensure(ctx, ctx->evc, ctx->evc_cap, n * EVC))) return st;
+    if ((st = ensure(ctx, ctx->evc_f, ctx->evc_f_cap, n * EVC))) return st;
+    if ((st = ensure(ctx, ctx->sitec, ctx->sitec_cap, n * sites * SC_N))) return st;
+    if ((st = ensure(ctx, ctx->sitec_f, ctx->sitec_f_cap, n * sites * SC_N))) return st;
+    if ((st = ensure(ctx, ctx->counts, ctx->counts_cap, n))) return st;
+    if ((st = ensure(ctx, ctx->off, ctx->off_cap, n + 1))) return st;
+    if ((st = ensure(ctx, ctx->scan, ctx->scan_cap, scan_tmp_size((int64_t)n)))) return st;
+    if ((st = ensure(ctx, ctx->status, ctx->status_cap, n))) return st;
+    if ((st = ensure(ctx, ctx->xsums, ctx->xsums_cap, (size_t)N_SNRGRAD_X * n))) return st;
+    if ((st = ensure(ctx, ctx->snr_tmp, ctx->snr_tmp_cap, n))) return st;
+    if ((st = ensure(ctx, ctx->partial, ctx->partial_cap, (size_t)max_items * nacc_max))) return st;
+    ctx->item_cap = max_items;
+    return GW_OK;
+}
 
 gw_status gw_set_profiling(gw_ctx *ctx, int enable)
 {

@@ -23,7 +23,9 @@ struct PointArgs {
     const float *sitec_f;     // [n][n_site][SC_N], FP32 copy for the mixed path
     const float2 *evc_f;      // [n][EVC], double-float copy for the mixed path
     const int64_t *item_off;  // [n+1] exclusive prefix of work items per event
-    int64_t n_ev, n_items;
+    int64_t n_ev;
+    int64_t n_items;          // capacity of partial in items; the kernels process
+                              // min(item_off[n_ev], n_items) items
     double *partial;          // [n_items][nacc]
     int nacc;
     const double *cov;        // logdet mode: covariance, packed, event-minor

@@ -165,9 +165,12 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
     double *cs = red_smem + 4 * GROUPS_PER_WARP * NACC * RS + (wib * GROUPS_PER_WARP + gid) * EVC;
     const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GROUPS_PER_WARP;
     const DevNet &net = A.net;
+    // work count from device memory (no host readback), bounded by the capacity
+    const int64_t n_total = A.item_off[A.n_ev];
+    const int64_t n_items = n_total < A.n_items ? n_total : A.n_items;
 
     for (int64_t it = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GROUPS_PER_WARP + gid;
-         it < A.n_items; it += ngroups) {
+         it < n_items; it += ngroups) {
         const int64_t e = find_event(A.item_off, A.n_ev, it);
         const int64_t j = it - A.item_off[e];
         const int64_t nj = A.item_off[e + 1] - A.item_off[e];

@@ -389,8 +389,8 @@ cudaError_t launch_scan(const int64_t *counts, int64_t n, int64_t *off, int64_t 
 // ------------------------------------------------------------------------
 // reduction of item partials: one thread per (event, accumulator), items of an
 // event summed in item order (deterministic).
-__global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc,
-                         const int64_t *item_off, const double *partial, const int32_t *status,
+__global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc, int64_t cap,
+                         const int64_t *item_off, const double *partial, int32_t *status,
                          double *snr, double *snr_det, double *fisher, const double *grad_snr,
                          double *grad_params, double *xsums)
 {
@@ -398,10 +398,13 @@ __global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc,
     int64_t e = t / nacc;
     int a = (int)(t - e * nacc);
     if (e >= n) return;
-    const bool bad = status[e] != 0;
     const int64_t i0 = item_off[e], i1 = item_off[e + 1];
+    const bool over = i1 > cap;   // items beyond the workspace capacity
+    if (over && a == 0) status[e] |= 64;
+    const bool bad = over || (status[e] & ~64) != 0;
     double s = 0.0;
-    for (int64_t it = i0; it < i1; it++) s += partial[it * nacc + a];
+    if (!over)
+        for (int64_t it = i0; it < i1; it++) s += partial[it * nacc + a];
     if (mode == MODE_FISHER) {
         const int npair = np * (np + 1) / 2;
         if (a == 0) {
@@ -417,7 +420,8 @@ __global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc,
     } else if (mode == MODE_SNRGRAD) {
         if (a > 0) {
             double s0 = 0.0;
-            for (int64_t it = i0; it < i1; it++) s0 += partial[it * nacc];
+            if (!over)
+                for (int64_t it = i0; it < i1; it++) s0 += partial[it * nacc];
             // d SNR / d theta = sum W Re(Q* g) / SNR
             grad_params[(int64_t)(a - 1) * n + e] = bad ? NAN : grad_snr[e] * s / sqrt(s0);
         }
@@ -425,9 +429,11 @@ __global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc,
 }
 
 // logdet mode: total over all items of each detector accumulator, fixed order
-__global__ void k_finish_total(int64_t n_items, int nacc, const double *partial, double *out)
+__global__ void k_finish_total(int64_t cap, const int64_t *total, int nacc, const double *partial,
+                               double *out)
 {
     __shared__ double sh[256];
+    const int64_t n_items = *total < cap ? *total : cap;
     int a = blockIdx.x;
     double s = 0.0;
     for (int64_t it = threadIdx.x; it < n_items; it += blockDim.x) s += partial[it * nacc + a];
@@ -497,14 +503,16 @@ cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const
                           double *grad_params, double *grad_gamma, double *xsums, cudaStream_t s)
 {
     if (mode == MODE_LOGDET) {
-        k_finish_total<<<a.nacc, 256, 0, s>>>(a.n_items, a.nacc, a.partial, grad_gamma);
+        k_finish_total<<<a.nacc, 256, 0, s>>>(a.n_items, a.item_off + a.n_ev, a.nacc, a.partial,
+                                              grad_gamma);
         return cudaGetLastError();
     }
     int64_t tot = a.n_ev * a.nacc;
     if (tot <= 0) return cudaSuccess;
     int bs = 256;
     k_finish<<<(unsigned)((tot + bs - 1) / bs), bs, 0, s>>>(mode, np, n_det, a.n_ev, a.nacc,
-                                                           a.item_off, a.partial, status, snr,
+                                                           a.n_items, a.item_off, a.partial,
+                                                           const_cast<int32_t *>(status), snr,
                                                            snr_det, fisher, grad_snr,
                                                            grad_params, xsums);
     return cudaGetLastError();

@@ -325,3 +325,41 @@ def test_full_size_c3_sampled_and_invariants(grid):
         assert torch.max(torch.abs(F[k_dd] * dl * dl / s2 - 1)).item() < itol
         Fs = gw.unpack(F[:, torch.as_tensor(pick, device="cuda")], 11).cpu().numpy()
         assert _rel_fisher(Fs, F_or).max() < tf
+
+
+def test_reserve_async_graph_and_overflow():
+    """gw_reserve: the asynchronous path replayed from a CUDA graph gives the
+    synchronous results; events past the reserved work items are flagged."""
+    cat, d, p = oracle_catalog("c3", 300)
+    det, psd, rot = gwcat.network("c3")
+    net = gw.Network(det, psd, rot)
+    gcat = _gpu_cat(cat)
+    up = torch.ones(gcat.n, dtype=torch.float64, device="cuda")
+    F0, s0, st0, g0 = gw.gw_fisher(gcat, net, 11, gw.GW_MIXED, grad_snr=up)
+    items = gw.work_items(gcat.npts)
+    try:
+        gw.gw_reserve(gcat.n, items, 1)
+        gw.gw_fisher(gcat, net, 11, gw.GW_MIXED, grad_snr=up)      # warm outside capture
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            F1, s1, st1, g1 = gw.gw_fisher(gcat, net, 11, gw.GW_MIXED, grad_snr=up)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(F1, F0) and torch.equal(s1, s0) and torch.equal(g1, g0)
+        assert torch.equal(st1, st0)
+        # too few items reserved: trailing events overflow, the rest are unchanged
+        gw.gw_reserve(gcat.n, items - 7, 1)
+        F2, s2, st2 = gw.gw_fisher(gcat, net, 11, gw.GW_FP64)
+        F3, s3, st3 = gw.gw_fisher(gcat, net, 11, gw.GW_FP64)
+        st2 = st2.cpu().numpy()
+        over = (st2 & gw.ST_OVERFLOW) != 0
+        assert 1 <= over.sum() <= 7 and over[-1] and not over[0]
+        assert np.all(np.isnan(F2.cpu().numpy()[:, over]))
+        gw.gw_reserve(0, 0, 0)
+        F4, s4, st4 = gw.gw_fisher(gcat, net, 11, gw.GW_FP64)
+        assert torch.equal(F2[:, ~torch.as_tensor(over, device="cuda")],
+                           F4[:, ~torch.as_tensor(over, device="cuda")])
+    finally:
+        gw.gw_reserve(0, 0, 0)
