@@ -203,9 +203,13 @@ gw_status gw_snr_vjp(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
 
 /* Vector-Jacobian product of L = sum_e log det Gamma_e with respect to the
  * orientation angle gamma_d of every detector d of the network, by Jacobi's
- * formula dL/dgamma = sum_e tr(C_e d Gamma_e/d gamma).  DEVICE in: cov
+ * formula dL/dgamma = sum_e tr(C_e d Gamma_e/d gamma), with
+ * d Gamma/d gamma = 2 Sym(sum W Re(g'^* g^T)) and g' the tangents of the
+ * detector rotated by 45 degrees times 2 (the pattern functions are linear in
+ * (sin 2 gamma, cos 2 gamma)).  Always FP64 (prec is accepted and ignored): its
+ * accuracy is ~1e-16 times the condition number of Gamma.  DEVICE in: cov
  * (layout of gw_fisher_inverse; events whose cov is NaN are skipped);
- * DEVICE out: grad_gamma [n_det] (overwritten). */
+ * DEVICE out: grad_gamma [n_det] (overwritten).  No counterpart in the paper. */
 gw_status gw_logdet_vjp_detangles(gw_ctx *ctx, const gw_catalog *cat,
                                   const gw_network *net, gw_precision prec, int n_par,
                                   const double *cov, double *grad_gamma, void *stream);

@@ -79,6 +79,7 @@ enum EvSlot : int {
     EV_TE = EV_TM + 8,                  // 8: d tau*/d eta | Mc
     EVC = EV_TE + 8
 };
+constexpr int NCOEF = EVC - EV_PM;   // polynomial coefficients of the point loop
 // B11 = (v^-5, v^-3, v^-2, v^-1, 1, v, v^2, v^5, v^7, ln v, v ln v)
 // B8  = (v^-5, v^-3, v^-2, v^-1, 1, v, v^2, v ln v)
 
@@ -106,7 +107,7 @@ enum Mode : int { MODE_SNR = 0, MODE_FISHER = 1, MODE_SNRGRAD = 2, MODE_LOGDET =
 // points, which amortises the per-lane start and the per-item reduction.
 constexpr int GROUP = 8;
 constexpr int GROUPS_PER_WARP = 32 / GROUP;
-constexpr int PPL_MAX = 32;                   // points per lane per work item (max)
+constexpr int PPL_MAX = 256 / GROUP;          // points per lane per work item (max)
 constexpr int CHUNK_MAX = GROUP * PPL_MAX;    // points per work item (max)
 
 }  // namespace gw

@@ -72,16 +72,6 @@ __device__ __forceinline__ DF df_from_double(double x)
 
 __device__ __forceinline__ float df_round(DF x) { return x.hi + x.lo; }
 
-// sum_q c[q] b[q] in double-float
-template <int N>
-__device__ __forceinline__ DF df_dot(const float2 *c, const DF (&b)[N])
-{
-    DF s = df_mul(df_of(c[N - 1]), b[N - 1]);
-#pragma unroll
-    for (int q = N - 2; q >= 0; q--) s = df_add(s, df_mul(df_of(c[q]), b[q]));
-    return s;
-}
-
 // packed FP32x2 subtraction (sm_100+)
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b)
 {
@@ -106,6 +96,89 @@ __device__ __forceinline__ void acc_pk(float2 &hn, float2 *ln, float2 a, float2 
     const float2 tn = __fadd2_rn(f2sub(hn, f2sub(s, bb)), f2sub(q, bb));
     hn = s;
     *ln = __fadd2_rn(*ln, f2sub(tn, e));
+}
+
+// Compensated dot products sum_q c_q b_q with double-float coefficients and
+// basis values (Dot2 of Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26 (2005)): the high products are summed with
+// error-free transforms (exact product error by an FMA, Knuth's two-sum) and
+// all errors, together with the cross products of high and low parts, are
+// summed into one compensation term.  The result is as accurate as if it were
+// computed in twice the FP32 precision.  dot2_pk evaluates two such sums at
+// once in the two lanes of packed FP32x2 operations: c[q] = (high part of the
+// lane-x coefficient, high part of lane y, low part x, low part y).
+struct DF2 {
+    float2 hi, lo;
+};
+
+template <int N>
+__device__ __forceinline__ DF2 dot2_pk(const float4 *c, const DF (&b)[N], const float (&nb)[N])
+{
+    float4 cq = c[0];
+    float2 ch = make_float2(cq.x, cq.y), cl = make_float2(cq.z, cq.w);
+    float2 bh = make_float2(b[0].hi, b[0].hi);
+    float2 s = __fmul2_rn(ch, bh);
+    float2 comp = __ffma2_rn(ch, make_float2(b[0].lo, b[0].lo),
+                             __ffma2_rn(ch, bh, __fmul2_rn(ch, make_float2(nb[0], nb[0]))));
+    comp = __ffma2_rn(cl, bh, comp);
+#pragma unroll
+    for (int q = 1; q < N; q++) {
+        cq = c[q];
+        ch = make_float2(cq.x, cq.y);
+        cl = make_float2(cq.z, cq.w);
+        bh = make_float2(b[q].hi, b[q].hi);
+        const float2 p = __fmul2_rn(ch, bh);
+        const float2 ne = __ffma2_rn(ch, make_float2(nb[q], nb[q]), p);   // p - c b, exact
+        const float2 t = __fadd2_rn(s, p);
+        const float2 bb = f2sub(t, s);
+        const float2 err = __fadd2_rn(f2sub(s, f2sub(t, bb)), f2sub(p, bb));
+        s = t;
+        comp = __fadd2_rn(comp, f2sub(err, ne));
+        comp = __ffma2_rn(ch, make_float2(b[q].lo, b[q].lo), comp);
+        comp = __ffma2_rn(cl, bh, comp);
+    }
+    return DF2{s, comp};
+}
+
+// scalar form: c[q] = (high part, low part)
+template <int N>
+__device__ __forceinline__ DF dot2_s(const float2 *c, const DF (&b)[N])
+{
+    float2 cq = c[0];
+    float s = cq.x * b[0].hi;
+    float comp = fmaf(cq.x, b[0].lo, fmaf(cq.x, b[0].hi, -s));
+    comp = fmaf(cq.y, b[0].hi, comp);
+#pragma unroll
+    for (int q = 1; q < N; q++) {
+        cq = c[q];
+        const float p = cq.x * b[q].hi;
+        const float e = fmaf(cq.x, b[q].hi, -p);
+        const DF t = two_sum(s, p);
+        s = t.hi;
+        comp += t.lo + e;
+        comp = fmaf(cq.x, b[q].lo, comp);
+        comp = fmaf(cq.y, b[q].hi, comp);
+    }
+    return fast_two_sum(s, comp);
+}
+
+// Layout of a work group's copy of the polynomial coefficients (floats):
+// d Psi/d Mc and d Psi/d eta interleaved for dot2_pk (11 x 4), slots 9 and 10
+// (4 x 4), d tau*/d Mc and d tau*/d eta (8 x 4), tau* as (hi, lo) pairs (8 x 2).
+constexpr int CO_PMPE = 0, CO_P910 = 44, CO_TMTE = 60, CO_T0 = 92;
+static_assert(CO_T0 + 16 == 2 * NCOEF, "coefficient copy layout");
+
+// float offset of component part (0 = high, 1 = low) of slot EV_PM + q
+__device__ __forceinline__ int coef_pos(int q, int part)
+{
+    const int s = EV_PM + q;
+    if (s < EV_PE) return CO_PMPE + 4 * (s - EV_PM) + 2 * part;
+    if (s < EV_P9) return CO_PMPE + 4 * (s - EV_PE) + 2 * part + 1;
+    if (s < EV_P10) return CO_P910 + 4 * (s - EV_P9) + 2 * part;
+    if (s < EV_T0) return CO_P910 + 4 * (s - EV_P10) + 2 * part + 1;
+    if (s < EV_TM) return CO_T0 + 2 * (s - EV_T0) + part;
+    if (s < EV_TE) return CO_TMTE + 4 * (s - EV_TM) + 2 * part;
+    return CO_TMTE + 4 * (s - EV_TE) + 2 * part + 1;
 }
 
 __device__ __forceinline__ int64_t find_event_m(const int64_t *off, int64_t n, int64_t it)
@@ -222,11 +295,15 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
     const int wib = threadIdx.x >> 5;
     const int gid = lane / GROUP, gl = lane % GROUP;
     const unsigned gmask = ((1u << GROUP) - 1u) << (gid * GROUP);
-    // compensation terms of the packed accumulators: lo[a * NT + thread]
-    float2 *mylo = reinterpret_cast<float2 *>(red_f) + threadIdx.x;
-    // per-group copy of the item's event constants (read every point from
-    // shared memory instead of being held in registers across the loop)
-    float2 *cs = reinterpret_cast<float2 *>(red_f) + NACC * NT + (wib * GROUPS_PER_WARP + gid) * EVC;
+    // compensation terms of the packed accumulators: lo[a * LDS + thread]
+    // (row stride LDS = NT + 1 keeps the group reduction free of bank conflicts)
+    constexpr int LDS = NT + 1;
+    float2 *const lo_base = reinterpret_cast<float2 *>(red_f);
+    float2 *mylo = lo_base + threadIdx.x;
+    // per-group copy of the item's polynomial coefficients (slots EV_PM ..
+    // EVC - 1, read every point from shared memory instead of being held in
+    // registers across the loop)
+    float2 *cs = lo_base + ((NACC * LDS + 1) & ~1) + (wib * GROUPS_PER_WARP + gid) * NCOEF;
     const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GROUPS_PER_WARP;
     const DevNet &net = A.net;
     // work count from device memory (no host readback), bounded by the capacity
@@ -242,9 +319,17 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
         const int64_t nj = A.item_off[e + 1] - A.item_off[e];
         const double *E = A.evc + e * (int64_t)EVC;
         const float2 *Eg = A.evc_f + e * (int64_t)EVC;
-        for (int q = gl; q < EVC; q += GROUP) cs[q] = Eg[q];
+        {
+            float *csf = reinterpret_cast<float *>(cs);
+            for (int q = gl; q < NCOEF; q += GROUP) {
+                const float2 c = Eg[EV_PM + q];
+                csf[coef_pos(q, 0)] = c.x;
+                csf[coef_pos(q, 1)] = c.y;
+            }
+        }
         __syncwarp(gmask);
-        const float2 *Ef = cs;
+        const float *cf = reinterpret_cast<const float *>(cs);
+
         const int N = (int)E[EV_NPTS];
         const int kb = (int)((int64_t)N * j / nj), ke = (int)((int64_t)N * (j + 1) / nj);
 
@@ -253,7 +338,7 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
 #pragma unroll
         for (int a = 0; a < NACC; a++) {
             acc[a] = make_float2(0.0f, 0.0f);
-            mylo[a * NT] = make_float2(0.0f, 0.0f);
+            mylo[a * LDS] = make_float2(0.0f, 0.0f);
         }
 
         int k = kb + gl;
@@ -264,17 +349,18 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
             DF v = df_from_double(exp(lnv_d));
             DF vinv = df_from_double(exp(-lnv_d));
             DF lnv = df_from_double(lnv_d);
-            float Aamp = (float)(E[EV_A0] * net.inv_sqrt_scale_ref) *
-                         expf((float)(-7.0 / 6.0 * lnf));
-            const DF rho = df_of(Ef[EV_RHOG]), rhoi = df_of(Ef[EV_RHOIG]);
-            const DF dlnv = df_of(Ef[EV_LNRHOG]);
-            const DF inv_pim = df_of(Ef[EV_INV_PIM]);
-            const float rA = Ef[EV_RAG].x;
-            const float wc0 = Ef[EV_WC0].x, wcm = Ef[EV_WCM].x, wcn = Ef[EV_WCN].x;
-            const float cp = Ef[EV_CP].x, cx = Ef[EV_CX].x;
-            const float dcp = Ef[EV_DCP].x, dcx = Ef[EV_DCX].x;
-            const float c2p = Ef[EV_C2PSI].x, s2p = Ef[EV_S2PSI].x;
-            const float aMc = Ef[EV_AMC].x, invdL = Ef[EV_INVDL].x;
+            // amplitude A0 f^(-7/6) as a double-float recurrence (an FP32 one
+            // would drift by ~1e-6 over a lane's points)
+            DF Aamp = df_from_double(E[EV_A0] * net.inv_sqrt_scale_ref * exp(-7.0 / 6.0 * lnf));
+            const DF rho = df_of(Eg[EV_RHOG]), rhoi = df_of(Eg[EV_RHOIG]);
+            const DF dlnv = df_of(Eg[EV_LNRHOG]);
+            const DF inv_pim = df_of(Eg[EV_INV_PIM]);
+            const DF rA = df_of(Eg[EV_RAG]);
+            const float wc0 = Eg[EV_WC0].x, wcm = Eg[EV_WCM].x, wcn = Eg[EV_WCN].x;
+            const float cp = Eg[EV_CP].x, cx = Eg[EV_CX].x;
+            const float dcp = Eg[EV_DCP].x, dcx = Eg[EV_DCX].x;
+            const float c2p = Eg[EV_C2PSI].x, s2p = Eg[EV_S2PSI].x;
+            const float aMc = Eg[EV_AMC].x, invdL = Eg[EV_INVDL].x;
 
 #pragma unroll 1
             for (; k < ke; k += GROUP) {
@@ -285,28 +371,35 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                 const DF v7 = df_mul(v5, v2), vl = df_mul(v, lnv);
                 const DF one = DF{1.0f, 0.0f};
                 const DF b11[11] = {vi5, vi3, vi2, vinv, one, v, v2, v5, v7, lnv, vl};
+                const float nb11[11] = {-vi5.hi, -vi3.hi, -vi2.hi, -vinv.hi, -1.0f, -v.hi,
+                                        -v2.hi, -v5.hi, -v7.hi, -lnv.hi, -vl.hi};
                 // (the empty asm statements keep the compiler from loading every
                 // coefficient of every polynomial at once, which spills registers)
-                const float dMcf = df_round(df_dot<11>(Ef + EV_PM, b11));
-                asm volatile("" ::: "memory");
-                const float dEtf = df_round(df_dot<11>(Ef + EV_PE, b11));
+                const DF2 pmpe = dot2_pk<11>(reinterpret_cast<const float4 *>(cf + CO_PMPE), b11, nb11);
+                const float dMcf = pmpe.hi.x + pmpe.lo.x;
+                const float dEtf = pmpe.hi.y + pmpe.lo.y;
                 asm volatile("" ::: "memory");
                 float d9 = 0.0f, d10 = 0.0f;
                 if (NP == 11) {
                     const DF b4[4] = {vi2, vinv, v5, v7};
-                    d9 = df_round(df_dot<4>(Ef + EV_P9, b4));
-                    d10 = df_round(df_dot<4>(Ef + EV_P10, b4));
+                    const float nb4[4] = {-vi2.hi, -vinv.hi, -v5.hi, -v7.hi};
+                    const DF2 p910 = dot2_pk<4>(reinterpret_cast<const float4 *>(cf + CO_P910), b4, nb4);
+                    d9 = p910.hi.x + p910.lo.x;
+                    d10 = p910.hi.y + p910.lo.y;
                     asm volatile("" ::: "memory");
                 }
                 DF tau = DF{0.0f, 0.0f};
                 float tMc = 0.0f, tEt = 0.0f;
                 if (ROT) {
                     const DF b8[8] = {vi5, vi3, vi2, vinv, one, v, v2, vl};
-                    tau = df_mul(df_dot<8>(Ef + EV_T0, b8), vi3);
+                    const float nb8[8] = {-vi5.hi, -vi3.hi, -vi2.hi, -vinv.hi, -1.0f, -v.hi,
+                                          -v2.hi, -vl.hi};
+                    tau = df_mul(dot2_s<8>(reinterpret_cast<const float2 *>(cf + CO_T0), b8), vi3);
                     asm volatile("" ::: "memory");
-                    tMc = (float)OMEGA_E * df_round(df_mul(df_dot<8>(Ef + EV_TM, b8), vi3));
-                    asm volatile("" ::: "memory");
-                    tEt = (float)OMEGA_E * df_round(df_mul(df_dot<8>(Ef + EV_TE, b8), vi3));
+                    const DF2 tmte = dot2_pk<8>(reinterpret_cast<const float4 *>(cf + CO_TMTE), b8, nb8);
+                    const float vi3f = df_round(vi3) * (float)OMEGA_E;
+                    tMc = (tmte.hi.x + tmte.lo.x) * vi3f;
+                    tEt = (tmte.hi.y + tmte.lo.y) * vi3f;
                     asm volatile("" ::: "memory");
                 }
                 const DF fdf = df_mul(v3, inv_pim);
@@ -315,6 +408,7 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
 
                 // ---------------- FP32: noise weight and amplitude per PSD
                 const float w = ff * (k == 0 ? wc0 : (k == N - 1 ? wcn : wcm));
+                const float Af = df_round(Aamp);
                 float sig[MAX_PSD];
 #pragma unroll
                 for (int p = 0; p < MAX_PSD; p++) {
@@ -326,7 +420,7 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                             const int pw = net.psd_pow[p][q];
                             S = fmaf(net.psd_coef_f[p][q], pw >= 0 ? ipowf(x, pw) : ipowf(xi, -pw), S);
                         }
-                        sig[p] = Aamp * sqrtf(4.0f * w / S);
+                        sig[p] = Af * sqrtf(4.0f * w / S);
                     } else {
                         sig[p] = 0.0f;
                     }
@@ -390,23 +484,22 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                         float gr[NP], gi[NP], qr, qi, xr, xi, tr, ti;
                         tangents_f<NP, ROT>(pt, sg * cp, sg * cx, sg * dcp, sg * dcx, aMc, invdL,
                                             ph, gr, gi, qr, qi, xr, xi, tr, ti);
-                        // tangents as (real, imaginary) pairs and their negations
-                        float2 G[NP], NG[NP];
+                        // tangents as (real, imaginary) pairs
+                        float2 G[NP];
 #pragma unroll
-                        for (int i = 0; i < NP; i++) {
-                            G[i] = make_float2(gr[i], gi[i]);
-                            NG[i] = make_float2(-gr[i], -gi[i]);
-                        }
+                        for (int i = 0; i < NP; i++) G[i] = make_float2(gr[i], gi[i]);
                         const float2 Q = make_float2(qr, qi);
                         if (MODE == MODE_FISHER) {
                             // Gamma_ij: real and imaginary products summed separately
-                            // (|Q|^2 = the (Phic, Phic) entry, copied at the end)
+                            // (|Q|^2 = the (Phic, Phic) entry, copied at the end); the
+                            // row's tangent is negated once for the whole row
                             int a = 1;
 #pragma unroll
                             for (int i = 0; i < NP; i++) {
+                                const float2 NGi = make_float2(-G[i].x, -G[i].y);
 #pragma unroll
                                 for (int jj = i; jj < NP; jj++) {
-                                    acc_pk(acc[a], mylo + a * NT, G[i], G[jj], NG[jj]);
+                                    acc_pk(acc[a], mylo + a * LDS, G[jj], G[i], NGi);
                                     a++;
                                 }
                                 if (i & 1) asm volatile("" ::: "memory");
@@ -414,63 +507,71 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                             // phase-free SNR-gradient sums (see N_SNRGRAD_X)
                             constexpr int X0 = 1 + NP * (NP + 1) / 2;
                             const float2 X = make_float2(xr, xi), NX = make_float2(-xr, -xi);
-                            const float2 T = make_float2(tr, ti), NT2 = make_float2(-tr, -ti);
-                            acc_pk(acc[X0 + 0], mylo + (X0 + 0) * NT, Q, X, NX);
-                            acc_pk(acc[X0 + 1], mylo + (X0 + 1) * NT,
+                            const float2 T = make_float2(tr, ti);
+                            const float2 NQ = make_float2(-qr, -qi);
+                            acc_pk(acc[X0 + 0], mylo + (X0 + 0) * LDS, Q, X, NX);
+                            acc_pk(acc[X0 + 1], mylo + (X0 + 1) * LDS,
                                    make_float2(ph.tMc * qr, ph.tMc * qi), X, NX);
-                            acc_pk(acc[X0 + 2], mylo + (X0 + 2) * NT,
+                            acc_pk(acc[X0 + 2], mylo + (X0 + 2) * LDS,
                                    make_float2(ph.teta * qr, ph.teta * qi), X, NX);
-                            acc_pk(acc[X0 + 3], mylo + (X0 + 3) * NT, Q, T, NT2);
-                            acc_pk(acc[X0 + 4], mylo + (X0 + 4) * NT, Q, G[5], NG[5]);
-                            acc_pk(acc[X0 + 5], mylo + (X0 + 5) * NT, Q, G[6], NG[6]);
+                            acc_pk(acc[X0 + 3], mylo + (X0 + 3) * LDS, T, Q, NQ);
+                            acc_pk(acc[X0 + 4], mylo + (X0 + 4) * LDS, G[5], Q, NQ);
+                            acc_pk(acc[X0 + 5], mylo + (X0 + 5) * LDS, G[6], Q, NQ);
                         } else if (MODE == MODE_SNR) {
                             const float2 NQ = make_float2(-qr, -qi);
                             acc_pk(acc[0], mylo, Q, Q, NQ);
                             const int dd = net.ifo_det[q];
 #pragma unroll
                             for (int d = 0; d < MAX_DET; d++)
-                                if (d == dd) acc_pk(acc[1 + d], mylo + (1 + d) * NT, Q, Q, NQ);
+                                if (d == dd) acc_pk(acc[1 + d], mylo + (1 + d) * LDS, Q, Q, NQ);
                         } else {   // MODE_SNRGRAD
                             const float2 NQ = make_float2(-qr, -qi);
                             acc_pk(acc[0], mylo, Q, Q, NQ);
 #pragma unroll
                             for (int i = 0; i < 8; i++)
-                                acc_pk(acc[1 + i], mylo + (1 + i) * NT, Q, G[i], NG[i]);
+                                acc_pk(acc[1 + i], mylo + (1 + i) * LDS, G[i], Q, NQ);
                         }
                     }
                 }
                 v = df_mul(v, rho);
                 vinv = df_mul(vinv, rhoi);
                 lnv = df_add(lnv, dlnv);
-                Aamp *= rA;
+                Aamp = df_mul(Aamp, rA);
             }
         }
-        // ---- group reduction: butterfly over the GROUP lanes in double-float
-        // (error-free two-sum of the high parts, compensations added), then
-        // every lane writes the accumulators a = gl (mod GROUP) in FP64
+        // ---- group reduction.  Every lane collapses its (real, imaginary)
+        // accumulators into one double-float value -(hn.x + hn.y + ln.x + ln.y)
+        // and stores it over its compensation slot; then lane gl sums the
+        // GROUP lanes' values of the entries a = gl (mod GROUP) in a fixed
+        // order (error-free two-sum of the high parts, compensations added)
+        // and writes them in FP64.
         double *out = A.partial + it * (int64_t)A.nacc;
         if (MODE == MODE_FISHER) {
             // SNR^2 = sum |Q|^2 = the (Phic, Phic) entry
             constexpr int k88 = 1 + 8 * NP - 8 * 7 / 2;
             acc[0] = acc[k88];
-            mylo[0] = mylo[k88 * NT];
+            mylo[0] = mylo[k88 * LDS];
         }
 #pragma unroll
         for (int a = 0; a < NACC; a++) {
-            // collapse (real, imaginary) parts: value = -(hn.x + hn.y + ln.x + ln.y)
-            const float2 l2 = mylo[a * NT];
+            const float2 l2 = mylo[a * LDS];
             const DF h = two_sum(acc[a].x, acc[a].y);
-            DF s = DF{-h.hi, -((l2.x + l2.y) + h.lo)};
+            mylo[a * LDS] = make_float2(-h.hi, -((l2.x + l2.y) + h.lo));
+        }
+        __syncwarp(gmask);
+        const float2 *grp = lo_base + (threadIdx.x - gl);
+#pragma unroll 1
+        for (int a = gl; a < NACC; a += GROUP) {
+            const float2 *r = grp + a * LDS;
+            float2 v0 = r[0];
+            DF t = DF{v0.x, v0.y};
 #pragma unroll
-            for (int o = 1; o < GROUP; o <<= 1) {
-                const float oh = __shfl_xor_sync(gmask, s.hi, o);
-                const float ol = __shfl_xor_sync(gmask, s.lo, o);
-                // identical operands on both lanes of a pair: same result on both
-                const DF t = (gl & o) ? two_sum(oh, s.hi) : two_sum(s.hi, oh);
-                s.hi = t.hi;
-                s.lo = ((gl & o) ? (ol + s.lo) : (s.lo + ol)) + t.lo;
+            for (int l = 1; l < GROUP; l++) {
+                const float2 u = r[l];
+                const DF h = two_sum(t.hi, u.x);
+                t = DF{h.hi, (t.lo + u.y) + h.lo};
             }
-            if ((a % GROUP) == gl && a < A.nacc) out[a] = (double)s.hi + (double)s.lo;
+            if (a < A.nacc) out[a] = (double)t.hi + (double)t.lo;
         }
         __syncwarp(gmask);
     }
@@ -480,7 +581,7 @@ template <int MODE, int NP, bool ROT>
 cudaError_t launch_one_m(const PointArgs &a, cudaStream_t s)
 {
     constexpr int NACC = NAccM<MODE, NP>::value;
-    const size_t smem = ((size_t)NACC * 128 + (size_t)4 * GROUPS_PER_WARP * EVC) * sizeof(float2);
+    const size_t smem = ((size_t)((NACC * 129 + 1) & ~1) + (size_t)4 * GROUPS_PER_WARP * NCOEF) * sizeof(float2);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t err = cudaFuncSetAttribute(k_points_mixed<MODE, NP, ROT>,
