@@ -152,3 +152,16 @@ def network(config: str):
     """Detector table [n_det, 6], PSD table [n_psd, 11], Earth-rotation flag."""
     net = NETWORKS[config]
     return net["det"].copy(), net["psd"].copy(), net["rotation"]
+
+
+def draw_arm_masks(n: int, n_arms: int, duty: float, seed: int | None = None) -> np.ndarray:
+    """Duty-factor draws (one Bernoulli trial per event and arm): bit a of the
+    returned uint32 mask of event e is set, i.e. arm a of the expanded network
+    (an L-shaped detector is one arm, a triangle three consecutive ones) is on
+    for the whole event, with probability ``duty``, independently."""
+    if not 0 < n_arms <= 32:
+        raise ValueError("1..32 arms")
+    rng = np.random.default_rng(SEED_BASE + 500 if seed is None else seed)
+    on = rng.random((n, n_arms)) < duty
+    return (on.astype(np.uint64) << np.arange(n_arms, dtype=np.uint64)).sum(1).astype(np.uint32)
+

@@ -59,12 +59,14 @@ def _load():
         lib.or_tau_star.restype = d
         lib.or_antenna.argtypes = [d] * 7 + [P, P]
         lib.or_strain.argtypes = [P, d, d, i32, i32, P, i32, P, P, P]
-        lib.or_snr.argtypes = [i64, P, P, P, P, i32, P, i32, P, i32, P, P, P]
-        lib.or_fisher.argtypes = [i64, P, P, P, P, P, i32, P, i32, P, i32, i32, P, P, P, P]
+        lib.or_snr.argtypes = [i64, P, P, P, P, P, i32, P, i32, P, i32, P, P, P]
+        lib.or_fisher.argtypes = [i64, P, P, P, P, P, P, i32, P, i32, P, i32, i32, P, P, P, P]
         lib.or_invert.argtypes = [i64, i32, P, d, P, P, P, P]
-        lib.or_snr_grad.argtypes = [i64, P, P, P, P, P, i32, P, i32, P, i32, i32, P]
-        lib.or_logdet_grad_gamma.argtypes = [i64, P, P, P, P, P, i32, P, i32, P, i32, i32, i32,
+        lib.or_snr_grad.argtypes = [i64, P, P, P, P, P, P, i32, P, i32, P, i32, i32, P]
+        lib.or_logdet_grad_gamma.argtypes = [i64, P, P, P, P, P, P, i32, P, i32, P, i32, i32, i32,
                                              P, d, P, P]
+        if lib.or_abi_version() != 2:
+            raise RuntimeError("stale oracle build: rebuild with oracle.build(force=True)")
         _lib = lib
     return _lib
 
@@ -135,21 +137,26 @@ def strain(ev, fmin, fmax, npts, det, rotation):
 
 
 class Catalog:
-    """Event rows [n,13], parameter set [n], grid (fmin, fmax, npts) per event."""
+    """Event rows [n,13], parameter set [n], grid (fmin, fmax, npts) per event, and
+    optional duty-factor arm masks [n] (bit a = arm a of the expanded network is
+    on; None = every arm on)."""
 
-    def __init__(self, ev, pset, fmin, fmax, npts):
+    def __init__(self, ev, pset, fmin, fmax, npts, arm_mask=None):
         self.ev = _f64(ev).reshape(-1, 13)
         n = self.ev.shape[0]
         self.pset = np.ascontiguousarray(np.broadcast_to(pset, (n,)), dtype=np.int8)
         self.fmin = _f64(np.broadcast_to(fmin, (n,)))
         self.fmax = _f64(np.broadcast_to(fmax, (n,)))
         self.npts = np.ascontiguousarray(np.broadcast_to(npts, (n,)), dtype=np.int32)
+        self.arm_mask = (None if arm_mask is None else
+                         np.ascontiguousarray(np.broadcast_to(arm_mask, (n,)), dtype=np.uint32))
 
     def __len__(self):
         return self.ev.shape[0]
 
     def subset(self, idx):
-        return Catalog(self.ev[idx], self.pset[idx], self.fmin[idx], self.fmax[idx], self.npts[idx])
+        return Catalog(self.ev[idx], self.pset[idx], self.fmin[idx], self.fmax[idx], self.npts[idx],
+                       None if self.arm_mask is None else self.arm_mask[idx])
 
 
 def snr(cat: Catalog, det, psd, rotation, per_arm=False):
@@ -160,7 +167,8 @@ def snr(cat: Catalog, det, psd, rotation, per_arm=False):
     out = np.empty(n)
     arm = np.empty((n, na)) if per_arm else None
     st = np.empty(n, dtype=np.int32)
-    _load().or_snr(n, _p(cat.ev), _p(cat.fmin), _p(cat.fmax), _p(cat.npts), det.shape[0],
+    _load().or_snr(n, _p(cat.ev), _p(cat.fmin), _p(cat.fmax), _p(cat.npts), _p(cat.arm_mask),
+                   det.shape[0],
                    _p(det), psd.shape[0], _p(psd), int(rotation), _p(out), _p(arm), _p(st))
     return (out, arm, st) if per_arm else (out, st)
 
@@ -175,7 +183,7 @@ def fisher(cat: Catalog, det, psd, rotation, n_par):
     err = np.empty(n)
     st = np.empty(n, dtype=np.int32)
     _load().or_fisher(n, _p(cat.ev), _p(cat.pset), _p(cat.fmin), _p(cat.fmax), _p(cat.npts),
-                      det.shape[0], _p(det), psd.shape[0], _p(psd), int(rotation), n_par,
+                      _p(cat.arm_mask), det.shape[0], _p(det), psd.shape[0], _p(psd), int(rotation), n_par,
                       _p(F), _p(s), _p(err), _p(st))
     return F, s, err, st
 
@@ -199,7 +207,7 @@ def snr_grad(cat: Catalog, det, psd, rotation, n_par):
     n = len(cat)
     g = np.empty((n, n_par))
     _load().or_snr_grad(n, _p(cat.ev), _p(cat.pset), _p(cat.fmin), _p(cat.fmax), _p(cat.npts),
-                        det.shape[0], _p(det), psd.shape[0], _p(psd), int(rotation), n_par, _p(g))
+                        _p(cat.arm_mask), det.shape[0], _p(det), psd.shape[0], _p(psd), int(rotation), n_par, _p(g))
     return g
 
 
@@ -213,7 +221,16 @@ def logdet_grad_gamma(cat: Catalog, det, psd, rotation, n_par, dets, step0=0.05)
     g = np.empty(len(dets))
     ld = np.empty(n)
     _load().or_logdet_grad_gamma(n, _p(cat.ev), _p(cat.pset), _p(cat.fmin), _p(cat.fmax),
-                                 _p(cat.npts), det.shape[0], _p(det), psd.shape[0], _p(psd),
+                                 _p(cat.npts), _p(cat.arm_mask), det.shape[0], _p(det), psd.shape[0], _p(psd),
                                  int(rotation), n_par, len(dets), _p(dets), float(step0),
                                  _p(g), _p(ld))
     return g, ld
+
+
+def select_snr(snr, threshold):
+    """Detection gate (Sec. 5, the snr_th option): the indices, in increasing
+    order, of the events whose network SNR exceeds the threshold; Fisher
+    matrices are computed for these events only.  NaN SNRs are never selected."""
+    snr = np.asarray(snr, dtype=np.float64)
+    return np.flatnonzero(snr > threshold).astype(np.int64)
+

@@ -28,6 +28,10 @@
  *                        (Sec. 3.1 footnote on Earth motion).
  *   or_snr ............. SNR_i^2 = 4 int |h|^2/S_n df; network sum in quadrature
  *                        (Sec. 3.2, Eqs. (3.1)-(3.2)); trapezoid on the log grid.
+ *                        SNR, Fisher and the two VJP references take optional
+ *                        per-event arm masks: the duty factor (Sec. 3.2, and the
+ *                        duty_factor option of Sec. 5), applied to each detector
+ *                        and to each arm of a triangle separately.
  *   or_fisher .......... Gamma_ij = 4 int Re(d_i h d_j h*)/S_n df, summed over
  *                        detectors and triangle arms (Sec. 3.2, Eq. (3.3)).
  *   or_invert .......... normalise by sqrt(diag), Cholesky inverse, condition
@@ -106,6 +110,19 @@ static int expand_arms(int ndet, const double *det, arm_t *arms, int maxarms)
         }
     }
     return na;
+}
+
+/* Duty factor (Sec. 3.2 and the duty_factor option of Sec. 5): each detector,
+ * and each arm of a triangle separately, is on or off for a whole event.  The
+ * arms of event e that are on are the bits of arm_mask[e] (bit a = arm a of
+ * the expanded list above); arm_mask == NULL means every arm is on.  The
+ * random draws are made by the caller and passed in.                       */
+static int select_arms(const arm_t *all, int na, const uint32_t *arm_mask, int64_t e, arm_t *out)
+{
+    int m = 0;
+    for (int a = 0; a < na; a++)
+        if (!arm_mask || ((arm_mask[e] >> a) & 1u)) out[m++] = all[a];
+    return m;
 }
 
 static ld psd_eval(const double *psd, int idx, ld f)
@@ -367,13 +384,14 @@ static ld snr2_event(const ld *th, ld tc_fid, ld fmin, ld fmax, int npts, int na
 }
 
 int or_snr(int64_t n, const double *ev, const double *fmin, const double *fmax,
-           const int32_t *npts, int ndet, const double *det, int npsd, const double *psd,
-           int rotation, double *snr, double *snr_arm, int32_t *status)
+           const int32_t *npts, const uint32_t *arm_mask, int ndet, const double *det,
+           int npsd, const double *psd, int rotation, double *snr, double *snr_arm,
+           int32_t *status)
 {
     (void)npsd;
-    arm_t arms[64];
-    int na = expand_arms(ndet, det, arms, 64);
-    if (na < 0) return -1;
+    arm_t all[64], arms[64];
+    int na = expand_arms(ndet, det, all, 64);
+    if (na < 0 || (arm_mask && na > 32)) return -1;
     ld per[64];
     for (int64_t e = 0; e < n; e++) {
         ld th[N_ALL]; load_event(ev + N_ALL * e, th);
@@ -384,9 +402,14 @@ int or_snr(int64_t n, const double *ev, const double *fmin, const double *fmax,
             if (snr_arm) for (int a = 0; a < na; a++) snr_arm[(size_t)e * na + a] = NAN;
             continue;
         }
-        ld s2 = snr2_event(th, th[I_TC], fmin[e], fmax[e], npts[e], na, arms, psd, rotation, per);
+        int non = select_arms(all, na, arm_mask, e, arms);
+        ld s2 = snr2_event(th, th[I_TC], fmin[e], fmax[e], npts[e], non, arms, psd, rotation, per);
         snr[e] = (double)sqrtl(s2);
-        if (snr_arm) for (int a = 0; a < na; a++) snr_arm[(size_t)e * na + a] = (double)sqrtl(per[a]);
+        if (snr_arm)
+            for (int a = 0, b = 0; a < na; a++) {
+                int on = !arm_mask || ((arm_mask[e] >> a) & 1u);
+                snr_arm[(size_t)e * na + a] = on ? (double)sqrtl(per[b++]) : 0.0;
+            }
     }
     return na;
 }
@@ -534,14 +557,14 @@ static int fisher_event(const ld *th, ld tc_fid, ld fmin, ld fmax, int npts, int
 /* exported Fisher: ev [n][13], pset [n]; out fisher [n][P][P] (full), snr [n],
  * fd_relerr [n] (largest Richardson error bar relative to |d_i h|, or NULL)   */
 int or_fisher(int64_t n, const double *ev, const int8_t *pset, const double *fmin,
-              const double *fmax, const int32_t *npts, int ndet, const double *det,
-              int npsd, const double *psd, int rotation, int n_par,
+              const double *fmax, const int32_t *npts, const uint32_t *arm_mask, int ndet,
+              const double *det, int npsd, const double *psd, int rotation, int n_par,
               double *fisher, double *snr, double *fd_relerr, int32_t *status)
 {
     (void)npsd;
-    arm_t arms[64];
-    int na = expand_arms(ndet, det, arms, 64);
-    if (na < 0) return -1;
+    arm_t all[64], arms[64];
+    int na = expand_arms(ndet, det, all, 64);
+    if (na < 0 || (arm_mask && na > 32)) return -1;
     ld G[16 * 16];
     for (int64_t e = 0; e < n; e++) {
         ld th[N_ALL]; load_event(ev + N_ALL * e, th);
@@ -557,9 +580,13 @@ int or_fisher(int64_t n, const double *ev, const int8_t *pset, const double *fmi
             if (fd_relerr) fd_relerr[e] = NAN;
             continue;
         }
-        ld s2, re;
-        fisher_event(th, th[I_TC], fmin[e], fmax[e], npts[e], P, slot, na, arms, psd, rotation,
-                     NULL, NULL, G, &s2, &re);
+        ld s2 = 0, re = 0;
+        int non = select_arms(all, na, arm_mask, e, arms);
+        if (non > 0)
+            fisher_event(th, th[I_TC], fmin[e], fmax[e], npts[e], P, slot, non, arms, psd,
+                         rotation, NULL, NULL, G, &s2, &re);
+        else   /* every arm off: no signal, no information */
+            for (int i = 0; i < P * P; i++) G[i] = 0;
         for (int i = 0; i < P * P; i++) Fo[i] = (double)G[i];
         snr[e] = (double)sqrtl(s2);
         if (fd_relerr) fd_relerr[e] = (double)re;
@@ -691,13 +718,14 @@ int or_invert(int64_t n, int P, const double *fisher, double cond_max, double *c
 
 /* d SNR / d theta_i for the event's Fisher parameters; out grad [n][P]  */
 int or_snr_grad(int64_t n, const double *ev, const int8_t *pset, const double *fmin,
-                const double *fmax, const int32_t *npts, int ndet, const double *det,
-                int npsd, const double *psd, int rotation, int n_par, double *grad)
+                const double *fmax, const int32_t *npts, const uint32_t *arm_mask, int ndet,
+                const double *det, int npsd, const double *psd, int rotation, int n_par,
+                double *grad)
 {
     (void)npsd;
-    arm_t arms[64];
-    int na = expand_arms(ndet, det, arms, 64);
-    if (na < 0) return -1;
+    arm_t all[64], arms[64];
+    int na = expand_arms(ndet, det, all, 64);
+    if (na < 0 || (arm_mask && na > 32)) return -1;
     for (int64_t e = 0; e < n; e++) {
         ld th[N_ALL]; load_event(ev + N_ALL * e, th);
         int slot[16];
@@ -708,6 +736,7 @@ int or_snr_grad(int64_t n, const double *ev, const int8_t *pset, const double *f
             continue;
         }
         ld tc_fid = th[I_TC];
+        int non = select_arms(all, na, arm_mask, e, arms);
         for (int i = 0; i < P; i++) {
             int s = slot[i];
             ld d0;
@@ -725,8 +754,8 @@ int or_snr_grad(int64_t n, const double *ev, const int8_t *pset, const double *f
                 ld tp[N_ALL], tm[N_ALL];
                 memcpy(tp, th, sizeof tp); memcpy(tm, th, sizeof tm);
                 tp[s] += d; tm[s] -= d;
-                ld sp = sqrtl(snr2_event(tp, tc_fid, fmin[e], fmax[e], npts[e], na, arms, psd, rotation, NULL));
-                ld sm = sqrtl(snr2_event(tm, tc_fid, fmin[e], fmax[e], npts[e], na, arms, psd, rotation, NULL));
+                ld sp = sqrtl(snr2_event(tp, tc_fid, fmin[e], fmax[e], npts[e], non, arms, psd, rotation, NULL));
+                ld sm = sqrtl(snr2_event(tm, tc_fid, fmin[e], fmax[e], npts[e], non, arms, psd, rotation, NULL));
                 R[m][0] = (sp - sm) / (tp[s] - tm[s]);
             }
             for (int j = 1; j < RICH_LEVELS; j++)
@@ -773,14 +802,15 @@ static ld logdet_l(int P, const ld *G)
  * so the differenced quantity is one smooth function of gamma.
  * out: grad [n_d]; logdet [n] (fiducial, may be NULL)                     */
 int or_logdet_grad_gamma(int64_t n, const double *ev, const int8_t *pset, const double *fmin,
-                         const double *fmax, const int32_t *npts, int ndet, const double *det,
-                         int npsd, const double *psd, int rotation, int n_par, int n_d,
-                         const int32_t *dets, double step0, double *grad, double *logdet)
+                         const double *fmax, const int32_t *npts, const uint32_t *arm_mask,
+                         int ndet, const double *det, int npsd, const double *psd, int rotation,
+                         int n_par, int n_d, const int32_t *dets, double step0, double *grad,
+                         double *logdet)
 {
     (void)npsd;
-    arm_t arms[64];
-    int na = expand_arms(ndet, det, arms, 64);
-    if (na < 0) return -1;
+    arm_t all[64], arms[64];
+    int na = expand_arms(ndet, det, all, 64);
+    if (na < 0 || (arm_mask && na > 32)) return -1;
     double *dcopy = malloc(sizeof(double) * 6 * ndet);
     ld G[256];
     for (int q = 0; q < n_d; q++) grad[q] = 0;
@@ -794,7 +824,8 @@ int or_logdet_grad_gamma(int64_t n, const double *ev, const int8_t *pset, const 
             continue;
         }
         ld steps[16], s2;
-        fisher_event(th, th[I_TC], fmin[e], fmax[e], npts[e], P, slot, na, arms, psd, rotation,
+        int non = select_arms(all, na, arm_mask, e, arms);
+        fisher_event(th, th[I_TC], fmin[e], fmax[e], npts[e], P, slot, non, arms, psd, rotation,
                      NULL, steps, G, &s2, NULL);
         if (logdet) logdet[e] = (double)logdet_l(P, G);
         for (int q = 0; q < n_d; q++) {
@@ -804,15 +835,16 @@ int or_logdet_grad_gamma(int64_t n, const double *ev, const int8_t *pset, const 
                 ld vals[2], span_p = 0, span_m = 0;
                 for (int sgn = 0; sgn < 2; sgn++) {
                     memcpy(dcopy, det, sizeof(double) * 6 * ndet);
-                    arm_t a2[64];
-                    int na2 = expand_arms(ndet, dcopy, a2, 64);
+                    arm_t a2[64], a2on[64];
+                    expand_arms(ndet, dcopy, a2, 64);
                     /* shift the orientation of every arm of detector dets[q] */
                     int first = 0;
                     for (int dd = 0; dd < dets[q]; dd++) first += ((int)det[6 * dd + 4] == 0) ? 1 : 3;
                     int cnt = ((int)det[6 * dets[q] + 4] == 0) ? 1 : 3;
                     for (int a = first; a < first + cnt; a++) a2[a].gam += (sgn == 0 ? d : -d);
                     if (sgn == 0) span_p = a2[first].gam; else span_m = a2[first].gam;
-                    fisher_event(th, th[I_TC], fmin[e], fmax[e], npts[e], P, slot, na2, a2, psd,
+                    int non2 = select_arms(a2, na, arm_mask, e, a2on);
+                    fisher_event(th, th[I_TC], fmin[e], fmax[e], npts[e], P, slot, non2, a2on, psd,
                                  rotation, steps, NULL, G, &s2, NULL);
                     vals[sgn] = logdet_l(P, G);
                 }
@@ -829,7 +861,7 @@ int or_logdet_grad_gamma(int64_t n, const double *ev, const int8_t *pset, const 
 }
 
 /* version tag so the Python side can check the build matches */
-int or_abi_version(void) { return 1; }
+int or_abi_version(void) { return 2; }
 
 /* grid length by the points-per-e-fold rule, clamped: N = clamp(ceil(k ln(fmax/fmin)), lo, hi) */
 int or_grid_npts(int64_t n, const double *fmin, const double *fmax, double per_efold,

@@ -12,31 +12,31 @@ _POOL = None
 
 def _worker_fisher(args):
     import oracle
-    ev, pset, fmin, fmax, npts, det, psd, rot, n_par = args
-    cat = oracle.Catalog(ev, pset, fmin, fmax, npts)
+    ev, pset, fmin, fmax, npts, mask, det, psd, rot, n_par = args
+    cat = oracle.Catalog(ev, pset, fmin, fmax, npts, mask)
     F, s, err, st = oracle.fisher(cat, det, psd, rot, n_par)
     return F[0], s[0], err[0], st[0]
 
 
 def _worker_snr(args):
     import oracle
-    ev, pset, fmin, fmax, npts, det, psd, rot = args
-    cat = oracle.Catalog(ev, pset, fmin, fmax, npts)
+    ev, pset, fmin, fmax, npts, mask, det, psd, rot = args
+    cat = oracle.Catalog(ev, pset, fmin, fmax, npts, mask)
     s, arm, st = oracle.snr(cat, det, psd, rot, per_arm=True)
     return s[0], arm[0], st[0]
 
 
 def _worker_grad(args):
     import oracle
-    ev, pset, fmin, fmax, npts, det, psd, rot, n_par = args
-    cat = oracle.Catalog(ev, pset, fmin, fmax, npts)
+    ev, pset, fmin, fmax, npts, mask, det, psd, rot, n_par = args
+    cat = oracle.Catalog(ev, pset, fmin, fmax, npts, mask)
     return oracle.snr_grad(cat, det, psd, rot, n_par)[0]
 
 
 def _worker_logdet(args):
     import oracle
-    ev, pset, fmin, fmax, npts, det, psd, rot, n_par, dets = args
-    cat = oracle.Catalog(ev, pset, fmin, fmax, npts)
+    ev, pset, fmin, fmax, npts, mask, det, psd, rot, n_par, dets = args
+    cat = oracle.Catalog(ev, pset, fmin, fmax, npts, mask)
     g, ld = oracle.logdet_grad_gamma(cat, det, psd, rot, n_par, dets)
     return g, ld[0]
 
@@ -51,7 +51,8 @@ def pool():
 
 
 def _tasks(cat, extra):
-    return [(cat.ev[e], cat.pset[e], cat.fmin[e], cat.fmax[e], cat.npts[e], *extra)
+    return [(cat.ev[e], cat.pset[e], cat.fmin[e], cat.fmax[e], cat.npts[e],
+             None if cat.arm_mask is None else cat.arm_mask[e], *extra)
             for e in range(len(cat))]
 
 

@@ -462,3 +462,105 @@ def test_logdet_grad_gamma_matches_jacobi_formula():
               - (fisher_at(det[di, 2] + 2 * h) - fisher_at(det[di, 2] - 2 * h))) / (12 * h)
         jac = np.trace(Finv @ dG)
         assert abs(gg[q] - jac) < 1e-4 * (abs(jac) + 1)
+
+
+# ---------------------------------------------------------------- duty factor
+def _masked(cat, masks):
+    return oracle.Catalog(cat.ev, cat.pset, cat.fmin, cat.fmax, cat.npts, masks)
+
+
+def test_arm_masks_snr_is_quadrature_sum_of_on_arms():
+    """Duty factor (Sec. 3.2; the duty_factor option of Sec. 5, applied to every
+    detector and to each arm of a triangle): the network SNR^2 of an event is the
+    sum of the SNR^2 of the arms that are on (Eq. (3.2)); the per-arm SNR of an
+    arm that is on does not depend on the others; no arm on gives zero."""
+    cat, _, _ = oracle_catalog("c4", 6, seed=31, max_npts=150)
+    det, psd, rot = gwcat.network("c4")
+    na = oracle.n_arms(det)
+    assert na == 5
+    s0, arm0, _ = oracle.snr(cat, det, psd, rot, per_arm=True)
+    masks = np.array([0b11111, 0b00001, 0b00110, 0b11000, 0, 0b10101], dtype=np.uint32)
+    s1, arm1, st1 = oracle.snr(_masked(cat, masks), det, psd, rot, per_arm=True)
+    assert (st1 == 0).all()
+    for e in range(len(masks)):
+        on = [(int(masks[e]) >> a) & 1 for a in range(na)]
+        expect2 = sum(arm0[e, a] ** 2 for a in range(na) if on[a])
+        assert abs(s1[e] ** 2 - expect2) <= 1e-13 * s0[e] ** 2
+        for a in range(na):
+            assert arm1[e, a] == (arm0[e, a] if on[a] else 0.0)
+    assert s1[0] == s0[0] and s1[4] == 0.0
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_masked_triangle_arm_equals_standalone_interferometer(k):
+    """A triangle is three co-located 60-degree interferometers (Sec. 3.3): with
+    only arm k on, SNR and Fisher equal those of a network that holds just an
+    L-shaped detector of opening 60 degrees at bisector gamma_T + 30 + 120 k deg."""
+    cat, _, _ = oracle_catalog("c1", 2, seed=5, max_npts=120)
+    det, psd, rot = gwcat.network("c1")
+    tri = det[0]
+    F1, s1, _, st1 = oracle.fisher(_masked(cat, np.uint32(1 << k)), det, psd, rot, 11)
+    solo = np.array([[tri[0], tri[1], tri[2] + math.pi / 6 + 2 * math.pi * k / 3, math.pi / 3,
+                      0, tri[5]]])
+    F2, s2, _, st2 = oracle.fisher(cat, solo, psd, rot, 11)
+    assert (st1 == 0).all() and (st2 == 0).all()
+    np.testing.assert_allclose(s1, s2, rtol=1e-13)
+    for e in range(2):
+        sc = np.sqrt(np.outer(np.diag(F2[e]), np.diag(F2[e])))
+        assert np.max(np.abs(F1[e] - F2[e]) / sc) < 1e-9
+
+
+def test_fisher_additive_over_disjoint_arm_sets():
+    """Gamma is a sum over detectors and arms (Eq. (3.3)): for disjoint arm sets A
+    and B, Gamma(A u B) = Gamma(A) + Gamma(B) (to the finite-difference error bar,
+    as each set picks its own steps); with no arm on Gamma = 0 and SNR = 0."""
+    cat, _, _ = oracle_catalog("c4", 3, seed=41, max_npts=120)
+    det, psd, rot = gwcat.network("c4")
+    FA, sA, _, _ = oracle.fisher(_masked(cat, np.uint32(0b00101)), det, psd, rot, 11)
+    FB, sB, _, _ = oracle.fisher(_masked(cat, np.uint32(0b11010)), det, psd, rot, 11)
+    F, s, _, _ = oracle.fisher(cat, det, psd, rot, 11)
+    F0, s0, _, st0 = oracle.fisher(_masked(cat, np.uint32(0)), det, psd, rot, 11)
+    np.testing.assert_allclose(sA ** 2 + sB ** 2, s ** 2, rtol=1e-13)
+    for e in range(3):
+        sc = np.sqrt(np.outer(np.diag(F[e]), np.diag(F[e])))
+        assert np.max(np.abs(FA[e] + FB[e] - F[e]) / sc) < 1e-8
+    assert (st0 == 0).all() and (F0 == 0).all() and (s0 == 0).all()
+
+
+def test_masked_snr_gradient_closed_forms():
+    """With any set of arms on, h is proportional to 1/dL, so d SNR / d dL = -SNR/dL;
+    SNR does not depend on Phic (h -> h e^{-i dPhic})."""
+    cat, _, _ = oracle_catalog("c4", 2, seed=43, max_npts=100)
+    det, psd, rot = gwcat.network("c4")
+    masks = np.array([0b01010, 0b10001], dtype=np.uint32)
+    mc = _masked(cat, masks)
+    g = oracle.snr_grad(mc, det, psd, rot, 11)
+    s, _ = oracle.snr(mc, det, psd, rot)
+    np.testing.assert_allclose(g[:, 2], -s / cat.ev[:, 2], rtol=1e-9)
+    assert np.all(np.abs(g[:, 8]) <= 1e-9 * s)
+
+
+def test_masked_off_detector_has_no_orientation_gradient():
+    """A detector that is off for every event contributes nothing to any Fisher
+    matrix, so d(sum log det Gamma)/d gamma of that detector is exactly zero,
+    while the detectors that are on keep their gradient."""
+    cat, _, _ = oracle_catalog("c4", 2, seed=47, max_npts=100)
+    det, psd, rot = gwcat.network("c4")
+    mc = _masked(cat, np.uint32(0b01111))          # triangle + first L on, second L off
+    g, ldet = oracle.logdet_grad_gamma(mc, det, psd, rot, 11, [1, 2])
+    assert np.isfinite(ldet).all()
+    assert g[1] == 0.0 and g[0] != 0.0
+
+
+def test_snr_gate_selection_brute_force():
+    """The detection gate (Sec. 5, snr_th) keeps exactly the events with SNR above
+    the threshold, in catalog order; NaN (flagged) events and SNR == threshold
+    are dropped.  Checked against a plain loop."""
+    rng = np.random.default_rng(3)
+    snr = rng.uniform(0, 30, 500)
+    snr[::37] = np.nan
+    snr[5] = 12.0
+    idx = oracle.select_snr(snr, 12.0)
+    brute = [e for e in range(len(snr)) if snr[e] == snr[e] and snr[e] > 12.0]
+    assert idx.tolist() == brute and idx.dtype == np.int64
+    assert oracle.select_snr(np.array([]), 1.0).size == 0
