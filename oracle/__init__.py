@@ -26,6 +26,7 @@ PARAMS = ("Mc", "eta", "dL", "theta", "phi", "iota", "psi", "tc", "Phic",
           "chi1z", "chi2z", "LamT", "dLamT")
 
 ST_NOT_PD, ST_COND_GT_MAX, ST_NONFINITE, ST_EMPTY_GRID, ST_BAD_PARAM, ST_ILL_COND = 1, 2, 4, 8, 16, 32
+ST_SVD_FALLBACK = 128
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gw_oracle.c")
@@ -65,7 +66,10 @@ def _load():
         lib.or_snr_grad.argtypes = [i64, P, P, P, P, P, P, i32, P, i32, P, i32, i32, P]
         lib.or_logdet_grad_gamma.argtypes = [i64, P, P, P, P, P, P, i32, P, i32, P, i32, i32, i32,
                                              P, d, P, P]
-        if lib.or_abi_version() != 2:
+        lib.or_fisher_eig.argtypes = [i64, i32, P, i32, P, P]
+        lib.or_covariance.argtypes = [i64, i32, P, ctypes.c_uint32, P, i32, d, d, P, P, P, P]
+        lib.or_sky_area.argtypes = [i64, i32, P, i32, i32, P, d, i32, P]
+        if lib.or_abi_version() != 3:
             raise RuntimeError("stale oracle build: rebuild with oracle.build(force=True)")
         _lib = lib
     return _lib
@@ -233,4 +237,50 @@ def select_snr(snr, threshold):
     matrices are computed for these events only.  NaN SNRs are never selected."""
     snr = np.asarray(snr, dtype=np.float64)
     return np.flatnonzero(snr > threshold).astype(np.int64)
+
+
+# inversion methods of covariance() (the invMethodIn options of Sec. 4.1)
+INV_CHO, INV_CHO_SVD, INV_SVD, INV_SVD_TRUNC, INV_SVD_REG, INV_LU = range(6)
+
+
+def fisher_eig(F, normalize=True):
+    """Eigenvalues [n, P] (ascending) and eigenvectors [n, P, P] (columns) of each
+    Fisher matrix, normalised by sqrt(diag) if ``normalize`` (CheckFisher)."""
+    F = _f64(F)
+    n, P, _ = F.shape
+    w = np.empty((n, P))
+    V = np.empty((n, P, P))
+    _load().or_fisher_eig(n, P, _p(F), int(normalize), _p(w), _p(V))
+    return w, V
+
+
+def covariance(F, keep=None, prior=None, method=INV_CHO_SVD, thresh=1e-15, cond_max=1e50):
+    """CovMatr with fixParams (``keep``: indices of the parameters kept) and
+    addPrior (``prior``: [P] values added to the diagonal of kept parameters).
+    Returns cov [n, Pk, Pk], condition number, inversion error, status."""
+    F = _f64(F)
+    n, P, _ = F.shape
+    keep = list(range(P)) if keep is None else sorted(keep)
+    mask = 0
+    for i in keep:
+        mask |= 1 << int(i)
+    Pk = len(keep)
+    C = np.empty((n, Pk, Pk))
+    k = np.empty(n)
+    e = np.empty(n)
+    st = np.empty(n, dtype=np.int32)
+    pr = None if prior is None else _f64(prior)
+    _load().or_covariance(n, P, _p(F), mask, _p(pr), int(method), float(thresh), float(cond_max),
+                          _p(C), _p(k), _p(e), _p(st))
+    return C, k, e, st
+
+
+def sky_area(C, i_theta, i_phi, theta, perc=90.0, units="SqDeg"):
+    """Delta Omega_perc% of each event (Sec. 4.1), 'SqDeg' or 'Sterad'."""
+    C = _f64(C)
+    n, P, _ = C.shape
+    out = np.empty(n)
+    _load().or_sky_area(n, P, _p(C), int(i_theta), int(i_phi), _p(_f64(theta)), float(perc),
+                        1 if units == "SqDeg" else 0, _p(out))
+    return out
 

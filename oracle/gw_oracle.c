@@ -40,6 +40,12 @@
  *   or_snr_grad ........ d SNR / d theta_i by Richardson differences of SNR.
  *   or_logdet_grad_gamma d (sum_e log det Gamma_e) / d gamma_d by Richardson
  *                        differences over the detector orientation.
+ *   or_fisher_eig ...... eigenvalues / eigenvectors of the (normalised) Fisher
+ *                        matrix (CheckFisher, Sec. 4.1), cyclic Jacobi.
+ *   or_covariance ...... CovMatr with its inversion methods (Cholesky, Cholesky
+ *                        with SVD fallback, SVD, truncated SVD, svd_reg, LU),
+ *                        fixParams and addPrior (Secs. 4.1-4.2).
+ *   or_sky_area ........ Delta Omega_X% (Sec. 4.1, the localisation formula).
  *
  * Conventions (the paper gives none of these formulas; they are fixed here):
  *   h = Q exp(i Phi),  Q = A [F+ (1+cos^2 iota)/2 + i Fx cos iota],
@@ -83,7 +89,7 @@ enum { I_MC, I_ETA, I_DL, I_TH, I_PH, I_IOTA, I_PSI, I_TC, I_PHIC,
 
 /* status bits (shared meaning with the library, defined independently) */
 enum { ST_NOT_PD = 1, ST_COND_GT_MAX = 2, ST_NONFINITE = 4, ST_EMPTY_GRID = 8,
-       ST_BAD_PARAM = 16, ST_ILL_COND = 32 };
+       ST_BAD_PARAM = 16, ST_ILL_COND = 32, ST_SVD_FALLBACK = 128 };
 
 /* ------------------------------------------------------------------ */
 /* detector table: per detector 6 doubles  lat, lon, gamma, zeta, shape, psd  */
@@ -714,6 +720,277 @@ int or_invert(int64_t n, int P, const double *fisher, double cond_max, double *c
 }
 
 /* ------------------------------------------------------------------ */
+/* Covariance tools (Sec. 4.1 and the manipulations listed in Sec. 4.2)  */
+
+/* cyclic Jacobi with eigenvectors: A = V diag(w) V^T (A destroyed; V[i*P+k] =
+ * component i of eigenvector k); eigenpairs sorted by increasing w and each
+ * eigenvector's largest-magnitude component made positive              */
+static void jacobi_eigv(int P, ld *A, ld *w, ld *V)
+{
+    for (int i = 0; i < P * P; i++) V[i] = 0;
+    for (int i = 0; i < P; i++) V[i * P + i] = 1;
+    for (int sweep = 0; sweep < 100; sweep++) {
+        ld off = 0, tot = 0;
+        for (int i = 0; i < P; i++)
+            for (int j = 0; j < P; j++) {
+                tot += A[i * P + j] * A[i * P + j];
+                if (i != j) off += A[i * P + j] * A[i * P + j];
+            }
+        if (off <= 1e-64L * tot) break;
+        for (int p = 0; p < P; p++)
+            for (int q = p + 1; q < P; q++) {
+                ld apq = A[p * P + q];
+                if (apq == 0) continue;
+                ld tau = (A[q * P + q] - A[p * P + p]) / (2.0L * apq);
+                ld t = (tau >= 0 ? 1.0L : -1.0L) / (fabsl(tau) + sqrtl(1.0L + tau * tau));
+                ld c = 1.0L / sqrtl(1.0L + t * t), sn = t * c;
+                for (int k = 0; k < P; k++) {
+                    ld akp = A[k * P + p], akq = A[k * P + q];
+                    A[k * P + p] = c * akp - sn * akq;
+                    A[k * P + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < P; k++) {
+                    ld apk = A[p * P + k], aqk = A[q * P + k];
+                    A[p * P + k] = c * apk - sn * aqk;
+                    A[q * P + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < P; k++) {
+                    ld vkp = V[k * P + p], vkq = V[k * P + q];
+                    V[k * P + p] = c * vkp - sn * vkq;
+                    V[k * P + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < P; i++) w[i] = A[i * P + i];
+    for (int a = 0; a < P; a++) {              /* selection sort, ascending */
+        int m = a;
+        for (int b = a + 1; b < P; b++) if (w[b] < w[m]) m = b;
+        if (m != a) {
+            ld t = w[a]; w[a] = w[m]; w[m] = t;
+            for (int i = 0; i < P; i++) { t = V[i * P + a]; V[i * P + a] = V[i * P + m]; V[i * P + m] = t; }
+        }
+    }
+    for (int k = 0; k < P; k++) {
+        int im = 0;
+        for (int i = 1; i < P; i++) if (fabsl(V[i * P + k]) > fabsl(V[im * P + k])) im = i;
+        if (V[im * P + k] < 0) for (int i = 0; i < P; i++) V[i * P + k] = -V[i * P + k];
+    }
+}
+
+/* Eigenvalues (ascending) and eigenvectors of each Fisher matrix, optionally
+ * of the matrix normalised by sqrt(diag) (CheckFisher, Sec. 4.1).
+ * in: fisher [n][P][P]; out: w [n][P], V [n][P][P] (V[e][i][k] = component i
+ * of eigenvector k), either may be NULL.                                 */
+int or_fisher_eig(int64_t n, int P, const double *fisher, int normalize, double *w, double *V)
+{
+    for (int64_t e = 0; e < n; e++) {
+        const double *G = fisher + (size_t)e * P * P;
+        ld A[256], wl[16], Vl[256], d[16];
+        int norm = normalize;
+        for (int i = 0; i < P; i++) if (!(G[i * P + i] > 0)) norm = 0;
+        for (int i = 0; i < P; i++) d[i] = norm ? sqrtl((ld)G[i * P + i]) : 1.0L;
+        for (int i = 0; i < P; i++)
+            for (int j = 0; j < P; j++) A[i * P + j] = (ld)G[i * P + j] / (d[i] * d[j]);
+        jacobi_eigv(P, A, wl, Vl);
+        if (w) for (int i = 0; i < P; i++) w[(size_t)e * P + i] = (double)wl[i];
+        if (V) for (int i = 0; i < P * P; i++) V[(size_t)e * P * P + i] = (double)Vl[i];
+    }
+    return 0;
+}
+
+/* Covariance with the options of CovMatr and the Fisher manipulations of
+ * Sec. 4.1-4.2.  For every event:
+ *   1. fixParams: keep only the parameters whose bit is set in `keep`
+ *      (rows and columns of fixed parameters removed before inversion);
+ *   2. addPrior: add prior[i] (if prior != NULL, indexed by the original
+ *      parameter slot) to the diagonal of the kept matrix;
+ *   3. normalise rows and columns by sqrt(diag) unless a diagonal element is
+ *      not positive (then no normalisation);
+ *   4. condition number = ratio of the largest to the smallest |eigenvalue|
+ *      of the normalised matrix; above cond_max the matrix is not inverted;
+ *   5. invert by `method`: 0 Cholesky; 1 Cholesky, SVD when not positive
+ *      definite (status bit 128); 2 SVD; 3 SVD with singular values below
+ *      thresh * max replaced by thresh * max; 4 SVD with them left out;
+ *      5 LU with partial pivoting.  The SVD of the symmetric matrix is its
+ *      eigendecomposition (singular values |w|, the signs kept on one side);
+ *   6. undo the normalisation; eps = max |Gamma C - 1| with the kept, prior-
+ *      added Gamma and the double-rounded C.
+ * out: cov [n][Pk][Pk] (Pk = number of kept parameters), cond2, inv_err, status */
+int or_covariance(int64_t n, int P, const double *fisher, uint32_t keep, const double *prior,
+                  int method, double thresh, double cond_max, double *cov, double *cond2,
+                  double *inv_err, int32_t *status)
+{
+    int idx[16], Pk = 0;
+    for (int i = 0; i < P; i++) if ((keep >> i) & 1u) idx[Pk++] = i;
+    if (Pk == 0) return -1;
+    for (int64_t e = 0; e < n; e++) {
+        const double *Gf = fisher + (size_t)e * P * P;
+        double *C = cov + (size_t)e * Pk * Pk;
+        ld G[256], Gh[256], A[256], Ch[256], d[16], w[16], V[256];
+        int st = 0;
+        for (int a = 0; a < Pk; a++)
+            for (int b = 0; b < Pk; b++) {
+                G[a * Pk + b] = (ld)Gf[idx[a] * P + idx[b]];
+                if (a == b && prior) G[a * Pk + b] += (ld)prior[idx[a]];
+                if (!isfinite((double)G[a * Pk + b])) st |= ST_NONFINITE;
+            }
+        if (st) {
+            for (int i = 0; i < Pk * Pk; i++) C[i] = NAN;
+            cond2[e] = NAN; inv_err[e] = NAN; status[e] = st;
+            continue;
+        }
+        int norm = 1;
+        for (int a = 0; a < Pk; a++) if (!(G[a * Pk + a] > 0)) norm = 0;
+        for (int a = 0; a < Pk; a++) d[a] = norm ? sqrtl(G[a * Pk + a]) : 1.0L;
+        for (int a = 0; a < Pk; a++)
+            for (int b = 0; b < Pk; b++) Gh[a * Pk + b] = G[a * Pk + b] / (d[a] * d[b]);
+        memcpy(A, Gh, sizeof(ld) * Pk * Pk);
+        jacobi_eigv(Pk, A, w, V);
+        ld smax = 0, smin = INFINITY;
+        for (int a = 0; a < Pk; a++) { smax = fmaxl(smax, fabsl(w[a])); smin = fminl(smin, fabsl(w[a])); }
+        ld kappa = smin > 0 ? smax / smin : INFINITY;
+        cond2[e] = (double)kappa;
+        if (kappa > 1.0L / DBL_EPSILON) st |= ST_ILL_COND;
+        if (kappa > cond_max) {
+            st |= ST_COND_GT_MAX;
+            for (int i = 0; i < Pk * Pk; i++) C[i] = NAN;
+            inv_err[e] = NAN; status[e] = st;
+            continue;
+        }
+        int use_svd = method >= 2 && method <= 4;
+        if (method == 0 || method == 1) {
+            /* Cholesky Gh = L L^T, C = L^-T L^-1 */
+            ld L[256], Li[256];
+            memset(L, 0, sizeof L);
+            int pd = 1;
+            for (int j = 0; j < Pk && pd; j++) {
+                ld sj = Gh[j * Pk + j];
+                for (int k = 0; k < j; k++) sj -= L[j * Pk + k] * L[j * Pk + k];
+                if (!(sj > 0)) { pd = 0; break; }
+                L[j * Pk + j] = sqrtl(sj);
+                for (int i = j + 1; i < Pk; i++) {
+                    ld t = Gh[i * Pk + j];
+                    for (int k = 0; k < j; k++) t -= L[i * Pk + k] * L[j * Pk + k];
+                    L[i * Pk + j] = t / L[j * Pk + j];
+                }
+            }
+            if (!pd) {
+                st |= ST_NOT_PD;
+                if (method == 0) {
+                    for (int i = 0; i < Pk * Pk; i++) C[i] = NAN;
+                    inv_err[e] = NAN; status[e] = st;
+                    continue;
+                }
+                st |= ST_SVD_FALLBACK;
+                use_svd = 1;
+            } else {
+                memset(Li, 0, sizeof Li);
+                for (int c = 0; c < Pk; c++)
+                    for (int i = c; i < Pk; i++) {
+                        ld t = (i == c) ? 1.0L : 0.0L;
+                        for (int k = c; k < i; k++) t -= L[i * Pk + k] * Li[k * Pk + c];
+                        Li[i * Pk + c] = t / L[i * Pk + i];
+                    }
+                for (int i = 0; i < Pk; i++)
+                    for (int j = 0; j < Pk; j++) {
+                        ld t = 0;
+                        for (int k = 0; k < Pk; k++) t += Li[k * Pk + i] * Li[k * Pk + j];
+                        Ch[i * Pk + j] = t;
+                    }
+            }
+        }
+        if (use_svd) {
+            /* inverse singular values: 1/w, with the small ones (|w| < thresh smax)
+             * replaced (method 3) or dropped (method 4) */
+            ld iw[16];
+            for (int k = 0; k < Pk; k++) {
+                ld a = fabsl(w[k]);
+                if (method == 3 && a < (ld)thresh * smax)
+                    iw[k] = (w[k] < 0 ? -1.0L : 1.0L) / ((ld)thresh * smax);
+                else if (method == 4 && a < (ld)thresh * smax)
+                    iw[k] = 0;
+                else
+                    iw[k] = 1.0L / w[k];
+            }
+            for (int i = 0; i < Pk; i++)
+                for (int j = 0; j < Pk; j++) {
+                    ld t = 0;
+                    for (int k = 0; k < Pk; k++) t += V[i * Pk + k] * iw[k] * V[j * Pk + k];
+                    Ch[i * Pk + j] = t;
+                }
+        } else if (method == 5) {
+            /* LU with partial pivoting, P Gh = L U, then columns of the inverse */
+            ld LU[256];
+            int piv[16];
+            memcpy(LU, Gh, sizeof(ld) * Pk * Pk);
+            for (int i = 0; i < Pk; i++) piv[i] = i;
+            int sing = 0;
+            for (int k = 0; k < Pk; k++) {
+                int m = k;
+                for (int i = k + 1; i < Pk; i++) if (fabsl(LU[i * Pk + k]) > fabsl(LU[m * Pk + k])) m = i;
+                if (LU[m * Pk + k] == 0) { sing = 1; break; }
+                if (m != k) {
+                    for (int j = 0; j < Pk; j++) { ld t = LU[k * Pk + j]; LU[k * Pk + j] = LU[m * Pk + j]; LU[m * Pk + j] = t; }
+                    int t = piv[k]; piv[k] = piv[m]; piv[m] = t;
+                }
+                for (int i = k + 1; i < Pk; i++) {
+                    LU[i * Pk + k] /= LU[k * Pk + k];
+                    for (int j = k + 1; j < Pk; j++) LU[i * Pk + j] -= LU[i * Pk + k] * LU[k * Pk + j];
+                }
+            }
+            if (sing) {
+                st |= ST_NOT_PD;
+                for (int i = 0; i < Pk * Pk; i++) C[i] = NAN;
+                inv_err[e] = NAN; status[e] = st;
+                continue;
+            }
+            for (int c = 0; c < Pk; c++) {
+                ld y[16];
+                for (int i = 0; i < Pk; i++) {
+                    ld t = (piv[i] == c) ? 1.0L : 0.0L;
+                    for (int k = 0; k < i; k++) t -= LU[i * Pk + k] * y[k];
+                    y[i] = t;
+                }
+                for (int i = Pk - 1; i >= 0; i--) {
+                    ld t = y[i];
+                    for (int k = i + 1; k < Pk; k++) t -= LU[i * Pk + k] * Ch[k * Pk + c];
+                    Ch[i * Pk + c] = t / LU[i * Pk + i];
+                }
+            }
+        }
+        for (int a = 0; a < Pk; a++)
+            for (int b = 0; b < Pk; b++) C[a * Pk + b] = (double)(Ch[a * Pk + b] / (d[a] * d[b]));
+        ld eps = 0;
+        for (int a = 0; a < Pk; a++)
+            for (int b = 0; b < Pk; b++) {
+                ld t = 0;
+                for (int k = 0; k < Pk; k++) t += G[a * Pk + k] * (ld)C[k * Pk + b];
+                eps = fmaxl(eps, fabsl(t - (a == b ? 1.0L : 0.0L)));
+            }
+        inv_err[e] = (double)eps;
+        status[e] = st;
+    }
+    return Pk;
+}
+
+/* Sky-localisation area at confidence level perc (percent), Sec. 4.1:
+ * Delta Omega = -2 pi |sin theta| sqrt(C_tt C_pp - C_tp^2) ln(1 - perc/100),
+ * in steradians (units 0) or square degrees (units 1).
+ * in: cov [n][P][P], theta [n]; slots it, ip of theta and phi; out: area [n] */
+int or_sky_area(int64_t n, int P, const double *cov, int it, int ip, const double *theta,
+                double perc, int units, double *area)
+{
+    for (int64_t e = 0; e < n; e++) {
+        const double *C = cov + (size_t)e * P * P;
+        ld det = (ld)C[it * P + it] * (ld)C[ip * P + ip] - (ld)C[it * P + ip] * (ld)C[it * P + ip];
+        ld a = -2.0L * OR_PI * fabsl(sinl((ld)theta[e])) * sqrtl(det) * log1pl(-(ld)perc / 100.0L);
+        if (units == 1) a *= (180.0L / OR_PI) * (180.0L / OR_PI);
+        area[e] = (double)a;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* VJP references by Richardson differences                             */
 
 /* d SNR / d theta_i for the event's Fisher parameters; out grad [n][P]  */
@@ -861,7 +1138,7 @@ int or_logdet_grad_gamma(int64_t n, const double *ev, const int8_t *pset, const 
 }
 
 /* version tag so the Python side can check the build matches */
-int or_abi_version(void) { return 2; }
+int or_abi_version(void) { return 3; }
 
 /* grid length by the points-per-e-fold rule, clamped: N = clamp(ceil(k ln(fmax/fmin)), lo, hi) */
 int or_grid_npts(int64_t n, const double *fmin, const double *fmax, double per_efold,

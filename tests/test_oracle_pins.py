@@ -564,3 +564,138 @@ def test_snr_gate_selection_brute_force():
     brute = [e for e in range(len(snr)) if snr[e] == snr[e] and snr[e] > 12.0]
     assert idx.tolist() == brute and idx.dtype == np.int64
     assert oracle.select_snr(np.array([]), 1.0).size == 0
+
+
+# ---------------------------------------------------------------- covariance tools
+def _spd(P, kappa_log10, rng):
+    """Random symmetric positive-definite matrix with a spread of eigenvalues and
+    a non-trivial diagonal scale."""
+    Q, _ = np.linalg.qr(rng.normal(size=(P, P)))
+    w = 10.0 ** np.linspace(0, -kappa_log10, P)
+    D = np.diag(10.0 ** rng.uniform(-3, 3, P))
+    return D @ (Q * w) @ Q.T @ D
+
+
+def test_fisher_eig_matches_library_and_residuals():
+    """CheckFisher (Sec. 4.1): eigenvalues equal LAPACK's (numpy.linalg.eigvalsh) on
+    the normalised matrix; A V = V diag(w) with V orthonormal."""
+    rng = np.random.default_rng(21)
+    F = np.stack([_spd(11, 6, rng) for _ in range(4)])
+    w, V = oracle.fisher_eig(F, normalize=True)
+    for e in range(4):
+        d = np.sqrt(np.diag(F[e]))
+        A = F[e] / np.outer(d, d)
+        np.testing.assert_allclose(w[e], np.linalg.eigvalsh(A), rtol=1e-9, atol=1e-14)
+        assert np.max(np.abs(A @ V[e] - V[e] * w[e])) < 1e-13
+        assert np.max(np.abs(V[e].T @ V[e] - np.eye(11))) < 1e-13
+    w2, _ = oracle.fisher_eig(F, normalize=False)
+    np.testing.assert_allclose(w2[0], np.linalg.eigvalsh(F[0]), rtol=1e-8, atol=1e-12 * np.abs(w2[0]).max())
+
+
+@pytest.mark.parametrize("method", range(6))
+def test_covariance_methods_agree_with_library_inverse(method):
+    """Every inversion method of CovMatr (Sec. 4.1) gives the inverse of a
+    positive-definite matrix; the normalisation is undone; eps = max|G C - 1|."""
+    rng = np.random.default_rng(22)
+    F = np.stack([_spd(11, 5, rng) for _ in range(3)])
+    C, k, eps, st = oracle.covariance(F, method=method)
+    assert (st == 0).all()
+    for e in range(3):
+        Cn = np.linalg.inv(F[e])
+        sc = np.sqrt(np.outer(np.diag(Cn), np.diag(Cn)))
+        assert np.max(np.abs(C[e] - Cn) / sc) < 1e-9
+        # eps of the double-rounded C: diagonal scales of 1e+-3 amplify its rounding
+        assert eps[e] < 1e-6
+        R = F[e].astype(np.longdouble) @ C[e].astype(np.longdouble) - np.eye(11)
+        assert abs(eps[e] - float(np.max(np.abs(R)))) < 1e-6 * eps[e]
+        d = np.sqrt(np.diag(F[e]))
+        wn = np.linalg.eigvalsh(F[e] / np.outer(d, d))
+        assert abs(k[e] / (wn[-1] / wn[0]) - 1) < 1e-6
+
+
+def test_covariance_svd_truncation_closed_forms():
+    """Truncated SVD and svd_reg (Sec. 4.1) on a matrix with unit diagonal, a 2x2
+    block [[1, c], [c, 1]] with c = 1 - 2^-52 (singular values 2 - 2^-52 and 2^-52,
+    ratio below the 1e-15 threshold) and the identity elsewhere.  Truncation
+    replaces 2^-52 by 1e-15 s_max; svd_reg drops it."""
+    P = 11
+    c = 1.0 - 2.0 ** -52
+    F = np.eye(P)
+    F[0, 1] = F[1, 0] = c
+    s1, s2 = 1.0 + c, 1.0 - c
+    assert s2 == 2.0 ** -52
+    v1 = np.array([1.0, 1.0]) / math.sqrt(2)
+    v2 = np.array([1.0, -1.0]) / math.sqrt(2)
+    C3, k3, _, st3 = oracle.covariance(F[None], method=oracle.INV_SVD_TRUNC, thresh=1e-15)
+    want3 = np.outer(v1, v1) / s1 + np.outer(v2, v2) / (1e-15 * s1)
+    np.testing.assert_allclose(C3[0, :2, :2], want3, rtol=1e-12)
+    C4, _, _, st4 = oracle.covariance(F[None], method=oracle.INV_SVD_REG, thresh=1e-15)
+    np.testing.assert_allclose(C4[0, :2, :2], np.outer(v1, v1) / s1, rtol=1e-12)
+    np.testing.assert_allclose(C4[0, 2:, 2:], np.eye(P - 2), rtol=1e-15)
+    assert abs(k3[0] / (s1 / s2) - 1) < 1e-3      # 2^-52 from a long-double Jacobi sweep
+    assert (st3 & oracle.ST_ILL_COND).all() and (st4 & oracle.ST_ILL_COND).all()
+
+
+def test_covariance_fix_prior_and_marginalisation_identities():
+    """fixParams = inverse of the kept block; marginalising = taking the block of
+    the full inverse, which equals the inverse of the Schur complement; addPrior =
+    inverse of Gamma + diag(prior), and a very tight prior approaches fixing."""
+    rng = np.random.default_rng(23)
+    F = np.stack([_spd(11, 4, rng) for _ in range(2)])
+    keep = [0, 1, 2, 3, 5, 7, 8]
+    drop = [4, 6, 9, 10]
+    Cf, _, _, st = oracle.covariance(F, keep=keep, method=oracle.INV_CHO)
+    Cfull, _, _, _ = oracle.covariance(F, method=oracle.INV_CHO)
+    prior = np.zeros(11)
+    prior[[4, 6]] = [3.0e2, 5.0e-1]
+    Cp, _, _, _ = oracle.covariance(F, prior=prior, method=oracle.INV_CHO)
+    big = np.zeros(11)
+    big[drop] = 1e30
+    Cb, _, _, _ = oracle.covariance(F, prior=big, method=oracle.INV_SVD)
+    for e in range(2):
+        A = F[e][np.ix_(keep, keep)]
+        np.testing.assert_allclose(Cf[e], np.linalg.inv(A), rtol=1e-9)
+        schur = A - F[e][np.ix_(keep, drop)] @ np.linalg.solve(F[e][np.ix_(drop, drop)],
+                                                               F[e][np.ix_(drop, keep)])
+        np.testing.assert_allclose(Cfull[e][np.ix_(keep, keep)], np.linalg.inv(schur), rtol=1e-8)
+        np.testing.assert_allclose(Cp[e], np.linalg.inv(F[e] + np.diag(prior)), rtol=1e-9)
+        np.testing.assert_allclose(Cb[e][np.ix_(keep, keep)], Cf[e], rtol=1e-8)
+
+
+def test_covariance_not_pd_fallbacks_and_cond_max():
+    """A symmetric indefinite matrix: Cholesky fails (NaN, status NOT_PD); the
+    default falls back to the SVD (status bit 128) and LU inverts it, both equal
+    to the library inverse; above cond_max nothing is inverted."""
+    rng = np.random.default_rng(24)
+    Q, _ = np.linalg.qr(rng.normal(size=(9, 9)))
+    F = ((Q * np.array([3, 2, 1.5, 1, 0.7, 0.5, -0.4, 0.3, 0.2])) @ Q.T)[None]
+    C0, _, _, st0 = oracle.covariance(F, method=oracle.INV_CHO)
+    assert st0[0] & oracle.ST_NOT_PD and np.isnan(C0).all()
+    want = np.linalg.inv(F[0])
+    for m, bit in ((oracle.INV_CHO_SVD, oracle.ST_SVD_FALLBACK), (oracle.INV_LU, 0)):
+        C, _, eps, st = oracle.covariance(F, method=m)
+        np.testing.assert_allclose(C[0], want, rtol=1e-9, atol=1e-12)
+        assert (st[0] & oracle.ST_SVD_FALLBACK) == bit and eps[0] < 1e-9
+    G = np.stack([_spd(11, 8, rng)])
+    C, k, _, st = oracle.covariance(G, cond_max=1e5)
+    assert st[0] & oracle.ST_COND_GT_MAX and np.isnan(C).all() and k[0] > 1e5
+
+
+def test_sky_area_is_the_gaussian_confidence_ellipse():
+    """Delta Omega_X (Sec. 4.1): for a Gaussian in (theta, phi) with covariance C,
+    the ellipse x^T C^-1 x <= k of solid angle Delta Omega = |sin theta| pi k
+    sqrt(det C) holds a fraction X of the probability (Monte Carlo, 2e6 draws)."""
+    rng = np.random.default_rng(25)
+    theta = 1.1
+    Cang = np.array([[4e-4, -1.5e-4], [-1.5e-4, 2.5e-4]])
+    C = np.eye(11) * 1e-2
+    C[3:5, 3:5] = Cang
+    for X in (50.0, 90.0):
+        a_sr = oracle.sky_area(C[None], 3, 4, [theta], perc=X, units="Sterad")[0]
+        a_dg = oracle.sky_area(C[None], 3, 4, [theta], perc=X, units="SqDeg")[0]
+        assert abs(a_dg / a_sr - (180 / math.pi) ** 2) < 1e-12 * a_dg / a_sr
+        k = a_sr / (abs(math.sin(theta)) * math.pi * math.sqrt(np.linalg.det(Cang)))
+        x = rng.multivariate_normal([0, 0], Cang, size=2_000_000)
+        q = np.einsum("ni,ij,nj->n", x, np.linalg.inv(Cang), x)
+        frac = np.mean(q <= k)
+        assert abs(frac - X / 100) < 2e-3, (X, frac)
