@@ -471,6 +471,11 @@ static void choose_steps(const ld *th, ld tc_fid, int P, const int *slot, int np
         if (s == I_MC) d0 = fminl(d0, 0.05L * th[I_MC]);
         if (s == I_DL) d0 = fminl(d0, 0.05L * th[I_DL]);
         if (s == I_ETA) d0 = fminl(d0, 0.3L * fminl(th[I_ETA], 0.25L - th[I_ETA]));
+        /* angles that move only the amplitude (iota near 0 or pi) have small
+         * rates and would get steps near 1 rad: cap them so the Richardson
+         * truncation error stays far below the derivative's size */
+        if (s == I_TH || s == I_PH || s == I_IOTA || s == I_PSI || s == I_PHIC)
+            d0 = fminl(d0, 0.05L);
         step[i] = d0;
     }
     free(hp); free(hm); free(h0);
