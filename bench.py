@@ -38,6 +38,11 @@ METRIC = "events/s (SNR + 11x11 Fisher), mixed vs FP64 path at stated error; % F
 WORKLOAD = "c3: 1e5 events, 70% BBH (5-80 Msun, spins) + 30% tidal BNS, ET-like triangle, " \
            "Earth rotation, per-event log grid 2 Hz..f_ISCO"
 WORKLOAD_C4 = "c4: 1e6 events drawn as c3 on five interferometers (triangle + two L)"
+WORKLOAD_GATED = ("c3-gated: the c3 catalog with a duty factor of 0.85 per triangle arm "
+                  "(seeded per-event arm masks), an SNR pass over every event, the SNR > 12 "
+                  "detection gate, then Fisher + inversion of the selected events")
+GATE_SNR = 12.0       # default snr_th of the paper's forecast driver (Sec. 5)
+GATE_DUTY = 0.85      # duty factor per arm of the gated workload
 N_PAR = 11
 SM_COUNT = 152
 DFMA_PER_CLK_SM = 2          # measured on GB300: 2 FP64 FMA / clock / SM (1.26 TFLOP/s)
@@ -45,7 +50,7 @@ FFMA_PER_CLK_SM = 128        # FP32 FMA lanes per SM (measured 117 / clock with 
 # DRAM bytes (read + write) per grid point of the Fisher point kernel, from one
 # ncu capture of the 2e4-event c3 catalog (4,376,070 points) of the current
 # kernels (profiles/k_points_*_fisher_c3.md); scaled by points to a full launch
-DRAM_BYTES_PER_POINT = {"mixed": (19.328768e6 + 80.128e3) / 4376070,
+DRAM_BYTES_PER_POINT = {"mixed": (21.669888e6 + 157.184e3) / 4376070,
                         "fp64": (16.705792e6 + 59.648e3) / 4376070}
 
 
@@ -58,10 +63,11 @@ def parse():
     ap.add_argument("--grid", choices=["literal", "stress"], default="literal")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--events", type=int, default=None)
-    ap.add_argument("--workload", choices=["c3", "c4"], default="c3",
+    ap.add_argument("--workload", choices=["c3", "c4", "c3-gated"], default="c3",
                     help="c3: 1e5 events on the triangle (headline); c4: 1e6 events on five "
                          "interferometers, the step adding the log-det VJP over the "
-                         "detector orientations")
+                         "detector orientations; c3-gated: c3 with duty-factor arm masks, "
+                         "an SNR pass and the SNR > 12 gate before the Fisher pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true",
                     help="launch the step call by call instead of replaying a CUDA graph")
@@ -208,14 +214,16 @@ def flops_per_point(n_site: int, n_ifo: int, precision: str) -> float:
     square root 35, recurrences 4; per site: Earth-angle sincos ~40, double
     angle 5, JKS/Doppler/phase combinations ~95; per virtual interferometer:
     patterns 38, tangents 46, sigma scaling 4, |Q|^2 3, 66-pair Gram update 265.
-    Mixed path (FP32 pipe): double-float basis 80, phase dot products 586 (two
-    11-term 220 each, two 4-term 73 each), tau* dot products 501, f 10,
-    roundings 8, recurrences 32, PSD weight 20; per site 122 (double-float
-    Earth angle 44, sincosf ~20, JKS/Doppler ~58); per virtual interferometer
-    1711 (patterns 38, tangents 60, scaling 4, 73 compensated accumulations of
-    22 flops: two products, two exact product errors, two two-sums, compensation)."""
+    Mixed path (FP32 pipe): double-float basis 80; compensated (Dot2) dot
+    products with double-float coefficients, 15 flops per term and lane: d Psi/d Mc
+    with d Psi/d eta (two lanes, 11 terms) 316, slots 9/10 (two lanes, 4 terms) 106,
+    tau* (one lane, 8 terms, times v^-3) 125, d tau*/d Mc with d tau*/d eta (two lanes,
+    8 terms) 228; f 12, recurrences 41, PSD weight 23; per site 122 (double-float
+    Earth angle 44, sincosf ~20, JKS/Doppler ~58); per virtual interferometer 1711
+    (patterns 38, tangents 60, scaling 4, 73 compensated accumulations of 22 flops:
+    two products, two exact product errors, two two-sums, compensation)."""
     if precision == "mixed":
-        shared = 80 + 586 + 501 + 10 + 8 + 32 + 20
+        shared = 80 + 316 + 106 + 125 + 228 + 12 + 41 + 23
         return shared + 122 * n_site + 1711 * n_ifo
     shared = 8 + 4 + 19 + 20 + 14 + 48 + 35 + 4
     return shared + 140 * n_site + 356 * n_ifo
@@ -252,12 +260,17 @@ def run_ours(a):
     import paper_2207_06910_gb300 as gw
 
     prec = gw.GW_MIXED if a.precision == "mixed" else gw.GW_FP64
+    gated = a.workload == "c3-gated"
+    cfg = "c3" if gated else a.workload
+    if gated:
+        a.eager = True      # the gate reads its count back: no single-graph step
     # weak scaling: every rank owns its own 1e5-event shard (seed offset by rank)
-    raw = gwcat.draw(a.workload, a.events, seed=shard_seed(rank), grid=a.grid)
+    raw = gwcat.draw(cfg, a.events, seed=shard_seed(rank), grid=a.grid)
     n = len(raw["m1"])
     rule = raw["npts_rule"]
-    det, psd, rot = gwcat.network(a.workload)
+    det, psd, rot = gwcat.network(cfg)
     net = gw.Network(det, psd, rot)
+    n_arms = sum(1 if int(r[4]) == 0 else 3 for r in det)
     keys = ("m1", "m2", "chi1", "chi2", "lam1", "lam2", "dL_Mpc", "tcoal", "fmin",
             "theta", "phi", "iota", "psi", "Phic")
     host = {k: torch.as_tensor(np.ascontiguousarray(raw[k], np.float64)).pin_memory() for k in keys}
@@ -265,6 +278,9 @@ def run_ours(a):
     host["pset"] = torch.as_tensor(np.ascontiguousarray(raw["pset"], np.int8)).pin_memory()
     if rule[0] == "given":
         host["npts"] = torch.as_tensor(np.ascontiguousarray(raw["npts"], np.int32)).pin_memory()
+    if gated:
+        masks = gwcat.draw_arm_masks(n, n_arms, GATE_DUTY, seed=shard_seed(rank) + 7)
+        host["arm_mask"] = torch.as_tensor(masks.view(np.int32)).pin_memory()
     dev = {k: v.cuda() for k, v in host.items()}
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -277,15 +293,27 @@ def run_ours(a):
 
     with_logdet = a.workload == "c4"
 
-    def step(d):
+    def gate(d):
+        """Prepared catalog of the step's Fisher pass: every event, or (gated
+        workload) the events passing the SNR gate, with their arm masks."""
         cat = prepare(d)
-        F, snr, st, g = gw.gw_fisher(cat, net, N_PAR, prec, grad_snr=grad_up)
+        if not gated:
+            return cat
+        cat = cat.with_arm_mask(d["arm_mask"])
+        snr_all, _ = gw.gw_snr(cat, net, prec)
+        return cat.select(gw.gw_select_snr(snr_all, GATE_SNR))
+
+    def step(d):
+        cat = gate(d)
+        F, snr, st, g = gw.gw_fisher(cat, net, N_PAR, prec, grad_snr=grad_up[:cat.n])
         cov, cond, err, sti = gw.gw_fisher_inverse(F, N_PAR)
         if with_logdet:
             gw.gw_logdet_vjp_detangles(cat, net, N_PAR, cov, gw.GW_FP64)
         return cat, F, snr, cov, cond, g, st
 
-    launches_per_step = 1 + 7 + 1 + (6 if with_logdet else 0)
+    # prepare 1; Fisher 7 (event setup, scan 3, point loop, finish, SNR VJP);
+    # inversion 1; log-det VJP 6; gated: SNR pass 6 and gate 5
+    launches_per_step = 1 + 7 + 1 + (6 if with_logdet else 0) + (11 if gated else 0)
     for _ in range(a.warmup):
         step(dev)
     torch.cuda.synchronize()
@@ -293,7 +321,13 @@ def run_ours(a):
     cat, F, snr, cov, cond, g, st = step(dev)
     torch.cuda.synchronize()
     assert int((st != 0).sum()) == 0, "events flagged in the benchmark catalog"
-    n_points = int(cat.npts.to(torch.int64).sum().item())
+    n_sel = cat.n
+    if gated:
+        sel_rows = cat.sel
+        n_points_all = int(cat.npts.to(torch.int64).sum().item())
+        n_points = int(cat.npts[sel_rows].to(torch.int64).sum().item())
+    else:
+        n_points = n_points_all = int(cat.npts.to(torch.int64).sum().item())
 
     # ---- reserve the workspace (asynchronous calls) and capture the step
     gw.gw_reserve(n, gw.work_items(cat.npts), net.n_det)
@@ -321,8 +355,8 @@ def run_ours(a):
     gw.gw_set_profiling(True)
     for _ in range(5):
         flush.zero_()
-        cat_p = prepare(dev)
-        gw.gw_fisher(cat_p, net, N_PAR, prec, grad_snr=grad_up)
+        cat_p = gate(dev)
+        gw.gw_fisher(cat_p, net, N_PAR, prec, grad_snr=grad_up[:cat_p.n])
         fisher_ms.append(gw.gw_point_kernel_ms())
     gw.gw_set_profiling(False)
     torch.cuda.synchronize()
@@ -348,10 +382,10 @@ def run_ours(a):
     total_ms = float(sum(step_ms))
 
     # ---- end to end: host (pinned) -> device, step, device -> host
-    outs_host = {"snr": torch.empty(n, dtype=torch.float64).pin_memory(),
-                 "F": torch.empty((N_PAR * (N_PAR + 1) // 2, n), dtype=torch.float64).pin_memory(),
-                 "cov": torch.empty((N_PAR * (N_PAR + 1) // 2, n), dtype=torch.float64).pin_memory(),
-                 "g": torch.empty((N_PAR, n), dtype=torch.float64).pin_memory()}
+    outs_host = {"snr": torch.empty(n_sel, dtype=torch.float64).pin_memory(),
+                 "F": torch.empty((N_PAR * (N_PAR + 1) // 2, n_sel), dtype=torch.float64).pin_memory(),
+                 "cov": torch.empty((N_PAR * (N_PAR + 1) // 2, n_sel), dtype=torch.float64).pin_memory(),
+                 "g": torch.empty((N_PAR, n_sel), dtype=torch.float64).pin_memory()}
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = sum(v.numel() * v.element_size() for v in outs_host.values())
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -378,7 +412,17 @@ def run_ours(a):
     if rank == 0:
         n_site = net.n_det
         n_ifo = sum(1 if int(r[4]) == 0 else 2 for r in det)
-        flops = flops_per_point(n_site, n_ifo, a.precision) * n_points
+        if gated:
+            # interferometers in use per selected event: a triangle with every arm
+            # on is two virtual ones, otherwise one per arm that is on
+            sel_np = sel_rows.cpu().numpy()
+            m = masks[sel_np].astype(np.int64) & 7
+            ifo_e = np.where(m == 7, 2, (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1))
+            pts_e = cat.npts[sel_rows].cpu().numpy().astype(np.float64)
+            flops = float(np.sum(pts_e * np.array([flops_per_point(n_site, int(k), a.precision)
+                                                   for k in ifo_e])))
+        else:
+            flops = flops_per_point(n_site, n_ifo, a.precision) * n_points
         sm_mhz = clocks.get("sm_mhz") or 2070.0
         per_clk = FFMA_PER_CLK_SM if a.precision == "mixed" else DFMA_PER_CLK_SM
         peak = SM_COUNT * per_clk * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s at the sampled clock
@@ -397,12 +441,17 @@ def run_ours(a):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
             "data": "synthetic (seeded, gwcat)",
-            "config": {"workload": WORKLOAD if a.workload == "c3" else WORKLOAD_C4,
+            "config": {"workload": {"c3": WORKLOAD, "c4": WORKLOAD_C4,
+                                    "c3-gated": WORKLOAD_GATED}[a.workload],
                        "n_events_per_gpu": n, "grid": a.grid,
-                       "points_per_step": n_points, "precision": a.precision, "n_par": N_PAR,
-                       "step": "prepare + SNR/Fisher with fused SNR VJP + Cholesky inversion"
+                       "points_per_step": n_points + (n_points_all if gated else 0),
+                       "precision": a.precision, "n_par": N_PAR,
+                       "step": ("prepare + SNR pass + gate + " if gated else "prepare + ")
+                               + "SNR/Fisher with fused SNR VJP + Cholesky inversion"
                                + (" + log-det VJP (FP64) over detector orientations"
                                   if with_logdet else ""),
+                       **({"selected_events": n_sel, "fisher_points": n_points}
+                          if gated else {}),
                        "l2": "flushed before every timed step (256 MiB write)",
                        "launch": "eager calls" if a.eager else "one CUDA graph replay per step",
                        "parallelism": f"event shards, {world} GPU(s), no collective"},

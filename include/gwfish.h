@@ -58,7 +58,9 @@ enum {
                                parameter set for n_par                         */
     GW_ST_ILL_COND = 32,    /* condition number above 1/DBL_EPSILON (Sec. 4:
                                inversion unreliable beyond inverse precision)  */
-    GW_ST_OVERFLOW = 64     /* work items beyond the gw_reserve capacity       */
+    GW_ST_OVERFLOW = 64,    /* work items beyond the gw_reserve capacity       */
+    GW_ST_SVD_FALLBACK = 128 /* gw_covariance: not positive definite, inverted
+                               by the SVD instead (GW_INV_CHO_SVD)             */
 };
 
 /* A work item is a run of at most GW_ITEM_POINTS consecutive grid points of one
@@ -72,7 +74,19 @@ enum {
  *   pset 1 -> chi1z, chi2z;  pset 2 -> LambdaTilde, deltaLambdaTilde.
  * pset 0 events have 9 parameters. */
 
-/* Catalog: structure of arrays, every pointer DEVICE, length n, read only. */
+/* Catalog: structure of arrays, every pointer DEVICE, read only.  The call
+ * processes n events; event i of the call is row r(i) of the columns, with
+ * r(i) = sel[i] when sel is given (the columns then hold at least
+ * max(sel) + 1 rows; sel need not be sorted) and r(i) = i otherwise.  Every
+ * per-event output is indexed by i.
+ *
+ * Duty factor (Sec. 3.2, and the duty_factor option of Sec. 5): each detector,
+ * and each arm of a triangle separately, is on or off for a whole event.
+ * arm_mask[r] bit a = 1 when arm a of the network is on for row r, the arms
+ * being numbered over the detectors in order (an L-shaped detector one arm, a
+ * triangle three, k = 0, 1, 2); NULL = every arm on.  The random draws are the
+ * caller's.  An event with every arm off has SNR 0 and a zero Fisher matrix
+ * (status 0; the inverse flags it GW_ST_NOT_PD). */
 typedef struct gw_catalog {
     int64_t n;
     const double *Mc, *eta, *dL, *theta, *phi, *iota, *psi, *tc, *Phic;
@@ -81,13 +95,17 @@ typedef struct gw_catalog {
     const int8_t *pset;               /* 0, 1 or 2 (see above)                */
     const double *fmin, *fmax;        /* grid ends [Hz]                       */
     const int32_t *npts;              /* grid points, log spaced (Sec. 2.2)   */
+    const uint32_t *arm_mask;         /* duty-factor arm masks, or NULL       */
+    const int64_t *sel;               /* [n] rows to process, or NULL         */
 } gw_catalog;
 
 /* Interferometer.  shape 0: L-shaped with opening angle zeta and bisector at
  * gamma counter-clockwise from local East; shape 1: triangle of three
  * co-located 60-degree interferometers (zeta ignored) whose bisectors are at
  * gamma + 30 deg + 120 deg k (Table 2: gamma of a triangle is its first arm).
- * Angles in radians.  psd indexes the network's PSD table. */
+ * Angles in radians.  psd indexes the network's PSD table.  A network has at
+ * most 32 arms and at most 24 interferometer entries (one per L, five per
+ * triangle: its two-interferometer form and its three arms). */
 typedef struct gw_detector {
     double lat, lon, gamma, zeta;
     int32_t shape, psd;
@@ -119,7 +137,7 @@ gw_status gw_create(gw_ctx **ctx, int device);
 gw_status gw_destroy(gw_ctx *ctx);
 /* Text of the last error on this context (static storage, never NULL). */
 const char *gw_last_error(const gw_ctx *ctx);
-/* ABI version of this header (incremented on any signature change): 2. */
+/* ABI version of this header (incremented on any signature change): 3. */
 int gw_abi_version(void);
 
 /* Reserve workspace for up to max_events events on up to max_sites detector
@@ -167,6 +185,15 @@ gw_status gw_snr(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
                  gw_precision prec, double *snr, double *snr_det, int32_t *status,
                  void *stream);
 
+/* Detection gate (Sec. 5, the snr_th option: Fisher matrices are computed only
+ * for events whose network SNR exceeds the threshold).  DEVICE in: snr [n];
+ * DEVICE out: sel [n capacity], the indices i with snr[i] > threshold in
+ * increasing order (NaN never passes); HOST out: *n_sel.  Synchronises
+ * `stream` to read the count.  The selected events are processed by passing
+ * sel (and n = *n_sel) in a gw_catalog. */
+gw_status gw_select_snr(gw_ctx *ctx, const double *snr, int64_t n, double threshold,
+                        int64_t *sel, int64_t *n_sel, void *stream);
+
 /* Network Fisher matrix (Sec. 3.2, Eq. 3.3) and SNR.  n_par = 9 (every event
  * pset 0) or 11 (every event pset 1 or 2).  DEVICE outputs:
  *   fisher [n_par(n_par+1)/2][n]: packed upper triangle, row-major over
@@ -213,6 +240,81 @@ gw_status gw_snr_vjp(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
 gw_status gw_logdet_vjp_detangles(gw_ctx *ctx, const gw_catalog *cat,
                                   const gw_network *net, gw_precision prec, int n_par,
                                   const double *cov, double *grad_gamma, void *stream);
+
+/* Detector strain h_a(f_k) = Q_a exp(i Phi_a) on every event's grid, for every
+ * arm a of the network (the arm numbering of gw_catalog.arm_mask: a triangle
+ * gives its three 60-degree arms), with the conventions of the Fisher pass:
+ * Phi = Psi_PN(f) + Psi_tidal(f) - Phic - pi/4 + Phi_D(f) at the fiducial tc
+ * (Secs. 2.2 and 3.1).  Phi is evaluated in FP64 and reduced modulo 2 pi by the
+ * Cody-Waite method; the sine and cosine of the reduced angle are FP64
+ * (GW_FP64) or FP32 (GW_MIXED).  total_points must equal the sum of the
+ * events' npts (checked: one read-back, the call synchronises `stream`).
+ * DEVICE out: re, im [n_arm][total_points], event e's points at
+ * [point_off[e], point_off[e+1]); freq [total_points] (or NULL);
+ * point_off [n + 1] (or NULL); status [n] (or NULL).  Arms that are off for
+ * the event (duty factor) get zeros; flagged events NaN. */
+gw_status gw_strain(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_precision prec,
+                    int64_t total_points, double *re, double *im, double *freq,
+                    int64_t *point_off, int32_t *status, void *stream);
+
+/* ---- Covariance tools (Sec. 4.1 and Sec. 4.2).  Matrices are packed like
+ * gw_fisher's output ([P(P+1)/2][n], DEVICE); one thread per event, FP64.
+ * A keep mask selects parameters: bit i set = slot i kept (0 = all kept); the
+ * kept slots, in increasing order, form the output's parameter list. */
+
+/* Inversion methods of gw_covariance (the options of CovMatr, Sec. 4.1). */
+typedef enum {
+    GW_INV_CHO = 0,        /* Cholesky; not positive definite: GW_ST_NOT_PD, NaN  */
+    GW_INV_CHO_SVD = 1,    /* Cholesky, SVD when not positive definite (the
+                              paper's default; sets GW_ST_SVD_FALLBACK)          */
+    GW_INV_SVD = 2,        /* eigendecomposition (the SVD of a symmetric matrix)  */
+    GW_INV_SVD_TRUNC = 3,  /* singular values below thresh * s_max raised to it  */
+    GW_INV_SVD_REG = 4,    /* singular values below thresh * s_max left out       */
+    GW_INV_LU = 5          /* LU with partial pivoting: the upper triangle of the
+                              LU inverse, inv_err of the full LU inverse          */
+} gw_inv_method;
+
+/* Eigenvalues (ascending) and eigenvectors of each Fisher matrix, normalised
+ * by sqrt(diag) when `normalize` and every diagonal element is positive
+ * (CheckFisher, Sec. 4.1).  DEVICE out: eigval [n_par][n] (or NULL), eigvec
+ * [n_par * n_par][n] (or NULL): component i of eigenvector k of event e at
+ * eigvec[(i * n_par + k) * n + e], largest-magnitude component positive.
+ * n_par <= 11.  Cyclic Jacobi in FP64. */
+gw_status gw_fisher_eig(gw_ctx *ctx, const double *fisher, int64_t n, int n_par, int normalize,
+                        double *eigval, double *eigvec, void *stream);
+
+/* Covariance with the Fisher manipulations of Sec. 4.2 and the inversion
+ * options of Sec. 4.1, per event: (1) fixParams: keep the parameters of
+ * `keep` (rows and columns of fixed parameters removed before inversion);
+ * (2) addPrior: add prior[i] (HOST [n_par] or NULL; finite, >= 0) to the
+ * diagonal entry of every kept slot i; (3) normalise by sqrt(diag) unless a
+ * diagonal element is not positive; (4) condition number = max|w| / min|w|
+ * over the eigenvalues w of the normalised matrix, above cond_max nothing is
+ * inverted (GW_ST_COND_GT_MAX, NaN); (5) invert by `method` (thresh in
+ * [0, 1): the singular-value floor ratio of methods 3 and 4, the paper's
+ * default 1e-15); (6) undo the normalisation; inv_err = max|Gamma C - 1| with
+ * the kept, prior-added Gamma.  DEVICE out: cov [Pk(Pk+1)/2][n] over the Pk
+ * kept parameters; cond, inv_err, status [n] (each may be NULL). */
+gw_status gw_covariance(gw_ctx *ctx, const double *fisher, int64_t n, int n_par, uint32_t keep,
+                        const double *prior, int method, double thresh, double cond_max,
+                        double *cov, double *cond, double *inv_err, int32_t *status,
+                        void *stream);
+
+/* The kept rows and columns of packed matrices: fixing parameters when
+ * applied to Fisher matrices, marginalising over the others when applied to
+ * covariances (Sec. 4.2).  DEVICE in [n_par(n_par+1)/2][n], DEVICE out
+ * [Pk(Pk+1)/2][n]. */
+gw_status gw_packed_submatrix(gw_ctx *ctx, const double *in, int64_t n, int n_par, uint32_t keep,
+                              double *out, void *stream);
+
+/* Sky-localisation area at confidence level perc (percent, in (0, 100)),
+ * Sec. 4.1: Delta Omega = -2 pi |sin theta| sqrt(C_tt C_pp - C_tp^2)
+ * ln(1 - perc/100), from the packed covariances (DEVICE [n_par(n_par+1)/2][n])
+ * with theta at slot i_theta and phi at slot i_phi; theta DEVICE [n] (rad).
+ * units 0: steradians, 1: square degrees.  DEVICE out: area [n]. */
+gw_status gw_sky_area(gw_ctx *ctx, const double *cov, int64_t n, int n_par, int i_theta,
+                      int i_phi, const double *theta, double perc, int units, double *area,
+                      void *stream);
 
 /* Allocation-free Fisher pass (no counterpart in the paper).
  *

@@ -33,7 +33,7 @@ _P = ctypes.c_void_p
 class gw_catalog(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64)] + [(k, _P) for k in (
         "Mc", "eta", "dL", "theta", "phi", "iota", "psi", "tc", "Phic",
-        "chi1z", "chi2z", "LamT", "dLamT", "pset", "fmin", "fmax", "npts")]
+        "chi1z", "chi2z", "LamT", "dLamT", "pset", "fmin", "fmax", "npts", "arm_mask", "sel")]
 
 
 class gw_detector(ctypes.Structure):
@@ -55,7 +55,9 @@ class gw_network(ctypes.Structure):
 
 EXPORTS = ("gw_create", "gw_destroy", "gw_last_error", "gw_abi_version", "gw_prepare_catalog",
            "gw_snr", "gw_fisher", "gw_fisher_inverse", "gw_snr_vjp", "gw_logdet_vjp_detangles",
-           "gw_set_profiling", "gw_point_kernel_ms", "gw_fisher_noalloc", "gw_reserve")
+           "gw_set_profiling", "gw_point_kernel_ms", "gw_fisher_noalloc", "gw_reserve",
+           "gw_select_snr", "gw_fisher_eig", "gw_covariance", "gw_packed_submatrix",
+           "gw_sky_area", "gw_strain")
 
 _lib = None
 
@@ -92,6 +94,14 @@ def load_library(path: str | None = None):
     lib.gw_destroy.restype = ctypes.c_int
     lib.gw_reserve.argtypes = [_P, i64, i64, ctypes.c_int]
     lib.gw_fisher_noalloc.argtypes = [C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
+    lib.gw_select_snr.argtypes = [_P, _P, i64, d, _P, ctypes.POINTER(i64), _P]
+    lib.gw_strain.argtypes = [_P, C, N, ctypes.c_int, i64, _P, _P, _P, _P, _P, _P]
+    lib.gw_fisher_eig.argtypes = [_P, _P, i64, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+    lib.gw_covariance.argtypes = [_P, _P, i64, ctypes.c_int, ctypes.c_uint32, _P, ctypes.c_int, d,
+                                  d, _P, _P, _P, _P, _P]
+    lib.gw_packed_submatrix.argtypes = [_P, _P, i64, ctypes.c_int, ctypes.c_uint32, _P, _P]
+    lib.gw_sky_area.argtypes = [_P, _P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, d,
+                                ctypes.c_int, _P, _P]
     lib.gw_set_profiling.argtypes = [_P, ctypes.c_int]
     lib.gw_point_kernel_ms.argtypes = [_P]
     lib.gw_point_kernel_ms.restype = ctypes.c_double
@@ -165,26 +175,33 @@ def _stream(stream=None):
 
 
 class Catalog:
-    """Device-resident catalog (structure of arrays, float64 / int8 / int32)."""
+    """Device-resident catalog (structure of arrays, float64 / int8 / int32), with
+    optional duty-factor arm masks (uint32 stored as int32, one per row) and an
+    optional selection of rows (int64 indices; the catalog then holds
+    ``len(sel)`` events)."""
 
     FIELDS = ("Mc", "eta", "dL", "theta", "phi", "iota", "psi", "tc", "Phic",
               "chi1z", "chi2z", "LamT", "dLamT")
 
-    def __init__(self, tensors: dict, pset, fmin, fmax, npts):
+    def __init__(self, tensors: dict, pset, fmin, fmax, npts, arm_mask=None, sel=None):
         self.t = {k: tensors.get(k) for k in self.FIELDS}
         self.pset, self.fmin, self.fmax, self.npts = pset, fmin, fmax, npts
-        self.n = int(self.t["Mc"].numel())
+        self.arm_mask, self.sel = arm_mask, sel
+        self.n = int(sel.numel()) if sel is not None else int(self.t["Mc"].numel())
 
     @classmethod
-    def from_numpy(cls, ev: np.ndarray, pset, fmin, fmax, npts, device="cuda"):
+    def from_numpy(cls, ev: np.ndarray, pset, fmin, fmax, npts, device="cuda", arm_mask=None):
         """From oracle-style event rows [n, 13] (order of ``FIELDS``)."""
         ev = np.asarray(ev, dtype=np.float64).reshape(-1, 13)
         n = ev.shape[0]
         t = {k: torch.as_tensor(np.ascontiguousarray(ev[:, i]), device=device)
              for i, k in enumerate(cls.FIELDS)}
         col = lambda a, dt: torch.as_tensor(np.array(np.broadcast_to(a, (n,)), dtype=dt), device=device)
+        mask = None
+        if arm_mask is not None:
+            mask = col(np.asarray(arm_mask, dtype=np.uint32).view(np.int32), np.int32)
         return cls(t, col(pset, np.int8), col(fmin, np.float64), col(fmax, np.float64),
-                   col(npts, np.int32))
+                   col(npts, np.int32), mask)
 
     def struct(self) -> gw_catalog:
         c = gw_catalog()
@@ -193,12 +210,27 @@ class Catalog:
             setattr(c, k, _ptr(self.t[k]))
         c.pset, c.fmin, c.fmax, c.npts = (_ptr(self.pset), _ptr(self.fmin), _ptr(self.fmax),
                                           _ptr(self.npts))
+        if self.arm_mask is not None and self.arm_mask.dtype != torch.int32:
+            raise TypeError("arm_mask must be an int32 (bit pattern of uint32) tensor")
+        if self.sel is not None and self.sel.dtype != torch.int64:
+            raise TypeError("sel must be an int64 tensor")
+        c.arm_mask, c.sel = _ptr(self.arm_mask), _ptr(self.sel)
         return c
 
     def with_field(self, name, tensor):
         t = dict(self.t)
         t[name] = tensor
-        return Catalog(t, self.pset, self.fmin, self.fmax, self.npts)
+        return Catalog(t, self.pset, self.fmin, self.fmax, self.npts, self.arm_mask, self.sel)
+
+    def with_arm_mask(self, arm_mask):
+        """Same rows with duty-factor arm masks (int32 tensor, one per row; None = all on)."""
+        return Catalog(self.t, self.pset, self.fmin, self.fmax, self.npts, arm_mask, self.sel)
+
+    def select(self, sel):
+        """The events at rows ``sel`` (int64 tensor) of this catalog's columns."""
+        if self.sel is not None:
+            sel = self.sel[sel]
+        return Catalog(self.t, self.pset, self.fmin, self.fmax, self.npts, self.arm_mask, sel)
 
 
 class Network:
@@ -294,6 +326,18 @@ def gw_snr(cat: Catalog, net: Network, prec=GW_FP64, per_detector=False, stream=
                                _ptr(sdet), _ptr(status), _stream(stream))
     _check(st, ctx)
     return (snr, sdet, status) if per_detector else (snr, status)
+
+
+def gw_select_snr(snr: torch.Tensor, threshold: float, stream=None) -> torch.Tensor:
+    """Detection gate (the snr_th option of Sec. 5): int64 indices of the events
+    with SNR above ``threshold``, in increasing order (synchronises the stream)."""
+    ctx = context()
+    n = int(snr.numel())
+    sel = torch.empty(n, dtype=torch.int64, device=snr.device)
+    cnt = ctypes.c_int64(0)
+    _check(load_library().gw_select_snr(ctx, _ptr(snr), n, float(threshold), _ptr(sel),
+                                        ctypes.byref(cnt), _stream(stream)), ctx)
+    return sel[:cnt.value]
 
 
 def gw_fisher(cat: Catalog, net: Network, n_par: int, prec=GW_FP64, stream=None, out=None,
@@ -406,3 +450,96 @@ class SNR(torch.autograd.Function):
         g = gw_snr_vjp(ctx_.cat, ctx_.net, ctx_.n_par, grad.to(torch.float64).contiguous(),
                        ctx_.prec)
         return g, None, None, None, None
+
+
+# ---- covariance tools (Secs. 4.1-4.2)
+GW_INV_CHO, GW_INV_CHO_SVD, GW_INV_SVD, GW_INV_SVD_TRUNC, GW_INV_SVD_REG, GW_INV_LU = range(6)
+GW_ST_SVD_FALLBACK = 128
+
+
+def _keep_mask(keep, n_par: int) -> tuple[int, int]:
+    if keep is None:
+        return 0, n_par
+    m = 0
+    for i in keep:
+        if not 0 <= int(i) < n_par:
+            raise ValueError(f"parameter slot {i} outside [0, {n_par})")
+        m |= 1 << int(i)
+    return m, bin(m).count("1")
+
+
+def gw_fisher_eig(fisher: torch.Tensor, n_par: int, normalize=True, vectors=True, stream=None):
+    """Eigenvalues [n_par, n] (ascending) and eigenvectors [n_par * n_par, n] of
+    packed Fisher matrices (CheckFisher)."""
+    ctx = context()
+    n = fisher.shape[1]
+    w = torch.empty((n_par, n), dtype=torch.float64, device=fisher.device)
+    V = torch.empty((n_par * n_par, n), dtype=torch.float64, device=fisher.device) if vectors else None
+    _check(load_library().gw_fisher_eig(ctx, _ptr(fisher), n, n_par, int(bool(normalize)), _ptr(w),
+                                        _ptr(V), _stream(stream)), ctx)
+    return w, V
+
+
+def gw_covariance(fisher: torch.Tensor, n_par: int, keep=None, prior=None, method=GW_INV_CHO_SVD,
+                  thresh=1e-15, cond_max=1e50, stream=None):
+    """Covariance after fixParams (``keep``: kept slots) and addPrior (``prior``:
+    [n_par] host values) with a CovMatr inversion method.  Returns (cov packed
+    over the kept parameters, cond [n], inv_err [n], status [n])."""
+    ctx = context()
+    n = fisher.shape[1]
+    mask, k = _keep_mask(keep, n_par)
+    cov = torch.empty((k * (k + 1) // 2, n), dtype=torch.float64, device=fisher.device)
+    cond = torch.empty(n, dtype=torch.float64, device=fisher.device)
+    err = torch.empty(n, dtype=torch.float64, device=fisher.device)
+    status = torch.empty(n, dtype=torch.int32, device=fisher.device)
+    pr = None
+    if prior is not None:
+        pr = (ctypes.c_double * n_par)(*[float(x) for x in np.broadcast_to(prior, (n_par,))])
+    _check(load_library().gw_covariance(ctx, _ptr(fisher), n, n_par, mask, pr, int(method),
+                                        float(thresh), float(cond_max), _ptr(cov), _ptr(cond),
+                                        _ptr(err), _ptr(status), _stream(stream)), ctx)
+    return cov, cond, err, status
+
+
+def gw_packed_submatrix(mat: torch.Tensor, n_par: int, keep, stream=None) -> torch.Tensor:
+    """Kept rows and columns of packed matrices (fix on Fisher, marginalise on C)."""
+    ctx = context()
+    n = mat.shape[1]
+    mask, k = _keep_mask(keep, n_par)
+    out = torch.empty((k * (k + 1) // 2, n), dtype=torch.float64, device=mat.device)
+    _check(load_library().gw_packed_submatrix(ctx, _ptr(mat), n, n_par, mask, _ptr(out),
+                                              _stream(stream)), ctx)
+    return out
+
+
+def gw_sky_area(cov: torch.Tensor, n_par: int, theta: torch.Tensor, i_theta=3, i_phi=4,
+                perc=90.0, units="SqDeg", stream=None) -> torch.Tensor:
+    """Delta Omega_perc% per event (Sec. 4.1), 'SqDeg' or 'Sterad'."""
+    ctx = context()
+    n = cov.shape[1]
+    area = torch.empty(n, dtype=torch.float64, device=cov.device)
+    _check(load_library().gw_sky_area(ctx, _ptr(cov), n, n_par, int(i_theta), int(i_phi),
+                                      _ptr(theta.contiguous()), float(perc),
+                                      1 if units == "SqDeg" else 0, _ptr(area), _stream(stream)), ctx)
+    return area
+
+
+def gw_strain(cat: Catalog, net: Network, prec=GW_FP64, stream=None):
+    """Strain of every arm on every event's grid: returns (re, im [n_arm, total],
+    freq [total], point_off [n + 1], status [n])."""
+    ctx = context()
+    dev = cat.npts.device
+    npts = cat.npts if cat.sel is None else cat.npts[cat.sel]
+    total = int(npts.clamp(min=0).to(torch.int64).sum().item())
+    n_arm = sum(1 if int(r[4]) == 0 else 3 for r in net.det_rows)
+    re = torch.empty((n_arm, total), dtype=torch.float64, device=dev)
+    im = torch.empty((n_arm, total), dtype=torch.float64, device=dev)
+    freq = torch.empty(total, dtype=torch.float64, device=dev)
+    off = torch.empty(cat.n + 1, dtype=torch.int64, device=dev)
+    status = torch.empty(cat.n, dtype=torch.int32, device=dev)
+    c = cat.struct()
+    _check(load_library().gw_strain(ctx, ctypes.byref(c), ctypes.byref(net.net), int(prec), total,
+                                    _ptr(re), _ptr(im), _ptr(freq), _ptr(off), _ptr(status),
+                                    _stream(stream)), ctx)
+    return re, im, freq, off, status
+

@@ -110,7 +110,7 @@ gw_status gwi_build_net(gw_ctx *ctx, const gw_network *net, DevNet &d)
         d.psd_inv_f0_f[p] = (float)(1.0 / P.f0);
     }
     d.inv_sqrt_scale_ref = 1.0 / std::sqrt(net->psd[0].scale);
-    int ni = 0;
+    int ni = 0, na = 0;
     for (int s = 0; s < net->n_det; s++) {
         const gw_detector &D = net->det[s];
         if (!std::isfinite(D.lat) || !std::isfinite(D.lon) || !std::isfinite(D.gamma) ||
@@ -123,24 +123,44 @@ gw_status gwi_build_net(gw_ctx *ctx, const gw_network *net, DevNet &d)
         d.site_slat[s] = std::sin(D.lat);
         d.site_clat[s] = std::cos(D.lat);
         d.site_lon[s] = D.lon;
+        const int n_arms_s = D.shape == 0 ? 1 : 3;
+        const int n_ifo_s = D.shape == 0 ? 1 : 5;
+        if (na + n_arms_s > MAX_ARM || ni + n_ifo_s > MAX_IFO)
+            return fail(ctx, GW_EUNSUPPORTED, "network: more than %d arms or %d interferometer "
+                        "entries", MAX_ARM, MAX_IFO);
         d.site_ifo0[s] = ni;
-        const int nv = D.shape == 0 ? 1 : 2;
-        for (int v = 0; v < nv; v++) {
-            // a triangle is two virtual 90-degree interferometers at gamma_T and
-            // gamma_T + 45 deg with amplitude sqrt(3/2) sin(60 deg) = 3/(2 sqrt 2)
-            const double g = D.gamma + (v ? 0.25 * M_PI : 0.0);
+        const uint32_t arms = ((1u << n_arms_s) - 1u) << na;
+        auto add = [&](double g, double amp, uint32_t need, uint32_t excl) {
             d.ifo_s2g[ni] = std::sin(2.0 * g);
             d.ifo_c2g[ni] = std::cos(2.0 * g);
-            d.ifo_amp[ni] = D.shape == 0 ? std::sin(D.zeta) : 1.5 / std::sqrt(2.0);
+            d.ifo_amp[ni] = amp;
             d.ifo_site[ni] = s;
             d.ifo_psd[ni] = D.psd;
             d.ifo_det[ni] = s;
+            d.ifo_need[ni] = need;
+            d.ifo_excl[ni] = excl;
             ni++;
+        };
+        if (D.shape == 0) {
+            add(D.gamma, std::sin(D.zeta), arms, 0u);
+        } else {
+            // every arm on: two virtual 90-degree interferometers at gamma_T and
+            // gamma_T + 45 deg with amplitude sqrt(3/2) sin(60 deg) = 3/(2 sqrt 2)
+            add(D.gamma, 1.5 / std::sqrt(2.0), arms, 0u);
+            add(D.gamma + 0.25 * M_PI, 1.5 / std::sqrt(2.0), arms, 0u);
+            // otherwise the arms that are on, each a 60-degree interferometer:
+            // a 90-degree one at its bisector with amplitude sin(60 deg)
+            for (int k = 0; k < 3; k++)
+                add(D.gamma + M_PI / 6.0 + 2.0 * M_PI * k / 3.0, std::sqrt(3.0) / 2.0,
+                    1u << (na + k), arms);
         }
+        na += n_arms_s;
         d.site_ifo1[s] = ni;
+        d.site_nslot[s] = D.shape == 0 ? 1 : 2;
     }
     d.n_site = net->n_det;
     d.n_ifo = ni;
+    d.n_arm = na;
     return GW_OK;
 }
 
@@ -164,6 +184,7 @@ DevCat gwi_dev_cat(const gw_catalog *c)
     d.iota = c->iota; d.psi = c->psi; d.tc = c->tc; d.Phic = c->Phic;
     d.chi1 = c->chi1z; d.chi2 = c->chi2z; d.LamT = c->LamT; d.dLamT = c->dLamT;
     d.pset = c->pset; d.fmin = c->fmin; d.fmax = c->fmax; d.npts = c->npts;
+    d.arm_mask = c->arm_mask; d.sel = c->sel;
     return d;
 }
 
@@ -182,6 +203,7 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_EINVAL, "bad precision");
     DevNet dn;
     if ((st = gwi_build_net(ctx, net, dn))) return st;
+    dn.masked = cat->arm_mask != nullptr;
     const int64_t n = cat->n;
     const bool mixed = prec == GW_MIXED && (mode == MODE_FISHER || mode == MODE_SNR ||
                                             mode == MODE_SNRGRAD);
@@ -261,8 +283,8 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     CK(launch_finish(mode, np, dn.n_det, pa, status, snr, snr_det, fisher, grad_snr, grad_params,
                      grad_gamma, xs, s));
     if (fused_grad)
-        CK(launch_snr_grad_from_fisher(n, np, mixed, dn.rotation, fisher, snr, xs, cat->Mc,
-                                       cat->dL, status, grad_snr, grad_params, s));
+        CK(launch_snr_grad_from_fisher(n, np, mixed, dn.rotation, fisher, snr, xs, ctx->evc,
+                                       status, grad_snr, grad_params, s));
     return GW_OK;
 }
 
@@ -270,7 +292,7 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
 
 extern "C" {
 
-int gw_abi_version(void) { return 2; }
+int gw_abi_version(void) { return 3; }
 
 gw_status gw_create(gw_ctx **out, int device)
 {
@@ -401,6 +423,160 @@ gw_status gw_snr(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_p
     c9.pset = nullptr;
     return run_points(ctx, &c9, net, prec, MODE_SNR, 9, status, snr, snr_det, nullptr, nullptr,
                       nullptr, nullptr, nullptr, stream);
+}
+
+gw_status gw_select_snr(gw_ctx *ctx, const double *snr, int64_t n, double threshold,
+                        int64_t *sel, int64_t *n_sel, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (n < 0 || !n_sel) return fail(ctx, GW_EINVAL, "select: n < 0 or n_sel null");
+    *n_sel = 0;
+    if (n == 0) return GW_OK;
+    if (!snr || !sel) return fail(ctx, GW_EINVAL, "select: null array");
+    if (std::isnan(threshold)) return fail(ctx, GW_EINVAL, "select: threshold is NaN");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    gw_status st;
+    if ((st = ensure(ctx, ctx->counts, ctx->counts_cap, (size_t)n))) return st;
+    if ((st = ensure(ctx, ctx->off, ctx->off_cap, (size_t)n + 1))) return st;
+    if ((st = ensure(ctx, ctx->scan, ctx->scan_cap, scan_tmp_size(n)))) return st;
+    CK(launch_select(snr, n, threshold, ctx->counts, ctx->off, ctx->scan, sel, s));
+    CK(cudaMemcpyAsync(n_sel, ctx->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return GW_OK;
+}
+
+namespace {
+// kept parameter slots of a keep mask over n_par parameters (0 = all)
+int kept_slots(uint32_t keep, int n_par, int *idx)
+{
+    if (keep == 0) keep = (1u << n_par) - 1u;
+    int k = 0;
+    for (int i = 0; i < n_par; i++)
+        if ((keep >> i) & 1u) idx[k++] = i;
+    return (keep >> n_par) ? -1 : k;
+}
+}  // namespace
+
+gw_status gw_fisher_eig(gw_ctx *ctx, const double *fisher, int64_t n, int n_par, int normalize,
+                        double *eigval, double *eigvec, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (n < 0 || n_par < 1 || n_par > 11) return fail(ctx, GW_EINVAL, "eig: bad n or n_par");
+    if (n == 0) return GW_OK;
+    if (!fisher || (!eigval && !eigvec)) return fail(ctx, GW_EINVAL, "eig: null array");
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_fisher_eig(n, n_par, normalize, fisher, eigval, eigvec, (cudaStream_t)stream));
+    return GW_OK;
+}
+
+gw_status gw_covariance(gw_ctx *ctx, const double *fisher, int64_t n, int n_par, uint32_t keep,
+                        const double *prior, int method, double thresh, double cond_max,
+                        double *cov, double *cond, double *inv_err, int32_t *status,
+                        void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (n < 0 || n_par < 1 || n_par > 11) return fail(ctx, GW_EINVAL, "covariance: bad n or n_par");
+    if (method < GW_INV_CHO || method > GW_INV_LU)
+        return fail(ctx, GW_EINVAL, "covariance: unknown method %d", method);
+    if (!(thresh >= 0.0) || !(thresh < 1.0))
+        return fail(ctx, GW_EINVAL, "covariance: thresh must be in [0, 1)");
+    CovArgs a;
+    memset(&a, 0, sizeof a);
+    a.n = n;
+    a.P = n_par;
+    a.Pk = kept_slots(keep, n_par, a.idx);
+    if (a.Pk < 1) return fail(ctx, GW_EINVAL, "covariance: keep mask 0x%x for %d parameters", keep, n_par);
+    if (prior)
+        for (int i = 0; i < n_par; i++) {
+            if (!std::isfinite(prior[i]) || prior[i] < 0.0)
+                return fail(ctx, GW_EINVAL, "covariance: prior[%d] must be finite and >= 0", i);
+            a.prior[i] = prior[i];
+        }
+    a.method = method;
+    a.thresh = thresh;
+    a.cond_max = std::isnan(cond_max) ? INFINITY : cond_max;
+    if (n == 0) return GW_OK;
+    if (!fisher || !cov) return fail(ctx, GW_EINVAL, "covariance: null array");
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_covariance(a, fisher, cov, cond, inv_err, status, (cudaStream_t)stream));
+    return GW_OK;
+}
+
+gw_status gw_packed_submatrix(gw_ctx *ctx, const double *in, int64_t n, int n_par, uint32_t keep,
+                              double *out, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (n < 0 || n_par < 1 || n_par > 11) return fail(ctx, GW_EINVAL, "submatrix: bad n or n_par");
+    SubIdx si;
+    const int K = kept_slots(keep, n_par, si.idx);
+    if (K < 1) return fail(ctx, GW_EINVAL, "submatrix: keep mask 0x%x for %d parameters", keep, n_par);
+    if (n == 0) return GW_OK;
+    if (!in || !out) return fail(ctx, GW_EINVAL, "submatrix: null array");
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_submatrix(n, n_par, K, si, in, out, (cudaStream_t)stream));
+    return GW_OK;
+}
+
+gw_status gw_sky_area(gw_ctx *ctx, const double *cov, int64_t n, int n_par, int i_theta,
+                      int i_phi, const double *theta, double perc, int units, double *area,
+                      void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (n < 0 || n_par < 2 || n_par > 11 || i_theta < 0 || i_theta >= n_par || i_phi < 0 ||
+        i_phi >= n_par || i_theta == i_phi)
+        return fail(ctx, GW_EINVAL, "sky_area: bad n, n_par or parameter slots");
+    if (!(perc > 0.0) || !(perc < 100.0) || (units != 0 && units != 1))
+        return fail(ctx, GW_EINVAL, "sky_area: perc must be in (0, 100), units 0 or 1");
+    if (n == 0) return GW_OK;
+    if (!cov || !theta || !area) return fail(ctx, GW_EINVAL, "sky_area: null array");
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_sky_area(n, n_par, i_theta, i_phi, cov, theta, perc, units, area,
+                       (cudaStream_t)stream));
+    return GW_OK;
+}
+
+gw_status gw_strain(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_precision prec,
+                    int64_t total_points, double *re, double *im, double *freq,
+                    int64_t *point_off, int32_t *status_out, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    gw_status st = gwi_check_cat(ctx, cat, 9);
+    if (st) return st;
+    if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_EINVAL, "strain: precision");
+    DevNet dn;
+    if ((st = gwi_build_net(ctx, net, dn))) return st;
+    const int64_t n = cat->n;
+    if (n == 0) return total_points == 0 ? GW_OK : fail(ctx, GW_EINVAL, "strain: total_points != 0");
+    if (!re || !im) return fail(ctx, GW_EINVAL, "strain: null output");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure(ctx, ctx->evc, ctx->evc_cap, (size_t)n * EVC))) return st;
+    if ((st = ensure(ctx, ctx->sitec, ctx->sitec_cap, (size_t)n * dn.n_site * SC_N))) return st;
+    if ((st = ensure(ctx, ctx->counts, ctx->counts_cap, (size_t)n))) return st;
+    if ((st = ensure(ctx, ctx->off, ctx->off_cap, (size_t)n + 1))) return st;
+    if ((st = ensure(ctx, ctx->scan, ctx->scan_cap, scan_tmp_size(n)))) return st;
+    int32_t *status = status_out;
+    if (!status) {
+        if ((st = ensure(ctx, ctx->status, ctx->status_cap, (size_t)n))) return st;
+        status = ctx->status;
+    }
+    int64_t *poff = point_off ? point_off : ctx->off;
+    CK(launch_point_offsets(cat->npts, cat->sel, n, ctx->counts, poff, ctx->scan, s));
+    int64_t tot = 0;
+    CK(cudaMemcpyAsync(&tot, poff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (tot != total_points)
+        return fail(ctx, GW_EINVAL, "strain: total_points %lld, the grids hold %lld points",
+                    (long long)total_points, (long long)tot);
+    // the per-event constants of the Fisher pass (parameter set ignored)
+    gw_catalog c9 = *cat;
+    c9.pset = nullptr;
+    const DevCat dc = gwi_dev_cat(&c9);
+    CK(launch_event_setup(dc, dn, 9, ctx->evc, ctx->sitec, nullptr, nullptr, status, ctx->counts, s));
+    CK(launch_strain(dn, n, total_points, prec == GW_MIXED ? 1 : 0, ctx->evc, ctx->sitec, status,
+                     poff, re, im, freq, s));
+    return GW_OK;
 }
 
 gw_status gw_fisher(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_precision prec,

@@ -18,7 +18,8 @@
 namespace gw {
 
 constexpr int MAX_SITE = 8;
-constexpr int MAX_IFO = 16;
+constexpr int MAX_IFO = 24;
+constexpr int MAX_ARM = 32;
 constexpr int MAX_DET = 8;
 constexpr int MAX_PSD = 4;
 constexpr int MAX_TERM = 4;
@@ -44,6 +45,14 @@ struct DevNet {
     int site_ifo0[MAX_SITE], site_ifo1[MAX_SITE];   // IFOs of site s: [ifo0, ifo1)
     int ifo_site[MAX_IFO], ifo_psd[MAX_IFO], ifo_det[MAX_IFO];
     double ifo_s2g[MAX_IFO], ifo_c2g[MAX_IFO], ifo_amp[MAX_IFO];
+    // duty factor: interferometer q is used for an event whose arm mask m has
+    // (m & need) == need and not (excl != 0 and (m & excl) == excl).  A
+    // triangle appears as its two-interferometer form (need = its three arms)
+    // and as its three single arms (need = that arm, excl = its three arms).
+    uint32_t ifo_need[MAX_IFO], ifo_excl[MAX_IFO];
+    int site_nslot[MAX_SITE];   // interferometers in use per event and site: 1 (L), 2 (triangle)
+    int n_arm;
+    int masked;                 // the call has arm masks: read the slots per event
     double psd_inv_f0[MAX_PSD], psd_f0[MAX_PSD];
     int psd_nterm[MAX_PSD];
     double psd_coef[MAX_PSD][MAX_TERM];   // scale * coef
@@ -70,7 +79,11 @@ enum EvSlot : int {
     EV_C2PSI, EV_S2PSI,
     EV_AMC,                             // 5 / (6 Mc)
     EV_INVDL,
-    EV_PM,                              // 11: d Psi / d Mc            (basis B11)
+    EV_IFOON,                           // bits of the interferometers in use (duty factor)
+    EV_ARMON,                           // the event's arm mask (duty factor)
+    EV_PHI0,                            // -Phic - pi/4 (strain phase constant)
+    EV_PSI,                             // 11: Psi_PN + Psi_tidal      (basis B11)
+    EV_PM = EV_PSI + 11,                // 11: d Psi / d Mc            (basis B11)
     EV_PE = EV_PM + 11,                 // 11: d Psi / d eta | Mc      (basis B11)
     EV_P9 = EV_PE + 11,                 // 4: slot 9  (v^-2, v^-1, v^5, v^7)
     EV_P10 = EV_P9 + 4,                 // 4: slot 10
@@ -89,6 +102,7 @@ enum SiteSlot : int {
     SC_A1, SC_A2, SC_A3, SC_A4, SC_A5, SC_B1, SC_B2, SC_B3, SC_B4,
     SC_A1T, SC_A2T, SC_A3T, SC_A4T, SC_A5T, SC_B1T, SC_B2T, SC_B3T, SC_B4T,
     SC_D1, SC_D2, SC_D1T, SC_D2T, // Doppler: R/c [cos lat sin th, sin lat cos th] and d/d theta
+    SC_SLOT0, SC_SLOT1,           // the interferometer entries in use (duty factor), -1 = none
     SC_X0LO,                      // FP32 table only: x0 - (float)x0 (double-float x0)
     SC_N
 };

@@ -14,6 +14,8 @@ struct DevCat {
     const int8_t *pset;
     const double *fmin, *fmax;
     const int32_t *npts;
+    const uint32_t *arm_mask;   // duty-factor arm masks per row, or null (all on)
+    const int64_t *sel;         // rows of the call's events, or null (identity)
 };
 
 struct PointArgs {
@@ -76,9 +78,42 @@ cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const
                           double *grad_params, double *grad_gamma, double *xsums, cudaStream_t s);
 
 // SNR vector-Jacobian product from a Fisher pass (see gw_fisher)
+// strain output (gw_strain.cu): off = exclusive scan of the events' grid lengths
+cudaError_t launch_point_offsets(const int32_t *npts, const int64_t *sel, int64_t n,
+                                 int64_t *counts, int64_t *off, int64_t *scan_tmp, cudaStream_t s);
+cudaError_t launch_strain(const DevNet &net, int64_t n, int64_t total, int mixed,
+                          const double *evc, const double *sitec, const int32_t *status,
+                          const int64_t *poff, double *re, double *im, double *freq,
+                          cudaStream_t s);
+
+// covariance tools (gw_covtools.cu)
+struct CovArgs {
+    int64_t n;
+    int P, Pk;             // parameters of the input, parameters kept
+    int idx[11];           // kept parameter slots, increasing
+    double prior[11];      // added to the diagonal, per original slot
+    int method;            // gw_inv_method
+    double thresh, cond_max;
+};
+struct SubIdx {
+    int idx[11];
+};
+cudaError_t launch_fisher_eig(int64_t n, int P, int normalize, const double *F, double *w,
+                              double *V, cudaStream_t s);
+cudaError_t launch_covariance(const CovArgs &a, const double *F, double *cov, double *cond,
+                              double *eps, int32_t *status, cudaStream_t s);
+cudaError_t launch_submatrix(int64_t n, int P, int K, const SubIdx &idx, const double *in,
+                             double *out, cudaStream_t s);
+cudaError_t launch_sky_area(int64_t n, int P, int it, int ip, const double *cov,
+                            const double *theta, double perc, int units, double *area,
+                            cudaStream_t s);
+
+// detection gate: sel = indices i with snr[i] > th (increasing); off[n] = count
+cudaError_t launch_select(const double *snr, int64_t n, double th, int64_t *flag, int64_t *off,
+                          int64_t *scan_tmp, int64_t *sel, cudaStream_t s);
 cudaError_t launch_snr_grad_from_fisher(int64_t n, int np, bool mixed, int rot,
                                         const double *fisher, const double *snr,
-                                        const double *xsums, const double *Mc, const double *dL,
+                                        const double *xsums, const double *evc,
                                         const int32_t *status, const double *grad_snr,
                                         double *grad_params, cudaStream_t s);
 

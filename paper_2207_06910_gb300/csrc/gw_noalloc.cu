@@ -68,6 +68,7 @@ extern "C" gw_status gw_fisher_noalloc(const gw_catalog *cat, const gw_network *
     if (st) return st;
     DevNet dn;
     if ((st = gwi_build_net(nullptr, net, dn))) return st;
+    dn.masked = cat->arm_mask != nullptr;
     const int64_t n = cat->n;
     if (n == 0) return GW_OK;
     if (!fisher || !status) return GW_EINVAL;

@@ -288,6 +288,7 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
 #pragma unroll 1
                 for (int s = 0; s < net.n_site; s++) {
                     const double *S = A.sitec + (e * net.n_site + s) * (int64_t)SC_N;
+                    if (net.masked && S[SC_SLOT0] < 0.0) continue;   // every arm of the site off
                     const double x = ROT ? fma(OMEGA_E, tau, S[SC_X0]) : S[SC_X0];
                     double sx, cxx;
                     sincos(x, &sx, &cxx);
@@ -328,8 +329,17 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
                         ph.Mc = ph.eta = ph.th = ph.ph = ph.tc = ph.p9 = ph.p10 = 0.0;
                     }
 #pragma unroll 1
-                    for (int q = net.site_ifo0[s]; q < net.site_ifo1[s]; q++) {
-                        const double amp = net.ifo_amp[q];
+                    for (int slot = 0; slot < net.site_nslot[s]; slot++) {
+                        // interferometer of this slot; an empty slot (duty factor)
+                        // runs with amplitude 0, so every group of a warp takes
+                        // the same path
+                        int q = net.masked ? (int)S[SC_SLOT0 + slot] : net.site_ifo0[s] + slot;
+                        double on = 1.0;
+                        if (q < 0) {
+                            q = net.site_ifo0[s];
+                            on = 0.0;
+                        }
+                        const double amp = net.ifo_amp[q] * on;
                         const Pat pt = patterns(net.ifo_s2g[q], net.ifo_c2g[q], amp * c2p,
                                                 amp * s2p, J);
                         const double sg = Wp[net.ifo_psd[q]];

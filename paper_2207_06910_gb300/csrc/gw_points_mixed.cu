@@ -429,6 +429,7 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
 #pragma unroll 1
                 for (int s = 0; s < net.n_site; s++) {
                     const float *S = A.sitec_f + (e * net.n_site + s) * (int64_t)SC_N;
+                    if (net.masked && S[SC_SLOT0] < 0.0f) continue;  // every arm of the site off
                     float xs;
                     if (ROT) {
                         // x = x0 + Omega_E tau* in double-float, reduced to about [-pi, pi]
@@ -476,8 +477,17 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                         ph.Mc = ph.eta = ph.th = ph.ph = ph.tc = ph.p9 = ph.p10 = 0.0f;
                     }
 #pragma unroll 1
-                    for (int q = net.site_ifo0[s]; q < net.site_ifo1[s]; q++) {
-                        const float amp = (float)net.ifo_amp[q];
+                    for (int slot = 0; slot < net.site_nslot[s]; slot++) {
+                        // interferometer of this slot; an empty slot (duty factor)
+                        // runs with amplitude 0, so every group of a warp takes
+                        // the same path
+                        int q = net.masked ? (int)S[SC_SLOT0 + slot] : net.site_ifo0[s] + slot;
+                        float on = 1.0f;
+                        if (q < 0) {
+                            q = net.site_ifo0[s];
+                            on = 0.0f;
+                        }
+                        const float amp = (float)net.ifo_amp[q] * on;
                         const PatF pt = patterns_f((float)net.ifo_s2g[q], (float)net.ifo_c2g[q],
                                                    amp * c2p, amp * s2p, J);
                         const float sg = sig[net.ifo_psd[q]];

@@ -95,24 +95,33 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= cat.n) return;
-    const double Mc = cat.Mc[e], eta = cat.eta[e], dL = cat.dL[e];
-    const double th = cat.theta[e], ph = cat.phi[e], io = cat.iota[e], ps = cat.psi[e];
-    const double tc = cat.tc[e];
-    const double c1 = cat.chi1 ? cat.chi1[e] : 0.0, c2 = cat.chi2 ? cat.chi2[e] : 0.0;
-    const double LT = cat.LamT ? cat.LamT[e] : 0.0, dLT = cat.dLamT ? cat.dLamT[e] : 0.0;
-    const int pset = cat.pset ? (int)cat.pset[e] : 0;
-    const double fmin = cat.fmin[e], fmx = cat.fmax[e];
-    const int N = cat.npts[e];
+    const int64_t r = cat.sel ? cat.sel[e] : e;     // catalog row of the call's event e
+    const double Mc = cat.Mc[r], eta = cat.eta[r], dL = cat.dL[r];
+    const double th = cat.theta[r], ph = cat.phi[r], io = cat.iota[r], ps = cat.psi[r];
+    const double tc = cat.tc[r];
+    const double c1 = cat.chi1 ? cat.chi1[r] : 0.0, c2 = cat.chi2 ? cat.chi2[r] : 0.0;
+    const double LT = cat.LamT ? cat.LamT[r] : 0.0, dLT = cat.dLamT ? cat.dLamT[r] : 0.0;
+    const int pset = cat.pset ? (int)cat.pset[r] : 0;
+    const double fmin = cat.fmin[r], fmx = cat.fmax[r];
+    const int N = cat.npts[r];
+    // duty factor: interferometer entries in use for this event's arm mask
+    const uint32_t am = cat.arm_mask ? cat.arm_mask[r] : 0xffffffffu;
+    uint32_t ifo_on = 0;
+    for (int q = 0; q < net.n_ifo; q++) {
+        const uint32_t need = net.ifo_need[q], excl = net.ifo_excl[q];
+        if ((am & need) == need && !(excl && (am & excl) == excl)) ifo_on |= 1u << q;
+    }
     int st = 0;
     if (!(Mc > 0.0) || !(eta > 0.0) || !(eta <= 0.25) || !(dL > 0.0)) st |= 16;
     if (pset < 0 || pset > 2 || ((np == 9) != (pset == 0))) st |= 16;
     if (!isfinite(th) || !isfinite(ph) || !isfinite(io) || !isfinite(ps) || !isfinite(tc) ||
         !isfinite(c1) || !isfinite(c2) || !isfinite(LT) || !isfinite(dLT) ||
-        !isfinite(cat.Phic[e]))
+        !isfinite(cat.Phic[r]))
         st |= 16;
     if (!(fmin > 0.0) || !(fmx > fmin) || !isfinite(fmx) || N < 2) st |= 8;
     status[e] = st;
-    counts[e] = st ? 0 : (int64_t)((N + CHUNK_MAX - 1) / CHUNK_MAX);
+    // no work items when no interferometer is in use (zero SNR and Fisher)
+    counts[e] = (st || !ifo_on) ? 0 : (int64_t)((N + CHUNK_MAX - 1) / CHUNK_MAX);
     if (st) return;
 
     double *E = evc + e * (int64_t)EVC;
@@ -148,6 +157,9 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
     E[EV_S2PSI] = s2p;
     E[EV_AMC] = 5.0 / (6.0 * Mc);
     E[EV_INVDL] = 1.0 / dL;
+    E[EV_IFOON] = (double)ifo_on;
+    E[EV_ARMON] = (double)am;
+    E[EV_PHI0] = -cat.Phic[r] - 0.25 * PI;
 
     // ---- TaylorF2 3.5PN phase coefficients (restricted PN)
     const double pi2 = PI * PI;
@@ -182,8 +194,10 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
                        + 2.0 * 76055.0 / 1728.0 * eta - 3.0 * 127825.0 / 1296.0 * eta * eta;
     const double dp7 = PI * (378515.0 / 1512.0 - 2.0 * 74045.0 / 756.0 * eta);
     const double dt12 = 6595.0 / 364.0 * (-2.0 / d) * dLT;
-    const double pre = 3.0 / (128.0 * eta);
     const double ie = 1.0 / eta;
+    const double pre = 3.0 / 128.0 * ie;
+    // reciprocals once (the FP64 divide is a multi-instruction sequence)
+    const double i3Mc = 1.0 / (3.0 * Mc), i5eta = 0.2 * ie;
     // v dPsi/dv
     const double V[11] = {-5.0, -3.0 * p2, -2.0 * p3, -p4, 3.0 * p5a, p6 + L6, 2.0 * p7,
                           5.0 * t10, 7.0 * t12, 0.0, L6};
@@ -191,9 +205,13 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
     const double De[11] = {-ie, 55.0 / 9.0 - p2 * ie, 4.0 * dbeta - p3 * ie, dp4 - p4 * ie,
                            dp5a * ln6h - p5c * ie, dp6 - p6 * ie, dp7 - p7 * ie, -t10 * ie,
                            dt12 - t12 * ie, 3.0 * (dp5a - p5a * ie), -L6 * ie};
+    // Psi itself (strain output): v^-5 (1, p2 v^2, p3 v^3, p4 v^4) + p5a (1 - 3 ln v_lso
+    // + 3 ln v) + (p6 + L6 ln v) v + p7 v^2 + tidal v^5, v^7, all times 3/(128 eta)
+    const double Ps[11] = {1.0, p2, p3, p4, p5c, p6, p7, t10, t12, 3.0 * p5a, L6};
     for (int k = 0; k < 11; k++) {
-        E[EV_PM + k] = pre * V[k] / (3.0 * Mc);
-        E[EV_PE + k] = pre * (De[k] - V[k] / (5.0 * eta));
+        E[EV_PSI + k] = pre * Ps[k];
+        E[EV_PM + k] = pre * V[k] * i3Mc;
+        E[EV_PE + k] = pre * (De[k] - V[k] * i5eta);
     }
     double q9[4] = {0, 0, 0, 0}, q10[4] = {0, 0, 0, 0};
     if (pset == 1) {
@@ -235,14 +253,16 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
                           dt6 - t6 * ie, dt7 - t7 * ie, -t6L * ie};
     for (int k = 0; k < 8; k++) {
         E[EV_T0 + k] = Kt * T0[k];
-        E[EV_TM + k] = Kt * Tv[k] / (3.0 * Mc);
-        E[EV_TE + k] = Kt * (Te[k] - Tv[k] / (5.0 * eta));
+        E[EV_TM + k] = Kt * Tv[k] * i3Mc;
+        E[EV_TE + k] = Kt * (Te[k] - Tv[k] * i5eta);
     }
 
-    // double-float (hi, lo) copy of every constant for the mixed path
+    // double-float (hi, lo) copy of the constants the mixed point loop reads
+    // (slots EV_WC0 .. EV_INVDL and the polynomial coefficients EV_PM ..)
     if (evc_f) {
         float2 *Ef = evc_f + e * (int64_t)EVC;
-        for (int q = 0; q < EVC; q++) {
+        for (int q = EV_WC0; q < EVC; q++) {
+            if (q > EV_INVDL && q < EV_PM) continue;
             const float hi = (float)E[q];
             Ef[q] = make_float2(hi, (float)(E[q] - (double)hi));
         }
@@ -284,6 +304,13 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
         S[SC_D2] = R_EARTH_S * sl * cth;
         S[SC_D1T] = R_EARTH_S * cl * cth;
         S[SC_D2T] = -R_EARTH_S * sl * sth;
+        // the (at most two) interferometer entries of this site in use: the
+        // point kernels run a fixed number of slots per site, whatever the mask
+        int slot[2] = {-1, -1}, nsl = 0;
+        for (int q = net.site_ifo0[s]; q < net.site_ifo1[s] && nsl < 2; q++)
+            if ((ifo_on >> q) & 1u) slot[nsl++] = q;
+        S[SC_SLOT0] = (double)slot[0];
+        S[SC_SLOT1] = (double)slot[1];
         S[SC_X0LO] = 0.0;
         if (sitec_f) {
             float *Sf = sitec_f + (e * net.n_site + s) * (int64_t)SC_N;
@@ -422,10 +449,40 @@ __global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc, int64
             double s0 = 0.0;
             if (!over)
                 for (int64_t it = i0; it < i1; it++) s0 += partial[it * nacc];
-            // d SNR / d theta = sum W Re(Q* g) / SNR
-            grad_params[(int64_t)(a - 1) * n + e] = bad ? NAN : grad_snr[e] * s / sqrt(s0);
+            // d SNR / d theta = sum W Re(Q* g) / SNR (zero when no arm is on)
+            grad_params[(int64_t)(a - 1) * n + e] =
+                bad ? NAN : (s0 > 0.0 ? grad_snr[e] * s / sqrt(s0) : 0.0);
         }
     }
+}
+
+// detection gate (snr_th): flags, then order-preserving compaction after an
+// exclusive scan of the flags
+__global__ void k_flag_gt(const double *snr, int64_t n, double th, int64_t *flag)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = snr[i] > th ? 1 : 0;
+}
+
+__global__ void k_compact(const double *snr, int64_t n, double th, const int64_t *off,
+                          int64_t *sel)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && snr[i] > th) sel[off[i]] = i;
+}
+
+cudaError_t launch_select(const double *snr, int64_t n, double th, int64_t *flag, int64_t *off,
+                          int64_t *scan_tmp, int64_t *sel, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int bs = 256;
+    const unsigned nb = (unsigned)((n + bs - 1) / bs);
+    k_flag_gt<<<nb, bs, 0, s>>>(snr, n, th, flag);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = launch_scan(flag, n, off, scan_tmp, s)) != cudaSuccess) return e;
+    k_compact<<<nb, bs, 0, s>>>(snr, n, th, off, sel);
+    return cudaGetLastError();
 }
 
 // logdet mode: total over all items of each detector accumulator, fixed order
@@ -453,23 +510,26 @@ __global__ void k_finish_total(int64_t cap, const int64_t *total, int nacc, cons
 //             Mc: 5/(6 Mc) SNR^2 + X1, eta: X2, dL: -SNR^2/dL, theta: X3, phi: X0,
 //             iota: X4, psi: X5, tc: -Omega_E X0, Phic and slots 9, 10: 0.
 __global__ void k_snr_grad(int64_t n, int np, int mixed, int rot, const double *F,
-                           const double *snr, const double *X, const double *Mc, const double *dL,
+                           const double *snr, const double *X, const double *evc,
                            const int32_t *status, const double *grad_snr, double *grad)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n) return;
     const bool bad = status[e] != 0;
-    const double s = snr[e], up = grad_snr[e], d = dL[e];
+    const double s = snr[e], up = grad_snr[e];
+    const double d = evc[e * (int64_t)EVC + EV_DL], Mc = evc[e * (int64_t)EVC + EV_MC];
     for (int i = 0; i < np; i++) {
         double g;
-        if (!mixed) {
+        if (!(s > 0.0)) {
+            g = 0.0;   // no arm on (duty factor): the SNR is identically zero
+        } else if (!mixed) {
             const int lo = i < 2 ? i : 2, hi = i < 2 ? 2 : i;
             const int k = lo * np - lo * (lo - 1) / 2 + (hi - lo);
             g = -d * F[(int64_t)k * n + e] / s;
         } else {
             const double s2 = s * s;
             switch (i) {
-            case 0: g = (5.0 / (6.0 * Mc[e]) * s2 + X[1 * n + e]) / s; break;
+            case 0: g = (5.0 / (6.0 * Mc) * s2 + X[1 * n + e]) / s; break;
             case 1: g = X[2 * n + e] / s; break;
             case 2: g = -s2 / (d * s); break;
             case 3: g = X[3 * n + e] / s; break;
@@ -486,14 +546,14 @@ __global__ void k_snr_grad(int64_t n, int np, int mixed, int rot, const double *
 
 cudaError_t launch_snr_grad_from_fisher(int64_t n, int np, bool mixed, int rot,
                                         const double *fisher, const double *snr,
-                                        const double *xsums, const double *Mc, const double *dL,
+                                        const double *xsums, const double *evc,
                                         const int32_t *status, const double *grad_snr,
                                         double *grad_params, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     int bs = 256;
     k_snr_grad<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(n, np, mixed ? 1 : 0, rot, fisher, snr,
-                                                            xsums, Mc, dL, status, grad_snr,
+                                                            xsums, evc, status, grad_snr,
                                                             grad_params);
     return cudaGetLastError();
 }
@@ -554,12 +614,16 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
     double kappa = NAN, eps = NAN;
     double C[NP][NP];
     if (!st) {
+        // reciprocals once: the FP64 divide is a multi-instruction sequence
+        double id[NP], il[NP];
+#pragma unroll
+        for (int i = 0; i < NP; i++) id[i] = 1.0 / d[i];
         double H[NP][NP], L[NP][NP];
 #pragma unroll
         for (int i = 0; i < NP; i++)
 #pragma unroll
             for (int j = 0; j < NP; j++) {
-                H[i][j] = G[i][j] / (d[i] * d[j]);
+                H[i][j] = G[i][j] * id[i] * id[j];
                 L[i][j] = 0.0;
             }
         // Cholesky H = L L^T
@@ -571,13 +635,13 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
             if (!(sjj > 0.0)) st |= 1;
             const double ljj = sqrt(sjj);
             L[j][j] = ljj;
-            const double il = 1.0 / ljj;
+            il[j] = 1.0 / ljj;
 #pragma unroll
             for (int i = j + 1; i < NP; i++) {
                 double t = H[i][j];
 #pragma unroll
                 for (int k = 0; k < j; k++) t -= L[i][k] * L[j][k];
-                L[i][j] = t * il;
+                L[i][j] = t * il[j];
             }
         }
         if (!st) {
@@ -591,39 +655,52 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
                     double t = (i == c) ? 1.0 : 0.0;
 #pragma unroll
                     for (int k = c; k < i; k++) t -= L[i][k] * M[k][c];
-                    M[i][c] = t / L[i][i];
+                    M[i][c] = t * il[i];
                 }
             }
-            // Hinv = M^T M
+            // Hinv = M^T M, one triangle; 1-norms of H and Hinv by columns
+            double colh[NP], coli[NP];
+#pragma unroll
+            for (int j = 0; j < NP; j++) {
+                colh[j] = 0.0;
+                coli[j] = 0.0;
+#pragma unroll
+                for (int i = 0; i < NP; i++) colh[j] += fabs(H[i][j]);
+            }
+#pragma unroll
+            for (int j = 0; j < NP; j++)
+#pragma unroll
+                for (int i = 0; i <= j; i++) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int k = j; k < NP; k++) t += M[k][i] * M[k][j];
+                    const double c = t * id[i] * id[j];
+                    C[i][j] = c;
+                    C[j][i] = c;
+                    coli[j] += fabs(t);
+                    if (i != j) coli[i] += fabs(t);
+                }
             double hn1 = 0.0, in1 = 0.0;
 #pragma unroll
             for (int j = 0; j < NP; j++) {
-                double colh = 0.0, coli = 0.0;
-#pragma unroll
-                for (int i = 0; i < NP; i++) {
-                    double t = 0.0;
-#pragma unroll
-                    for (int k = (i > j ? i : j); k < NP; k++) t += M[k][i] * M[k][j];
-                    C[i][j] = t / (d[i] * d[j]);
-                    coli += fabs(t);
-                    colh += fabs(H[i][j]);
-                }
-                hn1 = fmax(hn1, colh);
-                in1 = fmax(in1, coli);
+                hn1 = fmax(hn1, colh[j]);
+                in1 = fmax(in1, coli[j]);
             }
             kappa = hn1 * in1;
             if (kappa > 1.0 / DBL_EPSILON) st |= 32;
             if (kappa > cond_max) st |= 2;
-            eps = 0.0;
+            if (inv_err) {
+                eps = 0.0;
 #pragma unroll
-            for (int i = 0; i < NP; i++)
+                for (int i = 0; i < NP; i++)
 #pragma unroll
-                for (int j = 0; j < NP; j++) {
-                    double t = (i == j) ? -1.0 : 0.0;
+                    for (int j = 0; j < NP; j++) {
+                        double t = (i == j) ? -1.0 : 0.0;
 #pragma unroll
-                    for (int k = 0; k < NP; k++) t += G[i][k] * C[k][j];
-                    eps = fmax(eps, fabs(t));
-                }
+                        for (int k = 0; k < NP; k++) t = fma(G[i][k], C[k][j], t);
+                        eps = fmax(eps, fabs(t));
+                    }
+            }
         }
     }
     const bool ok = !(st & (1 | 2 | 4));
