@@ -51,7 +51,7 @@ FFMA_PER_CLK_SM = 128        # FP32 FMA lanes per SM (measured 117 / clock with 
 # ncu capture of the 2e4-event c3 catalog (4,376,070 points) of the current
 # kernels (profiles/k_points_*_fisher_c3.md); scaled by points to a full launch
 DRAM_BYTES_PER_POINT = {"mixed": (21.669888e6 + 157.184e3) / 4376070,
-                        "fp64": (16.705792e6 + 59.648e3) / 4376070}
+                        "fp64": (19.284224e6 + 91.136e3) / 4376070}
 
 
 def parse():

@@ -699,3 +699,53 @@ def test_sky_area_is_the_gaussian_confidence_ellipse():
         q = np.einsum("ni,ij,nj->n", x, np.linalg.inv(Cang), x)
         frac = np.mean(q <= k)
         assert abs(frac - X / 100) < 2e-3, (X, frac)
+
+
+# ---------------------------------------------------------------- Table 2 fixture
+def _table2():
+    import os
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "detectors_table2.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            name, lat, lon, gam, zeta, shape = line.split()
+            rows[name] = (float(lat), float(lon), float(gam), float(zeta), shape)
+    return rows
+
+
+def test_table2_triangle_is_the_configs_triangle():
+    """The synthetic networks' triangle is the ET Sardinia row of Table 2."""
+    lat, lon, gam, zeta, shape = _table2()["ETS"]
+    D = math.pi / 180
+    assert shape == "T"
+    np.testing.assert_allclose(gwcat.DET_TRI[:4], [lat * D, lon * D, gam * D, zeta * D], rtol=1e-15)
+    assert gwcat.DET_TRI[4] == 1
+
+
+def test_table2_hanford_livingston_delay():
+    """Table 2's H1 and L1 positions: for a source along the baseline the strain
+    phase difference grows as 2 pi f |r_H - r_L| / c (about 10 ms of light travel
+    between the sites); for a source perpendicular to it, as 0."""
+    t = _table2()
+    D = math.pi / 180
+    ev, _ = _one_event("c0", zero_spin=True)
+    g = OMEGA_E * ev[7]
+
+    def rvec(name):
+        lat, lon = t[name][0] * D, t[name][1] * D + g
+        return np.array([math.cos(lat) * math.cos(lon), math.cos(lat) * math.sin(lon), math.sin(lat)])
+
+    b = (rvec("H1") - rvec("L1")) * R_EARTH
+    dets = [np.array([[t[k][0] * D, t[k][1] * D, t[k][2] * D, t[k][3] * D, 0, 0]]) for k in ("H1", "L1")]
+    for n, want in ((b / np.linalg.norm(b), np.linalg.norm(b) / C_SI), (None, 0.0)):
+        if n is None:   # a direction perpendicular to the baseline
+            n = np.cross(b, [0.0, 0.0, 1.0])
+            n /= np.linalg.norm(n)
+        e2 = ev.copy()
+        e2[3] = math.acos(n[2])
+        e2[4] = math.atan2(n[1], n[0])
+        f, hH = oracle.strain(e2, 10.0, 400.0, 64, dets[0], 0)
+        _, hL = oracle.strain(e2, 10.0, 400.0, 64, dets[1], 0)
+        slope = np.polyfit(f, np.unwrap(np.angle(hH[0] / hL[0])), 1)[0]
+        assert abs(slope / (2 * math.pi) - want) < 1e-9 * max(want, 1e-3)
+    assert 9.9e-3 < np.linalg.norm(b) / C_SI < 1.01e-2
