@@ -581,7 +581,17 @@ cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const
 // ------------------------------------------------------------------------
 // Batched inversion (Sec. 4.1): normalise by sqrt(diag), Cholesky, triangular
 // inverse, C = L^-T L^-1 rescaled; 1-norm condition number of the normalised
-// matrix and eps = max |Gamma C - 1|.  One thread per event, FP64.
+// matrix and eps = max |Gamma C - 1|.  One thread per event, FP64.  The
+// factorisation works in place on one lower triangle (H, then L, then
+// M = L^-1) and the inverse is formed on one packed triangle, so that a
+// thread holds ~2 P(P+1)/2 values instead of five full matrices; the rows of
+// Gamma for eps are read again from the input.
+template <int NP>
+__device__ __forceinline__ constexpr int pkt(int i, int j)   // packed (i <= j)
+{
+    return i * NP - i * (i - 1) / 2 + (j - i);
+}
+
 template <int NP>
 __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, double cond_max,
                                                 double *cov, double *cond, double *inv_err,
@@ -590,95 +600,85 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
     constexpr int NK = NP * (NP + 1) / 2;
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n) return;
-    double G[NP][NP];
+    double A[NP][NP];       // lower triangle: H, then L, then M = L^-1
+    double Cu[NK];          // inverse, packed upper triangle (normalised, then rescaled)
+    double d[NP], id[NP], il[NP];
     int st = 0;
-    {
-        int k = 0;
 #pragma unroll
-        for (int i = 0; i < NP; i++)
+    for (int i = 0; i < NP; i++)
 #pragma unroll
-            for (int j = i; j < NP; j++) {
-                double v = F[(int64_t)k * n + e];
-                k++;
-                if (!isfinite(v)) st |= 4;
-                G[i][j] = v;
-                G[j][i] = v;
-            }
-    }
-    double d[NP];
+        for (int j = i; j < NP; j++) {
+            const double v = F[(int64_t)pkt<NP>(i, j) * n + e];
+            if (!isfinite(v)) st |= 4;
+            A[j][i] = v;
+        }
 #pragma unroll
     for (int i = 0; i < NP; i++) {
-        if (!(G[i][i] > 0.0)) st |= 1;
-        d[i] = sqrt(G[i][i]);
+        if (!(A[i][i] > 0.0)) st |= 1;
+        d[i] = sqrt(A[i][i]);
+        id[i] = 1.0 / d[i];      // reciprocals once: the FP64 divide is a sequence
     }
     double kappa = NAN, eps = NAN;
-    double C[NP][NP];
     if (!st) {
-        // reciprocals once: the FP64 divide is a multi-instruction sequence
-        double id[NP], il[NP];
+        // normalise, and the column 1-norms of H (symmetric: from the lower triangle)
+        double colh[NP];
 #pragma unroll
-        for (int i = 0; i < NP; i++) id[i] = 1.0 / d[i];
-        double H[NP][NP], L[NP][NP];
+        for (int j = 0; j < NP; j++) colh[j] = 0.0;
 #pragma unroll
         for (int i = 0; i < NP; i++)
 #pragma unroll
-            for (int j = 0; j < NP; j++) {
-                H[i][j] = G[i][j] * id[i] * id[j];
-                L[i][j] = 0.0;
+            for (int j = 0; j <= i; j++) {
+                A[i][j] *= id[i] * id[j];
+                colh[j] += fabs(A[i][j]);
+                if (i != j) colh[i] += fabs(A[i][j]);
             }
-        // Cholesky H = L L^T
+        // Cholesky H = L L^T in place
 #pragma unroll
         for (int j = 0; j < NP; j++) {
-            double sjj = H[j][j];
+            double sjj = A[j][j];
 #pragma unroll
-            for (int k = 0; k < j; k++) sjj -= L[j][k] * L[j][k];
+            for (int k = 0; k < j; k++) sjj -= A[j][k] * A[j][k];
             if (!(sjj > 0.0)) st |= 1;
             const double ljj = sqrt(sjj);
-            L[j][j] = ljj;
+            A[j][j] = ljj;
             il[j] = 1.0 / ljj;
 #pragma unroll
             for (int i = j + 1; i < NP; i++) {
-                double t = H[i][j];
+                double t = A[i][j];
 #pragma unroll
-                for (int k = 0; k < j; k++) t -= L[i][k] * L[j][k];
-                L[i][j] = t * il[j];
+                for (int k = 0; k < j; k++) t -= A[i][k] * A[j][k];
+                A[i][j] = t * il[j];
             }
         }
         if (!st) {
-            // M = L^-1 (lower), forward substitution column by column
-            double M[NP][NP];
-#pragma unroll
-            for (int c = 0; c < NP; c++) {
-#pragma unroll
-                for (int i = 0; i < NP; i++) {
-                    if (i < c) { M[i][c] = 0.0; continue; }
-                    double t = (i == c) ? 1.0 : 0.0;
-#pragma unroll
-                    for (int k = c; k < i; k++) t -= L[i][k] * M[k][c];
-                    M[i][c] = t * il[i];
-                }
-            }
-            // Hinv = M^T M, one triangle; 1-norms of H and Hinv by columns
-            double colh[NP], coli[NP];
+            // M = L^-1 in place, column by column from the left: M[i][j] =
+            // -(1/L[i][i]) sum_{k=j}^{i-1} L[i][k] M[k][j] reads L only in
+            // columns >= j of rows > i-1, which are still L
 #pragma unroll
             for (int j = 0; j < NP; j++) {
-                colh[j] = 0.0;
-                coli[j] = 0.0;
+                A[j][j] = il[j];
 #pragma unroll
-                for (int i = 0; i < NP; i++) colh[j] += fabs(H[i][j]);
-            }
-#pragma unroll
-            for (int j = 0; j < NP; j++)
-#pragma unroll
-                for (int i = 0; i <= j; i++) {
+                for (int i = j + 1; i < NP; i++) {
                     double t = 0.0;
 #pragma unroll
-                    for (int k = j; k < NP; k++) t += M[k][i] * M[k][j];
-                    const double c = t * id[i] * id[j];
-                    C[i][j] = c;
-                    C[j][i] = c;
+                    for (int k = j; k < i; k++) t = fma(A[i][k], A[k][j], t);
+                    A[i][j] = -t * il[i];
+                }
+            }
+            // Hinv = M^T M on one triangle; its column 1-norms; rescale to C
+            double coli[NP];
+#pragma unroll
+            for (int j = 0; j < NP; j++) coli[j] = 0.0;
+#pragma unroll
+            for (int i = 0; i < NP; i++)
+#pragma unroll
+                for (int j = i; j < NP; j++) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int k = j; k < NP; k++) t = fma(A[k][i], A[k][j], t);
                     coli[j] += fabs(t);
                     if (i != j) coli[i] += fabs(t);
+                    Cu[pkt<NP>(i, j)] = t * id[i] * id[j];
                 }
             double hn1 = 0.0, in1 = 0.0;
 #pragma unroll
@@ -690,34 +690,32 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
             if (kappa > 1.0 / DBL_EPSILON) st |= 32;
             if (kappa > cond_max) st |= 2;
             if (inv_err) {
+                // eps = max |Gamma C - 1|, Gamma row by row from the input
                 eps = 0.0;
 #pragma unroll
-                for (int i = 0; i < NP; i++)
+                for (int i = 0; i < NP; i++) {
+                    double g[NP];
+#pragma unroll
+                    for (int k = 0; k < NP; k++)
+                        g[k] = F[(int64_t)pkt<NP>(i < k ? i : k, i < k ? k : i) * n + e];
 #pragma unroll
                     for (int j = 0; j < NP; j++) {
                         double t = (i == j) ? -1.0 : 0.0;
 #pragma unroll
-                        for (int k = 0; k < NP; k++) t = fma(G[i][k], C[k][j], t);
+                        for (int k = 0; k < NP; k++)
+                            t = fma(g[k], Cu[pkt<NP>(k < j ? k : j, k < j ? j : k)], t);
                         eps = fmax(eps, fabs(t));
                     }
+                }
             }
         }
     }
     const bool ok = !(st & (1 | 2 | 4));
-    {
-        int k = 0;
 #pragma unroll
-        for (int i = 0; i < NP; i++)
-#pragma unroll
-            for (int j = i; j < NP; j++) {
-                cov[(int64_t)k * n + e] = ok ? C[i][j] : NAN;
-                k++;
-            }
-    }
+    for (int k = 0; k < NK; k++) cov[(int64_t)k * n + e] = ok ? Cu[k] : NAN;
     if (cond) cond[e] = (st & (1 | 4)) ? NAN : kappa;
     if (inv_err) inv_err[e] = ok ? eps : NAN;
     status[e] = st;
-    (void)NK;
 }
 
 cudaError_t launch_invert(const double *fisher, int64_t n, int np, double cond_max, double *cov,
