@@ -93,6 +93,7 @@ enum EvSlot : int {
     EVC = EV_TE + 8
 };
 constexpr int NCOEF = EVC - EV_PM;   // polynomial coefficients of the point loop
+constexpr int NSCAL = EV_INVDL - EV_WC0 + 1;   // scalar constants of the mixed point loop
 // B11 = (v^-5, v^-3, v^-2, v^-1, 1, v, v^2, v^5, v^7, ln v, v ln v)
 // B8  = (v^-5, v^-3, v^-2, v^-1, 1, v, v^2, v ln v)
 

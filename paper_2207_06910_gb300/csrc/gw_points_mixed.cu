@@ -304,6 +304,10 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
     // EVC - 1, read every point from shared memory instead of being held in
     // registers across the loop)
     float2 *cs = lo_base + ((NACC * LDS + 1) & ~1) + (wib * GROUPS_PER_WARP + gid) * NCOEF;
+    // per-group copy of the item's scalar constants EV_WC0 .. EV_INVDL, read
+    // where they are used (held in registers they would crowd out the sums)
+    float2 *csc = lo_base + ((NACC * LDS + 1) & ~1) + 4 * GROUPS_PER_WARP * NCOEF +
+                  (wib * GROUPS_PER_WARP + gid) * NSCAL;
     const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GROUPS_PER_WARP;
     const DevNet &net = A.net;
     // work count from device memory (no host readback), bounded by the capacity
@@ -327,6 +331,7 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                 csf[coef_pos(q, 1)] = c.y;
             }
         }
+        for (int q = gl; q < NSCAL; q += GROUP) csc[q] = Eg[EV_WC0 + q];
         __syncwarp(gmask);
         const float *cf = reinterpret_cast<const float *>(cs);
 
@@ -352,15 +357,7 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
             // amplitude A0 f^(-7/6) as a double-float recurrence (an FP32 one
             // would drift by ~1e-6 over a lane's points)
             DF Aamp = df_from_double(E[EV_A0] * net.inv_sqrt_scale_ref * exp(-7.0 / 6.0 * lnf));
-            const DF rho = df_of(Eg[EV_RHOG]), rhoi = df_of(Eg[EV_RHOIG]);
-            const DF dlnv = df_of(Eg[EV_LNRHOG]);
-            const DF inv_pim = df_of(Eg[EV_INV_PIM]);
-            const DF rA = df_of(Eg[EV_RAG]);
-            const float wc0 = Eg[EV_WC0].x, wcm = Eg[EV_WCM].x, wcn = Eg[EV_WCN].x;
-            const float cp = Eg[EV_CP].x, cx = Eg[EV_CX].x;
-            const float dcp = Eg[EV_DCP].x, dcx = Eg[EV_DCX].x;
-            const float c2p = Eg[EV_C2PSI].x, s2p = Eg[EV_S2PSI].x;
-            const float aMc = Eg[EV_AMC].x, invdL = Eg[EV_INVDL].x;
+#define SC(slot) csc[(slot) - EV_WC0]
 
 #pragma unroll 1
             for (; k < ke; k += GROUP) {
@@ -402,12 +399,12 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                     tEt = (tmte.hi.y + tmte.lo.y) * vi3f;
                     asm volatile("" ::: "memory");
                 }
-                const DF fdf = df_mul(v3, inv_pim);
+                const DF fdf = df_mul(v3, df_of(SC(EV_INV_PIM)));
                 const float ff = df_round(fdf);
                 const float twopif = (float)TWO_PI * ff;
 
                 // ---------------- FP32: noise weight and amplitude per PSD
-                const float w = ff * (k == 0 ? wc0 : (k == N - 1 ? wcn : wcm));
+                const float w = ff * (k == 0 ? SC(EV_WC0).x : (k == N - 1 ? SC(EV_WCN).x : SC(EV_WCM).x));
                 const float Af = df_round(Aamp);
                 float sig[MAX_PSD];
 #pragma unroll
@@ -489,10 +486,11 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                         }
                         const float amp = (float)net.ifo_amp[q] * on;
                         const PatF pt = patterns_f((float)net.ifo_s2g[q], (float)net.ifo_c2g[q],
-                                                   amp * c2p, amp * s2p, J);
+                                                   amp * SC(EV_C2PSI).x, amp * SC(EV_S2PSI).x, J);
                         const float sg = sig[net.ifo_psd[q]];
                         float gr[NP], gi[NP], qr, qi, xr, xi, tr, ti;
-                        tangents_f<NP, ROT>(pt, sg * cp, sg * cx, sg * dcp, sg * dcx, aMc, invdL,
+                        tangents_f<NP, ROT>(pt, sg * SC(EV_CP).x, sg * SC(EV_CX).x, sg * SC(EV_DCP).x,
+                                            sg * SC(EV_DCX).x, SC(EV_AMC).x, SC(EV_INVDL).x,
                                             ph, gr, gi, qr, qi, xr, xi, tr, ti);
                         // tangents as (real, imaginary) pairs
                         float2 G[NP];
@@ -543,10 +541,11 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                         }
                     }
                 }
-                v = df_mul(v, rho);
-                vinv = df_mul(vinv, rhoi);
-                lnv = df_add(lnv, dlnv);
-                Aamp = df_mul(Aamp, rA);
+                v = df_mul(v, df_of(SC(EV_RHOG)));
+                vinv = df_mul(vinv, df_of(SC(EV_RHOIG)));
+                lnv = df_add(lnv, df_of(SC(EV_LNRHOG)));
+                Aamp = df_mul(Aamp, df_of(SC(EV_RAG)));
+#undef SC
             }
         }
         // ---- group reduction.  Every lane collapses its (real, imaginary)
@@ -591,7 +590,7 @@ template <int MODE, int NP, bool ROT>
 cudaError_t launch_one_m(const PointArgs &a, cudaStream_t s)
 {
     constexpr int NACC = NAccM<MODE, NP>::value;
-    const size_t smem = ((size_t)((NACC * 129 + 1) & ~1) + (size_t)4 * GROUPS_PER_WARP * NCOEF) * sizeof(float2);
+    const size_t smem = ((size_t)((NACC * 129 + 1) & ~1) + (size_t)4 * GROUPS_PER_WARP * (NCOEF + NSCAL)) * sizeof(float2);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t err = cudaFuncSetAttribute(k_points_mixed<MODE, NP, ROT>,

@@ -90,6 +90,12 @@ cudaError_t launch_prepare(int64_t n, const double *m1, const double *m2, const 
 // at fixed f, so that every parameter derivative is one dot product with the
 // point's basis values.  At fixed f:  Mc d/dMc = (1/3) v d/dv  and
 // d/deta|Mc = d/deta|v - (1/(5 eta)) v d/dv  (v = (pi M f)^(1/3), M = Mc eta^-3/5).
+// constants of the event set-up, as doubles (ln 6, ln 4, pi^(-2/3), sqrt(5/24))
+constexpr double LN6 = 0x1.cab0bfa2a2002p+0;
+constexpr double LN4 = 0x1.62e42fefa39efp+0;
+constexpr double PI_M23 = 0x1.dd61fae9d2f10p-2;
+constexpr double SQRT_5_24 = 0x1.d363d1848dcbfp-2;
+
 __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec,
                               float *sitec_f, float2 *evc_f, int32_t *status, int64_t *counts)
 {
@@ -144,7 +150,7 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
     E[EV_RHOG] = exp(GROUP * lnr / 3.0);
     E[EV_RHOIG] = exp(-GROUP * lnr / 3.0);
     E[EV_LNRHOG] = GROUP * lnr / 3.0;
-    E[EV_A0] = sqrt(5.0 / 24.0) * pow(PI, -2.0 / 3.0) * pow(Mcs, 5.0 / 6.0) / (dL * GPC_S);
+    E[EV_A0] = SQRT_5_24 * PI_M23 * pow(Mcs, 5.0 / 6.0) / (dL * GPC_S);
     E[EV_RAG] = exp(-7.0 / 6.0 * GROUP * lnr);
     double si, ci, s2p, c2p;
     sincos(io, &si, &ci);
@@ -171,7 +177,7 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
     const double sigma = 79.0 / 8.0 * eta * c1 * c2;
     const double dbeta = 113.0 / 6.0 * (X2 * c2 - X1 * c1) / d + 25.0 / 4.0 * (c1 + c2);
     const double dsigma = 79.0 / 8.0 * c1 * c2;
-    const double ln6h = 1.0 + 1.5 * log(6.0);                 // 1 - 3 ln v_lso
+    const double ln6h = 1.0 + 1.5 * LN6;                      // 1 - 3 ln v_lso
     const double L6 = -6848.0 / 21.0;
     const double p2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
     const double p3 = -16.0 * PI + 4.0 * beta;
@@ -183,7 +189,7 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
                        - 6848.0 / 21.0 * EULER_GAMMA
                        + (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2) * eta
                        + 76055.0 / 1728.0 * eta * eta - 127825.0 / 1296.0 * eta * eta * eta;
-    const double p6 = p6c + L6 * log(4.0);
+    const double p6 = p6c + L6 * LN4;
     const double p7 = PI * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta
                             - 74045.0 / 756.0 * eta * eta);
     const double t10 = -39.0 / 2.0 * LT;
@@ -238,7 +244,7 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
                       + 6848.0 / 105.0 * EULER_GAMMA
                       + (3147553127.0 / 3048192.0 - 451.0 / 12.0 * pi2) * eta
                       - 15211.0 / 1728.0 * eta * eta + 25565.0 / 1296.0 * eta * eta * eta
-                      + 3424.0 / 105.0 * log(16.0);
+                      + 3424.0 / 105.0 * (2.0 * LN4);
     const double t6L = 6848.0 / 105.0;
     const double t7 = (-15419335.0 / 127008.0 - 75703.0 / 756.0 * eta
                        + 14809.0 / 378.0 * eta * eta) * PI;
