@@ -671,14 +671,16 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
                     A[i][j] = -t * il[i];
                 }
             }
-            // Hinv = M^T M on one triangle; its column 1-norms; rescale to C
+            // Hinv = M^T M on one triangle; its column 1-norms; rescale to C.
+            // Column j of Hinv reads rows >= j of M: going through j upwards
+            // lets rows of M die as the triangle of C fills (fewer live values)
             double coli[NP];
 #pragma unroll
             for (int j = 0; j < NP; j++) coli[j] = 0.0;
 #pragma unroll
-            for (int i = 0; i < NP; i++)
+            for (int j = 0; j < NP; j++)
 #pragma unroll
-                for (int j = i; j < NP; j++) {
+                for (int i = 0; i <= j; i++) {
                     double t = 0.0;
 #pragma unroll
                     for (int k = j; k < NP; k++) t = fma(A[k][i], A[k][j], t);
@@ -700,6 +702,8 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
                 eps = 0.0;
 #pragma unroll
                 for (int i = 0; i < NP; i++) {
+                    // (keeps the compiler from loading every row of Gamma at once)
+                    asm volatile("" ::: "memory");
                     double g[NP];
 #pragma unroll
                     for (int k = 0; k < NP; k++)
