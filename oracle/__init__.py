@@ -284,3 +284,17 @@ def sky_area(C, i_theta, i_phi, theta, perc=90.0, units="SqDeg"):
                         1 if units == "SqDeg" else 0, _p(out))
     return out
 
+
+def perturb_fisher(F, r, eps=1e-10):
+    """perturb_Fisher (Sec. 4.1): every element of each Fisher matrix perturbed at
+    the eps-th relative decimal, Gamma'_ij = Gamma_ij (1 + eps r_ij), with r the
+    caller's random numbers in [-1, 1] taken from the upper triangle (r_ji = r_ij,
+    so Gamma' stays symmetric).  F [n, P, P], r [n, P, P]."""
+    F = _f64(F)
+    r = _f64(r)
+    iu = np.triu_indices(F.shape[1])
+    rs = np.zeros_like(r)
+    rs[:, iu[0], iu[1]] = r[:, iu[0], iu[1]]
+    rs = rs + np.transpose(rs, (0, 2, 1)) - rs * np.eye(F.shape[1])
+    return F * (1.0 + eps * rs)
+

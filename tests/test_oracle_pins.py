@@ -749,3 +749,18 @@ def test_table2_hanford_livingston_delay():
         slope = np.polyfit(f, np.unwrap(np.angle(hH[0] / hL[0])), 1)[0]
         assert abs(slope / (2 * math.pi) - want) < 1e-9 * max(want, 1e-3)
     assert 9.9e-3 < np.linalg.norm(b) / C_SI < 1.01e-2
+
+
+def test_perturb_fisher_definition():
+    """perturb_Fisher (Sec. 4.1): symmetric relative perturbation at the eps-th
+    decimal; eps = 0 returns the input; |Gamma' - Gamma| <= eps |Gamma|."""
+    rng = np.random.default_rng(26)
+    F = np.stack([_spd(11, 4, rng) for _ in range(3)])
+    F = 0.5 * (F + np.transpose(F, (0, 2, 1)))
+    r = rng.uniform(-1, 1, F.shape)
+    Fp = oracle.perturb_fisher(F, r, 1e-10)
+    assert np.array_equal(oracle.perturb_fisher(F, r, 0.0), F)
+    assert np.array_equal(Fp, np.transpose(Fp, (0, 2, 1)))
+    assert np.all(np.abs(Fp - F) <= 1e-10 * np.abs(F) * (1 + 1e-15))
+    i, j = 2, 7
+    assert Fp[1, i, j] == F[1, i, j] * (1.0 + 1e-10 * r[1, i, j])
