@@ -307,6 +307,16 @@ gw_status gw_covariance(gw_ctx *ctx, const double *fisher, int64_t n, int n_par,
 gw_status gw_packed_submatrix(gw_ctx *ctx, const double *in, int64_t n, int n_par, uint32_t keep,
                               double *out, void *stream);
 
+/* perturb_Fisher (Sec. 4.1): every element of the packed Fisher matrices
+ * perturbed at the eps-th relative decimal, out = fisher * (1 + eps r), with r
+ * the caller's random numbers (DEVICE, same packed layout, e.g. uniform in
+ * [-1, 1]: the packed triangle keeps the matrices symmetric).  Inverting out
+ * and fisher with gw_covariance and comparing shows whether the inversion is
+ * stable.  DEVICE in: fisher, r [n_par(n_par+1)/2][n]; DEVICE out: out (may
+ * equal fisher). */
+gw_status gw_perturb_fisher(gw_ctx *ctx, const double *fisher, int64_t n, int n_par, double eps,
+                            const double *r, double *out, void *stream);
+
 /* Sky-localisation area at confidence level perc (percent, in (0, 100)),
  * Sec. 4.1: Delta Omega = -2 pi |sin theta| sqrt(C_tt C_pp - C_tp^2)
  * ln(1 - perc/100), from the packed covariances (DEVICE [n_par(n_par+1)/2][n])

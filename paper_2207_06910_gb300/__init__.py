@@ -57,7 +57,7 @@ EXPORTS = ("gw_create", "gw_destroy", "gw_last_error", "gw_abi_version", "gw_pre
            "gw_snr", "gw_fisher", "gw_fisher_inverse", "gw_snr_vjp", "gw_logdet_vjp_detangles",
            "gw_set_profiling", "gw_point_kernel_ms", "gw_fisher_noalloc", "gw_reserve",
            "gw_select_snr", "gw_fisher_eig", "gw_covariance", "gw_packed_submatrix",
-           "gw_sky_area", "gw_strain")
+           "gw_sky_area", "gw_strain", "gw_perturb_fisher")
 
 _lib = None
 
@@ -100,6 +100,7 @@ def load_library(path: str | None = None):
     lib.gw_covariance.argtypes = [_P, _P, i64, ctypes.c_int, ctypes.c_uint32, _P, ctypes.c_int, d,
                                   d, _P, _P, _P, _P, _P]
     lib.gw_packed_submatrix.argtypes = [_P, _P, i64, ctypes.c_int, ctypes.c_uint32, _P, _P]
+    lib.gw_perturb_fisher.argtypes = [_P, _P, i64, ctypes.c_int, d, _P, _P, _P]
     lib.gw_sky_area.argtypes = [_P, _P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, d,
                                 ctypes.c_int, _P, _P]
     lib.gw_set_profiling.argtypes = [_P, ctypes.c_int]
@@ -542,4 +543,14 @@ def gw_strain(cat: Catalog, net: Network, prec=GW_FP64, stream=None):
                                     _ptr(re), _ptr(im), _ptr(freq), _ptr(off), _ptr(status),
                                     _stream(stream)), ctx)
     return re, im, freq, off, status
+
+
+def gw_perturb_fisher(fisher: torch.Tensor, n_par: int, r: torch.Tensor, eps=1e-10,
+                      stream=None) -> torch.Tensor:
+    """perturb_Fisher (Sec. 4.1): fisher * (1 + eps r) on the packed triangle."""
+    ctx = context()
+    out = torch.empty_like(fisher)
+    _check(load_library().gw_perturb_fisher(ctx, _ptr(fisher), fisher.shape[1], n_par, float(eps),
+                                            _ptr(r.contiguous()), _ptr(out), _stream(stream)), ctx)
+    return out
 

@@ -518,6 +518,20 @@ gw_status gw_packed_submatrix(gw_ctx *ctx, const double *in, int64_t n, int n_pa
     return GW_OK;
 }
 
+gw_status gw_perturb_fisher(gw_ctx *ctx, const double *fisher, int64_t n, int n_par, double eps,
+                            const double *r, double *out, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (n < 0 || n_par < 1 || n_par > 11 || !std::isfinite(eps))
+        return fail(ctx, GW_EINVAL, "perturb: bad n, n_par or eps");
+    if (n == 0) return GW_OK;
+    if (!fisher || !r || !out) return fail(ctx, GW_EINVAL, "perturb: null array");
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_perturb(n * (int64_t)(n_par * (n_par + 1) / 2), eps, fisher, r, out,
+                      (cudaStream_t)stream));
+    return GW_OK;
+}
+
 gw_status gw_sky_area(gw_ctx *ctx, const double *cov, int64_t n, int n_par, int i_theta,
                       int i_phi, const double *theta, double perc, int units, double *area,
                       void *stream)

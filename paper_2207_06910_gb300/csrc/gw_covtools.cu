@@ -306,6 +306,15 @@ __global__ void k_sky_area(int64_t n, int P, int it, int ip, const double *cov, 
     area[e] = -2.0 * PI * fabs(sin(theta[e])) * sqrt(det) * lnq * scale;
 }
 
+// perturb_Fisher: Gamma'_ij = Gamma_ij (1 + eps r_ij) on the packed triangle
+// (explicitly rounded operations: no contraction into an FMA)
+__global__ void k_perturb(int64_t total, double eps, const double *F, const double *r, double *out)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = __dmul_rn(F[q], __dadd_rn(1.0, __dmul_rn(eps, r[q])));
+}
+
 unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
@@ -331,6 +340,16 @@ cudaError_t launch_submatrix(int64_t n, int P, int K, const SubIdx &idx, const d
 {
     if (n <= 0) return cudaSuccess;
     k_submatrix<<<blocks_for(n, 256), 256, 0, s>>>(n, P, K, idx, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_perturb(int64_t total, double eps, const double *F, const double *r,
+                           double *out, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    int64_t nb = (total + 255) / 256;
+    if (nb > 152 * 32) nb = 152 * 32;
+    k_perturb<<<(unsigned)nb, 256, 0, s>>>(total, eps, F, r, out);
     return cudaGetLastError();
 }
 

@@ -104,6 +104,8 @@ cudaError_t launch_covariance(const CovArgs &a, const double *F, double *cov, do
                               double *eps, int32_t *status, cudaStream_t s);
 cudaError_t launch_submatrix(int64_t n, int P, int K, const SubIdx &idx, const double *in,
                              double *out, cudaStream_t s);
+cudaError_t launch_perturb(int64_t total, double eps, const double *F, const double *r,
+                           double *out, cudaStream_t s);
 cudaError_t launch_sky_area(int64_t n, int P, int it, int ip, const double *cov,
                             const double *theta, double perc, int units, double *area,
                             cudaStream_t s);

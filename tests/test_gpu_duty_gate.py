@@ -185,3 +185,35 @@ def test_gated_pipeline_against_oracle(prec):
     dg = np.sqrt(np.einsum("eii->ei", F_or))
     rel = np.abs(Fg - F_or) / (dg[:, :, None] * dg[:, None, :])
     assert rel.max() < tol_f
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_largest_network_with_masks(prec):
+    """Eight detectors (three triangles and five L-shaped ones: 14 arms, 20
+    interferometer entries of the 24 the library holds) with random arm masks,
+    against the oracle; a network beyond the capacity is refused."""
+    D = np.pi / 180
+    det = np.array([[40.5 * D, 9.4 * D, 0.0, 60 * D, 1, 0],
+                    [50.7 * D, 5.9 * D, 10 * D, 60 * D, 1, 0],
+                    [-30 * D, 120 * D, 35 * D, 60 * D, 1, 1],
+                    [46.5 * D, -119.4 * D, 171 * D, 90 * D, 0, 1],
+                    [30.6 * D, -90.8 * D, 242.7 * D, 90 * D, 0, 1],
+                    [43.6 * D, 10.5 * D, 115.6 * D, 90 * D, 0, 1],
+                    [36.4 * D, 137.3 * D, 15.4 * D, 90 * D, 0, 0],
+                    [19.6 * D, 77.0 * D, 287.4 * D, 90 * D, 0, 0]])
+    _, psd, rot = gwcat.network("c4")
+    cat, d, p = oracle_catalog("c3", 3, seed=20220714 + 905, max_npts=150)
+    masks = gwcat.draw_arm_masks(3, 14, 0.7, seed=7)
+    cat = oracle.Catalog(cat.ev, cat.pset, cat.fmin, cat.fmax, cat.npts, masks)
+    F_or, s_or, _, _ = oracle_pool.fisher(cat, det, psd, rot, 11)
+    net = gw.Network(det, psd, rot)
+    F, snr, st = gw.gw_fisher(_gpu_cat(cat), net, 11, prec)
+    tol_f, tol_s = (1e-8, 1e-10) if prec == 0 else (2e-6, 1e-5)
+    assert np.all(st.cpu().numpy() == 0)
+    assert np.max(np.abs(snr.cpu().numpy() / s_or - 1)) < tol_s
+    Fg = gw.unpack(F, 11).cpu().numpy()
+    dg = np.sqrt(np.einsum("eii->ei", F_or))
+    assert (np.abs(Fg - F_or) / (dg[:, :, None] * dg[:, None, :])).max() < tol_f
+    big = np.concatenate([det[:3], det[:2], det[3:6]])      # five triangles: 28 entries
+    with pytest.raises(gw.GWError):
+        gw.gw_fisher(_gpu_cat(cat), gw.Network(big, psd, rot), 11, prec)
