@@ -219,12 +219,12 @@ def flops_per_point(n_site: int, n_ifo: int, precision: str) -> float:
     with d Psi/d eta (two lanes, 11 terms) 316, slots 9/10 (two lanes, 4 terms) 106,
     tau* (one lane, 8 terms, times v^-3) 125, d tau*/d Mc with d tau*/d eta (two lanes,
     8 terms) 228; f 12, recurrences 41, PSD weight 23; per site 122 (double-float
-    Earth angle 44, sincosf ~20, JKS/Doppler ~58); per virtual interferometer 1711
-    (patterns 38, tangents 60, scaling 4, 73 compensated accumulations of 22 flops:
+    Earth angle 44, sincosf ~20, JKS/Doppler ~58); per virtual interferometer 1619
+    (patterns 38, tangents 56, scaling 4, 69 compensated accumulations of 22 flops:
     two products, two exact product errors, two two-sums, compensation)."""
     if precision == "mixed":
         shared = 80 + 316 + 106 + 125 + 228 + 12 + 41 + 23
-        return shared + 122 * n_site + 1711 * n_ifo
+        return shared + 122 * n_site + 1619 * n_ifo
     shared = 8 + 4 + 19 + 20 + 14 + 48 + 35 + 4
     return shared + 140 * n_site + 356 * n_ifo
 

@@ -500,14 +500,20 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                         if (MODE == MODE_FISHER) {
                             // Gamma_ij: real and imaginary products summed separately
                             // (|Q|^2 = the (Phic, Phic) entry, copied at the end); the
-                            // row's tangent is negated once for the whole row
+                            // row's tangent is negated once for the whole row.  The d_L
+                            // tangent is taken exactly as -Q/d_L: its row sums
+                            // Re(g_j Q^*) and the reduction scales them by -1/d_L;
+                            // (d_L, d_L) and (d_L, Phic) follow from (Phic, Phic) and
+                            // Re(Q (iQ)^*) = 0, so they are not summed.
+                            G[2] = Q;
                             int a = 1;
 #pragma unroll
                             for (int i = 0; i < NP; i++) {
                                 const float2 NGi = make_float2(-G[i].x, -G[i].y);
 #pragma unroll
                                 for (int jj = i; jj < NP; jj++) {
-                                    acc_pk(acc[a], mylo + a * LDS, G[jj], G[i], NGi);
+                                    if (!(i == 2 && (jj == 2 || jj == 8)))
+                                        acc_pk(acc[a], mylo + a * LDS, G[jj], G[i], NGi);
                                     a++;
                                 }
                                 if (i & 1) asm volatile("" ::: "memory");
@@ -523,8 +529,8 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                             acc_pk(acc[X0 + 2], mylo + (X0 + 2) * LDS,
                                    make_float2(ph.teta * qr, ph.teta * qi), X, NX);
                             acc_pk(acc[X0 + 3], mylo + (X0 + 3) * LDS, T, Q, NQ);
-                            acc_pk(acc[X0 + 4], mylo + (X0 + 4) * LDS, G[5], Q, NQ);
-                            acc_pk(acc[X0 + 5], mylo + (X0 + 5) * LDS, G[6], Q, NQ);
+                            // X0 + 4, X0 + 5 (iota, psi) are the (iota, d_L), (psi, d_L)
+                            // sums above
                         } else if (MODE == MODE_SNR) {
                             const float2 NQ = make_float2(-qr, -qi);
                             acc_pk(acc[0], mylo, Q, Q, NQ);
