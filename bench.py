@@ -215,16 +215,18 @@ def flops_per_point(n_site: int, n_ifo: int, precision: str) -> float:
     angle 5, JKS/Doppler/phase combinations ~95; per virtual interferometer:
     patterns 38, tangents 46, sigma scaling 4, |Q|^2 3, 66-pair Gram update 265.
     Mixed path (FP32 pipe): double-float basis 80; compensated (Dot2) dot
-    products with double-float coefficients, 15 flops per term and lane: d Psi/d Mc
-    with d Psi/d eta (two lanes, 11 terms) 316, slots 9/10 (two lanes, 4 terms) 106,
-    tau* (one lane, 8 terms, times v^-3) 125, d tau*/d Mc with d tau*/d eta (two lanes,
-    8 terms) 228; f 12, recurrences 41, PSD weight 23; per site 122 (double-float
-    Earth angle 44, sincosf ~20, JKS/Doppler ~58); per virtual interferometer 1619
-    (patterns 38, tangents 56, scaling 4, 69 compensated accumulations of 22 flops:
-    two products, two exact product errors, two two-sums, compensation)."""
+    products with double-float coefficients, 13 flops per term and lane (the
+    product error and the addend's roundoff folded into one FMA): d Psi/d Mc with
+    d Psi/d eta (two lanes, 11 terms) 276, slots 9/10 (two lanes, 4 terms) 94,
+    tau* (one lane, 8 terms, times v^-3) 111, d tau*/d Mc with d tau*/d eta (two
+    lanes, 8 terms) 200; f 12, recurrences 41, PSD weight 23; per site 122
+    (double-float Earth angle 44, sincosf ~20, JKS/Doppler ~58); per virtual
+    interferometer 1343 (patterns 38, tangents 56, scaling 4, 69 compensated
+    accumulations of 18 flops: product, two-sum of the high parts, one FMA for
+    the product error and roundoff, compensation)."""
     if precision == "mixed":
-        shared = 80 + 316 + 106 + 125 + 228 + 12 + 41 + 23
-        return shared + 122 * n_site + 1619 * n_ifo
+        shared = 80 + 276 + 94 + 111 + 200 + 12 + 41 + 23
+        return shared + 122 * n_site + 1343 * n_ifo
     shared = 8 + 4 + 19 + 20 + 14 + 48 + 35 + 4
     return shared + 140 * n_site + 356 * n_ifo
 
@@ -381,28 +383,74 @@ def run_ours(a):
     step_ms = [s.elapsed_time(e) for s, e in ev]
     total_ms = float(sum(step_ms))
 
-    # ---- end to end: host (pinned) -> device, step, device -> host
+    # ---- end to end: host (pinned) -> device, step, device -> host.  Every step
+    # copies its own inputs up and its results down; the copies run on a copy
+    # stream, so the inputs of step i+1 go up and the results of step i come
+    # down while the GPU computes.  Two input sets (and, with graphs, two
+    # captured step graphs) alternate; one pair of events brackets all steps,
+    # including their L2 flushes.
+    dev2 = {k: v.clone() for k, v in dev.items()}
+    bufs, graphs, gouts = [dev, dev2], [graph, None], [gout, None]
+    if graph is not None:
+        graph2 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph2):
+            gouts[1] = step(dev2)
+        graph2.replay()
+        torch.cuda.synchronize()
+        graphs[1] = graph2
+
+    def run_on(b):
+        if graphs[b] is not None:
+            graphs[b].replay()
+            return gouts[b]
+        return step(bufs[b])
+
     outs_host = {"snr": torch.empty(n_sel, dtype=torch.float64).pin_memory(),
                  "F": torch.empty((N_PAR * (N_PAR + 1) // 2, n_sel), dtype=torch.float64).pin_memory(),
                  "cov": torch.empty((N_PAR * (N_PAR + 1) // 2, n_sel), dtype=torch.float64).pin_memory(),
                  "g": torch.empty((N_PAR, n_sel), dtype=torch.float64).pin_memory()}
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = sum(v.numel() * v.element_size() for v in outs_host.values())
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(a.steps)]
-    for i in range(a.steps):
-        flush.zero_()
-        e2e_ev[i][0].record(stream)
-        for k, v in host.items():
-            dev[k].copy_(v, non_blocking=True)
-        cat, F, snr, cov, cond, g, st = run_step()
-        outs_host["snr"].copy_(snr, non_blocking=True)
-        outs_host["F"].copy_(F, non_blocking=True)
-        outs_host["cov"].copy_(cov, non_blocking=True)
-        outs_host["g"].copy_(g, non_blocking=True)
-        e2e_ev[i][1].record(stream)
+    copy = torch.cuda.Stream()
+    h2d_ev = [torch.cuda.Event(), torch.cuda.Event()]
+    step_ev = [torch.cuda.Event(), torch.cuda.Event()]
+    d2h_ev = [torch.cuda.Event(), torch.cuda.Event()]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    e2e_ms = float(sum(s.elapsed_time(e) for s, e in e2e_ev))
+    t0.record(stream)
+    copy.wait_event(t0)
+    with torch.cuda.stream(copy):
+        for k, v in host.items():
+            bufs[0][k].copy_(v, non_blocking=True)
+        h2d_ev[0].record(copy)
+    keep = [None, None]
+    for i in range(a.steps):
+        b = i % 2
+        flush.zero_()
+        stream.wait_event(h2d_ev[b])          # this step's inputs are up
+        if i >= 2:
+            stream.wait_event(d2h_ev[b])      # step i-2's results are down
+        out = run_on(b)
+        step_ev[b].record(stream)
+        with torch.cuda.stream(copy):
+            if i + 1 < a.steps:
+                if i >= 1:
+                    copy.wait_event(step_ev[1 - b])   # step i-1 is done with that set
+                for k, v in host.items():
+                    bufs[1 - b][k].copy_(v, non_blocking=True)
+                h2d_ev[1 - b].record(copy)
+            copy.wait_event(step_ev[b])
+            cat, F, snr, cov, cond, g, st = out
+            for t, name in ((snr, "snr"), (F, "F"), (cov, "cov"), (g, "g")):
+                if graphs[b] is None:
+                    t.record_stream(copy)
+                outs_host[name].copy_(t, non_blocking=True)
+            d2h_ev[b].record(copy)
+        keep[b] = out
+    stream.wait_stream(copy)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = float(t0.elapsed_time(t1))
     gw.gw_reserve(0, 0, 0)
 
     (total_ms, e2e_ms, kern_ms), (value, e2e_value, _) = aggregate(
@@ -457,7 +505,9 @@ def run_ours(a):
                        "parallelism": f"event shards, {world} GPU(s), no collective"},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h,
+                    "copies": "pinned host buffers, on a copy stream overlapping the "
+                              "previous/next step's compute"},
             "gpu_launches": launches_per_step * a.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,

@@ -269,7 +269,6 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     pa.partial = ctx->partial;
     pa.nacc = nacc;
     pa.cov = cov;
-    pa.mixed = mixed ? 1 : 0;
     if (ctx->profiling) CK(cudaEventRecord(ctx->ev0, s));
     if (mixed) CK(launch_points_mixed(mode, np, dn.rotation, pa, s));
     else CK(launch_points_fp64(mode, np, dn.rotation, pa, s));

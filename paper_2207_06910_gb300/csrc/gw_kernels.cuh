@@ -31,7 +31,6 @@ struct PointArgs {
     double *partial;          // [n_items][nacc]
     int nacc;
     const double *cov;        // logdet mode: covariance, packed, event-minor
-    int mixed;                // partial sums from the mixed kernel (its Fisher layout)
 };
 
 // extra accumulators of the mixed Fisher kernel: phase-free SNR-gradient sums

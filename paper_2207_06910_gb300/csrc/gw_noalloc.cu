@@ -128,7 +128,6 @@ extern "C" gw_status gw_fisher_noalloc(const gw_catalog *cat, const gw_network *
     pa.partial = partial;
     pa.nacc = nacc;
     pa.cov = nullptr;
-    pa.mixed = mixed ? 1 : 0;
     cudaError_t e = mixed ? launch_points_mixed(MODE_FISHER, n_par, dn.rotation, pa, s)
                           : launch_points_fp64(MODE_FISHER, n_par, dn.rotation, pa, s);
     if (e != cudaSuccess) return GW_ECUDA;

@@ -82,20 +82,24 @@ __device__ __forceinline__ float2 f2sub(float2 a, float2 b)
     return *reinterpret_cast<float2 *>(&rd);
 }
 
-// Exact accumulation of the elementwise product a * b (two lanes: real and
-// imaginary parts) into a packed double-float accumulator that holds the
-// NEGATED sum: hn (register) + *ln (shared memory).  nb = -b.  With p = fl(a b)
-// and q = fl(a nb) = -p, e = fma(a, b, q) is the exact error of p; the two-sum
-// of hn + q is exact; so hn + ln = -(sum of a b) up to the FP32 rounding of ln.
+// Compensated accumulation of the elementwise product a * b (two lanes: real
+// and imaginary parts) into a packed double-float accumulator that holds the
+// NEGATED sum: hn (register) + *ln (shared memory).  nb = -b.  q = fl(-a b) is
+// added to hn with Knuth's two-sum s + t2 + t3 = hn + q, where t2 = hn's and
+// t3 = q - bb q's roundoff (bb = s - hn).  The correction the sum needs is
+// t2 + t3 - e with e = a b + q the product's exact rounding error; since
+// t3 - e = -(a b + bb), it is t2 - fma(a, b, bb): one FMA replaces the product
+// error and q's roundoff, and rounds only a quantity of roundoff size
+// (|a b + bb| <= |e| + |t3|), so hn + ln = -(sum of a b) to ~2^-48 relative.
 __device__ __forceinline__ void acc_pk(float2 &hn, float2 *ln, float2 a, float2 b, float2 nb)
 {
     const float2 q = __fmul2_rn(a, nb);
-    const float2 e = __ffma2_rn(a, b, q);
     const float2 s = __fadd2_rn(hn, q);
     const float2 bb = f2sub(s, hn);
-    const float2 tn = __fadd2_rn(f2sub(hn, f2sub(s, bb)), f2sub(q, bb));
+    const float2 t2 = f2sub(hn, f2sub(s, bb));
+    const float2 y = __ffma2_rn(a, b, bb);
     hn = s;
-    *ln = __fadd2_rn(*ln, f2sub(tn, e));
+    *ln = __fadd2_rn(*ln, f2sub(t2, y));
 }
 
 // Compensated dot products sum_q c_q b_q with double-float coefficients and
@@ -127,13 +131,16 @@ __device__ __forceinline__ DF2 dot2_pk(const float4 *c, const DF (&b)[N], const 
         ch = make_float2(cq.x, cq.y);
         cl = make_float2(cq.z, cq.w);
         bh = make_float2(b[q].hi, b[q].hi);
+        // two-sum t = s + p with nbb = s - t = -bb; the correction (s's roundoff
+        // t2, p's roundoff p - bb and the product error c b - p) is
+        // t2 + (c b - bb), the last term one FMA (see acc_pk)
         const float2 p = __fmul2_rn(ch, bh);
-        const float2 ne = __ffma2_rn(ch, make_float2(nb[q], nb[q]), p);   // p - c b, exact
         const float2 t = __fadd2_rn(s, p);
-        const float2 bb = f2sub(t, s);
-        const float2 err = __fadd2_rn(f2sub(s, f2sub(t, bb)), f2sub(p, bb));
+        const float2 nbb = f2sub(s, t);
+        const float2 t2 = f2sub(s, __fadd2_rn(t, nbb));
+        const float2 y = __ffma2_rn(ch, bh, nbb);
         s = t;
-        comp = __fadd2_rn(comp, f2sub(err, ne));
+        comp = __fadd2_rn(comp, __fadd2_rn(t2, y));
         comp = __ffma2_rn(ch, make_float2(b[q].lo, b[q].lo), comp);
         comp = __ffma2_rn(cl, bh, comp);
     }
@@ -152,10 +159,12 @@ __device__ __forceinline__ DF dot2_s(const float2 *c, const DF (&b)[N])
     for (int q = 1; q < N; q++) {
         cq = c[q];
         const float p = cq.x * b[q].hi;
-        const float e = fmaf(cq.x, b[q].hi, -p);
-        const DF t = two_sum(s, p);
-        s = t.hi;
-        comp += t.lo + e;
+        const float t = s + p;
+        const float nbb = s - t;
+        const float t2 = s - (t + nbb);
+        const float y = fmaf(cq.x, b[q].hi, nbb);   // c b - bb (see acc_pk)
+        s = t;
+        comp += t2 + y;
         comp = fmaf(cq.x, b[q].lo, comp);
         comp = fmaf(cq.y, b[q].hi, comp);
     }
@@ -560,19 +569,28 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
         // GROUP lanes' values of the entries a = gl (mod GROUP) in a fixed
         // order (error-free two-sum of the high parts, compensations added)
         // and writes them in FP64.
+        // In the Fisher layout, slots whose value is another slot's sum are
+        // filled first, from their source: SNR^2 and (d_L, d_L) from (Phic,
+        // Phic) (scaled by 1/d_L^2 below), the iota and psi SNR-gradient sums
+        // from the (d_L, iota) and (d_L, psi) sums; (d_L, Phic) stays zero.
         double *out = A.partial + it * (int64_t)A.nacc;
+        constexpr int k88 = 1 + 8 * NP - 8 * 7 / 2, k22 = 1 + 2 * NP - 1;
+        constexpr int X0 = 1 + NP * (NP + 1) / 2;
+        auto collapse = [&](const int src, const int dst) {
+            const float2 l2 = mylo[src * LDS];
+            const DF h = two_sum(acc[src].x, acc[src].y);
+            mylo[dst * LDS] = make_float2(-h.hi, -((l2.x + l2.y) + h.lo));
+        };
         if (MODE == MODE_FISHER) {
-            // SNR^2 = sum |Q|^2 = the (Phic, Phic) entry
-            constexpr int k88 = 1 + 8 * NP - 8 * 7 / 2;
-            acc[0] = acc[k88];
-            mylo[0] = mylo[k88 * LDS];
+            collapse(k88, 0);
+            collapse(k88, k22);
+            collapse(k22 + 3, X0 + 4);      // (d_L, iota)
+            collapse(k22 + 4, X0 + 5);      // (d_L, psi)
         }
 #pragma unroll
-        for (int a = 0; a < NACC; a++) {
-            const float2 l2 = mylo[a * LDS];
-            const DF h = two_sum(acc[a].x, acc[a].y);
-            mylo[a * LDS] = make_float2(-h.hi, -((l2.x + l2.y) + h.lo));
-        }
+        for (int a = 0; a < NACC; a++)
+            if (!(MODE == MODE_FISHER && (a == 0 || a == k22 || a == X0 + 4 || a == X0 + 5)))
+                collapse(a, a);
         __syncwarp(gmask);
         const float2 *grp = lo_base + (threadIdx.x - gl);
 #pragma unroll 1
@@ -586,7 +604,14 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                 const DF h = two_sum(t.hi, u.x);
                 t = DF{h.hi, (t.lo + u.y) + h.lo};
             }
-            if (a < A.nacc) out[a] = (double)t.hi + (double)t.lo;
+            double v = (double)t.hi + (double)t.lo + 0.0;
+            if (MODE == MODE_FISHER) {
+                // the d_L row sums Re(g_j Q^*): Gamma_{j,d_L} = -sum / d_L
+                const double idl = A.evc[e * (int64_t)EVC + EV_INVDL];
+                if (a == k22) v *= idl * idl;
+                else if (a == 3 || a == NP + 2 || (a > k22 && a <= k22 + NP - 3)) v *= -idl;
+            }
+            if (a < A.nacc) out[a] = v;
         }
         __syncwarp(gmask);
     }

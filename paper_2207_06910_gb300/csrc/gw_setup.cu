@@ -422,16 +422,10 @@ cudaError_t launch_scan(const int64_t *counts, int64_t n, int64_t *off, int64_t 
 // ------------------------------------------------------------------------
 // reduction of item partials: one thread per (event, accumulator), items of an
 // event summed in item order (deterministic).
-// packed upper-triangle position of (i, j), i <= j, over np parameters
-__device__ __forceinline__ int pk_of(int i, int j, int np)
-{
-    return i * np - i * (i - 1) / 2 + (j - i);
-}
-
 __global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc, int64_t cap,
                          const int64_t *item_off, const double *partial, int32_t *status,
                          double *snr, double *snr_det, double *fisher, const double *grad_snr,
-                         double *grad_params, double *xsums, int mixed, const double *evc)
+                         double *grad_params, double *xsums)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t e = t / nacc;
@@ -441,44 +435,9 @@ __global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc, int64
     const bool over = i1 > cap;   // items beyond the workspace capacity
     if (over && a == 0) status[e] |= 64;
     const bool bad = over || (status[e] & ~64) != 0;
-    // The mixed Fisher kernel takes the d_L tangent exactly as -Q/d_L: it sums
-    // Re(g_j Q^*) for the (j, d_L) entries (scaled by -1/d_L here), does not
-    // sum (d_L, d_L) = (Phic, Phic)/d_L^2 or (d_L, Phic) = 0, and its (iota,
-    // d_L) and (psi, d_L) sums are the SNR-gradient sums Re(Q^* dQ/d iota),
-    // Re(Q^* dQ/d psi).
-    int src = a;
-    double scale = 1.0;
-    if (mode == MODE_FISHER && mixed && !bad) {
-        const int npair = np * (np + 1) / 2;
-        if (a >= 1 && a <= npair) {
-            int k = a - 1, i = 0;
-            while (k >= np - i) {
-                k -= np - i;
-                i++;
-            }
-            const int j = i + k;
-            if (i == 2 || j == 2) {
-                const int o = i == 2 ? j : i;
-                const double dl = evc[e * (int64_t)EVC + EV_DL];
-                if (o == 2) {
-                    src = 1 + pk_of(8, 8, np);
-                    scale = 1.0 / (dl * dl);
-                } else if (o == 8) {
-                    scale = 0.0;
-                } else {
-                    scale = -1.0 / dl;
-                }
-            }
-        } else if (a == 1 + npair + 4) {
-            src = 1 + pk_of(2, 5, np);
-        } else if (a == 1 + npair + 5) {
-            src = 1 + pk_of(2, 6, np);
-        }
-    }
     double s = 0.0;
     if (!over)
-        for (int64_t it = i0; it < i1; it++) s += partial[it * nacc + src];
-    s *= scale;
+        for (int64_t it = i0; it < i1; it++) s += partial[it * nacc + a];
     if (mode == MODE_FISHER) {
         const int npair = np * (np + 1) / 2;
         if (a == 0) {
@@ -621,7 +580,7 @@ cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const
                                                            a.n_items, a.item_off, a.partial,
                                                            const_cast<int32_t *>(status), snr,
                                                            snr_det, fisher, grad_snr,
-                                                           grad_params, xsums, a.mixed, a.evc);
+                                                           grad_params, xsums);
     return cudaGetLastError();
 }
 
