@@ -50,7 +50,7 @@ FFMA_PER_CLK_SM = 128        # FP32 FMA lanes per SM (measured 117 / clock with 
 # DRAM bytes (read + write) per grid point of the Fisher point kernel, from one
 # ncu capture of the 2e4-event c3 catalog (4,376,070 points) of the current
 # kernels (profiles/k_points_*_fisher_c3.md); scaled by points to a full launch
-DRAM_BYTES_PER_POINT = {"mixed": (21.66784e6 + 11.776e3) / 4376070,
+DRAM_BYTES_PER_POINT = {"mixed": (23.10528e6 + 11.52e3) / 4376070,
                         "fp64": (19.284224e6 + 91.136e3) / 4376070}
 
 
