@@ -96,6 +96,23 @@ constexpr double LN4 = 0x1.62e42fefa39efp+0;
 constexpr double PI_M23 = 0x1.dd61fae9d2f10p-2;
 constexpr double SQRT_5_24 = 0x1.d363d1848dcbfp-2;
 
+// (hi, lo) FP32 pair of a double, hi = x rounded to FP32 (nearest, ties to
+// even) and lo = x - hi rounded to FP32.  The rounding of hi is done on the bit
+// pattern with integer operations, so only the exact difference and the
+// conversion of lo use the FP64 pipe (this kernel's bound) instead of three
+// conversions and a difference.  Values below FP32's normal range go to lo.
+__device__ __forceinline__ float2 split_f32(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    // keep 24 significant bits: drop the low 29 of the 52-bit mantissa
+    const unsigned long long r = (b + 0x0fffffffull + ((b >> 29) & 1ull)) & ~0x1fffffffull;
+    const unsigned ex = (unsigned)(r >> 52) & 0x7ffu;
+    if (ex < 1023u - 126u || ex > 1023u + 127u) return make_float2(0.0f, (float)x);
+    const unsigned fb = ((unsigned)(r >> 32) & 0x80000000u) | ((ex - 896u) << 23) |
+                        ((unsigned)(r >> 29) & 0x7fffffu);
+    return make_float2(__uint_as_float(fb), (float)(x - __longlong_as_double((long long)r)));
+}
+
 __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec,
                               float *sitec_f, float2 *evc_f, int32_t *status, int64_t *counts)
 {
@@ -132,7 +149,8 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
 
     double *E = evc + e * (int64_t)EVC;
     const double Mcs = Mc * T_SUN;
-    const double Ms = Mcs * pow(eta, -0.6);
+    // (x^y as exp(y ln x): a few ulp, at a fraction of pow's FP64 work)
+    const double Ms = Mcs * exp(-0.6 * log(eta));
     const double pim = PI * Ms;
     const double lnr = log(fmx / fmin) / (double)(N - 1);
     E[EV_MC] = Mc;
@@ -150,7 +168,7 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
     E[EV_RHOG] = exp(GROUP * lnr / 3.0);
     E[EV_RHOIG] = exp(-GROUP * lnr / 3.0);
     E[EV_LNRHOG] = GROUP * lnr / 3.0;
-    E[EV_A0] = SQRT_5_24 * PI_M23 * pow(Mcs, 5.0 / 6.0) / (dL * GPC_S);
+    E[EV_A0] = SQRT_5_24 * PI_M23 * exp(5.0 / 6.0 * log(Mcs)) / (dL * GPC_S);
     E[EV_RAG] = exp(-7.0 / 6.0 * GROUP * lnr);
     double si, ci, s2p, c2p;
     sincos(io, &si, &ci);
@@ -269,8 +287,7 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
         float2 *Ef = evc_f + e * (int64_t)EVC;
         for (int q = EV_WC0; q < EVC; q++) {
             if (q > EV_INVDL && q < EV_PM) continue;
-            const float hi = (float)E[q];
-            Ef[q] = make_float2(hi, (float)(E[q] - (double)hi));
+            Ef[q] = split_f32(E[q]);
         }
     }
 
@@ -285,7 +302,10 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
         const double sl = net.site_slat[s], cl = net.site_clat[s];
         const double c2l = 1.0 - 2.0 * sl * sl, s2l = 2.0 * sl * cl;
         double x0 = ph - net.site_lon[s] - OMEGA_E * tc;
-        x0 = remainder(x0, TWO_PI);
+        // x0 - 2 pi round(x0 / 2 pi): the FMA forms n 2 pi exactly and the
+        // difference (at most ~pi in magnitude) is representable, so this is
+        // exactly remainder(x0, 2 pi) up to the choice at +-pi
+        x0 = fma(-rint(x0 * (1.0 / TWO_PI)), TWO_PI, x0);
         S[SC_X0] = x0;
         S[SC_A1] = (3.0 - c2l) * (3.0 - c2d) / 16.0;
         S[SC_A2] = s2l * s2d / 4.0;
@@ -320,8 +340,14 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
         S[SC_X0LO] = 0.0;
         if (sitec_f) {
             float *Sf = sitec_f + (e * net.n_site + s) * (int64_t)SC_N;
-            for (int q = 0; q < SC_N; q++) Sf[q] = (float)S[q];
-            Sf[SC_X0LO] = (float)(x0 - (double)(float)x0);
+            // (float)S[q]: hi, or lo where the value is below FP32's normal range
+            for (int q = 0; q < SC_N; q++) {
+                const float2 v = split_f32(S[q]);
+                Sf[q] = v.x != 0.0f ? v.x : v.y;
+            }
+            const float2 xs = split_f32(x0);
+            Sf[SC_X0] = xs.x != 0.0f ? xs.x : xs.y;
+            Sf[SC_X0LO] = xs.x != 0.0f ? xs.y : 0.0f;
         }
     }
 }
@@ -608,21 +634,25 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
     if (e >= n) return;
     double A[NP][NP];       // lower triangle: H, then L, then M = L^-1
     double Cu[NK];          // inverse, packed upper triangle (normalised, then rescaled)
-    double d[NP], id[NP], il[NP];
+    double id[NP], il[NP];
     int st = 0;
+    // (the FP64 pipe is this kernel's bound: tests on the bit patterns go to
+    // the integer pipe, and one reciprocal square root replaces each
+    // square root and divide)
+    unsigned nonfin = 0;
 #pragma unroll
     for (int i = 0; i < NP; i++)
 #pragma unroll
         for (int j = i; j < NP; j++) {
             const double v = F[(int64_t)pkt<NP>(i, j) * n + e];
-            if (!isfinite(v)) st |= 4;
+            nonfin |= ((unsigned)(__double_as_longlong(v) >> 52) & 0x7ffu) == 0x7ffu;
             A[j][i] = v;
         }
+    if (nonfin) st |= 4;
 #pragma unroll
     for (int i = 0; i < NP; i++) {
         if (!(A[i][i] > 0.0)) st |= 1;
-        d[i] = sqrt(A[i][i]);
-        id[i] = 1.0 / d[i];      // reciprocals once: the FP64 divide is a sequence
+        id[i] = rsqrt(A[i][i]);   // 1 / sqrt(Gamma_ii)
     }
     double kappa = NAN, eps = NAN;
     if (!st) {
@@ -645,9 +675,7 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
 #pragma unroll
             for (int k = 0; k < j; k++) sjj -= A[j][k] * A[j][k];
             if (!(sjj > 0.0)) st |= 1;
-            const double ljj = sqrt(sjj);
-            A[j][j] = ljj;
-            il[j] = 1.0 / ljj;
+            il[j] = rsqrt(sjj);      // 1 / L_jj (L_jj itself is not read again)
 #pragma unroll
             for (int i = j + 1; i < NP; i++) {
                 double t = A[i][j];
@@ -698,8 +726,10 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
             if (kappa > 1.0 / DBL_EPSILON) st |= 32;
             if (kappa > cond_max) st |= 2;
             if (inv_err) {
-                // eps = max |Gamma C - 1|, Gamma row by row from the input
-                eps = 0.0;
+                // eps = max |Gamma C - 1|, Gamma row by row from the input; the
+                // maximum of |t| on the bit patterns (ordered as unsigned
+                // integers for finite doubles once the sign bit is cleared)
+                unsigned long long emax = 0;
 #pragma unroll
                 for (int i = 0; i < NP; i++) {
                     // (keeps the compiler from loading every row of Gamma at once)
@@ -714,9 +744,12 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
 #pragma unroll
                         for (int k = 0; k < NP; k++)
                             t = fma(g[k], Cu[pkt<NP>(k < j ? k : j, k < j ? j : k)], t);
-                        eps = fmax(eps, fabs(t));
+                        const unsigned long long tb =
+                            (unsigned long long)__double_as_longlong(t) & 0x7fffffffffffffffull;
+                        emax = tb > emax ? tb : emax;
                     }
                 }
+                eps = __longlong_as_double((long long)emax);
             }
         }
     }
