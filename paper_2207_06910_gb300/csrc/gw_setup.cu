@@ -12,6 +12,8 @@ namespace gw {
 
 // ------------------------------------------------------------------------
 // catalog preparation: one thread per event
+constexpr double SIX_SQRT6 = 0x1.d64d51e0db1c6p+3;   // 6^(3/2), correctly rounded
+
 __global__ void k_prepare(int64_t n, const double *m1, const double *m2, const double *chi1,
                           const double *chi2, const double *lam1, const double *lam2,
                           const double *dL_Mpc, const uint8_t *zflag, const double *tcoal,
@@ -41,7 +43,7 @@ __global__ void k_prepare(int64_t n, const double *m1, const double *m2, const d
     double dlt = 0.5 * (d * (1.0 - 13272.0 / 1319.0 * et + 8944.0 / 1319.0 * et * et) * sL
                         + (1.0 - 15910.0 / 1319.0 * et + 32850.0 / 1319.0 * et * et
                            + 3380.0 / 1319.0 * et * et * et) * dLam);
-    Mc[e] = M * pow(et, 0.6);
+    Mc[e] = M * exp(0.6 * log(et));      // eta^(3/5): a few ulp, a fraction of pow's work
     eta[e] = et;
     dL_Gpc[e] = dL_Mpc[e] * 1.0e-3;
     chi1o[e] = ca;
@@ -49,7 +51,7 @@ __global__ void k_prepare(int64_t n, const double *m1, const double *m2, const d
     LamT[e] = lt;
     dLamT[e] = dlt;
     tc_s[e] = tcoal[e] * T_SIDEREAL;
-    double fi = 1.0 / (pow(6.0, 1.5) * PI * M * T_SUN);
+    double fi = 1.0 / (SIX_SQRT6 * PI * M * T_SUN);   // 1 / (6^(3/2) pi M)
     fmax_o[e] = fi;
     int32_t np;
     if (npts_given) {
@@ -446,44 +448,62 @@ cudaError_t launch_scan(const int64_t *counts, int64_t n, int64_t *off, int64_t 
 }
 
 // ------------------------------------------------------------------------
-// reduction of item partials: one thread per (event, accumulator), items of an
-// event summed in item order (deterministic).
-__global__ void k_finish(int mode, int np, int n_det, int64_t n, int nacc, int64_t cap,
-                         const int64_t *item_off, const double *partial, int32_t *status,
-                         double *snr, double *snr_det, double *fisher, const double *grad_snr,
-                         double *grad_params, double *xsums)
+// reduction of item partials: one block per tile of FIN_EV consecutive events.
+// Their items are consecutive rows of `partial`, so the block reads one
+// contiguous span (accumulator fastest) and sums each event's items in item
+// order (deterministic) into shared memory; every output row is then written
+// as one coalesced run of FIN_EV events (the outputs are event-minor).
+constexpr int FIN_EV = 32;
+constexpr int FIN_BS = 256;
+
+__global__ void __launch_bounds__(FIN_BS) k_finish(int mode, int np, int n_det, int64_t n,
+                                                   int nacc, int64_t cap,
+                                                   const int64_t *item_off,
+                                                   const double *partial, int32_t *status,
+                                                   double *snr, double *snr_det, double *fisher,
+                                                   const double *grad_snr, double *grad_params,
+                                                   double *xsums)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t e = t / nacc;
-    int a = (int)(t - e * nacc);
-    if (e >= n) return;
-    const int64_t i0 = item_off[e], i1 = item_off[e + 1];
-    const bool over = i1 > cap;   // items beyond the workspace capacity
-    if (over && a == 0) status[e] |= 64;
-    const bool bad = over || (status[e] & ~64) != 0;
-    double s = 0.0;
-    if (!over)
-        for (int64_t it = i0; it < i1; it++) s += partial[it * nacc + a];
-    if (mode == MODE_FISHER) {
-        const int npair = np * (np + 1) / 2;
-        if (a == 0) {
-            if (snr) snr[e] = bad ? NAN : sqrt(s);
-        } else if (a <= npair) {
-            fisher[(int64_t)(a - 1) * n + e] = bad ? NAN : s;
-        } else if (xsums) {
-            xsums[(int64_t)(a - 1 - npair) * n + e] = bad ? NAN : s;
-        }
-    } else if (mode == MODE_SNR) {
-        if (a == 0) snr[e] = bad ? NAN : sqrt(s);
-        else if (snr_det) snr_det[(int64_t)(a - 1) * n + e] = bad ? NAN : sqrt(s);
-    } else if (mode == MODE_SNRGRAD) {
-        if (a > 0) {
-            double s0 = 0.0;
-            if (!over)
-                for (int64_t it = i0; it < i1; it++) s0 += partial[it * nacc];
-            // d SNR / d theta = sum W Re(Q* g) / SNR (zero when no arm is on)
-            grad_params[(int64_t)(a - 1) * n + e] =
-                bad ? NAN : (s0 > 0.0 ? grad_snr[e] * s / sqrt(s0) : 0.0);
+    extern __shared__ double fin_s[];     // [nacc][FIN_EV + 1]
+    constexpr int LD = FIN_EV + 1;
+    const int64_t e0 = blockIdx.x * (int64_t)FIN_EV;
+    const int ne = (int)(n - e0 < FIN_EV ? n - e0 : FIN_EV);
+    for (int q = threadIdx.x; q < ne * nacc; q += FIN_BS) {
+        const int le = q / nacc, a = q - le * nacc;
+        const int64_t i0 = item_off[e0 + le], i1 = item_off[e0 + le + 1];
+        double s = 0.0;
+        if (i1 <= cap)                    // items beyond the workspace capacity: none
+            for (int64_t it = i0; it < i1; it++) s += partial[it * nacc + a];
+        fin_s[a * LD + le] = s;
+    }
+    __syncthreads();
+    const int npair = np * (np + 1) / 2;
+    for (int q = threadIdx.x; q < nacc * FIN_EV; q += FIN_BS) {
+        const int a = q / FIN_EV, le = q - a * FIN_EV;
+        if (le >= ne) continue;
+        const int64_t e = e0 + le;
+        const bool over = item_off[e + 1] > cap;
+        if (over && a == 0) status[e] |= 64;
+        const bool bad = over || (status[e] & ~64) != 0;
+        const double s = fin_s[a * LD + le];
+        if (mode == MODE_FISHER) {
+            if (a == 0) {
+                if (snr) snr[e] = bad ? NAN : sqrt(s);
+            } else if (a <= npair) {
+                fisher[(int64_t)(a - 1) * n + e] = bad ? NAN : s;
+            } else if (xsums) {
+                xsums[(int64_t)(a - 1 - npair) * n + e] = bad ? NAN : s;
+            }
+        } else if (mode == MODE_SNR) {
+            if (a == 0) snr[e] = bad ? NAN : sqrt(s);
+            else if (snr_det) snr_det[(int64_t)(a - 1) * n + e] = bad ? NAN : sqrt(s);
+        } else if (mode == MODE_SNRGRAD) {
+            if (a > 0) {
+                const double s0 = fin_s[le];
+                // d SNR / d theta = sum W Re(Q* g) / SNR (zero when no arm is on)
+                grad_params[(int64_t)(a - 1) * n + e] =
+                    bad ? NAN : (s0 > 0.0 ? grad_snr[e] * s / sqrt(s0) : 0.0);
+            }
         }
     }
 }
@@ -599,14 +619,12 @@ cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const
                                               grad_gamma);
         return cudaGetLastError();
     }
-    int64_t tot = a.n_ev * a.nacc;
-    if (tot <= 0) return cudaSuccess;
-    int bs = 256;
-    k_finish<<<(unsigned)((tot + bs - 1) / bs), bs, 0, s>>>(mode, np, n_det, a.n_ev, a.nacc,
-                                                           a.n_items, a.item_off, a.partial,
-                                                           const_cast<int32_t *>(status), snr,
-                                                           snr_det, fisher, grad_snr,
-                                                           grad_params, xsums);
+    if (a.n_ev <= 0 || a.nacc <= 0) return cudaSuccess;
+    const size_t smem = (size_t)a.nacc * (FIN_EV + 1) * sizeof(double);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    k_finish<<<(unsigned)((a.n_ev + FIN_EV - 1) / FIN_EV), FIN_BS, smem, s>>>(
+        mode, np, n_det, a.n_ev, a.nacc, a.n_items, a.item_off, a.partial,
+        const_cast<int32_t *>(status), snr, snr_det, fisher, grad_snr, grad_params, xsums);
     return cudaGetLastError();
 }
 
