@@ -152,25 +152,29 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
     double *E = evc + e * (int64_t)EVC;
     const double Mcs = Mc * T_SUN;
     // (x^y as exp(y ln x): a few ulp, at a fraction of pow's FP64 work)
-    const double Ms = Mcs * exp(-0.6 * log(eta));
+    const double lMcs = log(Mcs), leta = log(eta);
+    const double Ms = Mcs * exp(-0.6 * leta);
     const double pim = PI * Ms;
     const double lnr = log(fmx / fmin) / (double)(N - 1);
+    const double em = expm1(lnr);                 // r - 1, r = f_(k+1) / f_k
+    const double emn = em / (1.0 + em);           // 1 - 1/r
     E[EV_MC] = Mc;
     E[EV_ETA] = eta;
     E[EV_DL] = dL;
     E[EV_NPTS] = (double)N;
     E[EV_LNR] = lnr;
-    E[EV_WC0] = 0.5 * expm1(lnr);
-    E[EV_WCM] = sinh(lnr);
-    E[EV_WCN] = -0.5 * expm1(-lnr);
+    E[EV_WC0] = 0.5 * em;
+    E[EV_WCM] = 0.5 * em + 0.5 * emn;            // sinh(ln r) = (r - 1/r) / 2
+    E[EV_WCN] = 0.5 * emn;
     E[EV_LNF0] = log(fmin);
     E[EV_LNPIM] = log(pim);
     E[EV_INV_PIM] = 1.0 / pim;
     E[EV_PIM] = pim;
-    E[EV_RHOG] = exp(GROUP * lnr / 3.0);
-    E[EV_RHOIG] = exp(-GROUP * lnr / 3.0);
+    const double rhog = exp(GROUP * lnr / 3.0);
+    E[EV_RHOG] = rhog;
+    E[EV_RHOIG] = 1.0 / rhog;
     E[EV_LNRHOG] = GROUP * lnr / 3.0;
-    E[EV_A0] = SQRT_5_24 * PI_M23 * exp(5.0 / 6.0 * log(Mcs)) / (dL * GPC_S);
+    E[EV_A0] = SQRT_5_24 * PI_M23 * exp(5.0 / 6.0 * lMcs) / (dL * GPC_S);
     E[EV_RAG] = exp(-7.0 / 6.0 * GROUP * lnr);
     double si, ci, s2p, c2p;
     sincos(io, &si, &ci);
@@ -631,15 +635,19 @@ cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const
 // ------------------------------------------------------------------------
 // Batched inversion (Sec. 4.1): normalise by sqrt(diag), Cholesky, triangular
 // inverse, C = L^-T L^-1 rescaled; 1-norm condition number of the normalised
-// matrix and eps = max |Gamma C - 1|.  One thread per event, FP64.  The
-// factorisation works in place on one lower triangle (H, then L, then
-// M = L^-1) and the inverse is formed on one packed triangle, so that a
-// thread holds ~2 P(P+1)/2 values instead of five full matrices; the rows of
-// Gamma for eps are read again from the input.
+// matrix and eps = max |Gamma C - 1|.  One thread per event, FP64.  Everything
+// happens in place on one packed lower triangle (H, then L, then M = L^-1,
+// then C), so that a thread holds P(P+1)/2 values; the rows of Gamma for eps
+// are read again from the input.
 template <int NP>
-__device__ __forceinline__ constexpr int pkt(int i, int j)   // packed (i <= j)
+__device__ __forceinline__ constexpr int pkt(int i, int j)   // packed upper (i <= j)
 {
     return i * NP - i * (i - 1) / 2 + (j - i);
+}
+
+__device__ __forceinline__ constexpr int plt(int i, int j)   // packed lower (j <= i)
+{
+    return i * (i + 1) / 2 + j;
 }
 
 template <int NP>
@@ -650,8 +658,7 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
     constexpr int NK = NP * (NP + 1) / 2;
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n) return;
-    double A[NP][NP];       // lower triangle: H, then L, then M = L^-1
-    double Cu[NK];          // inverse, packed upper triangle (normalised, then rescaled)
+    double T[NK];           // lower triangle: H, then L, then M = L^-1, then C
     double id[NP], il[NP];
     int st = 0;
     // (the FP64 pipe is this kernel's bound: tests on the bit patterns go to
@@ -661,85 +668,107 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
 #pragma unroll
     for (int i = 0; i < NP; i++)
 #pragma unroll
-        for (int j = i; j < NP; j++) {
+        for (int j = 0; j < NP; j++) {
+            if (j < i) continue;
             const double v = F[(int64_t)pkt<NP>(i, j) * n + e];
             nonfin |= ((unsigned)(__double_as_longlong(v) >> 52) & 0x7ffu) == 0x7ffu;
-            A[j][i] = v;
+            T[plt(j, i)] = v;
         }
     if (nonfin) st |= 4;
 #pragma unroll
     for (int i = 0; i < NP; i++) {
-        if (!(A[i][i] > 0.0)) st |= 1;
-        id[i] = rsqrt(A[i][i]);   // 1 / sqrt(Gamma_ii)
+        if (!(T[plt(i, i)] > 0.0)) st |= 1;
+        id[i] = rsqrt(T[plt(i, i)]);   // 1 / sqrt(Gamma_ii)
     }
     double kappa = NAN, eps = NAN;
     if (!st) {
-        // normalise, and the column 1-norms of H (symmetric: from the lower triangle)
+        // normalise, and the 1-norm of H (symmetric: column sums from the lower triangle)
         double colh[NP];
 #pragma unroll
         for (int j = 0; j < NP; j++) colh[j] = 0.0;
 #pragma unroll
         for (int i = 0; i < NP; i++)
 #pragma unroll
-            for (int j = 0; j <= i; j++) {
-                A[i][j] *= id[i] * id[j];
-                colh[j] += fabs(A[i][j]);
-                if (i != j) colh[i] += fabs(A[i][j]);
+            for (int j = 0; j < NP; j++) {
+                if (j > i) continue;
+                T[plt(i, j)] *= id[i] * id[j];
+                colh[j] += fabs(T[plt(i, j)]);
+                if (i != j) colh[i] += fabs(T[plt(i, j)]);
             }
-        // Cholesky H = L L^T in place
+        double hn1 = 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; j++) hn1 = fmax(hn1, colh[j]);
+        // Cholesky H = L L^T in place (the diagonal of L is kept as 1 / L_jj only)
 #pragma unroll
         for (int j = 0; j < NP; j++) {
-            double sjj = A[j][j];
+            double sjj = T[plt(j, j)];
 #pragma unroll
-            for (int k = 0; k < j; k++) sjj -= A[j][k] * A[j][k];
+            for (int k = 0; k < NP; k++)
+                if (k < j) sjj -= T[plt(j, k)] * T[plt(j, k)];
             if (!(sjj > 0.0)) st |= 1;
-            il[j] = rsqrt(sjj);      // 1 / L_jj (L_jj itself is not read again)
+            il[j] = rsqrt(sjj);
 #pragma unroll
-            for (int i = j + 1; i < NP; i++) {
-                double t = A[i][j];
+            for (int i = 0; i < NP; i++) {
+                if (i <= j) continue;
+                double t = T[plt(i, j)];
 #pragma unroll
-                for (int k = 0; k < j; k++) t -= A[i][k] * A[j][k];
-                A[i][j] = t * il[j];
+                for (int k = 0; k < NP; k++)
+                    if (k < j) t -= T[plt(i, k)] * T[plt(j, k)];
+                T[plt(i, j)] = t * il[j];
             }
         }
         if (!st) {
-            // M = L^-1 in place, column by column from the left: M[i][j] =
-            // -(1/L[i][i]) sum_{k=j}^{i-1} L[i][k] M[k][j] reads L only in
-            // columns >= j of rows > i-1, which are still L
+            // M = L^-1 in place, column by column from the left: M_ij =
+            // -(1/L_ii) sum_{k=j}^{i-1} L_ik M_kj reads L only in columns >= j
+            // of rows > i-1, which are still L
 #pragma unroll
             for (int j = 0; j < NP; j++) {
-                A[j][j] = il[j];
+                T[plt(j, j)] = il[j];
 #pragma unroll
-                for (int i = j + 1; i < NP; i++) {
+                for (int i = 0; i < NP; i++) {
+                    if (i <= j) continue;
                     double t = 0.0;
 #pragma unroll
-                    for (int k = j; k < i; k++) t = fma(A[i][k], A[k][j], t);
-                    A[i][j] = -t * il[i];
+                    for (int k = 0; k < NP; k++)
+                        if (k >= j && k < i) t = fma(T[plt(i, k)], T[plt(k, j)], t);
+                    T[plt(i, j)] = -t * il[i];
                 }
             }
-            // Hinv = M^T M on one triangle; its column 1-norms; rescale to C.
-            // Column j of Hinv reads rows >= j of M: going through j upwards
-            // lets rows of M die as the triangle of C fills (fewer live values)
+            // Hinv = M^T M in place, row by row from the top: Hinv_ij (j <= i)
+            // = sum_{k>=i} M_ki M_kj reads rows >= i of M only, and of row i
+            // only M_ii and M_ij, so the diagonal entry is written last.  Its
+            // 1-norm, then the rescaled C = D^-1 Hinv D^-1 in place.
             double coli[NP];
 #pragma unroll
             for (int j = 0; j < NP; j++) coli[j] = 0.0;
 #pragma unroll
-            for (int j = 0; j < NP; j++)
+            for (int i = 0; i < NP; i++) {
 #pragma unroll
-                for (int i = 0; i <= j; i++) {
+                for (int j = 0; j < NP; j++) {
+                    if (j >= i) continue;
                     double t = 0.0;
 #pragma unroll
-                    for (int k = j; k < NP; k++) t = fma(A[k][i], A[k][j], t);
+                    for (int k = 0; k < NP; k++)
+                        if (k >= i) t = fma(T[plt(k, i)], T[plt(k, j)], t);
                     coli[j] += fabs(t);
-                    if (i != j) coli[i] += fabs(t);
-                    Cu[pkt<NP>(i, j)] = t * id[i] * id[j];
+                    coli[i] += fabs(t);
+                    T[plt(i, j)] = t;
                 }
-            double hn1 = 0.0, in1 = 0.0;
+                double t = 0.0;
 #pragma unroll
-            for (int j = 0; j < NP; j++) {
-                hn1 = fmax(hn1, colh[j]);
-                in1 = fmax(in1, coli[j]);
+                for (int k = 0; k < NP; k++)
+                    if (k >= i) t = fma(T[plt(k, i)], T[plt(k, i)], t);
+                coli[i] += fabs(t);
+                T[plt(i, i)] = t;
             }
+            double in1 = 0.0;
+#pragma unroll
+            for (int j = 0; j < NP; j++) in1 = fmax(in1, coli[j]);
+#pragma unroll
+            for (int i = 0; i < NP; i++)
+#pragma unroll
+                for (int j = 0; j < NP; j++)
+                    if (j <= i) T[plt(i, j)] *= id[i] * id[j];
             kappa = hn1 * in1;
             if (kappa > 1.0 / DBL_EPSILON) st |= 32;
             if (kappa > cond_max) st |= 2;
@@ -761,7 +790,7 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
                         double t = (i == j) ? -1.0 : 0.0;
 #pragma unroll
                         for (int k = 0; k < NP; k++)
-                            t = fma(g[k], Cu[pkt<NP>(k < j ? k : j, k < j ? j : k)], t);
+                            t = fma(g[k], T[k > j ? plt(k, j) : plt(j, k)], t);
                         const unsigned long long tb =
                             (unsigned long long)__double_as_longlong(t) & 0x7fffffffffffffffull;
                         emax = tb > emax ? tb : emax;
@@ -773,7 +802,10 @@ __global__ void __launch_bounds__(128) k_invert(const double *F, int64_t n, doub
     }
     const bool ok = !(st & (1 | 2 | 4));
 #pragma unroll
-    for (int k = 0; k < NK; k++) cov[(int64_t)k * n + e] = ok ? Cu[k] : NAN;
+    for (int i = 0; i < NP; i++)
+#pragma unroll
+        for (int j = 0; j < NP; j++)
+            if (j >= i) cov[(int64_t)pkt<NP>(i, j) * n + e] = ok ? T[plt(j, i)] : NAN;
     if (cond) cond[e] = (st & (1 | 4)) ? NAN : kappa;
     if (inv_err) inv_err[e] = ok ? eps : NAN;
     status[e] = st;
