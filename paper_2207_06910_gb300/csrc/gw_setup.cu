@@ -115,10 +115,19 @@ __device__ __forceinline__ float2 split_f32(double x)
     return make_float2(__uint_as_float(fb), (float)(x - __longlong_as_double((long long)r)));
 }
 
-__global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec,
-                              float *sitec_f, float2 *evc_f, int32_t *status, int64_t *counts)
+constexpr int SETUP_BS = 128;   // threads per block: two warps per 32 events
+
+__global__ void __launch_bounds__(SETUP_BS)
+k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec, float *sitec_f,
+              float2 *evc_f, int32_t *status, int64_t *counts)
 {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // two warps per 32 events (the set-up is a long chain of dependent FP64
+    // operations: twice the warps hide twice the latency): the even warp of a
+    // pair writes the status, the scalars and the phase coefficients, the odd
+    // one tau* and the per-site constants; each warp follows one path
+    const int part = (threadIdx.x >> 5) & 1;
+    const int64_t e = ((int64_t)blockIdx.x * (SETUP_BS / 64) + (threadIdx.x >> 6)) * 32 +
+                      (threadIdx.x & 31);
     if (e >= cat.n) return;
     const int64_t r = cat.sel ? cat.sel[e] : e;     // catalog row of the call's event e
     const double Mc = cat.Mc[r], eta = cat.eta[r], dL = cat.dL[r];
@@ -144,216 +153,223 @@ __global__ void k_event_setup(DevCat cat, DevNet net, int np, double *evc, doubl
         !isfinite(cat.Phic[r]))
         st |= 16;
     if (!(fmin > 0.0) || !(fmx > fmin) || !isfinite(fmx) || N < 2) st |= 8;
-    status[e] = st;
-    // no work items when no interferometer is in use (zero SNR and Fisher)
-    counts[e] = (st || !ifo_on) ? 0 : (int64_t)((N + CHUNK_MAX - 1) / CHUNK_MAX);
+    if (part == 0) {
+        status[e] = st;
+        // no work items when no interferometer is in use (zero SNR and Fisher)
+        counts[e] = (st || !ifo_on) ? 0 : (int64_t)((N + CHUNK_MAX - 1) / CHUNK_MAX);
+    }
     if (st) return;
 
     double *E = evc + e * (int64_t)EVC;
+    float2 *Ef = evc_f ? evc_f + e * (int64_t)EVC : nullptr;
     const double Mcs = Mc * T_SUN;
     // (x^y as exp(y ln x): a few ulp, at a fraction of pow's FP64 work)
-    const double lMcs = log(Mcs), leta = log(eta);
+    const double leta = log(eta);
     const double Ms = Mcs * exp(-0.6 * leta);
-    const double pim = PI * Ms;
-    const double lnr = log(fmx / fmin) / (double)(N - 1);
-    const double em = expm1(lnr);                 // r - 1, r = f_(k+1) / f_k
-    const double emn = em / (1.0 + em);           // 1 - 1/r
-    E[EV_MC] = Mc;
-    E[EV_ETA] = eta;
-    E[EV_DL] = dL;
-    E[EV_NPTS] = (double)N;
-    E[EV_LNR] = lnr;
-    E[EV_WC0] = 0.5 * em;
-    E[EV_WCM] = 0.5 * em + 0.5 * emn;            // sinh(ln r) = (r - 1/r) / 2
-    E[EV_WCN] = 0.5 * emn;
-    E[EV_LNF0] = log(fmin);
-    E[EV_LNPIM] = log(pim);
-    E[EV_INV_PIM] = 1.0 / pim;
-    E[EV_PIM] = pim;
-    const double rhog = exp(GROUP * lnr / 3.0);
-    E[EV_RHOG] = rhog;
-    E[EV_RHOIG] = 1.0 / rhog;
-    E[EV_LNRHOG] = GROUP * lnr / 3.0;
-    E[EV_A0] = SQRT_5_24 * PI_M23 * exp(5.0 / 6.0 * lMcs) / (dL * GPC_S);
-    E[EV_RAG] = exp(-7.0 / 6.0 * GROUP * lnr);
-    double si, ci, s2p, c2p;
-    sincos(io, &si, &ci);
-    sincos(2.0 * ps, &s2p, &c2p);
-    E[EV_CP] = 0.5 * (1.0 + ci * ci);
-    E[EV_CX] = ci;
-    E[EV_DCP] = -ci * si;
-    E[EV_DCX] = -si;
-    E[EV_C2PSI] = c2p;
-    E[EV_S2PSI] = s2p;
-    E[EV_AMC] = 5.0 / (6.0 * Mc);
-    E[EV_INVDL] = 1.0 / dL;
-    E[EV_IFOON] = (double)ifo_on;
-    E[EV_ARMON] = (double)am;
-    E[EV_PHI0] = -cat.Phic[r] - 0.25 * PI;
-
-    // ---- TaylorF2 3.5PN phase coefficients (restricted PN)
     const double pi2 = PI * PI;
-    const double d = sqrt(fmax(0.0, 1.0 - 4.0 * eta));
-    const double X1 = 0.5 * (1.0 + d), X2 = 0.5 * (1.0 - d);
-    const double b1 = 113.0 / 12.0 * X1 * X1 + 25.0 * eta / 4.0;
-    const double b2 = 113.0 / 12.0 * X2 * X2 + 25.0 * eta / 4.0;
-    const double beta = b1 * c1 + b2 * c2;
-    const double sigma = 79.0 / 8.0 * eta * c1 * c2;
-    const double dbeta = 113.0 / 6.0 * (X2 * c2 - X1 * c1) / d + 25.0 / 4.0 * (c1 + c2);
-    const double dsigma = 79.0 / 8.0 * c1 * c2;
-    const double ln6h = 1.0 + 1.5 * LN6;                      // 1 - 3 ln v_lso
-    const double L6 = -6848.0 / 21.0;
-    const double p2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
-    const double p3 = -16.0 * PI + 4.0 * beta;
-    const double p4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta
-                      - 10.0 * sigma;
-    const double p5a = PI * (38645.0 / 756.0 - 65.0 / 9.0 * eta);
-    const double p5c = p5a * ln6h;
-    const double p6c = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi2
-                       - 6848.0 / 21.0 * EULER_GAMMA
-                       + (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2) * eta
-                       + 76055.0 / 1728.0 * eta * eta - 127825.0 / 1296.0 * eta * eta * eta;
-    const double p6 = p6c + L6 * LN4;
-    const double p7 = PI * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta
-                            - 74045.0 / 756.0 * eta * eta);
-    const double t10 = -39.0 / 2.0 * LT;
-    const double t12 = -3115.0 / 64.0 * LT + 6595.0 / 364.0 * d * dLT;
-    const double dp4 = 27145.0 / 504.0 + 2.0 * 3085.0 / 72.0 * eta - 10.0 * dsigma;
-    const double dp5a = -65.0 * PI / 9.0;
-    const double dp6 = -15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2
-                       + 2.0 * 76055.0 / 1728.0 * eta - 3.0 * 127825.0 / 1296.0 * eta * eta;
-    const double dp7 = PI * (378515.0 / 1512.0 - 2.0 * 74045.0 / 756.0 * eta);
-    const double dt12 = 6595.0 / 364.0 * (-2.0 / d) * dLT;
     const double ie = 1.0 / eta;
-    const double pre = 3.0 / 128.0 * ie;
     // reciprocals once (the FP64 divide is a multi-instruction sequence)
     const double i3Mc = 1.0 / (3.0 * Mc), i5eta = 0.2 * ie;
-    // v dPsi/dv
-    const double V[11] = {-5.0, -3.0 * p2, -2.0 * p3, -p4, 3.0 * p5a, p6 + L6, 2.0 * p7,
-                          5.0 * t10, 7.0 * t12, 0.0, L6};
-    // dPsi/deta at fixed v (before the prefactor)
-    const double De[11] = {-ie, 55.0 / 9.0 - p2 * ie, 4.0 * dbeta - p3 * ie, dp4 - p4 * ie,
-                           dp5a * ln6h - p5c * ie, dp6 - p6 * ie, dp7 - p7 * ie, -t10 * ie,
-                           dt12 - t12 * ie, 3.0 * (dp5a - p5a * ie), -L6 * ie};
-    // Psi itself (strain output): v^-5 (1, p2 v^2, p3 v^3, p4 v^4) + p5a (1 - 3 ln v_lso
-    // + 3 ln v) + (p6 + L6 ln v) v + p7 v^2 + tidal v^5, v^7, all times 3/(128 eta)
-    const double Ps[11] = {1.0, p2, p3, p4, p5c, p6, p7, t10, t12, 3.0 * p5a, L6};
-    for (int k = 0; k < 11; k++) {
-        E[EV_PSI + k] = pre * Ps[k];
-        E[EV_PM + k] = pre * V[k] * i3Mc;
-        E[EV_PE + k] = pre * (De[k] - V[k] * i5eta);
-    }
-    double q9[4] = {0, 0, 0, 0}, q10[4] = {0, 0, 0, 0};
-    if (pset == 1) {
-        q9[0] = 4.0 * b1;
-        q9[1] = -10.0 * 79.0 / 8.0 * eta * c2;
-        q10[0] = 4.0 * b2;
-        q10[1] = -10.0 * 79.0 / 8.0 * eta * c1;
-    } else if (pset == 2) {
-        q9[2] = -39.0 / 2.0;
-        q9[3] = -3115.0 / 64.0;
-        q10[3] = 6595.0 / 364.0 * d;
-    }
-    for (int k = 0; k < 4; k++) {
-        E[EV_P9 + k] = pre * q9[k];
-        E[EV_P10 + k] = pre * q10[k];
-    }
-    // ---- tau*(f), 3.5PN (Buonanno et al. 2009 Eq. 3.8b), basis B8 times v^-3
-    const double Kt = 5.0 * Ms / (256.0 * eta);
-    const double t2 = 743.0 / 252.0 + 11.0 / 3.0 * eta;
-    const double t3 = -32.0 / 5.0 * PI;
-    const double t4 = 3058673.0 / 508032.0 + 5429.0 / 504.0 * eta + 617.0 / 72.0 * eta * eta;
-    const double t5 = (-7729.0 / 252.0 + 13.0 / 3.0 * eta) * PI;
-    const double t6 = -10052469856691.0 / 23471078400.0 + 128.0 / 3.0 * pi2
-                      + 6848.0 / 105.0 * EULER_GAMMA
-                      + (3147553127.0 / 3048192.0 - 451.0 / 12.0 * pi2) * eta
-                      - 15211.0 / 1728.0 * eta * eta + 25565.0 / 1296.0 * eta * eta * eta
-                      + 3424.0 / 105.0 * (2.0 * LN4);
-    const double t6L = 6848.0 / 105.0;
-    const double t7 = (-15419335.0 / 127008.0 - 75703.0 / 756.0 * eta
-                       + 14809.0 / 378.0 * eta * eta) * PI;
-    const double dt4 = 5429.0 / 504.0 + 2.0 * 617.0 / 72.0 * eta;
-    const double dt5 = 13.0 / 3.0 * PI;
-    const double dt6 = 3147553127.0 / 3048192.0 - 451.0 / 12.0 * pi2
-                       - 2.0 * 15211.0 / 1728.0 * eta + 3.0 * 25565.0 / 1296.0 * eta * eta;
-    const double dt7 = PI * (-75703.0 / 756.0 + 2.0 * 14809.0 / 378.0 * eta);
-    const double T0[8] = {1.0, t2, t3, t4, t5, t6, t7, t6L};
-    const double Tv[8] = {-5.0, -3.0 * t2, -2.0 * t3, -t4, 0.0, t6 + t6L, 2.0 * t7, t6L};
-    const double Te[8] = {-ie, 11.0 / 3.0 - t2 * ie, -t3 * ie, dt4 - t4 * ie, dt5 - t5 * ie,
-                          dt6 - t6 * ie, dt7 - t7 * ie, -t6L * ie};
-    for (int k = 0; k < 8; k++) {
-        E[EV_T0 + k] = Kt * T0[k];
-        E[EV_TM + k] = Kt * Tv[k] * i3Mc;
-        E[EV_TE + k] = Kt * (Te[k] - Tv[k] * i5eta);
-    }
+    if (part == 0) {
+        const double pim = PI * Ms;
+        const double lnr = log(fmx / fmin) / (double)(N - 1);
+        const double em = expm1(lnr);                 // r - 1, r = f_(k+1) / f_k
+        const double emn = em / (1.0 + em);           // 1 - 1/r
+        E[EV_MC] = Mc;
+        E[EV_ETA] = eta;
+        E[EV_DL] = dL;
+        E[EV_NPTS] = (double)N;
+        E[EV_LNR] = lnr;
+        E[EV_WC0] = 0.5 * em;
+        E[EV_WCM] = 0.5 * em + 0.5 * emn;            // sinh(ln r) = (r - 1/r) / 2
+        E[EV_WCN] = 0.5 * emn;
+        E[EV_LNF0] = log(fmin);
+        E[EV_LNPIM] = log(pim);
+        E[EV_INV_PIM] = 1.0 / pim;
+        E[EV_PIM] = pim;
+        const double rhog = exp(GROUP * lnr / 3.0);
+        E[EV_RHOG] = rhog;
+        E[EV_RHOIG] = 1.0 / rhog;
+        E[EV_LNRHOG] = GROUP * lnr / 3.0;
+        E[EV_A0] = SQRT_5_24 * PI_M23 * exp(5.0 / 6.0 * log(Mcs)) / (dL * GPC_S);
+        E[EV_RAG] = exp(-7.0 / 6.0 * GROUP * lnr);
+        double si, ci, s2p, c2p;
+        sincos(io, &si, &ci);
+        sincos(2.0 * ps, &s2p, &c2p);
+        E[EV_CP] = 0.5 * (1.0 + ci * ci);
+        E[EV_CX] = ci;
+        E[EV_DCP] = -ci * si;
+        E[EV_DCX] = -si;
+        E[EV_C2PSI] = c2p;
+        E[EV_S2PSI] = s2p;
+        E[EV_AMC] = 5.0 / (6.0 * Mc);
+        E[EV_INVDL] = 1.0 / dL;
+        E[EV_IFOON] = (double)ifo_on;
+        E[EV_ARMON] = (double)am;
+        E[EV_PHI0] = -cat.Phic[r] - 0.25 * PI;
 
-    // double-float (hi, lo) copy of the constants the mixed point loop reads
-    // (slots EV_WC0 .. EV_INVDL and the polynomial coefficients EV_PM ..)
-    if (evc_f) {
-        float2 *Ef = evc_f + e * (int64_t)EVC;
-        for (int q = EV_WC0; q < EVC; q++) {
-            if (q > EV_INVDL && q < EV_PM) continue;
-            Ef[q] = split_f32(E[q]);
+        // ---- TaylorF2 3.5PN phase coefficients (restricted PN)
+        const double d = sqrt(fmax(0.0, 1.0 - 4.0 * eta));
+        const double X1 = 0.5 * (1.0 + d), X2 = 0.5 * (1.0 - d);
+        const double b1 = 113.0 / 12.0 * X1 * X1 + 25.0 * eta / 4.0;
+        const double b2 = 113.0 / 12.0 * X2 * X2 + 25.0 * eta / 4.0;
+        const double beta = b1 * c1 + b2 * c2;
+        const double sigma = 79.0 / 8.0 * eta * c1 * c2;
+        const double dbeta = 113.0 / 6.0 * (X2 * c2 - X1 * c1) / d + 25.0 / 4.0 * (c1 + c2);
+        const double dsigma = 79.0 / 8.0 * c1 * c2;
+        const double ln6h = 1.0 + 1.5 * LN6;                      // 1 - 3 ln v_lso
+        const double L6 = -6848.0 / 21.0;
+        const double p2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
+        const double p3 = -16.0 * PI + 4.0 * beta;
+        const double p4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta
+                          - 10.0 * sigma;
+        const double p5a = PI * (38645.0 / 756.0 - 65.0 / 9.0 * eta);
+        const double p5c = p5a * ln6h;
+        const double p6c = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi2
+                           - 6848.0 / 21.0 * EULER_GAMMA
+                           + (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2) * eta
+                           + 76055.0 / 1728.0 * eta * eta - 127825.0 / 1296.0 * eta * eta * eta;
+        const double p6 = p6c + L6 * LN4;
+        const double p7 = PI * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta
+                                - 74045.0 / 756.0 * eta * eta);
+        const double t10 = -39.0 / 2.0 * LT;
+        const double t12 = -3115.0 / 64.0 * LT + 6595.0 / 364.0 * d * dLT;
+        const double dp4 = 27145.0 / 504.0 + 2.0 * 3085.0 / 72.0 * eta - 10.0 * dsigma;
+        const double dp5a = -65.0 * PI / 9.0;
+        const double dp6 = -15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2
+                           + 2.0 * 76055.0 / 1728.0 * eta - 3.0 * 127825.0 / 1296.0 * eta * eta;
+        const double dp7 = PI * (378515.0 / 1512.0 - 2.0 * 74045.0 / 756.0 * eta);
+        const double dt12 = 6595.0 / 364.0 * (-2.0 / d) * dLT;
+        const double pre = 3.0 / 128.0 * ie;
+        // v dPsi/dv
+        const double V[11] = {-5.0, -3.0 * p2, -2.0 * p3, -p4, 3.0 * p5a, p6 + L6, 2.0 * p7,
+                              5.0 * t10, 7.0 * t12, 0.0, L6};
+        // dPsi/deta at fixed v (before the prefactor)
+        const double De[11] = {-ie, 55.0 / 9.0 - p2 * ie, 4.0 * dbeta - p3 * ie, dp4 - p4 * ie,
+                               dp5a * ln6h - p5c * ie, dp6 - p6 * ie, dp7 - p7 * ie, -t10 * ie,
+                               dt12 - t12 * ie, 3.0 * (dp5a - p5a * ie), -L6 * ie};
+        // Psi itself (strain output): v^-5 (1, p2 v^2, p3 v^3, p4 v^4) + p5a (1 - 3 ln v_lso
+        // + 3 ln v) + (p6 + L6 ln v) v + p7 v^2 + tidal v^5, v^7, all times 3/(128 eta)
+        const double Ps[11] = {1.0, p2, p3, p4, p5c, p6, p7, t10, t12, 3.0 * p5a, L6};
+        for (int k = 0; k < 11; k++) {
+            E[EV_PSI + k] = pre * Ps[k];
+            E[EV_PM + k] = pre * V[k] * i3Mc;
+            E[EV_PE + k] = pre * (De[k] - V[k] * i5eta);
         }
-    }
-
-    // ---- per-site JKS coefficients (pattern functions as functions of the
-    // hour-angle-like x = phi - lon - g) and Doppler factors.
-    double sth, cth;
-    sincos(th, &sth, &cth);
-    const double sd = cth, cd = sth;                  // delta = pi/2 - theta
-    const double s2d = 2.0 * sth * cth, c2d = sth * sth - cth * cth;
-    for (int s = 0; s < net.n_site; s++) {
-        double *S = sitec + (e * net.n_site + s) * (int64_t)SC_N;
-        const double sl = net.site_slat[s], cl = net.site_clat[s];
-        const double c2l = 1.0 - 2.0 * sl * sl, s2l = 2.0 * sl * cl;
-        double x0 = ph - net.site_lon[s] - OMEGA_E * tc;
-        // x0 - 2 pi round(x0 / 2 pi): the FMA forms n 2 pi exactly and the
-        // difference (at most ~pi in magnitude) is representable, so this is
-        // exactly remainder(x0, 2 pi) up to the choice at +-pi
-        x0 = fma(-rint(x0 * (1.0 / TWO_PI)), TWO_PI, x0);
-        S[SC_X0] = x0;
-        S[SC_A1] = (3.0 - c2l) * (3.0 - c2d) / 16.0;
-        S[SC_A2] = s2l * s2d / 4.0;
-        S[SC_A3] = 0.75 * cl * cl * cd * cd;
-        S[SC_A4] = -sl * (3.0 - c2d) / 4.0;
-        S[SC_A5] = -cl * s2d / 2.0;
-        S[SC_B1] = sl * sd;
-        S[SC_B2] = cl * cd;
-        S[SC_B3] = (3.0 - c2l) * sd / 4.0;
-        S[SC_B4] = s2l * cd / 2.0;
-        // d/dtheta = -d/ddelta
-        S[SC_A1T] = -(3.0 - c2l) * s2d / 8.0;
-        S[SC_A2T] = -s2l * c2d / 2.0;
-        S[SC_A3T] = 0.75 * cl * cl * s2d;
-        S[SC_A4T] = sl * s2d / 2.0;
-        S[SC_A5T] = cl * c2d;
-        S[SC_B1T] = -sl * cd;
-        S[SC_B2T] = cl * sd;
-        S[SC_B3T] = -(3.0 - c2l) * cd / 4.0;
-        S[SC_B4T] = s2l * sd / 2.0;
-        S[SC_D1] = R_EARTH_S * cl * sth;
-        S[SC_D2] = R_EARTH_S * sl * cth;
-        S[SC_D1T] = R_EARTH_S * cl * cth;
-        S[SC_D2T] = -R_EARTH_S * sl * sth;
-        // the (at most two) interferometer entries of this site in use: the
-        // point kernels run a fixed number of slots per site, whatever the mask
-        int slot[2] = {-1, -1}, nsl = 0;
-        for (int q = net.site_ifo0[s]; q < net.site_ifo1[s] && nsl < 2; q++)
-            if ((ifo_on >> q) & 1u) slot[nsl++] = q;
-        S[SC_SLOT0] = (double)slot[0];
-        S[SC_SLOT1] = (double)slot[1];
-        S[SC_X0LO] = 0.0;
-        if (sitec_f) {
-            float *Sf = sitec_f + (e * net.n_site + s) * (int64_t)SC_N;
-            // (float)S[q]: hi, or lo where the value is below FP32's normal range
-            for (int q = 0; q < SC_N; q++) {
-                const float2 v = split_f32(S[q]);
-                Sf[q] = v.x != 0.0f ? v.x : v.y;
+        double q9[4] = {0, 0, 0, 0}, q10[4] = {0, 0, 0, 0};
+        if (pset == 1) {
+            q9[0] = 4.0 * b1;
+            q9[1] = -10.0 * 79.0 / 8.0 * eta * c2;
+            q10[0] = 4.0 * b2;
+            q10[1] = -10.0 * 79.0 / 8.0 * eta * c1;
+        } else if (pset == 2) {
+            q9[2] = -39.0 / 2.0;
+            q9[3] = -3115.0 / 64.0;
+            q10[3] = 6595.0 / 364.0 * d;
+        }
+        for (int k = 0; k < 4; k++) {
+            E[EV_P9 + k] = pre * q9[k];
+            E[EV_P10 + k] = pre * q10[k];
+        }
+        // double-float (hi, lo) copy of the constants the mixed point loop reads
+        // (slots EV_WC0 .. EV_INVDL and the polynomial coefficients EV_PM ..)
+        if (Ef) {
+            for (int q = EV_WC0; q < EV_T0; q++) {
+                if (q > EV_INVDL && q < EV_PM) continue;
+                Ef[q] = split_f32(E[q]);
             }
-            const float2 xs = split_f32(x0);
-            Sf[SC_X0] = xs.x != 0.0f ? xs.x : xs.y;
-            Sf[SC_X0LO] = xs.x != 0.0f ? xs.y : 0.0f;
+        }
+    } else {
+        // ---- tau*(f), 3.5PN (Buonanno et al. 2009 Eq. 3.8b), basis B8 times v^-3
+        const double Kt = 5.0 * Ms / (256.0 * eta);
+        const double t2 = 743.0 / 252.0 + 11.0 / 3.0 * eta;
+        const double t3 = -32.0 / 5.0 * PI;
+        const double t4 = 3058673.0 / 508032.0 + 5429.0 / 504.0 * eta + 617.0 / 72.0 * eta * eta;
+        const double t5 = (-7729.0 / 252.0 + 13.0 / 3.0 * eta) * PI;
+        const double t6 = -10052469856691.0 / 23471078400.0 + 128.0 / 3.0 * pi2
+                          + 6848.0 / 105.0 * EULER_GAMMA
+                          + (3147553127.0 / 3048192.0 - 451.0 / 12.0 * pi2) * eta
+                          - 15211.0 / 1728.0 * eta * eta + 25565.0 / 1296.0 * eta * eta * eta
+                          + 3424.0 / 105.0 * (2.0 * LN4);
+        const double t6L = 6848.0 / 105.0;
+        const double t7 = (-15419335.0 / 127008.0 - 75703.0 / 756.0 * eta
+                           + 14809.0 / 378.0 * eta * eta) * PI;
+        const double dt4 = 5429.0 / 504.0 + 2.0 * 617.0 / 72.0 * eta;
+        const double dt5 = 13.0 / 3.0 * PI;
+        const double dt6 = 3147553127.0 / 3048192.0 - 451.0 / 12.0 * pi2
+                           - 2.0 * 15211.0 / 1728.0 * eta + 3.0 * 25565.0 / 1296.0 * eta * eta;
+        const double dt7 = PI * (-75703.0 / 756.0 + 2.0 * 14809.0 / 378.0 * eta);
+        const double T0[8] = {1.0, t2, t3, t4, t5, t6, t7, t6L};
+        const double Tv[8] = {-5.0, -3.0 * t2, -2.0 * t3, -t4, 0.0, t6 + t6L, 2.0 * t7, t6L};
+        const double Te[8] = {-ie, 11.0 / 3.0 - t2 * ie, -t3 * ie, dt4 - t4 * ie, dt5 - t5 * ie,
+                              dt6 - t6 * ie, dt7 - t7 * ie, -t6L * ie};
+        for (int k = 0; k < 8; k++) {
+            E[EV_T0 + k] = Kt * T0[k];
+            E[EV_TM + k] = Kt * Tv[k] * i3Mc;
+            E[EV_TE + k] = Kt * (Te[k] - Tv[k] * i5eta);
+        }
+
+        if (Ef)
+            for (int q = EV_T0; q < EVC; q++) Ef[q] = split_f32(E[q]);
+
+        // ---- per-site JKS coefficients (pattern functions as functions of the
+        // hour-angle-like x = phi - lon - g) and Doppler factors.
+        double sth, cth;
+        sincos(th, &sth, &cth);
+        const double sd = cth, cd = sth;                  // delta = pi/2 - theta
+        const double s2d = 2.0 * sth * cth, c2d = sth * sth - cth * cth;
+        for (int s = 0; s < net.n_site; s++) {
+            double *S = sitec + (e * net.n_site + s) * (int64_t)SC_N;
+            const double sl = net.site_slat[s], cl = net.site_clat[s];
+            const double c2l = 1.0 - 2.0 * sl * sl, s2l = 2.0 * sl * cl;
+            double x0 = ph - net.site_lon[s] - OMEGA_E * tc;
+            // x0 - 2 pi round(x0 / 2 pi): the FMA forms n 2 pi exactly and the
+            // difference (at most ~pi in magnitude) is representable, so this is
+            // exactly remainder(x0, 2 pi) up to the choice at +-pi
+            x0 = fma(-rint(x0 * (1.0 / TWO_PI)), TWO_PI, x0);
+            S[SC_X0] = x0;
+            S[SC_A1] = (3.0 - c2l) * (3.0 - c2d) / 16.0;
+            S[SC_A2] = s2l * s2d / 4.0;
+            S[SC_A3] = 0.75 * cl * cl * cd * cd;
+            S[SC_A4] = -sl * (3.0 - c2d) / 4.0;
+            S[SC_A5] = -cl * s2d / 2.0;
+            S[SC_B1] = sl * sd;
+            S[SC_B2] = cl * cd;
+            S[SC_B3] = (3.0 - c2l) * sd / 4.0;
+            S[SC_B4] = s2l * cd / 2.0;
+            // d/dtheta = -d/ddelta
+            S[SC_A1T] = -(3.0 - c2l) * s2d / 8.0;
+            S[SC_A2T] = -s2l * c2d / 2.0;
+            S[SC_A3T] = 0.75 * cl * cl * s2d;
+            S[SC_A4T] = sl * s2d / 2.0;
+            S[SC_A5T] = cl * c2d;
+            S[SC_B1T] = -sl * cd;
+            S[SC_B2T] = cl * sd;
+            S[SC_B3T] = -(3.0 - c2l) * cd / 4.0;
+            S[SC_B4T] = s2l * sd / 2.0;
+            S[SC_D1] = R_EARTH_S * cl * sth;
+            S[SC_D2] = R_EARTH_S * sl * cth;
+            S[SC_D1T] = R_EARTH_S * cl * cth;
+            S[SC_D2T] = -R_EARTH_S * sl * sth;
+            // the (at most two) interferometer entries of this site in use: the
+            // point kernels run a fixed number of slots per site, whatever the mask
+            int slot[2] = {-1, -1}, nsl = 0;
+            for (int q = net.site_ifo0[s]; q < net.site_ifo1[s] && nsl < 2; q++)
+                if ((ifo_on >> q) & 1u) slot[nsl++] = q;
+            S[SC_SLOT0] = (double)slot[0];
+            S[SC_SLOT1] = (double)slot[1];
+            S[SC_X0LO] = 0.0;
+            if (sitec_f) {
+                float *Sf = sitec_f + (e * net.n_site + s) * (int64_t)SC_N;
+                // (float)S[q]: hi, or lo where the value is below FP32's normal range
+                for (int q = 0; q < SC_N; q++) {
+                    const float2 v = split_f32(S[q]);
+                    Sf[q] = v.x != 0.0f ? v.x : v.y;
+                }
+                const float2 xs = split_f32(x0);
+                Sf[SC_X0] = xs.x != 0.0f ? xs.x : xs.y;
+                Sf[SC_X0LO] = xs.x != 0.0f ? xs.y : 0.0f;
+            }
         }
     }
 }
@@ -363,10 +379,10 @@ cudaError_t launch_event_setup(const DevCat &cat, const DevNet &net, int np, dou
                                int64_t *counts, cudaStream_t s)
 {
     if (cat.n <= 0) return cudaSuccess;
-    int bs = 128;
-    int64_t nb = (cat.n + bs - 1) / bs;
-    k_event_setup<<<(unsigned)nb, bs, 0, s>>>(cat, net, np, evc, sitec, sitec_f, evc_f, status,
-                                              counts);
+    const int64_t per_block = SETUP_BS / 2;       // events per block
+    const int64_t nb = (cat.n + per_block - 1) / per_block;
+    k_event_setup<<<(unsigned)nb, SETUP_BS, 0, s>>>(cat, net, np, evc, sitec, sitec_f, evc_f,
+                                                   status, counts);
     return cudaGetLastError();
 }
 
