@@ -65,8 +65,8 @@ def parse():
     ap.add_argument("--events", type=int, default=None)
     ap.add_argument("--workload", choices=["c3", "c4", "c3-gated"], default="c3",
                     help="c3: 1e5 events on the triangle (headline); c4: 1e6 events on five "
-                         "interferometers, the step adding the log-det VJP over the "
-                         "detector orientations; c3-gated: c3 with duty-factor arm masks, "
+                         "interferometers, the step adding the log-det VJP over the two "
+                         "L detectors' orientations; c3-gated: c3 with duty-factor arm masks, "
                          "an SNR pass and the SNR > 12 gate before the Fisher pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true",
@@ -294,6 +294,9 @@ def run_ours(a):
         return gw_prepare_dev(gw, d, rule, n)
 
     with_logdet = a.workload == "c4"
+    # the orientation gradient the c4 study asks for: the L-shaped detectors
+    # (network rows of shape 0); the triangle's entry is not formed
+    l_mask = sum(1 << k for k, r in enumerate(net.det_rows) if int(r[4]) == 0)
 
     def gate(d):
         """Prepared catalog of the step's Fisher pass: every event, or (gated
@@ -310,7 +313,7 @@ def run_ours(a):
         F, snr, st, g = gw.gw_fisher(cat, net, N_PAR, prec, grad_snr=grad_up[:cat.n])
         cov, cond, err, sti = gw.gw_fisher_inverse(F, N_PAR)
         if with_logdet:
-            gw.gw_logdet_vjp_detangles(cat, net, N_PAR, cov, gw.GW_FP64)
+            gw.gw_logdet_vjp_detangles(cat, net, N_PAR, cov, gw.GW_FP64, det_mask=l_mask)
         return cat, F, snr, cov, cond, g, st
 
     # prepare 1; Fisher 7 (event setup, scan 3, point loop, finish, SNR VJP);
@@ -496,7 +499,7 @@ def run_ours(a):
                        "precision": a.precision, "n_par": N_PAR,
                        "step": ("prepare + SNR pass + gate + " if gated else "prepare + ")
                                + "SNR/Fisher with fused SNR VJP + Cholesky inversion"
-                               + (" + log-det VJP (FP64) over detector orientations"
+                               + (" + log-det VJP (FP64) over the two L detectors' orientations"
                                   if with_logdet else ""),
                        **({"selected_events": n_sel, "fisher_points": n_points}
                           if gated else {}),

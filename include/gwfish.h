@@ -137,7 +137,7 @@ gw_status gw_create(gw_ctx **ctx, int device);
 gw_status gw_destroy(gw_ctx *ctx);
 /* Text of the last error on this context (static storage, never NULL). */
 const char *gw_last_error(const gw_ctx *ctx);
-/* ABI version of this header (incremented on any signature change): 3. */
+/* ABI version of this header (incremented on any signature change or addition): 4. */
 int gw_abi_version(void);
 
 /* Reserve workspace for up to max_events events on up to max_sites detector
@@ -240,6 +240,19 @@ gw_status gw_snr_vjp(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
 gw_status gw_logdet_vjp_detangles(gw_ctx *ctx, const gw_catalog *cat,
                                   const gw_network *net, gw_precision prec, int n_par,
                                   const double *cov, double *grad_gamma, void *stream);
+
+/* gw_logdet_vjp_detangles for the detectors of det_mask only (bit d: detector d
+ * of the network, d < n_det), e.g. the L-shaped detectors of a network whose
+ * orientations are being optimised.  A detector's gradient sums only its own
+ * interferometers, so the point loop skips the sites of the other detectors
+ * (the cost scales with the selected ones) and the selected entries equal
+ * those of gw_logdet_vjp_detangles bit for bit.  DEVICE out: grad_gamma [n_det]
+ * (overwritten; entries of detectors outside det_mask are NaN).  det_mask with
+ * no bit below n_det fails with GW_EINVAL.  No counterpart in the paper. */
+gw_status gw_logdet_vjp_detangles_masked(gw_ctx *ctx, const gw_catalog *cat,
+                                         const gw_network *net, gw_precision prec, int n_par,
+                                         const double *cov, uint32_t det_mask,
+                                         double *grad_gamma, void *stream);
 
 /* Detector strain h_a(f_k) = Q_a exp(i Phi_a) on every event's grid, for every
  * arm a of the network (the arm numbering of gw_catalog.arm_mask: a triangle

@@ -57,7 +57,7 @@ EXPORTS = ("gw_create", "gw_destroy", "gw_last_error", "gw_abi_version", "gw_pre
            "gw_snr", "gw_fisher", "gw_fisher_inverse", "gw_snr_vjp", "gw_logdet_vjp_detangles",
            "gw_set_profiling", "gw_point_kernel_ms", "gw_fisher_noalloc", "gw_reserve",
            "gw_select_snr", "gw_fisher_eig", "gw_covariance", "gw_packed_submatrix",
-           "gw_sky_area", "gw_strain", "gw_perturb_fisher")
+           "gw_sky_area", "gw_strain", "gw_perturb_fisher", "gw_logdet_vjp_detangles_masked")
 
 _lib = None
 
@@ -88,6 +88,8 @@ def load_library(path: str | None = None):
     lib.gw_fisher_inverse.argtypes = [_P, _P, i64, ctypes.c_int, d, _P, _P, _P, _P, _P]
     lib.gw_snr_vjp.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P]
     lib.gw_logdet_vjp_detangles.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+    lib.gw_logdet_vjp_detangles_masked.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P,
+                                                   ctypes.c_uint32, _P, _P]
     for name in EXPORTS:
         if name not in ("gw_last_error", "gw_abi_version", "gw_destroy", "gw_point_kernel_ms"):
             getattr(lib, name).restype = ctypes.c_int
@@ -410,14 +412,21 @@ def gw_snr_vjp(cat: Catalog, net: Network, n_par: int, grad_snr: torch.Tensor, p
 
 
 def gw_logdet_vjp_detangles(cat: Catalog, net: Network, n_par: int, cov: torch.Tensor,
-                            prec=GW_FP64, stream=None, out=None):
-    """d(sum_e log det Gamma_e)/d gamma_d for every detector d -> [n_det]."""
+                            prec=GW_FP64, stream=None, out=None, det_mask=None):
+    """d(sum_e log det Gamma_e)/d gamma_d for every detector d -> [n_det];
+    with ``det_mask`` (bit d: detector d) only for those detectors, the others
+    NaN (``gw_logdet_vjp_detangles_masked``)."""
     ctx = context()
     g = out if out is not None else torch.empty(net.n_det, dtype=torch.float64, device=cov.device)
     c = cat.struct()
-    st = load_library().gw_logdet_vjp_detangles(ctx, ctypes.byref(c), ctypes.byref(net.net),
-                                                int(prec), n_par, _ptr(cov), _ptr(g),
-                                                _stream(stream))
+    lib = load_library()
+    if det_mask is None:
+        st = lib.gw_logdet_vjp_detangles(ctx, ctypes.byref(c), ctypes.byref(net.net), int(prec),
+                                         n_par, _ptr(cov), _ptr(g), _stream(stream))
+    else:
+        st = lib.gw_logdet_vjp_detangles_masked(ctx, ctypes.byref(c), ctypes.byref(net.net),
+                                                int(prec), n_par, _ptr(cov), int(det_mask),
+                                                _ptr(g), _stream(stream))
     _check(st, ctx)
     return g
 

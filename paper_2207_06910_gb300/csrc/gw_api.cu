@@ -190,11 +190,22 @@ DevCat gwi_dev_cat(const gw_catalog *c)
 
 namespace {
 
+// log-det gradient of an empty catalog: 0 for the selected detectors, NaN
+// (all bits set) for the others
+gw_status logdet_zero(gw_ctx *ctx, int n_det, uint32_t det_mask, double *grad_gamma,
+                      cudaStream_t s)
+{
+    for (int d = 0; d < n_det; d++)
+        CK(cudaMemsetAsync(grad_gamma + d, (det_mask >> d) & 1u ? 0 : 0xff, sizeof(double), s));
+    return GW_OK;
+}
+
 // event setup -> scan -> point loop -> reduction
 gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_precision prec,
                      int mode, int np, int32_t *status_out, double *snr, double *snr_det,
                      double *fisher, const double *grad_snr, double *grad_params,
-                     const double *cov, double *grad_gamma, void *stream)
+                     const double *cov, double *grad_gamma, void *stream,
+                     uint32_t det_mask = 0xffffffffu)
 {
     cudaStream_t s = (cudaStream_t)stream;
     gw_status st = gwi_check_cat(ctx, cat, np);
@@ -210,8 +221,10 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     const int nacc = n_acc(mode, np, dn.n_det, mixed);
     // fused SNR vector-Jacobian product of a Fisher pass
     const bool fused_grad = mode == MODE_FISHER && grad_params != nullptr;
+    if (mode == MODE_LOGDET && !(det_mask & ((dn.n_det < 32 ? 1u << dn.n_det : 0u) - 1u)))
+        return fail(ctx, GW_EINVAL, "logdet_vjp: det_mask selects no detector of the network");
     if (n == 0) {
-        if (mode == MODE_LOGDET) CK(cudaMemsetAsync(grad_gamma, 0, sizeof(double) * dn.n_det, s));
+        if (mode == MODE_LOGDET) return logdet_zero(ctx, dn.n_det, det_mask, grad_gamma, s);
         return GW_OK;
     }
     CK(cudaSetDevice(ctx->device));
@@ -269,6 +282,7 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     pa.partial = ctx->partial;
     pa.nacc = nacc;
     pa.cov = cov;
+    pa.det_mask = det_mask;
     if (ctx->profiling) CK(cudaEventRecord(ctx->ev0, s));
     if (mixed) CK(launch_points_mixed(mode, np, dn.rotation, pa, s));
     else CK(launch_points_fp64(mode, np, dn.rotation, pa, s));
@@ -276,10 +290,8 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
         CK(cudaEventRecord(ctx->ev1, s));
         ctx->ev_recorded = true;
     }
-    if (mode == MODE_LOGDET && n_items == 0) {
-        CK(cudaMemsetAsync(grad_gamma, 0, sizeof(double) * dn.n_det, s));
-        return GW_OK;
-    }
+    if (mode == MODE_LOGDET && n_items == 0)
+        return logdet_zero(ctx, dn.n_det, det_mask, grad_gamma, s);
     CK(launch_finish(mode, np, dn.n_det, pa, status, snr, snr_det, fisher, grad_snr, grad_params,
                      grad_gamma, xs, s));
     if (fused_grad)
@@ -292,7 +304,7 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
 
 extern "C" {
 
-int gw_abi_version(void) { return 3; }
+int gw_abi_version(void) { return 4; }
 
 gw_status gw_create(gw_ctx **out, int device)
 {
@@ -644,6 +656,18 @@ gw_status gw_logdet_vjp_detangles(gw_ctx *ctx, const gw_catalog *cat, const gw_n
     if (!grad_gamma || (!cov && cat->n > 0)) return fail(ctx, GW_EINVAL, "logdet_vjp: null array");
     return run_points(ctx, cat, net, prec, MODE_LOGDET, n_par, nullptr, nullptr, nullptr,
                       nullptr, nullptr, nullptr, cov, grad_gamma, stream);
+}
+
+gw_status gw_logdet_vjp_detangles_masked(gw_ctx *ctx, const gw_catalog *cat,
+                                         const gw_network *net, gw_precision prec, int n_par,
+                                         const double *cov, uint32_t det_mask,
+                                         double *grad_gamma, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (!cat) return fail(ctx, GW_EINVAL, "catalog: null");
+    if (!grad_gamma || (!cov && cat->n > 0)) return fail(ctx, GW_EINVAL, "logdet_vjp: null array");
+    return run_points(ctx, cat, net, prec, MODE_LOGDET, n_par, nullptr, nullptr, nullptr,
+                      nullptr, nullptr, nullptr, cov, grad_gamma, stream, det_mask);
 }
 
 }  // extern "C"

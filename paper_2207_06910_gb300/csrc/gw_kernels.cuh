@@ -31,6 +31,8 @@ struct PointArgs {
     double *partial;          // [n_items][nacc]
     int nacc;
     const double *cov;        // logdet mode: covariance, packed, event-minor
+    uint32_t det_mask = 0xffffffffu;   // logdet mode: detectors whose orientation
+                                       // gradient is formed (bit d); other sites skipped
 };
 
 // extra accumulators of the mixed Fisher kernel: phase-free SNR-gradient sums

@@ -287,6 +287,8 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
                 // ---- sites
 #pragma unroll 1
                 for (int s = 0; s < net.n_site; s++) {
+                    // (site s is detector s) log-det gradient: only the requested detectors
+                    if (MODE == MODE_LOGDET && !((A.det_mask >> s) & 1u)) continue;
                     const double *S = A.sitec + (e * net.n_site + s) * (int64_t)SC_N;
                     if (net.masked && S[SC_SLOT0] < 0.0) continue;   // every arm of the site off
                     const double x = ROT ? fma(OMEGA_E, tau, S[SC_X0]) : S[SC_X0];

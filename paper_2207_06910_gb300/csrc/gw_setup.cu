@@ -559,7 +559,7 @@ cudaError_t launch_select(const double *snr, int64_t n, double th, int64_t *flag
 
 // logdet mode: total over all items of each detector accumulator, fixed order
 __global__ void k_finish_total(int64_t cap, const int64_t *total, int nacc, const double *partial,
-                               double *out)
+                               uint32_t det_mask, double *out)
 {
     __shared__ double sh[256];
     const int64_t n_items = *total < cap ? *total : cap;
@@ -572,7 +572,7 @@ __global__ void k_finish_total(int64_t cap, const int64_t *total, int nacc, cons
         if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[a] = sh[0];
+    if (threadIdx.x == 0) out[a] = (det_mask >> a) & 1u ? sh[0] : NAN;   // NaN: not requested
 }
 
 // SNR vector-Jacobian product after a Fisher pass, one thread per event.
@@ -636,7 +636,7 @@ cudaError_t launch_finish(int mode, int np, int n_det, const PointArgs &a, const
 {
     if (mode == MODE_LOGDET) {
         k_finish_total<<<a.nacc, 256, 0, s>>>(a.n_items, a.item_off + a.n_ev, a.nacc, a.partial,
-                                              grad_gamma);
+                                              a.det_mask, grad_gamma);
         return cudaGetLastError();
     }
     if (a.n_ev <= 0 || a.nacc <= 0) return cudaSuccess;
