@@ -249,6 +249,15 @@ def aggregate(times_ms, n_events: int, steps: int, world: int, dist=None, device
     return t, rates
 
 
+def sum_over_ranks(t, world: int, dist=None):
+    """Whole-job value of a per-shard partial sum, in place: the log-det
+    gradient is a sum over events, so the ranks' gradients over their shards
+    add up (all-reduce SUM, 8 bytes per detector).  A no-op on one rank."""
+    if world > 1 and dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -312,9 +321,10 @@ def run_ours(a):
         cat = gate(d)
         F, snr, st, g = gw.gw_fisher(cat, net, N_PAR, prec, grad_snr=grad_up[:cat.n])
         cov, cond, err, sti = gw.gw_fisher_inverse(F, N_PAR)
+        gg = None
         if with_logdet:
-            gw.gw_logdet_vjp_detangles(cat, net, N_PAR, cov, gw.GW_FP64, det_mask=l_mask)
-        return cat, F, snr, cov, cond, g, st
+            gg = gw.gw_logdet_vjp_detangles(cat, net, N_PAR, cov, gw.GW_FP64, det_mask=l_mask)
+        return cat, F, snr, cov, cond, g, st, gg
 
     # prepare 1; Fisher 7 (event setup, scan 3, point loop, finish, SNR VJP);
     # inversion 1; log-det VJP 6; gated: SNR pass 6 and gate 5
@@ -323,7 +333,7 @@ def run_ours(a):
         step(dev)
     torch.cuda.synchronize()
     # sanity of the timed configuration: no event flagged by the point loop
-    cat, F, snr, cov, cond, g, st = step(dev)
+    cat, F, snr, cov, cond, g, st, gg = step(dev)
     torch.cuda.synchronize()
     assert int((st != 0).sum()) == 0, "events flagged in the benchmark catalog"
     n_sel = cat.n
@@ -349,10 +359,14 @@ def run_ours(a):
         assert int((gout[6] != 0).sum()) == 0 and torch.allclose(gout[2], snr, rtol=1e-12)
 
     def run_step():
+        out = gout
         if graph is not None:
             graph.replay()
-            return gout
-        return step(dev)
+        else:
+            out = step(dev)
+        if with_logdet:   # the job's gradient: sum of the ranks' shard gradients
+            sum_over_ranks(out[7], world, dist if world > 1 else None)
+        return out
 
     # Fisher point-kernel duration: a few eager Fisher calls with the library's
     # event hooks (read before any later point kernel of the step)
@@ -403,15 +417,21 @@ def run_ours(a):
         graphs[1] = graph2
 
     def run_on(b):
+        out = gouts[b]
         if graphs[b] is not None:
             graphs[b].replay()
-            return gouts[b]
-        return step(bufs[b])
+        else:
+            out = step(bufs[b])
+        if with_logdet:
+            sum_over_ranks(out[7], world, dist if world > 1 else None)
+        return out
 
     outs_host = {"snr": torch.empty(n_sel, dtype=torch.float64).pin_memory(),
                  "F": torch.empty((N_PAR * (N_PAR + 1) // 2, n_sel), dtype=torch.float64).pin_memory(),
                  "cov": torch.empty((N_PAR * (N_PAR + 1) // 2, n_sel), dtype=torch.float64).pin_memory(),
                  "g": torch.empty((N_PAR, n_sel), dtype=torch.float64).pin_memory()}
+    if with_logdet:
+        outs_host["gg"] = torch.empty(net.n_det, dtype=torch.float64).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = sum(v.numel() * v.element_size() for v in outs_host.values())
     copy = torch.cuda.Stream()
@@ -443,8 +463,9 @@ def run_ours(a):
                     bufs[1 - b][k].copy_(v, non_blocking=True)
                 h2d_ev[1 - b].record(copy)
             copy.wait_event(step_ev[b])
-            cat, F, snr, cov, cond, g, st = out
-            for t, name in ((snr, "snr"), (F, "F"), (cov, "cov"), (g, "g")):
+            cat, F, snr, cov, cond, g, st, gg = out
+            res = ((snr, "snr"), (F, "F"), (cov, "cov"), (g, "g"))
+            for t, name in res + (((gg, "gg"),) if with_logdet else ()):
                 if graphs[b] is None:
                     t.record_stream(copy)
                 outs_host[name].copy_(t, non_blocking=True)
