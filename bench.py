@@ -526,7 +526,9 @@ def run_ours(a):
                           if gated else {}),
                        "l2": "flushed before every timed step (256 MiB write)",
                        "launch": "eager calls" if a.eager else "one CUDA graph replay per step",
-                       "parallelism": f"event shards, {world} GPU(s), no collective"},
+                       "parallelism": f"event shards, {world} GPU(s), " + (
+                           "log-det gradient all-reduced (SUM) per step" if with_logdet
+                           and world > 1 else "no collective")},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
