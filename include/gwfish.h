@@ -342,26 +342,29 @@ gw_status gw_sky_area(gw_ctx *ctx, const double *cov, int64_t n, int n_par, int 
 /* Allocation-free Fisher pass (no counterpart in the paper).
  *
  * The same computation as gw_fisher (SNR and packed Fisher matrix, same
- * kernels, same results) for callers that cannot allocate device memory while
- * they run: code inside a stream capture that forbids cudaMalloc, applications
- * whose device memory is reserved up front by their own fixed-size pool, or
- * real-time loops that cannot afford an allocation's latency or failure.  It
- * takes no gw_ctx (a context allocates its workspace lazily) and calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * kernels, same results) for callers that must not allocate device memory
+ * while they run: applications that hand all device memory to their own
+ * fixed-size pool at start-up (a cudaMalloc would fail or steal from the
+ * pool), and long-running or latency-bound loops that cannot afford an
+ * allocation's latency, its implicit synchronisation or its possible failure
+ * in the middle of a job.  It takes no gw_ctx (a context allocates its
+ * workspace lazily) and calls no cudaMalloc, cudaFree or other allocating
+ * routine.
  *
  * Workspace: one static device array of GW_NOALLOC_SCRATCH_MIB MiB, held by
  * every GPU that loads the library until the process exits.  It fits about
  * n * (1.6 kB + 0.3 kB per detector) of event constants plus one partial-sum
  * row (~0.6 kB) per work item of at most 256 grid points; a request that does
- * not fit returns GW_ETOOLARGE without computing fisher or snr (status may
+ * not fit returns GW_ETOOLARGE without writing fisher or snr (status may
  * already hold the per-event checks).  For example, 1e4 events of up to 512
- * points each on one triangle fit.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress,
- * with that device current): make that first call before any stream capture.
- * All calls share the array, so calls that overlap on the GPU (several streams
- * or host threads at once) race and must be serialised by the caller; nothing
- * from an earlier call is read.  Like gw_fisher, it reads back one 8-byte work
- * count (a synchronisation of `stream`).
+ * points each on one triangle fit.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress, with that device current):
+ * make that first call before any stream capture on the device.  All calls
+ * share the array and each call overwrites what it uses, so calls that overlap
+ * on the GPU (several streams or host threads at once) race and must be
+ * serialised by the caller; nothing from an earlier call is read.  Like
+ * gw_fisher, it reads back one 8-byte work count (a synchronisation of
+ * `stream`).
  * Arguments as gw_fisher; DEVICE outputs fisher [n_par(n_par+1)/2][n] and
  * status [n] are required, snr [n] may be NULL. */
 #define GW_NOALLOC_SCRATCH_MIB 32

@@ -1149,10 +1149,10 @@ int or_abi_version(void) { return 3; }
 int or_grid_npts(int64_t n, const double *fmin, const double *fmax, double per_efold,
                  int lo, int hi, int32_t *npts)
 {
-    /* an integer decided by floating point: taken in double precision, the
-     * precision in which the library takes it */
+    /* N = ceil(per_efold ln(fmax / fmin)), clamped to [lo, hi]: the definition,
+     * in long double */
     for (int64_t e = 0; e < n; e++) {
-        double x = ceil(per_efold * log(fmax[e] / fmin[e]));
+        ld x = ceill((ld)per_efold * logl((ld)fmax[e] / (ld)fmin[e]));
         if (!(x == x) || x < lo) x = lo;
         if (x > hi) x = hi;
         npts[e] = (int32_t)x;

@@ -2,9 +2,40 @@
 // kernels (gw_setup.cu, gw_points_fp64.cu, gw_points_mixed.cu).
 #pragma once
 
+#include <atomic>
+
 #include "gw_internal.cuh"
 
 namespace gw {
+
+// ---- per-device launch facts.  cudaFuncSetAttribute acts on the current
+// device only, and the SM count sizes the persistent grids, so both are kept
+// per device (devices 0..63; beyond that they are taken on every launch).
+constexpr int MAX_CACHED_DEV = 64;
+
+inline int current_device()
+{
+    int dev = 0;
+    return cudaGetDevice(&dev) == cudaSuccess ? dev : 0;
+}
+
+// one bit per device: the kernel's attribute has been set there
+struct PerDeviceOnce {
+    std::atomic<unsigned long long> bits{0};
+};
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per device and kernel
+template <typename K>
+cudaError_t set_smem_once(PerDeviceOnce &once, K kernel, size_t smem)
+{
+    const int dev = current_device();
+    const unsigned long long bit = dev < MAX_CACHED_DEV ? 1ull << dev : 0ull;
+    if (bit && (once.bits.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && bit) once.bits.fetch_or(bit, std::memory_order_release);
+    return e;
+}
 
 // catalog in device memory (pointers may be null where the ABI allows)
 struct DevCat {
@@ -124,6 +155,7 @@ cudaError_t launch_snr_grad_from_fisher(int64_t n, int np, bool mixed, int rot,
 cudaError_t launch_invert(const double *fisher, int64_t n, int np, double cond_max, double *cov,
                           double *cond, double *inv_err, int32_t *status, cudaStream_t s);
 
+int device_sm_count();                      // SM count of the current device (cached per device)
 int points_grid_size(int blocks_per_sm);   // persistent grid (blocks) for the point kernels
 
 }  // namespace gw

@@ -2,23 +2,24 @@
 // allocation.
 //
 // Who needs it: callers that must not allocate device memory while they run,
-// for example code running inside a CUDA stream capture that forbids
-// cudaMalloc, a host application whose memory is reserved up front by a
-// fixed-size pool it manages itself, or a real-time loop that cannot afford an
-// allocation's latency or its possible failure.  gw_fisher allocates its
-// workspace lazily inside a gw_ctx, so those callers cannot use it.
+// for example an application that gives all device memory to its own
+// fixed-size pool at start-up (a cudaMalloc would then fail, or take memory
+// the pool counts on), or a long-running or latency-bound loop that cannot
+// afford an allocation's latency, its implicit synchronisation or its
+// possible failure halfway through a job.  gw_fisher allocates its workspace
+// lazily inside a gw_ctx, so those callers cannot use it.
 //
 // How: the workspace (per-event constants, work-item offsets, per-item partial
 // sums) is carved out of one file-scope __device__ array of GW_NOALLOC_SCRATCH
 // bytes that every GPU loading the library holds until the process exits.
 // Host code cannot use the array's symbol as an address; its device address
 // is obtained once per device with cudaGetSymbolAddress (on the first call on
-// that device, with that device current) and passed to the kernels.  The
-// kernels are the ones gw_fisher runs; every scratch word they read in a call
-// is written earlier in the same call, so the previous call's contents never
-// matter.  All calls share the array: calls whose work overlaps on the GPU
-// (concurrent streams, or several host threads) race on it and must be
-// serialised by the caller.
+// that device, with that device current, so that first call belongs before
+// any stream capture) and passed to the kernels.  The kernels are the ones
+// gw_fisher runs; every scratch word they read in a call is written earlier in
+// the same call, so the previous call's contents never matter.  All calls
+// share the array: calls whose work overlaps on the GPU (concurrent streams,
+// or several host threads) race on it and must be serialised by the caller.
 #include <cstdio>
 #include <mutex>
 

@@ -434,14 +434,9 @@ cudaError_t launch_one(const PointArgs &a, cudaStream_t s)
     constexpr int NACC = NAccOf<MODE, NP>::value;
     const size_t smem = ((size_t)4 * GROUPS_PER_WARP * NACC * (GROUP + 1) +
                          (size_t)4 * GROUPS_PER_WARP * EVC) * sizeof(double);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t err = cudaFuncSetAttribute(k_points_fp64<MODE, NP, ROT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
-        if (err != cudaSuccess) return err;
-        attr_set = true;
-    }
+    static PerDeviceOnce attr;
+    cudaError_t err = set_smem_once(attr, k_points_fp64<MODE, NP, ROT>, smem);
+    if (err != cudaSuccess) return err;
     if (a.n_items <= 0) return cudaSuccess;
     k_points_fp64<MODE, NP, ROT><<<points_grid_size(2), 128, smem, s>>>(a);
     return cudaGetLastError();
@@ -456,17 +451,22 @@ cudaError_t launch_mode(int np, int rot, const PointArgs &a, cudaStream_t s)
 
 }  // namespace
 
-int points_grid_size(int blocks_per_sm)
+int device_sm_count()
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
+    static std::atomic<int> cache[MAX_CACHED_DEV];   // 0 = not looked up yet
+    const int dev = current_device();
+    int sms = dev < MAX_CACHED_DEV ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (sms > 0) return sms;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0) {
+        cudaGetLastError();
+        sms = 1;
     }
-    return blocks_per_sm * sms;
+    if (dev < MAX_CACHED_DEV) cache[dev].store(sms, std::memory_order_relaxed);
+    return sms;
 }
+
+int points_grid_size(int blocks_per_sm) { return blocks_per_sm * device_sm_count(); }
 
 cudaError_t launch_points_fp64(int mode, int np, int rot, const PointArgs &a, cudaStream_t s)
 {

@@ -622,14 +622,9 @@ cudaError_t launch_one_m(const PointArgs &a, cudaStream_t s)
 {
     constexpr int NACC = NAccM<MODE, NP>::value;
     const size_t smem = ((size_t)((NACC * 129 + 1) & ~1) + (size_t)4 * GROUPS_PER_WARP * (NCOEF + NSCAL)) * sizeof(float2);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t err = cudaFuncSetAttribute(k_points_mixed<MODE, NP, ROT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
-        if (err != cudaSuccess) return err;
-        attr_set = true;
-    }
+    static PerDeviceOnce attr;
+    cudaError_t err = set_smem_once(attr, k_points_mixed<MODE, NP, ROT>, smem);
+    if (err != cudaSuccess) return err;
     if (a.n_items <= 0) return cudaSuccess;
     k_points_mixed<MODE, NP, ROT><<<points_grid_size(2), 128, smem, s>>>(a);
     return cudaGetLastError();

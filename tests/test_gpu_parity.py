@@ -323,8 +323,19 @@ def test_prepare_matches_oracle_full_c3():
         # FP64 against long double over a few operations: a few ulp
         assert np.allclose(got, p[k], rtol=4e-15, atol=4e-15 * np.max(np.abs(p[k]))), k
     assert np.allclose(cat.fmax.cpu().numpy(), p["fisco"], rtol=1e-13, atol=0)
-    npts_or = oracle.grid_npts(d["fmin"], cat.fmax.cpu().numpy(), *d["npts_rule"][1:])
-    assert np.array_equal(cat.npts.cpu().numpy(), npts_or)
+    # grid length: ceil(40 ln(f_ISCO / f_min)) from the oracle's own f_ISCO.  An
+    # argument within a few ulp of an integer may round to either side in the
+    # GPU's double precision; those events are excused and counted.
+    per, lo, hi = d["npts_rule"][1:]
+    npts_or = oracle.grid_npts(d["fmin"], p["fisco"], per, lo, hi)
+    x = per * np.log(p["fisco"] / d["fmin"])
+    near = np.abs(x - np.rint(x)) <= 16 * np.finfo(float).eps * np.abs(x)
+    near &= (np.rint(x) >= lo) & (np.rint(x) <= hi + 1)
+    got = cat.npts.cpu().numpy()
+    bad = (got != npts_or) & ~near
+    print(f"grid lengths: {near.sum()} of {len(x)} arguments within 16 ulp of an integer")
+    assert not bad.any(), np.nonzero(bad)[0][:10]
+    assert np.all(np.abs(got - npts_or)[near] <= 1)
 
 
 @pytest.mark.parametrize("grid", ["literal", "stress"])

@@ -147,6 +147,24 @@ def test_grid_rule():
     assert list(n) == [200, math.ceil(40 * math.log(1e4)), 200]
 
 
+def test_grid_rule_at_integer_boundary():
+    """ceil(40 ln(fmax/fmin)) for the doubles fmax next to 2 e^(369/40), where
+    the argument is within 5e-14 of the integer 369: the oracle must follow the
+    definition (a 200-bit evaluation decides), which double precision misses
+    for arguments a few 1e-15 above the integer."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 200
+    f0 = float(2 * mpmath.exp(mpmath.mpf(369) / 40))
+    fmax = [f0]
+    for _ in range(6):
+        fmax.insert(0, float(np.nextafter(fmax[0], -np.inf)))
+        fmax.append(float(np.nextafter(fmax[-1], np.inf)))
+    fmax = np.array(fmax)
+    want = [int(mpmath.ceil(40 * mpmath.log(mpmath.mpf(f) / 2))) for f in fmax]
+    got = oracle.grid_npts(np.full(len(fmax), 2.0), fmax, 40.0, 200, 20000)
+    assert list(got) == want and 369 in want and 370 in want
+
+
 # ---------------------------------------------------------------- antenna patterns
 def test_antenna_tensor_equals_jks():
     """Pattern functions by tensor contraction equal the JKS closed form."""
