@@ -69,7 +69,10 @@ def _load():
         lib.or_fisher_eig.argtypes = [i64, i32, P, i32, P, P]
         lib.or_covariance.argtypes = [i64, i32, P, ctypes.c_uint32, P, i32, d, d, P, P, P, P]
         lib.or_sky_area.argtypes = [i64, i32, P, i32, i32, P, d, i32, P]
-        if lib.or_abi_version() != 3:
+        lib.or_set_psd_tables.argtypes = [i32, P, P, P, P]
+        lib.or_psd_eval.argtypes = [P, i32, d]
+        lib.or_psd_eval.restype = d
+        if lib.or_abi_version() != 4:
             raise RuntimeError("stale oracle build: rebuild with oracle.build(force=True)")
         _lib = lib
     return _lib
@@ -99,6 +102,30 @@ def prepare(m1, m2, chi1, chi2, lam1, lam2, dL_Mpc, zflag, tcoal):
     lib.or_prepare(n, *[_p(a) for a in ins], *[_p(a) for a in outs])
     keys = ("Mc", "eta", "dL", "chi1z", "chi2z", "LamT", "dLamT", "tc", "fisco")
     return dict(zip(keys, outs))
+
+
+def set_psd_tables(tables) -> None:
+    """Tabulated noise curves (Sec. 3.1, the psd_path / is_ASD options):
+    ``tables`` is a list of (f, values, is_asd); a PSD row ``table_row(k, scale)``
+    then reads table k with log-log linear interpolation, zero weight outside
+    the tabulated range."""
+    n = np.array([len(t[0]) for t in tables], dtype=np.int64)
+    f = _f64(np.concatenate([t[0] for t in tables])) if tables else np.zeros(1)
+    v = _f64(np.concatenate([t[1] for t in tables])) if tables else np.zeros(1)
+    asd = np.array([1 if t[2] else 0 for t in tables], dtype=np.int32)
+    if _load().or_set_psd_tables(len(tables), _p(n), _p(f), _p(v), _p(asd)) != 0:
+        raise ValueError("tables need >= 2 points, f > 0 strictly increasing, values > 0")
+
+
+def psd_eval(psd, idx: int, f: float) -> float:
+    """S_n(f) of row ``idx`` of a PSD table (rows as in ``snr``)."""
+    psd = _f64(psd).reshape(-1, 11)
+    return _load().or_psd_eval(_p(psd), int(idx), float(f))
+
+
+def table_row(k: int, scale: float = 1.0):
+    """PSD row reading table k (see set_psd_tables), times ``scale``."""
+    return [1.0, float(scale), -(k + 1), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0]
 
 
 def set_fd_target(target: float = 0.1) -> None:

@@ -26,6 +26,8 @@
  *                        (Sec. 3.1, with Earth rotation along t(f)).
  *   or_strain .......... detector strain with Earth-rotation Doppler phase
  *                        (Sec. 3.1 footnote on Earth motion).
+ *   or_set_psd_tables .. tabulated noise curves (Sec. 3.1, psd_path / is_ASD),
+ *                        log-log linear interpolation.
  *   or_snr ............. SNR_i^2 = 4 int |h|^2/S_n df; network sum in quadrature
  *                        (Sec. 3.2, Eqs. (3.1)-(3.2)); trapezoid on the log grid.
  *                        SNR, Fisher and the two VJP references take optional
@@ -131,14 +133,77 @@ static int select_arms(const arm_t *all, int na, const uint32_t *arm_mask, int64
     return m;
 }
 
+/* Tabulated noise curves (the psd_path / is_ASD detector options of Sec. 3.1):
+ * a PSD row whose term count is -(k+1) reads table k, given as frequencies f_j
+ * (strictly increasing, > 0) and values S_j (> 0; amplitude spectral density
+ * when is_asd, squared here).  S_n(f) is the straight line through
+ * (ln f_j, ln S_j) and (ln f_{j+1}, ln S_{j+1}) for f_j <= f <= f_{j+1}, times
+ * the row's scale; outside [f_0, f_last] the detector is blind (S_n infinite,
+ * zero weight). */
+#define OR_MAX_TAB 8
+static int g_ntab = 0;
+static int64_t g_tab_n[OR_MAX_TAB];
+static ld *g_tab_lnf[OR_MAX_TAB], *g_tab_lns[OR_MAX_TAB];
+
+int or_set_psd_tables(int ntab, const int64_t *n, const double *f, const double *s,
+                      const int32_t *is_asd)
+{
+    for (int k = 0; k < g_ntab; k++) { free(g_tab_lnf[k]); free(g_tab_lns[k]); }
+    g_ntab = 0;
+    if (ntab < 0 || ntab > OR_MAX_TAB) return 1;
+    int64_t o = 0;
+    for (int k = 0; k < ntab; k++) {          /* check every table first */
+        if (n[k] < 2) return 1;
+        for (int64_t j = 0; j < n[k]; j++)
+            if (!(f[o + j] > 0) || !(s[o + j] > 0) || (j > 0 && !(f[o + j] > f[o + j - 1])))
+                return 1;
+        o += n[k];
+    }
+    o = 0;
+    for (int k = 0; k < ntab; k++) {
+        g_tab_lnf[k] = malloc(sizeof(ld) * n[k]);
+        g_tab_lns[k] = malloc(sizeof(ld) * n[k]);
+        g_tab_n[k] = n[k];
+        for (int64_t j = 0; j < n[k]; j++) {
+            g_tab_lnf[k][j] = logl((ld)f[o + j]);
+            g_tab_lns[k][j] = (is_asd && is_asd[k] ? 2.0L : 1.0L) * logl((ld)s[o + j]);
+        }
+        o += n[k];
+    }
+    g_ntab = ntab;
+    return 0;
+}
+
+static ld psd_table(int k, ld f)
+{
+    const ld x = logl(f);
+    const ld *lf = g_tab_lnf[k], *ls = g_tab_lns[k];
+    const int64_t n = g_tab_n[k];
+    if (x < lf[0] || x > lf[n - 1]) return INFINITY;
+    int64_t lo = 0, hi = n - 1;            /* lf[lo] <= x <= lf[hi] */
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) / 2;
+        if (lf[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    return expl(ls[lo] + (ls[hi] - ls[lo]) * (x - lf[lo]) / (lf[hi] - lf[lo]));
+}
+
 static ld psd_eval(const double *psd, int idx, ld f)
 {
     const double *q = psd + 11 * idx;
     ld s = 0;
     int nt = (int)q[2];
+    if (nt < 0) {
+        int k = -nt - 1;
+        return k < g_ntab ? (ld)q[1] * psd_table(k, f) : NAN;
+    }
     for (int j = 0; j < nt; j++) s += (ld)q[3 + j] * powl(f / (ld)q[0], (ld)q[7 + j]);
     return (ld)q[1] * s;
 }
+
+/* S_n(f) of PSD row idx (exported for the pins) */
+double or_psd_eval(const double *psd, int idx, double f) { return (double)psd_eval(psd, idx, f); }
 
 /* ------------------------------------------------------------------ */
 /* TaylorF2 phase (restricted PN), all masses in seconds                */
@@ -1143,7 +1208,7 @@ int or_logdet_grad_gamma(int64_t n, const double *ev, const int8_t *pset, const 
 }
 
 /* version tag so the Python side can check the build matches */
-int or_abi_version(void) { return 3; }
+int or_abi_version(void) { return 4; }
 
 /* grid length by the points-per-e-fold rule, clamped: N = clamp(ceil(k ln(fmax/fmin)), lo, hi) */
 int or_grid_npts(int64_t n, const double *fmin, const double *fmax, double per_efold,

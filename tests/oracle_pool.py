@@ -12,7 +12,9 @@ _POOL = None
 
 def _worker_fisher(args):
     import oracle
-    ev, pset, fmin, fmax, npts, mask, det, psd, rot, n_par = args
+    ev, pset, fmin, fmax, npts, mask, det, psd, rot, n_par = args[:10]
+    if len(args) > 10:            # tabulated PSDs of this network
+        oracle.set_psd_tables(args[10])
     cat = oracle.Catalog(ev, pset, fmin, fmax, npts, mask)
     F, s, err, st = oracle.fisher(cat, det, psd, rot, n_par)
     return F[0], s[0], err[0], st[0]
@@ -20,7 +22,9 @@ def _worker_fisher(args):
 
 def _worker_snr(args):
     import oracle
-    ev, pset, fmin, fmax, npts, mask, det, psd, rot = args
+    ev, pset, fmin, fmax, npts, mask, det, psd, rot = args[:9]
+    if len(args) > 9:
+        oracle.set_psd_tables(args[9])
     cat = oracle.Catalog(ev, pset, fmin, fmax, npts, mask)
     s, arm, st = oracle.snr(cat, det, psd, rot, per_arm=True)
     return s[0], arm[0], st[0]
@@ -56,14 +60,16 @@ def _tasks(cat, extra):
             for e in range(len(cat))]
 
 
-def fisher(cat, det, psd, rot, n_par):
-    out = pool().map(_worker_fisher, _tasks(cat, (det, psd, rot, n_par)))
+def fisher(cat, det, psd, rot, n_par, tables=None):
+    extra = (det, psd, rot, n_par) + ((tables,) if tables is not None else ())
+    out = pool().map(_worker_fisher, _tasks(cat, extra))
     return (np.array([o[0] for o in out]), np.array([o[1] for o in out]),
             np.array([o[2] for o in out]), np.array([o[3] for o in out]))
 
 
-def snr(cat, det, psd, rot):
-    out = pool().map(_worker_snr, _tasks(cat, (det, psd, rot)))
+def snr(cat, det, psd, rot, tables=None):
+    extra = (det, psd, rot) + ((tables,) if tables is not None else ())
+    out = pool().map(_worker_snr, _tasks(cat, extra))
     return (np.array([o[0] for o in out]), np.array([o[1] for o in out]),
             np.array([o[2] for o in out]))
 

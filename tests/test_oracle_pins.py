@@ -268,6 +268,61 @@ def test_snr_geometric_series_closed_form(p_exp):
     assert abs(s[0] ** 2 - integral) <= 2e-7 * integral
 
 
+# ---------------------------------------------------------------- tabulated PSD
+def test_psd_table_interpolation_pins():
+    """Tabulated noise curves (Sec. 3.1, psd_path / is_ASD): log-log linear
+    interpolation reproduces a power law exactly, gives the geometric mean at
+    the logarithmic midpoint of two nodes and the node values at the nodes,
+    squares an amplitude spectral density, multiplies by the row's scale, and
+    is blind (infinite noise) outside the table; bad tables are refused."""
+    f = np.geomspace(1.0, 1e4, 41)
+    S = 3e-49 * (f / 10.0) ** -4.0
+    oracle.set_psd_tables([(f, S, False), (f, np.sqrt(S), True),
+                           (np.array([10.0, 100.0]), np.array([4e-48, 1e-50]), False)])
+    rows = [oracle.table_row(0), oracle.table_row(1, 0.5), oracle.table_row(2)]
+    for x in np.exp(RNG.uniform(0.0, math.log(1e4), 50)):
+        want = 3e-49 * (x / 10.0) ** -4.0
+        assert abs(oracle.psd_eval(rows, 0, x) / want - 1) < 1e-13
+        assert abs(oracle.psd_eval(rows, 1, x) / (0.5 * want) - 1) < 1e-13
+    mid = oracle.psd_eval(rows, 2, math.sqrt(1000.0))
+    assert abs(mid / math.sqrt(4e-48 * 1e-50) - 1) < 1e-14
+    assert abs(oracle.psd_eval(rows, 2, 10.0) / 4e-48 - 1) < 1e-15
+    assert abs(oracle.psd_eval(rows, 2, 100.0) / 1e-50 - 1) < 1e-15
+    assert math.isinf(oracle.psd_eval(rows, 2, 9.999)) and math.isinf(oracle.psd_eval(rows, 2, 100.01))
+    for bad in ([1.0, 1.0], [2.0, 1.0]):
+        with pytest.raises(ValueError):
+            oracle.set_psd_tables([(np.array(bad), np.array([1.0, 1.0]), False)])
+    with pytest.raises(ValueError):
+        oracle.set_psd_tables([(np.array([1.0, 2.0]), np.array([1.0, 0.0]), False)])
+
+
+def test_snr_with_psd_table_closed_forms():
+    """SNR with a tabulated power law equals the SNR with the analytic power
+    law; a table covering only part of the grid sums only the grid points
+    inside it (trapezoid weights of the full grid), which for a power law is a
+    partial geometric sum in closed form."""
+    ev, _ = _one_event("c0", zero_spin=True)
+    det = np.array([[0.75, 0.17, 0.35, math.pi / 2, 0, 0]])
+    fmin, fmax, n = 10.0, 900.0, 300
+    f = np.geomspace(1.0, 1e4, 21)
+    oracle.set_psd_tables([(f, 3e-49 * (f / 10.0) ** -4.0, False),
+                           (np.array([40.0, 200.0]), 3e-49 * (np.array([40.0, 200.0]) / 10.0) ** -4.0,
+                            False)])
+    cat = oracle.Catalog(ev, 0, fmin, fmax, n)
+    s_an, _ = oracle.snr(cat, det, [[10.0, 3e-49, 1, 1.0, 0, 0, 0, -4.0, 0, 0, 0]], 0)
+    s_tab, _ = oracle.snr(cat, det, [oracle.table_row(0)], 0)
+    assert abs(s_tab[0] / s_an[0] - 1) < 1e-13
+    s_part, _ = oracle.snr(cat, det, [oracle.table_row(1)], 0)
+    Mc, eta, dL, th, ph, io, ps, tc = ev[:8]
+    fp, fx = jks(det[0, 0], det[0, 2], det[0, 3], th, ph, ps, det[0, 1] + OMEGA_E * tc)
+    pol2 = abs(fp * (1 + math.cos(io) ** 2) / 2 + 1j * fx * math.cos(io)) ** 2
+    fk, wk = geom_grid(fmin, fmax, n)
+    inside = (fk >= 40.0) & (fk <= 200.0)
+    want = np.sum(4 * amp0(Mc, dL) ** 2 * pol2 * wk[inside] * fk[inside] ** (-7 / 3)
+                  / (3e-49 * (fk[inside] / 10.0) ** -4.0))
+    assert 0 < inside.sum() < n and abs(s_part[0] ** 2 / want - 1) < 1e-12
+
+
 # ---------------------------------------------------------------- Fisher closed forms
 def _fisher1(ev, pset, fmin, fmax, n, det, psd, rot, P):
     cat = oracle.Catalog(ev, pset, fmin, fmax, n)
