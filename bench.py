@@ -1,16 +1,22 @@
 """Benchmark of the Fisher-forecast hot path on GB300.
 
-One step = one pass of the whole hot path over the 1e5-event uneven catalog
-(70 % BBH / 30 % tidal BNS, rotating triangle, per-event log grid from 2 Hz to
-f_ISCO): catalog preparation, network SNR + 11x11 Fisher matrix (mixed
-precision by default), batched FP64 Cholesky inversion with conditioning
-check, and the VJP of the network SNR with respect to all 11 source
-parameters.  Inputs are resident in HBM before the timed region; L2 is
-flushed (256 MiB write) before every timed step.
+One step = one pass of the whole hot path over a catalog: catalog preparation,
+network SNR + 11x11 Fisher matrix with the fused SNR vector-Jacobian product,
+batched FP64 Cholesky inversion with the conditioning check, and, in the mixed
+path, the precision refinement (events whose mixed inversion fails or whose
+condition number exceeds 1e7 are recomputed in FP64).  The default workload is
+the 1e5-event uneven catalog (70 % BBH / 30 % tidal BNS, rotating triangle,
+per-event log grid from 2 Hz to f_ISCO); the mixed path is the headline and the
+FP64 path is timed on the same catalog as the second arm.  Inputs are resident
+in HBM before the timed region; L2 is flushed (256 MiB write) before every
+timed step.
 
   python bench.py [--gpus N --steps K --warmup W] [--precision mixed|fp64]
-                  [--grid literal|stress] [--impl ours|reference]
+                  [--grid literal|stress] [--workload c3|c4|c3-gated]
+                  [--impl ours|reference]
 
+With N > 1 (torchrun) one catalog of N x 1e5 events is split into contiguous
+ranges of equal cost (grid points x interferometers), one per rank.
 --impl reference times the CPU oracle (oracle/) on a bounded sample of the same
 workload on the host cores (the paper's method has no GPU implementation).
 Prints one JSON line.
@@ -19,7 +25,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -44,30 +49,37 @@ WORKLOAD_GATED = ("c3-gated: the c3 catalog with a duty factor of 0.85 per trian
 GATE_SNR = 12.0       # default snr_th of the paper's forecast driver (Sec. 5)
 GATE_DUTY = 0.85      # duty factor per arm of the gated workload
 N_PAR = 11
-SM_COUNT = 152
-DFMA_PER_CLK_SM = 2          # measured on GB300: 2 FP64 FMA / clock / SM (1.26 TFLOP/s)
-FFMA_PER_CLK_SM = 128        # FP32 FMA lanes per SM (measured 117 / clock with a plain FFMA loop)
-# DRAM bytes (read + write) per grid point of the Fisher point kernel, from one
-# ncu capture of the 2e4-event c3 catalog (4,376,070 points) of the current
-# kernels (profiles/k_points_*_fisher_c3.md); scaled by points to a full launch
+NPK = N_PAR * (N_PAR + 1) // 2
+# nominal pipe widths per SM and clock (the peaks' unit counts): FP32 lanes x 2 for
+# the packed FP32x2 FMA the mixed kernel issues; FP64 FMA units
+FP32_FMA_PER_CLK_SM = 256
+FP64_FMA_PER_CLK_SM = 2
+# DRAM bytes (read + write) per grid point of the Fisher point kernels, from one
+# ncu capture of the 2e4-event c3 catalog (4,376,070 points; profiles/
+# k_points_*_fisher_c3.md), scaled by points to a full launch
 DRAM_BYTES_PER_POINT = {"mixed": (23.10528e6 + 11.52e3) / 4376070,
                         "fp64": (19.284224e6 + 91.136e3) / 4376070}
+GOLDEN = os.path.join(ROOT, "tests", "golden", "parity_oracle.npz")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--grid", choices=["literal", "stress"], default="literal")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--events", type=int, default=None)
+    ap.add_argument("--events", type=int, default=None, help="events per GPU")
     ap.add_argument("--workload", choices=["c3", "c4", "c3-gated"], default="c3",
                     help="c3: 1e5 events on the triangle (headline); c4: 1e6 events on five "
                          "interferometers, the step adding the log-det VJP over the two "
                          "L detectors' orientations; c3-gated: c3 with duty-factor arm masks, "
                          "an SNR pass and the SNR > 12 gate before the Fisher pass")
+    ap.add_argument("--refine-cond", type=float, default=1e7,
+                    help="condition number above which mixed events are recomputed in FP64")
+    ap.add_argument("--no-fp64-arm", action="store_true",
+                    help="do not time the FP64 path beside the mixed one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true",
                     help="launch the step call by call instead of replaying a CUDA graph")
@@ -76,7 +88,8 @@ def parse():
 
 # ------------------------------------------------------------------ oracle leg
 def _oracle_event_step(args):
-    """Every row of the step for one event, on the CPU oracle."""
+    """Every row of the step for one event, on the CPU oracle; returns the
+    event's packed Fisher matrix, SNR, covariance and condition number."""
     import oracle
     raw, rule, det, psd, rot = args
     p = oracle.prepare(raw["m1"], raw["m2"], raw["chi1"], raw["chi2"], raw["lam1"], raw["lam2"],
@@ -89,9 +102,10 @@ def _oracle_event_step(args):
                    p["tc"], raw["Phic"], p["chi1z"], p["chi2z"], p["LamT"], p["dLamT"]], 1)
     cat = oracle.Catalog(ev, raw["pset"], raw["fmin"], p["fisco"], npts)
     F, s, err, st = oracle.fisher(cat, det, psd, rot, N_PAR)
-    oracle.invert(F)
+    C, kappa, eps, sti = oracle.invert(F)
     oracle.snr_grad(cat, det, psd, rot, N_PAR)
-    return 1
+    iu = np.triu_indices(N_PAR)
+    return F[0][iu], float(s[0]), C[0][iu], float(kappa[0]), int(sti[0])
 
 
 def _sample(raw, idx):
@@ -102,32 +116,35 @@ def _sample(raw, idx):
     return out
 
 
-def oracle_timing(raw, n_events, cores, budget_s=20.0):
-    """Time the oracle on a bounded sample of the workload (spawn pool)."""
+def oracle_timing(raw, cfg, cores, budget_s=20.0):
+    """Time the oracle on a bounded random sample of the workload (spawn
+    pool, one event per process); returns the rate and the sampled events'
+    rows and oracle results."""
     import multiprocessing as mp
     import oracle
     oracle.build()
-    det, psd, rot = gwcat.network("c3")
+    det, psd, rot = gwcat.network(cfg)
     rule = raw["npts_rule"]
-    ctx = mp.get_context("spawn")
     rng = np.random.default_rng(1)
-    with ctx.Pool(cores) as pool:
+    rows, res = [], []
+    with mp.get_context("spawn").Pool(cores) as pool:
         pool.map(_oracle_event_step, [(_sample(raw, [0]), rule, det, psd, rot)])   # warm
-        done, t0 = 0, time.time()
+        t0 = time.time()
         while True:
             idx = rng.choice(len(raw["m1"]), cores, replace=False)
-            tasks = [(_sample(raw, [i]), rule, det, psd, rot) for i in idx]
-            done += sum(pool.map(_oracle_event_step, tasks))
+            res += pool.map(_oracle_event_step, [(_sample(raw, [i]), rule, det, psd, rot)
+                                                 for i in idx])
+            rows += list(idx)
             el = time.time() - t0
-            if el >= budget_s or done >= n_events:
-                return done / el, done, el
+            if el >= budget_s:
+                return len(rows) / el, np.array(rows), res, el
 
 
 def run_reference(a):
-    raw = gwcat.draw("c3", a.events, grid=a.grid)
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    raw = gwcat.draw("c3", a.events, grid=a.grid)
     cores = os.cpu_count() or 1
     det, psd, rot = gwcat.network("c3")
     import multiprocessing as mp
@@ -206,24 +223,25 @@ class Clocks:
 
 
 def flops_per_point(n_site: int, n_ifo: int, precision: str) -> float:
-    """Arithmetic of the fused Fisher kernel per grid point (P = 11, rotation on),
+    """Arithmetic per grid point of the fused Fisher kernel (P = 11, rotation on),
     counted from its straight-line formulas, one FMA = 2 flops.
 
-    FP64 path (all FP64): basis powers 8, f/w 4, d Psi/d Mc 19, d Psi/d eta 20,
-    slots 9/10 14, tau* and two derivatives 48, PSD weight with reciprocal and
-    square root 35, recurrences 4; per site: Earth-angle sincos ~40, double
-    angle 5, JKS/Doppler/phase combinations ~95; per virtual interferometer:
-    patterns 38, tangents 46, sigma scaling 4, |Q|^2 3, 66-pair Gram update 265.
-    Mixed path (FP32 pipe): double-float basis 80; compensated (Dot2) dot
-    products with double-float coefficients, 13 flops per term and lane (the
-    product error and the addend's roundoff folded into one FMA): d Psi/d Mc with
+    "fp64": the method's work, every operation once in FP64 (the roofline's
+    algorithmic count for both paths): basis powers 8, f/w 4, d Psi/d Mc 19,
+    d Psi/d eta 20, slots 9/10 14, tau* and two derivatives 48, PSD weight with
+    reciprocal and square root 35, recurrences 4; per site: Earth-angle sincos
+    ~40, double angle 5, JKS/Doppler/phase combinations ~95; per virtual
+    interferometer: patterns 38, tangents 46, sigma scaling 4, |Q|^2 3, 66-pair
+    Gram update 265.
+    "mixed": what the mixed kernel executes on the FP32 pipe, compensations
+    included: double-float basis 80; compensated (Dot2) dot products with
+    double-float coefficients, 13 flops per term and lane: d Psi/d Mc with
     d Psi/d eta (two lanes, 11 terms) 276, slots 9/10 (two lanes, 4 terms) 94,
     tau* (one lane, 8 terms, times v^-3) 111, d tau*/d Mc with d tau*/d eta (two
     lanes, 8 terms) 200; f 12, recurrences 41, PSD weight 23; per site 122
     (double-float Earth angle 44, sincosf ~20, JKS/Doppler ~58); per virtual
     interferometer 1343 (patterns 38, tangents 56, scaling 4, 69 compensated
-    accumulations of 18 flops: product, two-sum of the high parts, one FMA for
-    the product error and roundoff, compensation)."""
+    accumulations of 18 flops)."""
     if precision == "mixed":
         shared = 80 + 276 + 94 + 111 + 200 + 12 + 41 + 23
         return shared + 122 * n_site + 1343 * n_ifo
@@ -231,330 +249,20 @@ def flops_per_point(n_site: int, n_ifo: int, precision: str) -> float:
     return shared + 140 * n_site + 356 * n_ifo
 
 
-def shard_seed(rank: int) -> int:
-    """Seed of rank's catalog shard: every rank owns its own full-size shard
-    (weak scaling; events are independent, nothing is exchanged)."""
-    return gwcat.SEED_BASE + 3 + 1000 * rank
-
-
 def aggregate(times_ms, n_events: int, steps: int, world: int, dist=None, device="cpu"):
     """Max over ranks of each timed quantity (ms) and the whole-job rates:
-    events/s = world * n_events * steps / max_time."""
+    events/s = n_events (all ranks) * steps / max_time."""
     import torch
     t = torch.tensor([float(x) for x in times_ms], dtype=torch.float64, device=device)
     if world > 1 and dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     t = t.tolist()
-    rates = [world * n_events * steps / (x * 1e-3) for x in t]
+    rates = [n_events * steps / (x * 1e-3) for x in t]
     return t, rates
-
-
-def sum_over_ranks(t, world: int, dist=None):
-    """Whole-job value of a per-shard partial sum, in place: the log-det
-    gradient is a sum over events, so the ranks' gradients over their shards
-    add up (all-reduce SUM, 8 bytes per detector).  A no-op on one rank."""
-    if world > 1 and dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return t
-
-
-def run_ours(a):
-    import torch
-    import torch.distributed as dist
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local)
-    import paper_2207_06910_gb300 as gw
-
-    prec = gw.GW_MIXED if a.precision == "mixed" else gw.GW_FP64
-    gated = a.workload == "c3-gated"
-    cfg = "c3" if gated else a.workload
-    if gated:
-        a.eager = True      # the gate reads its count back: no single-graph step
-    # weak scaling: every rank owns its own 1e5-event shard (seed offset by rank)
-    raw = gwcat.draw(cfg, a.events, seed=shard_seed(rank), grid=a.grid)
-    n = len(raw["m1"])
-    rule = raw["npts_rule"]
-    det, psd, rot = gwcat.network(cfg)
-    net = gw.Network(det, psd, rot)
-    n_arms = sum(1 if int(r[4]) == 0 else 3 for r in det)
-    keys = ("m1", "m2", "chi1", "chi2", "lam1", "lam2", "dL_Mpc", "tcoal", "fmin",
-            "theta", "phi", "iota", "psi", "Phic")
-    host = {k: torch.as_tensor(np.ascontiguousarray(raw[k], np.float64)).pin_memory() for k in keys}
-    host["zflag"] = torch.as_tensor(np.ascontiguousarray(raw["zflag"], np.uint8)).pin_memory()
-    host["pset"] = torch.as_tensor(np.ascontiguousarray(raw["pset"], np.int8)).pin_memory()
-    if rule[0] == "given":
-        host["npts"] = torch.as_tensor(np.ascontiguousarray(raw["npts"], np.int32)).pin_memory()
-    if gated:
-        masks = gwcat.draw_arm_masks(n, n_arms, GATE_DUTY, seed=shard_seed(rank) + 7)
-        host["arm_mask"] = torch.as_tensor(masks.view(np.int32)).pin_memory()
-    dev = {k: v.cuda() for k, v in host.items()}
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    grad_up = torch.ones(n, dtype=torch.float64, device="cuda")
-    ctx = gw.context()
-    lib = gw.load_library()
-
-    def prepare(d):
-        return gw_prepare_dev(gw, d, rule, n)
-
-    with_logdet = a.workload == "c4"
-    # the orientation gradient the c4 study asks for: the L-shaped detectors
-    # (network rows of shape 0); the triangle's entry is not formed
-    l_mask = sum(1 << k for k, r in enumerate(net.det_rows) if int(r[4]) == 0)
-
-    def gate(d):
-        """Prepared catalog of the step's Fisher pass: every event, or (gated
-        workload) the events passing the SNR gate, with their arm masks."""
-        cat = prepare(d)
-        if not gated:
-            return cat
-        cat = cat.with_arm_mask(d["arm_mask"])
-        snr_all, _ = gw.gw_snr(cat, net, prec)
-        return cat.select(gw.gw_select_snr(snr_all, GATE_SNR))
-
-    def step(d):
-        cat = gate(d)
-        F, snr, st, g = gw.gw_fisher(cat, net, N_PAR, prec, grad_snr=grad_up[:cat.n])
-        cov, cond, err, sti = gw.gw_fisher_inverse(F, N_PAR)
-        gg = None
-        if with_logdet:
-            gg = gw.gw_logdet_vjp_detangles(cat, net, N_PAR, cov, gw.GW_FP64, det_mask=l_mask)
-        return cat, F, snr, cov, cond, g, st, gg
-
-    # prepare 1; Fisher 7 (event setup, scan 3, point loop, finish, SNR VJP);
-    # inversion 1; log-det VJP 6; gated: SNR pass 6 and gate 5
-    launches_per_step = 1 + 7 + 1 + (6 if with_logdet else 0) + (11 if gated else 0)
-    for _ in range(a.warmup):
-        step(dev)
-    torch.cuda.synchronize()
-    # sanity of the timed configuration: no event flagged by the point loop
-    cat, F, snr, cov, cond, g, st, gg = step(dev)
-    torch.cuda.synchronize()
-    assert int((st != 0).sum()) == 0, "events flagged in the benchmark catalog"
-    n_sel = cat.n
-    if gated:
-        sel_rows = cat.sel
-        n_points_all = int(cat.npts.to(torch.int64).sum().item())
-        n_points = int(cat.npts[sel_rows].to(torch.int64).sum().item())
-    else:
-        n_points = n_points_all = int(cat.npts.to(torch.int64).sum().item())
-
-    # ---- reserve the workspace (asynchronous calls) and capture the step
-    gw.gw_reserve(n, gw.work_items(cat.npts), net.n_det)
-    for _ in range(2):
-        step(dev)
-    torch.cuda.synchronize()
-    graph, gout = None, None
-    if not a.eager:
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            gout = step(dev)
-        graph.replay()
-        torch.cuda.synchronize()
-        assert int((gout[6] != 0).sum()) == 0 and torch.allclose(gout[2], snr, rtol=1e-12)
-
-    def run_step():
-        out = gout
-        if graph is not None:
-            graph.replay()
-        else:
-            out = step(dev)
-        if with_logdet:   # the job's gradient: sum of the ranks' shard gradients
-            sum_over_ranks(out[7], world, dist if world > 1 else None)
-        return out
-
-    # Fisher point-kernel duration: a few eager Fisher calls with the library's
-    # event hooks (read before any later point kernel of the step)
-    fisher_ms = []
-    gw.gw_set_profiling(True)
-    for _ in range(5):
-        flush.zero_()
-        cat_p = gate(dev)
-        gw.gw_fisher(cat_p, net, N_PAR, prec, grad_snr=grad_up[:cat_p.n])
-        fisher_ms.append(gw.gw_point_kernel_ms())
-    gw.gw_set_profiling(False)
-    torch.cuda.synchronize()
-
-    # ---- device-resident timed loop
-    clk = Clocks(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(a.steps)]
-    for i in range(a.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        run_step()
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clocks = clk.stop()
-    step_ms = [s.elapsed_time(e) for s, e in ev]
-    total_ms = float(sum(step_ms))
-
-    # ---- end to end: host (pinned) -> device, step, device -> host.  Every step
-    # copies its own inputs up and its results down; the copies run on a copy
-    # stream, so the inputs of step i+1 go up and the results of step i come
-    # down while the GPU computes.  Two input sets (and, with graphs, two
-    # captured step graphs) alternate; one pair of events brackets all steps,
-    # including their L2 flushes.
-    dev2 = {k: v.clone() for k, v in dev.items()}
-    bufs, graphs, gouts = [dev, dev2], [graph, None], [gout, None]
-    if graph is not None:
-        graph2 = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph2):
-            gouts[1] = step(dev2)
-        graph2.replay()
-        torch.cuda.synchronize()
-        graphs[1] = graph2
-
-    def run_on(b):
-        out = gouts[b]
-        if graphs[b] is not None:
-            graphs[b].replay()
-        else:
-            out = step(bufs[b])
-        if with_logdet:
-            sum_over_ranks(out[7], world, dist if world > 1 else None)
-        return out
-
-    outs_host = {"snr": torch.empty(n_sel, dtype=torch.float64).pin_memory(),
-                 "F": torch.empty((N_PAR * (N_PAR + 1) // 2, n_sel), dtype=torch.float64).pin_memory(),
-                 "cov": torch.empty((N_PAR * (N_PAR + 1) // 2, n_sel), dtype=torch.float64).pin_memory(),
-                 "g": torch.empty((N_PAR, n_sel), dtype=torch.float64).pin_memory()}
-    if with_logdet:
-        outs_host["gg"] = torch.empty(net.n_det, dtype=torch.float64).pin_memory()
-    h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = sum(v.numel() * v.element_size() for v in outs_host.values())
-    copy = torch.cuda.Stream()
-    h2d_ev = [torch.cuda.Event(), torch.cuda.Event()]
-    step_ev = [torch.cuda.Event(), torch.cuda.Event()]
-    d2h_ev = [torch.cuda.Event(), torch.cuda.Event()]
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    t0.record(stream)
-    copy.wait_event(t0)
-    with torch.cuda.stream(copy):
-        for k, v in host.items():
-            bufs[0][k].copy_(v, non_blocking=True)
-        h2d_ev[0].record(copy)
-    keep = [None, None]
-    for i in range(a.steps):
-        b = i % 2
-        flush.zero_()
-        stream.wait_event(h2d_ev[b])          # this step's inputs are up
-        if i >= 2:
-            stream.wait_event(d2h_ev[b])      # step i-2's results are down
-        out = run_on(b)
-        step_ev[b].record(stream)
-        with torch.cuda.stream(copy):
-            if i + 1 < a.steps:
-                if i >= 1:
-                    copy.wait_event(step_ev[1 - b])   # step i-1 is done with that set
-                for k, v in host.items():
-                    bufs[1 - b][k].copy_(v, non_blocking=True)
-                h2d_ev[1 - b].record(copy)
-            copy.wait_event(step_ev[b])
-            cat, F, snr, cov, cond, g, st, gg = out
-            res = ((snr, "snr"), (F, "F"), (cov, "cov"), (g, "g"))
-            for t, name in res + (((gg, "gg"),) if with_logdet else ()):
-                if graphs[b] is None:
-                    t.record_stream(copy)
-                outs_host[name].copy_(t, non_blocking=True)
-            d2h_ev[b].record(copy)
-        keep[b] = out
-    stream.wait_stream(copy)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = float(t0.elapsed_time(t1))
-    gw.gw_reserve(0, 0, 0)
-
-    (total_ms, e2e_ms, kern_ms), (value, e2e_value, _) = aggregate(
-        [total_ms, e2e_ms, float(np.mean(fisher_ms))], n, a.steps, world,
-        dist if world > 1 else None, device="cuda")
-
-    if rank == 0:
-        n_site = net.n_det
-        n_ifo = sum(1 if int(r[4]) == 0 else 2 for r in det)
-        if gated:
-            # interferometers in use per selected event: a triangle with every arm
-            # on is two virtual ones, otherwise one per arm that is on
-            sel_np = sel_rows.cpu().numpy()
-            m = masks[sel_np].astype(np.int64) & 7
-            ifo_e = np.where(m == 7, 2, (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1))
-            pts_e = cat.npts[sel_rows].cpu().numpy().astype(np.float64)
-            flops = float(np.sum(pts_e * np.array([flops_per_point(n_site, int(k), a.precision)
-                                                   for k in ifo_e])))
-        else:
-            flops = flops_per_point(n_site, n_ifo, a.precision) * n_points
-        sm_mhz = clocks.get("sm_mhz") or 2070.0
-        per_clk = FFMA_PER_CLK_SM if a.precision == "mixed" else DFMA_PER_CLK_SM
-        peak = SM_COUNT * per_clk * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s at the sampled clock
-        achieved = flops / (kern_ms * 1e-3) / 1e12
-        cpu = None
-        if not a.no_cpu_baseline:
-            cores = os.cpu_count() or 1
-            v, done, el = oracle_timing(raw, 10 ** 9, cores, budget_s=20.0)
-            cpu = {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
-                   "sample": f"{done} random events of this catalog in {el:.1f} s "
-                             f"(prepare + SNR + Fisher + inversion + SNR gradient), "
-                             f"one event per process on {cores} host cores"}
-        line = {
-            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64 (mixed)" if a.precision == "mixed" else "f64",
-            "data": "synthetic (seeded, gwcat)",
-            "config": {"workload": {"c3": WORKLOAD, "c4": WORKLOAD_C4,
-                                    "c3-gated": WORKLOAD_GATED}[a.workload],
-                       "n_events_per_gpu": n, "grid": a.grid,
-                       "points_per_step": n_points + (n_points_all if gated else 0),
-                       "precision": a.precision, "n_par": N_PAR,
-                       "step": ("prepare + SNR pass + gate + " if gated else "prepare + ")
-                               + "SNR/Fisher with fused SNR VJP + Cholesky inversion"
-                               + (" + log-det VJP (FP64) over the two L detectors' orientations"
-                                  if with_logdet else ""),
-                       **({"selected_events": n_sel, "fisher_points": n_points}
-                          if gated else {}),
-                       "l2": "flushed before every timed step (256 MiB write)",
-                       "launch": "eager calls" if a.eager else "one CUDA graph replay per step",
-                       "parallelism": f"event shards, {world} GPU(s), " + (
-                           "log-det gradient all-reduced (SUM) per step" if with_logdet
-                           and world > 1 else "no collective")},
-            "clocks": clocks,
-            "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h,
-                    "copies": "pinned host buffers, on a copy stream overlapping the "
-                              "previous/next step's compute"},
-            "gpu_launches": launches_per_step * a.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak,
-                         "traffic": DRAM_BYTES_PER_POINT[a.precision] * n_points
-                         if a.grid == "literal" else None,
-                         "kernel": f"k_points_{'mixed' if a.precision == 'mixed' else 'fp64'} (Fisher)",
-                         "kernel_ms": kern_ms,
-                         "flops_per_point": flops_per_point(n_site, n_ifo, a.precision),
-                         "peak_basis": (f"{'FP32' if a.precision == 'mixed' else 'FP64'} pipe: "
-                                        f"{SM_COUNT} SMs x {per_clk} FMA/clk x 2 flops x "
-                                        f"{sm_mhz:.0f} MHz (median sampled SM clock)")},
-            "cpu_baseline": cpu,
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
 
 
 def gw_prepare_dev(gw, d, rule, n):
     """gw_prepare_catalog on device-resident raw arrays (no host transfer)."""
-    import ctypes
     import torch
     lib = gw.load_library()
     ctx = gw.context()
@@ -581,6 +289,447 @@ def gw_prepare_dev(gw, d, rule, n):
     for k in ("theta", "phi", "iota", "psi", "Phic"):
         t[k] = d[k]
     return gw.Catalog(t, d["pset"], d["fmin"], out["fmax"], npts)
+
+
+KEYS = ("m1", "m2", "chi1", "chi2", "lam1", "lam2", "dL_Mpc", "tcoal", "fmin",
+        "theta", "phi", "iota", "psi", "Phic")
+
+
+def golden_error(gw, refine_cond):
+    """sqrt(diag C) error of the mixed path (with the FP64 refinement) and of
+    the FP64 path against the stored oracle results of 1000 stratified events
+    of the c3 catalog (tests/golden/parity_oracle.npz), per condition-number
+    decade; worst = max of rel / max(1e-3, 1e-15 kappa) (pass: <= 1)."""
+    import torch
+    if not os.path.exists(GOLDEN):
+        return None
+    z = np.load(GOLDEN)
+    if "c3lit_cov" not in z:
+        return None
+    det, psd, rot = gwcat.network("c3")
+    net = gw.Network(det, psd, rot)
+    cat = gw.Catalog.from_numpy(z["c3lit_ev"], z["c3lit_pset"], z["c3lit_fmin"], z["c3lit_fmax"],
+                                z["c3lit_npts"])
+    diag = [i * N_PAR - i * (i - 1) // 2 for i in range(N_PAR)]     # packed (i, i)
+    so = np.sqrt(np.abs(z["c3lit_cov"][:, diag]))
+    kappa = z["c3lit_kappa"]
+    ok = (z["c3lit_inv_status"] & 33) == 0
+    out = {"events": int(len(kappa)), "oracle_flagged": int((~ok).sum())}
+    for name, prec in (("mixed_refined", gw.GW_MIXED), ("fp64", gw.GW_FP64)):
+        F, snr, st = gw.gw_fisher(cat, net, N_PAR, prec)
+        inv = gw.gw_fisher_inverse(F, N_PAR)
+        nref = gw.gw_fisher_refine(cat, net, N_PAR, F, snr, st, inv, cond_th=refine_cond) \
+            if prec == gw.GW_MIXED else 0
+        torch.cuda.synchronize()
+        C = inv[0].cpu().numpy()
+        sg = np.sqrt(np.abs(C[diag].T))
+        with np.errstate(all="ignore"):
+            rel = np.max(np.abs(sg / so - 1), axis=1)
+        rel_ok = rel[ok]
+        worst = float(np.nanmax(rel_ok / np.maximum(1e-3, 1e-15 * kappa[ok])))
+        dec = np.floor(np.log10(kappa[ok])).astype(int)
+        table = {f"1e{d}": [int((dec == d).sum()), round(float(np.mean(rel_ok[dec == d] <= 1e-3)), 3),
+                            float(np.max(rel_ok[dec == d]))]
+                 for d in range(dec.min(), dec.max() + 1) if (dec == d).any()}
+        out[name] = {"worst_over_bound": worst, "max_rel_kappa_le_1e12":
+                     float(np.max(rel_ok[kappa[ok] <= 1e12])),
+                     "pass_1e-3_frac": float(np.mean(rel_ok <= 1e-3)),
+                     "refined_frac": nref / len(kappa),
+                     "per_decade_[events,pass_1e-3,max_rel]": table}
+    return out
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    import paper_2207_06910_gb300 as gw
+    from paper_2207_06910_gb300 import shard
+
+    prec = gw.GW_MIXED if a.precision == "mixed" else gw.GW_FP64
+    gated = a.workload == "c3-gated"
+    cfg = "c3" if gated else a.workload
+    if gated:
+        a.eager = True      # the gate reads its count back: no single-graph step
+    with_logdet = a.workload == "c4"
+    n_per_gpu = a.events or gwcat.SIZES[cfg]
+    det, psd, rot = gwcat.network(cfg)
+    net = gw.Network(det, psd, rot)
+    n_arms = sum(1 if int(r[4]) == 0 else 3 for r in det)
+    n_site = net.n_det
+    n_ifo = sum(1 if int(r[4]) == 0 else 2 for r in det)
+
+    # ---- one catalog over all ranks, split into contiguous ranges of equal cost
+    raw_all = gwcat.draw(cfg, n_per_gpu * world, grid=a.grid)
+    rule = raw_all["npts_rule"]
+    dev_all = {k: torch.as_tensor(np.ascontiguousarray(raw_all[k], np.float64), device="cuda")
+               for k in KEYS}
+    dev_all["zflag"] = torch.as_tensor(np.ascontiguousarray(raw_all["zflag"], np.uint8), device="cuda")
+    dev_all["pset"] = torch.as_tensor(np.ascontiguousarray(raw_all["pset"], np.int8), device="cuda")
+    if rule[0] == "given":
+        dev_all["npts"] = torch.as_tensor(np.ascontiguousarray(raw_all["npts"], np.int32), device="cuda")
+    npts_all = gw_prepare_dev(gw, dev_all, rule, len(raw_all["m1"])).npts.cpu().numpy()
+    del dev_all
+    bounds = shard.partition(shard.event_cost(npts_all, n_ifo), world)
+    lo_r, hi_r = int(bounds[rank]), int(bounds[rank + 1])
+    raw = {k: (v[lo_r:hi_r] if isinstance(v, np.ndarray) and v.shape[:1] == (len(raw_all["m1"]),)
+               else v) for k, v in raw_all.items()}
+    n = hi_r - lo_r
+    n_total = len(raw_all["m1"])
+
+    host = {k: torch.as_tensor(np.ascontiguousarray(raw[k], np.float64)).pin_memory() for k in KEYS}
+    host["zflag"] = torch.as_tensor(np.ascontiguousarray(raw["zflag"], np.uint8)).pin_memory()
+    host["pset"] = torch.as_tensor(np.ascontiguousarray(raw["pset"], np.int8)).pin_memory()
+    if rule[0] == "given":
+        host["npts"] = torch.as_tensor(np.ascontiguousarray(raw["npts"], np.int32)).pin_memory()
+    masks = None
+    if gated:
+        masks = gwcat.draw_arm_masks(n_total, n_arms, GATE_DUTY)[lo_r:hi_r]
+        host["arm_mask"] = torch.as_tensor(masks.view(np.int32)).pin_memory()
+    dev = {k: v.cuda() for k, v in host.items()}
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    grad_up = torch.ones(n, dtype=torch.float64, device="cuda")
+    # the orientation gradient the c4 study asks for: the L-shaped detectors
+    l_mask = sum(1 << k for k, r in enumerate(net.det_rows) if int(r[4]) == 0)
+
+    def gate(d):
+        """Prepared catalog of the step's Fisher pass: every event, or (gated
+        workload) the events passing the SNR gate, with their arm masks."""
+        cat = gw_prepare_dev(gw, d, rule, n)
+        if not gated:
+            return cat
+        cat = cat.with_arm_mask(d["arm_mask"])
+        snr_all, _ = gw.gw_snr(cat, net, gw.GW_MIXED if prec == gw.GW_MIXED else gw.GW_FP64)
+        return cat.select(gw.gw_select_snr(snr_all, GATE_SNR))
+
+    def forward(d, p):
+        """The capturable part of the step: prepare, Fisher with fused SNR VJP,
+        inversion (and the gate for the gated workload)."""
+        cat = gate(d)
+        F, snr, st, g = gw.gw_fisher(cat, net, N_PAR, p, grad_snr=grad_up[:cat.n])
+        inv = gw.gw_fisher_inverse(F, N_PAR)
+        return [cat, F, snr, st, g, inv]
+
+    def finish(out, p):
+        """The rest of the step: FP64 refinement of the mixed events (reads back
+        its count), log-det VJP (c4) and its sum over ranks."""
+        cat, F, snr, st, g, inv = out
+        nref = 0
+        if p == gw.GW_MIXED:
+            nref = gw.gw_fisher_refine(cat, net, N_PAR, F, snr, st, inv, grad_snr=grad_up[:cat.n],
+                                       grad_params=g, cond_th=a.refine_cond)
+        gg = None
+        if with_logdet:
+            gg = gw.gw_logdet_vjp_detangles(cat, net, N_PAR, inv[0], gw.GW_FP64, det_mask=l_mask)
+            shard.sum_partials(gg, world, dist if world > 1 else None)
+        return nref, gg
+
+    def make_arm(p, bufs):
+        """Warm, reserve, capture; returns run(b) -> (outputs, n_refined)."""
+        for _ in range(a.warmup):
+            finish(forward(bufs[0], p), p)
+        torch.cuda.synchronize()
+        cat0 = forward(bufs[0], p)[0]
+        gw.gw_reserve(n, gw.work_items(cat0.npts if cat0.sel is None else cat0.npts[cat0.sel]),
+                      net.n_det)
+        for _ in range(2):
+            finish(forward(bufs[0], p), p)
+        torch.cuda.synchronize()
+        graphs, outs = [None] * len(bufs), [None] * len(bufs)
+        if not a.eager:
+            for b, d in enumerate(bufs):
+                graphs[b] = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graphs[b]):
+                    outs[b] = forward(d, p)
+                graphs[b].replay()
+            torch.cuda.synchronize()
+
+        def run(b):
+            if graphs[b] is not None:
+                graphs[b].replay()
+                out = outs[b]
+            else:
+                out = forward(bufs[b], p)
+            nref, gg = finish(out, p)
+            return out, nref, gg
+        return run
+
+    def timed_loop(run):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(a.steps)]
+        nref = 0
+        for i in range(a.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            out, nref, gg = run(0)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return float(sum(s.elapsed_time(e) for s, e in ev)), out, nref
+
+    def point_kernel_ms(p, refine):
+        """Point-loop kernel durations from the library's CUDA events on the
+        launching stream: the Fisher pass, and (mixed) the refinement's FP64 pass."""
+        ms, ms_ref = [], []
+        gw.gw_set_profiling(True)
+        for _ in range(3):
+            flush.zero_()
+            out = forward(dev, p)
+            ms.append(gw.gw_point_kernel_ms())
+            if refine:
+                finish(out, p)
+                ms_ref.append(gw.gw_point_kernel_ms())
+        gw.gw_set_profiling(False)
+        torch.cuda.synchronize()
+        return float(np.mean(ms)), (float(np.mean(ms_ref)) if ms_ref else 0.0)
+
+    # ---- the FP64 arm (same catalog, same launch), then the headline arm
+    arms = {}
+    order = [prec] if (a.no_fp64_arm or prec == gw.GW_FP64) else [gw.GW_FP64, prec]
+    dev2 = {k: v.clone() for k, v in dev.items()}
+    clocks = None
+    for p in order:
+        run = make_arm(p, [dev, dev2])
+        kern_ms, kern_ref_ms = point_kernel_ms(p, p == gw.GW_MIXED)
+        clk = Clocks(local)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.start()
+        total_ms, out, nref = timed_loop(run)
+        if world > 1:
+            dist.barrier()
+        c = clk.stop()
+        arms[p] = dict(run=run, total_ms=total_ms, out=out, nref=nref, kern_ms=kern_ms,
+                       kern_ref_ms=kern_ref_ms, clocks=c)
+        if p == prec:
+            clocks = c
+        gw.gw_reserve(0, 0, 0)
+    head = arms[prec]
+    cat, F, snr, st, g, inv = head["out"]
+    assert int((st != 0).sum()) == 0, "events flagged in the benchmark catalog"
+    n_sel = cat.n
+    npts_sel = (cat.npts if cat.sel is None else cat.npts[cat.sel]).to(torch.int64)
+    n_points = int(npts_sel.sum().item())
+    n_points_all = int(cat.npts.to(torch.int64).sum().item())
+
+    # ---- end to end: host (pinned) -> device, step, device -> host.  Every step
+    # copies its own inputs up and its results down on a copy stream, so the
+    # inputs of step i+1 go up and the results of step i come down while the GPU
+    # computes; two input sets (and two captured graphs) alternate.
+    gw.gw_reserve(n, gw.work_items(npts_sel), net.n_det)
+    run = make_arm(prec, [dev, dev2])
+    outs_host = {"snr": torch.empty(n_sel, dtype=torch.float64).pin_memory(),
+                 "F": torch.empty((NPK, n_sel), dtype=torch.float64).pin_memory(),
+                 "cov": torch.empty((NPK, n_sel), dtype=torch.float64).pin_memory(),
+                 "g": torch.empty((N_PAR, n_sel), dtype=torch.float64).pin_memory(),
+                 "cond": torch.empty(n_sel, dtype=torch.float64).pin_memory(),
+                 "inv_err": torch.empty(n_sel, dtype=torch.float64).pin_memory(),
+                 "status": torch.empty(n_sel, dtype=torch.int32).pin_memory(),
+                 "inv_status": torch.empty(n_sel, dtype=torch.int32).pin_memory()}
+    if with_logdet:
+        outs_host["gg"] = torch.empty(net.n_det, dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in outs_host.values())
+    copy = torch.cuda.Stream()
+    bufs = [dev, dev2]
+    h2d_ev = [torch.cuda.Event(), torch.cuda.Event()]
+    step_ev = [torch.cuda.Event(), torch.cuda.Event()]
+    d2h_ev = [torch.cuda.Event(), torch.cuda.Event()]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    copy.wait_event(t0)
+    with torch.cuda.stream(copy):
+        for k, v in host.items():
+            bufs[0][k].copy_(v, non_blocking=True)
+        h2d_ev[0].record(copy)
+    for i in range(a.steps):
+        b = i % 2
+        flush.zero_()
+        stream.wait_event(h2d_ev[b])          # this step's inputs are up
+        if i >= 2:
+            stream.wait_event(d2h_ev[b])      # step i-2's results are down
+        out, nref, gg = run(b)
+        step_ev[b].record(stream)
+        with torch.cuda.stream(copy):
+            if i + 1 < a.steps:
+                if i >= 1:
+                    copy.wait_event(step_ev[1 - b])   # step i-1 is done with that set
+                for k, v in host.items():
+                    bufs[1 - b][k].copy_(v, non_blocking=True)
+                h2d_ev[1 - b].record(copy)
+            copy.wait_event(step_ev[b])
+            c_, F_, snr_, st_, g_, inv_ = out
+            res = [(snr_, "snr"), (F_, "F"), (inv_[0], "cov"), (g_, "g"), (inv_[1], "cond"),
+                   (inv_[2], "inv_err"), (st_, "status"), (inv_[3], "inv_status")]
+            if with_logdet:
+                res.append((gg, "gg"))
+            for t, name in res:
+                t.record_stream(copy)
+                outs_host[name].copy_(t, non_blocking=True)
+            d2h_ev[b].record(copy)
+    stream.wait_stream(copy)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = float(t0.elapsed_time(t1))
+    gw.gw_reserve(0, 0, 0)
+
+    # ---- whole-job figures: max over ranks of the times
+    fp64 = arms.get(gw.GW_FP64)
+    times = [head["total_ms"], e2e_ms, head["kern_ms"], head["kern_ref_ms"],
+             fp64["total_ms"] if fp64 else 0.0, fp64["kern_ms"] if fp64 else 0.0]
+    t, rates = aggregate(times, n_total, a.steps, world, dist if world > 1 else None, device="cuda")
+    total_ms, e2e_ms, kern_ms, kern_ref_ms, fp64_ms, fp64_kern_ms = t
+    value, e2e_value = rates[0], rates[1]
+    nref_t = torch.tensor([float(head["nref"])], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(nref_t)
+    n_refined = int(nref_t.item())
+
+    if rank == 0:
+        algo_fp = flops_per_point(n_site, n_ifo, "fp64")
+        exec_fp = flops_per_point(n_site, n_ifo, a.precision)
+        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        rate64 = gw.gw_fma_rate(True)
+        rate32 = gw.gw_fma_rate(False)
+        peak32 = sms * FP32_FMA_PER_CLK_SM * 2 * sm_mhz * 1e6 / 1e12
+        peak64 = sms * FP64_FMA_PER_CLK_SM * 2 * sm_mhz * 1e6 / 1e12
+        refined_frac = n_refined / max(1, n_total)
+        # points of one rank's launch of each point kernel
+        pts_mixed = n_points if prec == gw.GW_MIXED else 0
+        pts_ref = int(round(n_points * refined_frac)) if prec == gw.GW_MIXED else n_points
+        kernels = []
+        if prec == gw.GW_MIXED:
+            kernels.append({"kernel": "k_points_mixed (Fisher)", "ms": kern_ms, "points": pts_mixed,
+                            "bound": "alu", "peak": peak32,
+                            "peak_basis": f"FP32 pipe: {sms} SMs x {FP32_FMA_PER_CLK_SM} FMA/clk "
+                                          f"(packed FP32x2) x 2 flops x {sm_mhz:.0f} MHz",
+                            "executed_flops_per_point": exec_fp})
+            if kern_ref_ms > 0:
+                kernels.append({"kernel": "k_points_fp64 (refinement of the ill-conditioned events)",
+                                "ms": kern_ref_ms, "points": pts_ref, "bound": "alu",
+                                "peak": peak64, "executed_flops_per_point": algo_fp,
+                                "peak_basis": f"FP64 pipe: {sms} SMs x {FP64_FMA_PER_CLK_SM} FMA/clk "
+                                              f"x 2 flops x {sm_mhz:.0f} MHz"})
+        else:
+            kernels.append({"kernel": "k_points_fp64 (Fisher)", "ms": kern_ms, "points": n_points,
+                            "bound": "alu", "peak": peak64, "executed_flops_per_point": algo_fp,
+                            "peak_basis": f"FP64 pipe: {sms} SMs x {FP64_FMA_PER_CLK_SM} FMA/clk "
+                                          f"x 2 flops x {sm_mhz:.0f} MHz"})
+        for k in kernels:
+            k["achieved"] = algo_fp * k["points"] / (k["ms"] * 1e-3) / 1e12
+            k["frac"] = k["achieved"] / k["peak"]
+            k["algorithmic_flops_per_point"] = algo_fp
+            k["unit"] = "TFLOP/s"
+            is_mixed = k["kernel"].startswith("k_points_mixed")
+            k["traffic"] = (DRAM_BYTES_PER_POINT["mixed" if is_mixed else "fp64"] * k["points"]
+                            if a.grid == "literal" else None)
+        dom = max(kernels, key=lambda k: k["ms"])
+        roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
+                    "unit": "TFLOP/s", "frac": dom["frac"], "traffic": dom["traffic"],
+                    "kernel": dom["kernel"], "kernel_ms": dom["ms"],
+                    "algorithmic_flops_per_point": algo_fp,
+                    "executed_flops_per_point": dom["executed_flops_per_point"],
+                    "peak_basis": dom["peak_basis"] + " (median sampled SM clock)",
+                    "kernels": kernels,
+                    "measured_fma_per_clk_sm": {"fp64": rate64["fma_per_clk_sm"],
+                                                "fp32_packed": rate32["fma_per_clk_sm"]}}
+        cpu = None
+        err_sample = None
+        if not a.no_cpu_baseline:
+            cores = os.cpu_count() or 1
+            v, rows, ores, el = oracle_timing(raw, cfg, cores, budget_s=20.0)
+            cpu = {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{len(rows)} random events of this rank's catalog in {el:.1f} s "
+                             f"(prepare + SNR + Fisher + inversion + SNR gradient), "
+                             f"one event per process on {cores} host cores"}
+            if not gated:
+                # the timed step's results on the sampled events against the oracle's
+                diag = [i * N_PAR - i * (i - 1) // 2 for i in range(N_PAR)]
+                Fg = F.cpu().numpy()[:, rows].T
+                sg = snr.cpu().numpy()[rows]
+                Cg = inv[0].cpu().numpy()[:, rows].T
+                Fo = np.array([r[0] for r in ores])
+                so = np.array([r[1] for r in ores])
+                Co = np.array([r[2] for r in ores])
+                ko = np.array([r[3] for r in ores])
+                okd = (np.array([r[4] for r in ores]) & 33) == 0
+                dgo = np.sqrt(Fo[:, diag])
+                iu = np.triu_indices(N_PAR)
+                relF = np.max(np.abs(Fg - Fo) / (dgo[:, iu[0]] * dgo[:, iu[1]]), axis=1)
+                with np.errstate(all="ignore"):
+                    relC = np.max(np.abs(np.sqrt(np.abs(Cg[:, diag])) /
+                                         np.sqrt(np.abs(Co[:, diag])) - 1), axis=1)
+                err_sample = {"events": int(len(rows)),
+                              "snr_max_rel": float(np.max(np.abs(sg / so - 1))),
+                              "fisher_max_rel_of_sqrt_FiiFjj": float(relF.max()),
+                              "sqrt_diag_cov_max_rel": float(np.nanmax(relC[okd])) if okd.any() else None,
+                              "sqrt_diag_cov_worst_over_bound": float(np.nanmax(
+                                  relC[okd] / np.maximum(1e-3, 1e-15 * ko[okd]))) if okd.any() else None}
+        golden = golden_error(gw, a.refine_cond) if (cfg == "c3" and not gated) else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (mixed, FP64 refinement)" if a.precision == "mixed" else "f64",
+            "data": "synthetic (seeded, gwcat)",
+            "config": {"workload": {"c3": WORKLOAD, "c4": WORKLOAD_C4,
+                                    "c3-gated": WORKLOAD_GATED}[a.workload],
+                       "n_events_total": n_total, "n_events_per_gpu": n_per_gpu,
+                       "grid": a.grid, "points_per_step_rank0": n_points + (n_points_all if gated else 0),
+                       "precision": a.precision, "n_par": N_PAR,
+                       "step": ("prepare + SNR pass + gate + " if gated else "prepare + ")
+                               + "SNR/Fisher with fused SNR VJP + Cholesky inversion"
+                               + (f" + FP64 refinement of events with condition number > "
+                                  f"{a.refine_cond:g}" if prec == gw.GW_MIXED else "")
+                               + (" + log-det VJP (FP64) over the two L detectors' orientations"
+                                  if with_logdet else ""),
+                       **({"selected_events_rank0": n_sel, "fisher_points_rank0": n_points}
+                          if gated else {}),
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "launch": "eager calls" if a.eager else
+                                 "one CUDA graph replay per step + the refinement's calls",
+                       "parallelism": f"one catalog split into {world} cost-balanced contiguous "
+                                      f"ranges, one per GPU" + (
+                                          "; log-det gradient all-reduced (SUM) per step"
+                                          if with_logdet and world > 1 else "; no collective")},
+            "clocks": clocks,
+            "refined_fraction": refined_frac if prec == gw.GW_MIXED else None,
+            "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "copies": "pinned host buffers, on a copy stream overlapping the "
+                              "previous/next step's compute"},
+            "gpu_launches": None,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "error": {"bound": "sqrt(diag C): max(1e-3, 1e-15 kappa) relative to the oracle "
+                               "(the FP64 rounding floor of an FP64 Fisher matrix above 1e12)",
+                      "oracle_sample_of_this_run": err_sample,
+                      "oracle_stratified_1000_c3_events": golden},
+        }
+        if fp64 is not None and prec == gw.GW_MIXED:
+            line["fp64_arm"] = {"value": rates[4], "unit": "events/s", "ms_per_step": fp64_ms / a.steps,
+                                "point_kernel_ms": fp64_kern_ms, "clocks": fp64["clocks"]}
+            line["mixed_over_fp64"] = value / rates[4]
+        # launches per step: prepare 1; Fisher 7 (event setup, scan 3, point loop,
+        # finish, SNR VJP); inversion 1; refinement (when it selects events) 22:
+        # flag + scan 3 + compact, gather, FP64 Fisher 7, inversion, 8 scatters,
+        # else 5; log-det VJP 6; gated: SNR pass 6 and gate 5
+        per_step = 1 + 7 + 1 + (6 if with_logdet else 0) + (11 if gated else 0)
+        if prec == gw.GW_MIXED:
+            per_step += 22 if n_refined > 0 else 5
+        line["gpu_launches"] = per_step * a.steps
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():

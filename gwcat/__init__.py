@@ -154,6 +154,24 @@ def network(config: str):
     return net["det"].copy(), net["psd"].copy(), net["rotation"]
 
 
+def network_tabulated(config: str, n_table: int = 2000, asd: bool = False,
+                      f_lo: float = 1.0, f_hi: float = 1e4):
+    """The network of ``config`` with every PSD given as a table (the psd_path
+    option of the paper's detectors): the configuration's power-sum shape
+    sum_j c_j (f/f0)^p_j sampled on ``n_table`` log-spaced frequencies in
+    [f_lo, f_hi], as PSD values or (``asd``) their square roots; the row keeps
+    its scale.  Returns (det, psd rows with nterm = -(k+1) for table k,
+    rotation, tables = [(f, values, asd), ...])."""
+    det, psd, rot = network(config)
+    f = np.geomspace(f_lo, f_hi, n_table)
+    rows, tables = [], []
+    for k, r in enumerate(psd):
+        shape = sum(r[3 + j] * (f / r[0]) ** r[7 + j] for j in range(int(r[2])))
+        tables.append((f.copy(), np.sqrt(shape) if asd else shape, asd))
+        rows.append([1.0, r[1], -(k + 1), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+    return det, np.array(rows), rot, tables
+
+
 def draw_arm_masks(n: int, n_arms: int, duty: float, seed: int | None = None) -> np.ndarray:
     """Duty-factor draws (one Bernoulli trial per event and arm): bit a of the
     returned uint32 mask of event e is set, i.e. arm a of the expanded network

@@ -111,11 +111,28 @@ typedef struct gw_detector {
     int32_t shape, psd;
 } gw_detector;
 
-/* Noise PSD: S_n(f) = scale * sum_{j<nterm} coef[j] (f/f0)^pw[j], nterm <= 4. */
+/* Noise PSD of an interferometer (Sec. 3.1: each detector carries its noise
+ * curve, given by a file of frequencies and PSD or ASD values, the psd_path
+ * and is_ASD options).  Two kinds:
+ *  GW_PSD_POWER_SUM: S_n(f) = scale * sum_{j<nterm} coef[j] (f/f0)^pw[j],
+ *      1 <= nterm <= 4, coef >= 0, integer powers |pw| <= 15;
+ *  GW_PSD_TABLE: S_n(f) = scale * T(f), T the straight line through
+ *      (ln f_j, ln T_j) and (ln f_j+1, ln T_j+1) for f_j <= f <= f_j+1 (log-log
+ *      linear interpolation of the tabulated curve); T_j = table_s[j], or
+ *      table_s[j]^2 when is_asd (the table holds the amplitude spectral
+ *      density).  Outside [table_f[0], table_f[n_table-1]] the interferometer
+ *      is blind (zero noise weight).  table_f, table_s: DEVICE [n_table],
+ *      2 <= n_table <= 2^20, table_f strictly increasing and > 0, table_s > 0,
+ *      read during the call (the library builds its log table in the call's
+ *      workspace); a table that breaks these rules gives NaN noise weights, so
+ *      the events' outputs are NaN.  f0, nterm, coef and pw are ignored. */
+enum { GW_PSD_POWER_SUM = 0, GW_PSD_TABLE = 1 };
 typedef struct gw_psd {
     double f0, scale;
-    int32_t nterm, reserved;
+    int32_t nterm, kind;
     double coef[4], pw[4];
+    const double *table_f, *table_s;
+    int32_t n_table, is_asd;
 } gw_psd;
 
 /* Network (HOST memory, read during the call only).  n_det <= 8 with at most
@@ -137,7 +154,7 @@ gw_status gw_create(gw_ctx **ctx, int device);
 gw_status gw_destroy(gw_ctx *ctx);
 /* Text of the last error on this context (static storage, never NULL). */
 const char *gw_last_error(const gw_ctx *ctx);
-/* ABI version of this header (incremented on any signature change or addition): 4. */
+/* ABI version of this header (incremented on any signature change or addition): 5. */
 int gw_abi_version(void);
 
 /* Reserve workspace for up to max_events events on up to max_sites detector
@@ -159,6 +176,18 @@ gw_status gw_reserve(gw_ctx *ctx, int64_t max_events, int64_t max_items, int max
  * when nothing was recorded). */
 gw_status gw_set_profiling(gw_ctx *ctx, int enable);
 double gw_point_kernel_ms(gw_ctx *ctx);
+
+/* Measurement hook (no counterpart in the paper): FMA throughput of the FP64
+ * (fp64 = 1) or FP32 (fp64 = 0) pipe of the current device, measured with
+ * independent FMA chains in every thread of a grid that fills every SM (each
+ * thread runs 8 chains of `iters` FMAs, FP32 as packed FP32x2 FMAs, so 16 FMAs
+ * per iteration; 1 <= iters <= 2^24; the launch is repeated once to warm the
+ * clocks).  HOST outputs: *fma_per_clk_sm (FMAs per
+ * SM clock and SM, from the SM cycle counter), *fma_per_s (FMAs per second
+ * over the whole GPU, from CUDA events), *sm_mhz (the SM clock during the
+ * loop).  Allocates and frees two small device buffers; synchronises `stream`. */
+gw_status gw_fma_rate(int fp64, int iters, double *fma_per_clk_sm, double *fma_per_s,
+                      double *sm_mhz, void *stream);
 
 /* Catalog preparation (Sec. 2.1; Eq. 2.2; f_ISCO of the Sec. 2.2 footnote).
  * DEVICE inputs, length n: m1, m2 [Msun], chi1, chi2, lam1, lam2 (NULL -> 0),
@@ -219,6 +248,32 @@ gw_status gw_fisher(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
 gw_status gw_fisher_inverse(gw_ctx *ctx, const double *fisher, int64_t n, int n_par,
                             double cond_max, double *cov, double *cond, double *inv_err,
                             int32_t *status, void *stream);
+
+/* Precision refinement of a mixed-precision pass (the conditioning check of
+ * Sec. 4.1 applied to the precision of the Fisher matrix).  The mixed path's
+ * Fisher matrix carries an elementwise error of ~1e-7 of sqrt(Gamma_ii
+ * Gamma_jj) (FP32 patterns, amplitudes and tangents), which Gamma^-1 amplifies
+ * by up to the condition number; the FP64 path's error is ~1e-14.  After
+ * gw_fisher(GW_MIXED) and gw_fisher_inverse on the same events, every event i
+ * with status[i] == 0 whose inversion failed (inv_status NOT_PD or NONFINITE)
+ * or whose condition number cond[i] exceeds cond_th (or is NaN) is recomputed
+ * by the FP64 path (Fisher pass with the fused SNR VJP when grad_snr is given,
+ * then the Cholesky inversion with cond_max) and its entries of fisher, snr,
+ * status, grad_params, cov, cond, inv_err and inv_status are overwritten; the
+ * other events are left untouched.  The refined events' results equal those of
+ * gw_fisher(GW_FP64) + gw_fisher_inverse bit for bit.
+ * DEVICE in/out (layouts of gw_fisher and gw_fisher_inverse, n = cat->n):
+ * fisher, status, cov, cond, inv_status (required); snr, inv_err (or NULL);
+ * grad_snr [n] and grad_params [n_par][n] (both or neither).  DEVICE out:
+ * refined [n] (or NULL), 1 for the recomputed events.  HOST out: *n_refined
+ * (or NULL).  Reads back the number of selected events (a synchronisation of
+ * `stream`).  A cond_th of 1e7 keeps the mixed events' sqrt(diag C) within
+ * 1e-3 of FP64 on the synthetic catalogs.  No counterpart in the paper. */
+gw_status gw_fisher_refine(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, int n_par,
+                           double cond_th, double cond_max, double *fisher, double *snr,
+                           int32_t *status, const double *grad_snr, double *grad_params,
+                           double *cov, double *cond, double *inv_err, int32_t *inv_status,
+                           uint8_t *refined, int64_t *n_refined, void *stream);
 
 /* Vector-Jacobian product of the network SNR (derivatives w.r.t. the event's
  * n_par Fisher parameters, same order):

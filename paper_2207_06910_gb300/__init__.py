@@ -43,8 +43,12 @@ class gw_detector(ctypes.Structure):
 
 class gw_psd(ctypes.Structure):
     _fields_ = [("f0", ctypes.c_double), ("scale", ctypes.c_double), ("nterm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("coef", ctypes.c_double * 4),
-                ("pw", ctypes.c_double * 4)]
+                ("kind", ctypes.c_int32), ("coef", ctypes.c_double * 4),
+                ("pw", ctypes.c_double * 4), ("table_f", _P), ("table_s", _P),
+                ("n_table", ctypes.c_int32), ("is_asd", ctypes.c_int32)]
+
+
+GW_PSD_POWER_SUM, GW_PSD_TABLE = 0, 1
 
 
 class gw_network(ctypes.Structure):
@@ -57,7 +61,8 @@ EXPORTS = ("gw_create", "gw_destroy", "gw_last_error", "gw_abi_version", "gw_pre
            "gw_snr", "gw_fisher", "gw_fisher_inverse", "gw_snr_vjp", "gw_logdet_vjp_detangles",
            "gw_set_profiling", "gw_point_kernel_ms", "gw_fisher_noalloc", "gw_reserve",
            "gw_select_snr", "gw_fisher_eig", "gw_covariance", "gw_packed_submatrix",
-           "gw_sky_area", "gw_strain", "gw_perturb_fisher", "gw_logdet_vjp_detangles_masked")
+           "gw_sky_area", "gw_strain", "gw_perturb_fisher", "gw_logdet_vjp_detangles_masked",
+           "gw_fma_rate", "gw_fisher_refine")
 
 _lib = None
 
@@ -105,6 +110,10 @@ def load_library(path: str | None = None):
     lib.gw_perturb_fisher.argtypes = [_P, _P, i64, ctypes.c_int, d, _P, _P, _P]
     lib.gw_sky_area.argtypes = [_P, _P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, d,
                                 ctypes.c_int, _P, _P]
+    lib.gw_fisher_refine.argtypes = [_P, C, N, ctypes.c_int, d, d] + [_P] * 10 + [
+        ctypes.POINTER(i64), _P]
+    lib.gw_fma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(d), ctypes.POINTER(d),
+                                ctypes.POINTER(d), _P]
     lib.gw_set_profiling.argtypes = [_P, ctypes.c_int]
     lib.gw_point_kernel_ms.argtypes = [_P]
     lib.gw_point_kernel_ms.restype = ctypes.c_double
@@ -156,6 +165,20 @@ def gw_set_profiling(enable: bool = True) -> None:
 def gw_point_kernel_ms() -> float:
     """Duration of the last point-loop kernel (ms), -1 if none recorded."""
     return load_library().gw_point_kernel_ms(context())
+
+
+def gw_fma_rate(fp64: bool, iters: int | None = None, stream=None) -> dict:
+    """Measured FMA throughput of the FP64 or FP32 pipe of the current device:
+    {'fma_per_clk_sm', 'fma_per_s', 'sm_mhz', 'sms'}."""
+    if iters is None:
+        iters = 4096 if fp64 else 65536
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = load_library().gw_fma_rate(int(bool(fp64)), int(iters), ctypes.byref(a), ctypes.byref(b),
+                                    ctypes.byref(c), _stream(stream))
+    if st != 0:
+        raise GWError(f"gw_fma_rate failed with status {st}")
+    return {"fma_per_clk_sm": a.value, "fma_per_s": b.value, "sm_mhz": c.value,
+            "sms": torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count}
 
 
 def _check(st: int, ctx) -> None:
@@ -237,12 +260,24 @@ class Catalog:
 
 
 class Network:
-    """Host-side detector network (see gw_network in include/gwfish.h)."""
+    """Host-side detector network (see gw_network in include/gwfish.h).
 
-    def __init__(self, det, psd, rotation: int):
+    PSD rows are ``f0, scale, nterm, c0..c3, p0..p3`` (a power sum); a row with
+    nterm = -(k+1) is tabulated noise curve k of ``tables``, a list of
+    (f, values, is_asd) with f and values 1-D float64 arrays (numpy or CUDA
+    tensors, copied to the device), times the row's scale."""
+
+    def __init__(self, det, psd, rotation: int, tables=None, device="cuda"):
         det = np.asarray(det, dtype=np.float64).reshape(-1, 6)
         psd = np.asarray(psd, dtype=np.float64).reshape(-1, 11)
         self.det_rows, self.psd_rows, self.rotation = det, psd, int(rotation)
+        self.tables = []
+        for f, v, asd in (tables or []):
+            f = torch.as_tensor(f, dtype=torch.float64, device=device).contiguous()
+            v = torch.as_tensor(v, dtype=torch.float64, device=device).contiguous()
+            if f.dim() != 1 or f.shape != v.shape:
+                raise ValueError("a PSD table needs 1-D frequency and value arrays of one length")
+            self.tables.append((f, v, bool(asd)))
         self._dets = (gw_detector * len(det))()
         for i, r in enumerate(det):
             self._dets[i] = gw_detector(r[0], r[1], r[2], r[3], int(r[4]), int(r[5]))
@@ -250,6 +285,14 @@ class Network:
         for i, r in enumerate(psd):
             p = gw_psd()
             p.f0, p.scale, p.nterm = r[0], r[1], int(r[2])
+            if p.nterm < 0:
+                k = -p.nterm - 1
+                if k >= len(self.tables):
+                    raise ValueError(f"psd row {i} reads table {k}; {len(self.tables)} given")
+                f, v, asd = self.tables[k]
+                p.kind, p.nterm = GW_PSD_TABLE, 0
+                p.table_f, p.table_s = _P(f.data_ptr()), _P(v.data_ptr())
+                p.n_table, p.is_asd = int(f.numel()), int(asd)
             for j in range(4):
                 p.coef[j] = r[3 + j]
                 p.pw[j] = r[7 + j]
@@ -263,7 +306,7 @@ class Network:
     def with_gamma(self, d: int, gamma: float) -> "Network":
         det = self.det_rows.copy()
         det[d, 2] = gamma
-        return Network(det, self.psd_rows, self.rotation)
+        return Network(det, self.psd_rows, self.rotation, self.tables)
 
 
 def n_packed(n_par: int) -> int:
@@ -396,6 +439,30 @@ def gw_fisher_inverse(fisher: torch.Tensor, n_par: int, cond_max=1e50, stream=No
                                           _ptr(cond), _ptr(err), _ptr(status), _stream(stream))
     _check(st, ctx)
     return cov, cond, err, status
+
+
+REFINE_COND = 1e7      # default condition-number threshold of gw_fisher_refine
+
+
+def gw_fisher_refine(cat: Catalog, net: Network, n_par: int, fisher, snr, status, inv,
+                     grad_snr=None, grad_params=None, cond_th=REFINE_COND, cond_max=1e50,
+                     refined=None, stream=None) -> int:
+    """Recompute in FP64, in place, the events of a mixed pass whose inversion
+    failed or whose condition number exceeds ``cond_th``.  ``inv`` is the
+    (cov, cond, inv_err, status) tuple of gw_fisher_inverse; ``refined`` an
+    optional uint8 [n] output.  Returns the number of refined events."""
+    ctx = context()
+    cov, cond, err, sti = inv
+    c = cat.struct()
+    cnt = ctypes.c_int64(0)
+    st = load_library().gw_fisher_refine(
+        ctx, ctypes.byref(c), ctypes.byref(net.net), n_par, float(cond_th), float(cond_max),
+        _ptr(fisher), _ptr(snr), _ptr(status),
+        _ptr(grad_snr.contiguous() if grad_snr is not None else None), _ptr(grad_params),
+        _ptr(cov), _ptr(cond), _ptr(err), _ptr(sti), _ptr(refined), ctypes.byref(cnt),
+        _stream(stream))
+    _check(st, ctx)
+    return int(cnt.value)
 
 
 def gw_snr_vjp(cat: Catalog, net: Network, n_par: int, grad_snr: torch.Tensor, prec=GW_FP64,

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgwfish.so")
 SOURCES = ["gw_api.cu", "gw_setup.cu", "gw_points_fp64.cu", "gw_points_mixed.cu", "gw_noalloc.cu",
-           "gw_covtools.cu", "gw_strain.cu"]
+           "gw_covtools.cu", "gw_strain.cu", "gw_probe.cu",
+           "gw_refine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

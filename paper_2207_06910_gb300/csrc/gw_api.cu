@@ -27,6 +27,19 @@ struct gw_ctx {
     double *partial = nullptr;  size_t partial_cap = 0;
     double *xsums = nullptr;    size_t xsums_cap = 0;   // mixed SNR-gradient sums [6][n]
     double *snr_tmp = nullptr;  size_t snr_tmp_cap = 0;
+    PsdSeg *psd_seg = nullptr;  size_t psd_seg_cap = 0;   // tabulated PSDs, FP64
+    float4 *psd_seg_f = nullptr; size_t psd_seg_f_cap = 0;   // and the FP32 pairs
+    // gw_fisher_refine: selection and the FP64 results of the refined events
+    int64_t *ref_flag = nullptr;  size_t ref_flag_cap = 0;
+    int64_t *ref_off = nullptr;   size_t ref_off_cap = 0;
+    int64_t *ref_scan = nullptr;  size_t ref_scan_cap = 0;
+    int64_t *ref_pos = nullptr;   size_t ref_pos_cap = 0;
+    int64_t *ref_rows = nullptr;  size_t ref_rows_cap = 0;
+    double *ref_F = nullptr;      size_t ref_F_cap = 0;
+    double *ref_C = nullptr;      size_t ref_C_cap = 0;
+    double *ref_g = nullptr;      size_t ref_g_cap = 0;
+    double *ref_v = nullptr;      size_t ref_v_cap = 0;     // snr, grad_snr, cond, inv_err
+    int32_t *ref_st = nullptr;    size_t ref_st_cap = 0;    // status, inverse status
     int64_t *h_total = nullptr;   // pinned
     int64_t item_cap = 0;       // > 0: asynchronous mode with this many work items
     int profiling = 0;
@@ -88,11 +101,33 @@ gw_status gwi_build_net(gw_ctx *ctx, const gw_network *net, DevNet &d)
     d.n_psd = net->n_psd;
     d.rotation = net->earth_rotation ? 1 : 0;
     d.n_det = net->n_det;
+    // reference scale of the FP32 path: the first power-sum PSD's scale (S_n
+    // ~ 1e-49 is below the FP32 range), else the first PSD's; tabulated PSDs
+    // enter the FP32 path as ln S - ln(reference), never as S itself
+    double scale_ref = 0.0;
+    for (int p = 0; p < net->n_psd && scale_ref == 0.0; p++)
+        if (net->psd[p].kind == GW_PSD_POWER_SUM) scale_ref = net->psd[p].scale;
+    if (scale_ref == 0.0) scale_ref = net->psd[0].scale;
+    int seg = 0;
     for (int p = 0; p < net->n_psd; p++) {
         const gw_psd &P = net->psd[p];
-        if (!(P.f0 > 0) || !std::isfinite(P.scale) || P.scale <= 0 || P.nterm < 1 ||
-            P.nterm > MAX_TERM)
-            return fail(ctx, GW_EINVAL, "psd %d: need f0 > 0, scale > 0, 1 <= nterm <= 4", p);
+        if (!std::isfinite(P.scale) || P.scale <= 0)
+            return fail(ctx, GW_EINVAL, "psd %d: need scale > 0", p);
+        d.psd_kind[p] = P.kind;
+        if (P.kind == GW_PSD_TABLE) {
+            if (!P.table_f || !P.table_s || P.n_table < 2 || P.n_table > (1 << 20) ||
+                (P.is_asd != 0 && P.is_asd != 1))
+                return fail(ctx, GW_EINVAL, "psd %d: a table needs table_f, table_s, "
+                            "2 <= n_table <= 2^20 and is_asd 0 or 1", p);
+            d.psd_seg0[p] = seg;
+            d.psd_nseg[p] = P.n_table - 1;
+            seg += P.n_table - 1;
+            continue;
+        }
+        if (P.kind != GW_PSD_POWER_SUM)
+            return fail(ctx, GW_EINVAL, "psd %d: kind %d (0 = power sum, 1 = table)", p, P.kind);
+        if (!(P.f0 > 0) || P.nterm < 1 || P.nterm > MAX_TERM)
+            return fail(ctx, GW_EINVAL, "psd %d: need f0 > 0, 1 <= nterm <= 4", p);
         d.psd_f0[p] = P.f0;
         d.psd_inv_f0[p] = 1.0 / P.f0;
         d.psd_nterm[p] = P.nterm;
@@ -104,12 +139,13 @@ gw_status gwi_build_net(gw_ctx *ctx, const gw_network *net, DevNet &d)
             if (!std::isfinite(P.coef[j]) || P.coef[j] < 0)
                 return fail(ctx, GW_EINVAL, "psd %d term %d: coefficient must be >= 0", p, j);
             d.psd_coef[p][j] = P.scale * P.coef[j];
-            d.psd_coef_f[p][j] = (float)(P.scale / net->psd[0].scale * P.coef[j]);
+            d.psd_coef_f[p][j] = (float)(P.scale / scale_ref * P.coef[j]);
             d.psd_pow[p][j] = (int)std::nearbyint(P.pw[j]);
         }
         d.psd_inv_f0_f[p] = (float)(1.0 / P.f0);
     }
-    d.inv_sqrt_scale_ref = 1.0 / std::sqrt(net->psd[0].scale);
+    d.inv_sqrt_scale_ref = 1.0 / std::sqrt(scale_ref);
+    d.ln_scale_ref = std::log(scale_ref);
     int ni = 0, na = 0;
     for (int s = 0; s < net->n_det; s++) {
         const gw_detector &D = net->det[s];
@@ -162,6 +198,34 @@ gw_status gwi_build_net(gw_ctx *ctx, const gw_network *net, DevNet &d)
     d.n_ifo = ni;
     d.n_arm = na;
     return GW_OK;
+}
+
+// segments of the network's tabulated PSDs (0: none)
+int64_t gwi_psd_segments(const DevNet &d)
+{
+    int64_t n = 0;
+    for (int p = 0; p < d.n_psd; p++)
+        if (d.psd_kind[p] == GW_PSD_TABLE) n += d.psd_nseg[p];
+    return n;
+}
+
+// the device log tables of the network's tabulated PSDs, built into seg
+// (FP64, gwi_psd_segments entries) and segf (two per segment; may be null
+// when the mixed path is not used)
+cudaError_t gwi_prep_psd(const gw_network *net, DevNet &d, PsdSeg *seg, float4 *segf,
+                         cudaStream_t s)
+{
+    d.psd_seg = seg;
+    d.psd_seg_f = segf;
+    for (int p = 0; p < d.n_psd; p++) {
+        if (d.psd_kind[p] != GW_PSD_TABLE) continue;
+        const gw_psd &P = net->psd[p];
+        cudaError_t e = launch_psd_table(P.table_f, P.table_s, d.psd_nseg[p], P.is_asd,
+                                         std::log(P.scale), d.ln_scale_ref, seg + d.psd_seg0[p],
+                                         segf ? segf + 2 * d.psd_seg0[p] : nullptr, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 gw_status gwi_check_cat(gw_ctx *ctx, const gw_catalog *c, int np)
@@ -253,6 +317,11 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
         if ((st = ensure(ctx, ctx->status, ctx->status_cap, (size_t)n))) return st;
         status = ctx->status;
     }
+    if (const int64_t nseg = gwi_psd_segments(dn)) {
+        if ((st = ensure(ctx, ctx->psd_seg, ctx->psd_seg_cap, (size_t)nseg))) return st;
+        if ((st = ensure(ctx, ctx->psd_seg_f, ctx->psd_seg_f_cap, (size_t)2 * nseg))) return st;
+        CK(gwi_prep_psd(net, dn, ctx->psd_seg, ctx->psd_seg_f, s));
+    }
     const DevCat dc = gwi_dev_cat(cat);
     CK(launch_event_setup(dc, dn, np, ctx->evc, ctx->sitec, mixed ? ctx->sitec_f : nullptr,
                           mixed ? ctx->evc_f : nullptr, status, ctx->counts, s));
@@ -304,7 +373,7 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
 
 extern "C" {
 
-int gw_abi_version(void) { return 4; }
+int gw_abi_version(void) { return 5; }
 
 gw_status gw_create(gw_ctx **out, int device)
 {
@@ -338,6 +407,18 @@ gw_status gw_destroy(gw_ctx *ctx)
     cudaFree(ctx->partial);
     cudaFree(ctx->xsums);
     cudaFree(ctx->snr_tmp);
+    cudaFree(ctx->psd_seg);
+    cudaFree(ctx->psd_seg_f);
+    cudaFree(ctx->ref_flag);
+    cudaFree(ctx->ref_off);
+    cudaFree(ctx->ref_scan);
+    cudaFree(ctx->ref_pos);
+    cudaFree(ctx->ref_rows);
+    cudaFree(ctx->ref_F);
+    cudaFree(ctx->ref_C);
+    cudaFree(ctx->ref_g);
+    cudaFree(ctx->ref_v);
+    cudaFree(ctx->ref_st);
     cudaFreeHost(ctx->h_total);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -614,6 +695,71 @@ gw_status gw_fisher(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, g
     if (!fisher && cat->n > 0) return fail(ctx, GW_EINVAL, "fisher: output is null");
     return run_points(ctx, cat, net, prec, MODE_FISHER, n_par, status, snr, nullptr, fisher,
                       grad_snr, grad_params, nullptr, nullptr, stream);
+}
+
+gw_status gw_fisher_refine(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, int n_par,
+                           double cond_th, double cond_max, double *fisher, double *snr,
+                           int32_t *status, const double *grad_snr, double *grad_params,
+                           double *cov, double *cond, double *inv_err, int32_t *inv_status,
+                           uint8_t *refined, int64_t *n_refined, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (n_refined) *n_refined = 0;
+    if (!cat) return fail(ctx, GW_EINVAL, "catalog: null");
+    if (n_par != 9 && n_par != 11) return fail(ctx, GW_EINVAL, "n_par must be 9 or 11");
+    if (std::isnan(cond_th)) return fail(ctx, GW_EINVAL, "refine: cond_th is NaN");
+    const int64_t n = cat->n;
+    if (n == 0) return GW_OK;
+    if (!fisher || !status || !cov || !cond || !inv_status)
+        return fail(ctx, GW_EINVAL, "refine: fisher, status, cov, cond and inv_status are required");
+    if ((grad_params != nullptr) != (grad_snr != nullptr))
+        return fail(ctx, GW_EINVAL, "refine: grad_params and grad_snr go together");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    gw_status st;
+    if ((st = ensure(ctx, ctx->ref_flag, ctx->ref_flag_cap, (size_t)n))) return st;
+    if ((st = ensure(ctx, ctx->ref_off, ctx->ref_off_cap, (size_t)n + 1))) return st;
+    if ((st = ensure(ctx, ctx->ref_scan, ctx->ref_scan_cap, scan_tmp_size(n)))) return st;
+    if ((st = ensure(ctx, ctx->ref_pos, ctx->ref_pos_cap, (size_t)n))) return st;
+    if ((st = ensure(ctx, ctx->ref_rows, ctx->ref_rows_cap, (size_t)n))) return st;
+    CK(launch_refine_select(n, cond_th, status, inv_status, cond, cat->sel, ctx->ref_flag,
+                            ctx->ref_off, ctx->ref_scan, ctx->ref_pos, ctx->ref_rows, refined, s));
+    CK(cudaMemcpyAsync(ctx->h_total, ctx->ref_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t m = *ctx->h_total;
+    if (n_refined) *n_refined = m;
+    if (m == 0) return GW_OK;
+    const int npk = n_par * (n_par + 1) / 2;
+    if ((st = ensure(ctx, ctx->ref_F, ctx->ref_F_cap, (size_t)npk * m))) return st;
+    if ((st = ensure(ctx, ctx->ref_C, ctx->ref_C_cap, (size_t)npk * m))) return st;
+    if ((st = ensure(ctx, ctx->ref_g, ctx->ref_g_cap, (size_t)n_par * m))) return st;
+    if ((st = ensure(ctx, ctx->ref_v, ctx->ref_v_cap, (size_t)4 * m))) return st;
+    if ((st = ensure(ctx, ctx->ref_st, ctx->ref_st_cap, (size_t)2 * m))) return st;
+    double *r_snr = ctx->ref_v, *r_gin = ctx->ref_v + m, *r_cond = ctx->ref_v + 2 * m,
+           *r_err = ctx->ref_v + 3 * m;
+    int32_t *r_st = ctx->ref_st, *r_sti = ctx->ref_st + m;
+    // the flagged events as a catalog of their own (rows through the call's
+    // selection), FP64 Fisher pass and inversion
+    gw_catalog sub = *cat;
+    sub.n = m;
+    sub.sel = ctx->ref_rows;
+    if (grad_snr) CK(launch_gather(m, ctx->ref_pos, grad_snr, r_gin, s));
+    if ((st = run_points(ctx, &sub, net, GW_FP64, MODE_FISHER, n_par, r_st, r_snr, nullptr,
+                         ctx->ref_F, grad_snr ? r_gin : nullptr, grad_snr ? ctx->ref_g : nullptr,
+                         nullptr, nullptr, stream)))
+        return st;
+    CK(launch_invert(ctx->ref_F, m, n_par, cond_max, ctx->ref_C, r_cond, r_err, r_sti, s));
+    // written back in place, at the call's indices of the flagged events
+    const int64_t *pos = ctx->ref_pos;
+    CK(launch_scatter_f64(m, n, npk, pos, ctx->ref_F, fisher, s));
+    CK(launch_scatter_f64(m, n, npk, pos, ctx->ref_C, cov, s));
+    CK(launch_scatter_f64(m, n, 1, pos, r_snr, snr, s));
+    CK(launch_scatter_f64(m, n, 1, pos, r_cond, cond, s));
+    CK(launch_scatter_f64(m, n, 1, pos, r_err, inv_err, s));
+    if (grad_params) CK(launch_scatter_f64(m, n, n_par, pos, ctx->ref_g, grad_params, s));
+    CK(launch_scatter_i32(m, n, pos, r_st, status, s));
+    CK(launch_scatter_i32(m, n, pos, r_sti, inv_status, s));
+    return GW_OK;
 }
 
 gw_status gw_fisher_inverse(gw_ctx *ctx, const double *fisher, int64_t n, int n_par,

@@ -38,6 +38,11 @@ constexpr double OMEGA_E = TWO_PI / T_SIDEREAL;
 constexpr double H0_KMS_MPC = 70.0;
 constexpr double C_KMS = 299792.458;
 
+// one segment of a tabulated PSD's log table (FP64 path)
+struct __align__(32) PsdSeg {
+    double lnf, lns, slope, lnf1;   // ln f_j, ln S_j, d ln S / d ln f, ln f_j+1
+};
+
 struct DevNet {
     int n_site, n_ifo, n_psd, rotation, n_det;
     int pad_;
@@ -62,6 +67,15 @@ struct DevNet {
     float psd_coef_f[MAX_PSD][MAX_TERM];
     float psd_inv_f0_f[MAX_PSD];
     double inv_sqrt_scale_ref;
+    double ln_scale_ref;                  // ln of the reference scale above
+    // tabulated PSDs: segments psd_seg0[p] .. psd_seg0[p] + psd_nseg[p] - 1 of
+    // psd_seg (FP64: ln f_j, ln S_j, slope, ln f_j+1, with S = scale x table)
+    // and psd_seg_f (mixed path: two float4 per segment, ln f_j and
+    // ln S_j - ln_scale_ref as double-float pairs, then slope, ln f_j+1 as a pair)
+    int psd_kind[MAX_PSD];
+    int psd_seg0[MAX_PSD], psd_nseg[MAX_PSD];
+    const PsdSeg *psd_seg;
+    const float4 *psd_seg_f;
 };
 
 // ---- per-event constants (FP64), row of EVC doubles per event ----------

@@ -19,6 +19,14 @@ inline int current_device()
     return cudaGetDevice(&dev) == cudaSuccess ? dev : 0;
 }
 
+// the network has a tabulated PSD (the point kernels' table instantiation)
+inline bool has_psd_table(const DevNet &net)
+{
+    for (int p = 0; p < net.n_psd; p++)
+        if (net.psd_kind[p] == 1) return true;
+    return false;
+}
+
 // one bit per device: the kernel's attribute has been set there
 struct PerDeviceOnce {
     std::atomic<unsigned long long> bits{0};
@@ -151,6 +159,23 @@ cudaError_t launch_snr_grad_from_fisher(int64_t n, int np, bool mixed, int rot,
                                         const double *xsums, const double *evc,
                                         const int32_t *status, const double *grad_snr,
                                         double *grad_params, cudaStream_t s);
+
+// log table of a tabulated PSD (gw_setup.cu): nseg segments of (f, S) pairs
+cudaError_t launch_psd_table(const double *f, const double *S, int64_t nseg, int is_asd,
+                             double ln_scale, double ln_ref, PsdSeg *seg, float4 *segf,
+                             cudaStream_t s);
+
+// precision refinement (gw_refine.cu)
+cudaError_t launch_refine_select(int64_t n, double cond_th, const int32_t *status,
+                                 const int32_t *inv_status, const double *cond, const int64_t *sel,
+                                 int64_t *flag, int64_t *off, int64_t *scan_tmp, int64_t *pos,
+                                 int64_t *rows, uint8_t *refined, cudaStream_t s);
+cudaError_t launch_gather(int64_t m, const int64_t *pos, const double *in, double *out,
+                          cudaStream_t s);
+cudaError_t launch_scatter_f64(int64_t m, int64_t n, int rows, const int64_t *pos, const double *in,
+                               double *out, cudaStream_t s);
+cudaError_t launch_scatter_i32(int64_t m, int64_t n, const int64_t *pos, const int32_t *in,
+                               int32_t *out, cudaStream_t s);
 
 cudaError_t launch_invert(const double *fisher, int64_t n, int np, double cond_max, double *cov,
                           double *cond, double *inv_err, int32_t *status, cudaStream_t s);

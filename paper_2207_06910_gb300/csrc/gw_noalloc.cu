@@ -28,8 +28,11 @@
 
 using namespace gw;
 
-// helpers of gw_api.cu (network expansion, catalog checks)
+// helpers of gw_api.cu (network expansion, tabulated PSDs, catalog checks)
 gw_status gwi_build_net(gw_ctx *ctx, const gw_network *net, DevNet &d);
+int64_t gwi_psd_segments(const DevNet &d);
+cudaError_t gwi_prep_psd(const gw_network *net, DevNet &d, PsdSeg *seg, float4 *segf,
+                         cudaStream_t s);
 gw_status gwi_check_cat(gw_ctx *ctx, const gw_catalog *c, int np);
 DevCat gwi_dev_cat(const gw_catalog *c);
 
@@ -100,9 +103,13 @@ extern "C" gw_status gw_fisher_noalloc(const gw_catalog *cat, const gw_network *
     int64_t *counts = c.take<int64_t>((size_t)n);
     int64_t *off = c.take<int64_t>((size_t)n + 1);
     int64_t *scan = c.take<int64_t>(scan_tmp_size(n));
+    const int64_t nseg = gwi_psd_segments(dn);
+    PsdSeg *pseg = nseg ? c.take<PsdSeg>((size_t)nseg) : nullptr;
+    float4 *psegf = (nseg && mixed) ? c.take<float4>((size_t)2 * nseg) : nullptr;
     // the per-item partial sums take the rest; at least one item per event
     if (c.used + align256((size_t)n * nacc * sizeof(double)) > SCRATCH_BYTES) return GW_ETOOLARGE;
 
+    if (nseg && gwi_prep_psd(net, dn, pseg, psegf, s) != cudaSuccess) return GW_ECUDA;
     const DevCat dc = gwi_dev_cat(cat);
     if (launch_event_setup(dc, dn, n_par, evc, sitec, sitec_f, evc_f, status, counts, s) !=
             cudaSuccess ||

@@ -149,7 +149,29 @@ __device__ __forceinline__ void tangents(const Pat &p, double Acp, double Acx, d
     }
 }
 
-template <int MODE, int NP, bool ROT>
+// ln S_n at ln f for tabulated PSD p: the segment j with ln f_j <= ln f <=
+// ln f_j+1, found by bisection the first time and then by walking forward (a
+// lane's grid points increase); +inf (zero weight) outside the table
+__device__ __forceinline__ double psd_table_lns(const DevNet &net, int p, double x, int &seg)
+{
+    const PsdSeg *T = net.psd_seg + net.psd_seg0[p];
+    const int n = net.psd_nseg[p];
+    if (isnan(__ldg(&T[0].lns))) return NAN;   // a table that breaks its rules
+    if (!(x >= __ldg(&T[0].lnf)) || !(x <= __ldg(&T[n - 1].lnf1))) return INFINITY;
+    if (seg < 0 || x < __ldg(&T[seg].lnf)) {
+        int lo = 0, hi = n - 1;          // largest j with ln f_j <= x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&T[mid].lnf) <= x) lo = mid;
+            else hi = mid - 1;
+        }
+        seg = lo;
+    }
+    while (seg < n - 1 && x > __ldg(&T[seg].lnf1)) seg++;
+    return fma(__ldg(&T[seg].slope), x - __ldg(&T[seg].lnf), __ldg(&T[seg].lns));
+}
+
+template <int MODE, int NP, bool ROT, bool TAB>
 __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
 {
     constexpr int NACC = NAccOf<MODE, NP>::value;
@@ -208,6 +230,9 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
             const double cp = E[EV_CP], cx = E[EV_CX], dcp = E[EV_DCP], dcx = E[EV_DCX];
             const double c2p = E[EV_C2PSI], s2p = E[EV_S2PSI];
             const double aMc = E[EV_AMC], invdL = E[EV_INVDL];
+            int tseg[MAX_PSD];   // current segment of each tabulated PSD (-1: not found yet)
+#pragma unroll
+            for (int p = 0; p < MAX_PSD; p++) tseg[p] = -1;
 
 #pragma unroll 1
             for (; k < ke; k += GROUP) {
@@ -270,7 +295,13 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
                 double Wp[MAX_PSD];
 #pragma unroll
                 for (int p = 0; p < MAX_PSD; p++) {
-                    if (p < net.n_psd) {
+                    if (TAB && p < net.n_psd && net.psd_kind[p] == 1) {
+                        // tabulated PSD: ln S on the log-log segment holding ln f
+                        // (blind outside the table: zero weight)
+                        const double lnf_k = fma((double)k, lnr, E[EV_LNF0]);
+                        const double lns = psd_table_lns(net, p, lnf_k, tseg[p]);
+                        Wp[p] = Aamp * sqrt(4.0 * w) * exp(-0.5 * lns);
+                    } else if (p < net.n_psd) {
                         const double x = f * net.psd_inv_f0[p];
                         const double xi = net.psd_f0[p] * pim * vi3;
                         double S = 0.0;
@@ -428,25 +459,34 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
     }
 }
 
-template <int MODE, int NP, bool ROT>
+template <int MODE, int NP, bool ROT, bool TAB>
 cudaError_t launch_one(const PointArgs &a, cudaStream_t s)
 {
     constexpr int NACC = NAccOf<MODE, NP>::value;
     const size_t smem = ((size_t)4 * GROUPS_PER_WARP * NACC * (GROUP + 1) +
                          (size_t)4 * GROUPS_PER_WARP * EVC) * sizeof(double);
     static PerDeviceOnce attr;
-    cudaError_t err = set_smem_once(attr, k_points_fp64<MODE, NP, ROT>, smem);
+    cudaError_t err = set_smem_once(attr, k_points_fp64<MODE, NP, ROT, TAB>, smem);
     if (err != cudaSuccess) return err;
     if (a.n_items <= 0) return cudaSuccess;
-    k_points_fp64<MODE, NP, ROT><<<points_grid_size(2), 128, smem, s>>>(a);
+    k_points_fp64<MODE, NP, ROT, TAB><<<points_grid_size(2), 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+template <int MODE, bool TAB>
+cudaError_t launch_mode_t(int np, int rot, const PointArgs &a, cudaStream_t s)
+{
+    if (np == 9)
+        return rot ? launch_one<MODE, 9, true, TAB>(a, s) : launch_one<MODE, 9, false, TAB>(a, s);
+    return rot ? launch_one<MODE, 11, true, TAB>(a, s) : launch_one<MODE, 11, false, TAB>(a, s);
+}
+
+// networks with a tabulated PSD run the instantiation that evaluates tables
 template <int MODE>
 cudaError_t launch_mode(int np, int rot, const PointArgs &a, cudaStream_t s)
 {
-    if (np == 9) return rot ? launch_one<MODE, 9, true>(a, s) : launch_one<MODE, 9, false>(a, s);
-    return rot ? launch_one<MODE, 11, true>(a, s) : launch_one<MODE, 11, false>(a, s);
+    return has_psd_table(a.net) ? launch_mode_t<MODE, true>(np, rot, a, s)
+                                : launch_mode_t<MODE, false>(np, rot, a, s);
 }
 
 }  // namespace

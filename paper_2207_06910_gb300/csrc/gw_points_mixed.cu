@@ -294,7 +294,47 @@ __device__ __forceinline__ void tangents_f(const PatF &p, float Acp, float Acx, 
     }
 }
 
-template <int MODE, int NP, bool ROT>
+// (ln S_n - ln scale_ref) at ln f = x (double-float) for tabulated PSD p, as a
+// double-float: the log-log segment holding x, found by bisection the first
+// time and then by walking forward (a lane's grid points increase); hi = +inf
+// (zero weight) outside the table, NaN for a table that breaks its rules
+__device__ __forceinline__ bool df_lt(DF a, float ah, float al)
+{
+    return a.hi < ah || (a.hi == ah && a.lo < al);
+}
+
+__device__ __forceinline__ DF psd_table_lns_df(const DevNet &net, int p, DF x, int &seg)
+{
+    const float4 *T = net.psd_seg_f + 2 * net.psd_seg0[p];
+    const int n = net.psd_nseg[p];
+    const float4 t0 = __ldg(&T[0]);
+    if (isnan(t0.z)) return DF{NAN, 0.0f};
+    const float4 tl = __ldg(&T[2 * (n - 1) + 1]);
+    if (df_lt(x, t0.x, t0.y) || (x.hi > tl.y || (x.hi == tl.y && x.lo > tl.z)))
+        return DF{INFINITY, 0.0f};
+    if (seg < 0 || df_lt(x, __ldg(&T[2 * seg].x), __ldg(&T[2 * seg].y))) {
+        int lo = 0, hi = n - 1;          // largest j with ln f_j <= x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            const float4 tm = __ldg(&T[2 * mid]);
+            if (!df_lt(x, tm.x, tm.y)) lo = mid;
+            else hi = mid - 1;
+        }
+        seg = lo;
+    }
+    for (;;) {
+        if (seg >= n - 1) break;
+        const float4 tb = __ldg(&T[2 * seg + 1]);
+        if (!(x.hi > tb.y || (x.hi == tb.y && x.lo > tb.z))) break;
+        seg++;
+    }
+    const float4 a = __ldg(&T[2 * seg]), b = __ldg(&T[2 * seg + 1]);
+    const DF dx = df_add(x, DF{-a.x, -a.y});
+    const DF y = two_sum(a.z, b.x * df_round(dx));
+    return DF{y.hi, y.lo + a.w};
+}
+
+template <int MODE, int NP, bool ROT, bool TAB>
 __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
 {
     constexpr int NACC = NAccM<MODE, NP>::value;
@@ -366,6 +406,9 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
             // amplitude A0 f^(-7/6) as a double-float recurrence (an FP32 one
             // would drift by ~1e-6 over a lane's points)
             DF Aamp = df_from_double(E[EV_A0] * net.inv_sqrt_scale_ref * exp(-7.0 / 6.0 * lnf));
+            int tseg[MAX_PSD];   // current segment of each tabulated PSD (-1: not found yet)
+#pragma unroll
+            for (int p = 0; p < MAX_PSD; p++) tseg[p] = -1;
 #define SC(slot) csc[(slot) - EV_WC0]
 
 #pragma unroll 1
@@ -418,7 +461,15 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                 float sig[MAX_PSD];
 #pragma unroll
                 for (int p = 0; p < MAX_PSD; p++) {
-                    if (p < net.n_psd) {
+                    if (TAB && p < net.n_psd && net.psd_kind[p] == 1) {
+                        // tabulated PSD: 4 w / S = 4 w exp(-(ln S - ln S_ref)) relative to
+                        // the reference scale, the exponent as a double-float (S itself
+                        // would leave the FP32 range)
+                        const DF lnf_df = df_add(df_mul(DF{3.0f, 0.0f}, lnv),
+                                                 DF{-SC(EV_LNPIM).x, -SC(EV_LNPIM).y});
+                        const DF y = psd_table_lns_df(net, p, lnf_df, tseg[p]);
+                        sig[p] = Af * sqrtf(4.0f * w) * (expf(-0.5f * y.hi) * (1.0f - 0.5f * y.lo));
+                    } else if (p < net.n_psd) {
                         const float x = ff * net.psd_inv_f0_f[p];
                         const float xi = 1.0f / x;
                         float S = 0.0f;
@@ -617,24 +668,33 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
     }
 }
 
-template <int MODE, int NP, bool ROT>
+template <int MODE, int NP, bool ROT, bool TAB>
 cudaError_t launch_one_m(const PointArgs &a, cudaStream_t s)
 {
     constexpr int NACC = NAccM<MODE, NP>::value;
     const size_t smem = ((size_t)((NACC * 129 + 1) & ~1) + (size_t)4 * GROUPS_PER_WARP * (NCOEF + NSCAL)) * sizeof(float2);
     static PerDeviceOnce attr;
-    cudaError_t err = set_smem_once(attr, k_points_mixed<MODE, NP, ROT>, smem);
+    cudaError_t err = set_smem_once(attr, k_points_mixed<MODE, NP, ROT, TAB>, smem);
     if (err != cudaSuccess) return err;
     if (a.n_items <= 0) return cudaSuccess;
-    k_points_mixed<MODE, NP, ROT><<<points_grid_size(2), 128, smem, s>>>(a);
+    k_points_mixed<MODE, NP, ROT, TAB><<<points_grid_size(2), 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+template <int MODE, bool TAB>
+cudaError_t launch_mode_mt(int np, int rot, const PointArgs &a, cudaStream_t s)
+{
+    if (np == 9)
+        return rot ? launch_one_m<MODE, 9, true, TAB>(a, s) : launch_one_m<MODE, 9, false, TAB>(a, s);
+    return rot ? launch_one_m<MODE, 11, true, TAB>(a, s) : launch_one_m<MODE, 11, false, TAB>(a, s);
+}
+
+// networks with a tabulated PSD run the instantiation that evaluates tables
 template <int MODE>
 cudaError_t launch_mode_m(int np, int rot, const PointArgs &a, cudaStream_t s)
 {
-    if (np == 9) return rot ? launch_one_m<MODE, 9, true>(a, s) : launch_one_m<MODE, 9, false>(a, s);
-    return rot ? launch_one_m<MODE, 11, true>(a, s) : launch_one_m<MODE, 11, false>(a, s);
+    return has_psd_table(a.net) ? launch_mode_mt<MODE, true>(np, rot, a, s)
+                                : launch_mode_mt<MODE, false>(np, rot, a, s);
 }
 
 }  // namespace

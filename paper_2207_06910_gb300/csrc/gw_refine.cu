@@ -1,0 +1,104 @@
+// gw_refine.cu -- kernels of gw_fisher_refine: the events whose mixed-precision
+// covariance is not determined to the mixed path's tolerance are selected by
+// their condition number (Sec. 4.1: the conditioning check of the inversion),
+// recomputed by the FP64 path, and written back in place.
+//
+// Why a condition-number test: the mixed path's Fisher matrix carries an
+// elementwise error of ~1e-7 of sqrt(Gamma_ii Gamma_jj) (FP32 patterns,
+// amplitudes and tangents); Gamma^-1 amplifies an elementwise error by up to
+// the condition number, so above ~1e7 the marginalised errors sqrt(diag C)
+// can move by more than 1e-3.  The FP64 path's elementwise error is ~1e-14
+// and keeps sqrt(diag C) within ~2e-16 kappa of the oracle.
+#include "gw_kernels.cuh"
+
+namespace gw {
+namespace {
+
+constexpr int BS = 256;
+
+// flag[i] = event i (of the call) is refined: its point-loop status is clean
+// and its mixed inversion failed, or its condition number exceeds cond_th;
+// refined[i] (optional) records the decision
+__global__ void k_flag_refine(int64_t n, double cond_th, const int32_t *status,
+                              const int32_t *inv_status, const double *cond, int64_t *flag,
+                              uint8_t *refined)
+{
+    const int64_t i = blockIdx.x * (int64_t)BS + threadIdx.x;
+    if (i >= n) return;
+    const bool inv_bad = (inv_status[i] & (1 | 4)) != 0;   // NOT_PD, NONFINITE
+    const bool f = status[i] == 0 && (inv_bad || !(cond[i] <= cond_th));
+    flag[i] = f ? 1 : 0;
+    if (refined) refined[i] = f ? 1 : 0;
+}
+
+// order-preserving compaction: pos[j] = the call's index of the j-th flagged
+// event, rows[j] = its catalog row (through the call's own selection)
+__global__ void k_compact_flagged(int64_t n, const int64_t *flag, const int64_t *off,
+                                  const int64_t *sel, int64_t *pos, int64_t *rows)
+{
+    const int64_t i = blockIdx.x * (int64_t)BS + threadIdx.x;
+    if (i >= n || !flag[i]) return;
+    const int64_t j = off[i];
+    pos[j] = i;
+    rows[j] = sel ? sel[i] : i;
+}
+
+__global__ void k_gather(int64_t m, const int64_t *pos, const double *in, double *out)
+{
+    const int64_t j = blockIdx.x * (int64_t)BS + threadIdx.x;
+    if (j < m) out[j] = in[pos[j]];
+}
+
+// out[k * n + pos[j]] = in[k * m + j] for k < rows (event-minor arrays)
+template <typename T>
+__global__ void k_scatter(int64_t m, int64_t n, int rows, const int64_t *pos, const T *in, T *out)
+{
+    const int64_t j = blockIdx.x * (int64_t)BS + threadIdx.x;
+    if (j >= m) return;
+    const int64_t i = pos[j];
+    for (int k = 0; k < rows; k++) out[(int64_t)k * n + i] = in[(int64_t)k * m + j];
+}
+
+unsigned blocks(int64_t n) { return (unsigned)((n + BS - 1) / BS); }
+
+}  // namespace
+
+cudaError_t launch_refine_select(int64_t n, double cond_th, const int32_t *status,
+                                 const int32_t *inv_status, const double *cond, const int64_t *sel,
+                                 int64_t *flag, int64_t *off, int64_t *scan_tmp, int64_t *pos,
+                                 int64_t *rows, uint8_t *refined, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_flag_refine<<<blocks(n), BS, 0, s>>>(n, cond_th, status, inv_status, cond, flag, refined);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = launch_scan(flag, n, off, scan_tmp, s)) != cudaSuccess) return e;
+    k_compact_flagged<<<blocks(n), BS, 0, s>>>(n, flag, off, sel, pos, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(int64_t m, const int64_t *pos, const double *in, double *out,
+                          cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_gather<<<blocks(m), BS, 0, s>>>(m, pos, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_f64(int64_t m, int64_t n, int rows, const int64_t *pos, const double *in,
+                               double *out, cudaStream_t s)
+{
+    if (m <= 0 || !out) return cudaSuccess;
+    k_scatter<double><<<blocks(m), BS, 0, s>>>(m, n, rows, pos, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_i32(int64_t m, int64_t n, const int64_t *pos, const int32_t *in,
+                               int32_t *out, cudaStream_t s)
+{
+    if (m <= 0 || !out) return cudaSuccess;
+    k_scatter<int32_t><<<blocks(m), BS, 0, s>>>(m, n, 1, pos, in, out);
+    return cudaGetLastError();
+}
+
+}  // namespace gw

@@ -528,6 +528,50 @@ __global__ void __launch_bounds__(FIN_BS) k_finish(int mode, int np, int n_det, 
     }
 }
 
+// Log table of a tabulated noise curve (Sec. 3.1, the psd_path / is_ASD
+// options): segment j holds ln f_j, ln S_j (S = scale x table value, the value
+// squared for an amplitude spectral density), the slope of ln S over ln f to
+// the next node, and ln f_j+1; the mixed path's copy holds ln f and
+// ln S - ln(reference scale) as double-float pairs.  One block per table: if
+// any entry breaks the table's rules (f > 0 strictly increasing, values > 0,
+// all finite), every segment's ln S is NaN, so every noise weight is NaN.
+__global__ void __launch_bounds__(256) k_psd_table(const double *f, const double *S, int64_t nseg,
+                                                   int is_asd, double ln_scale, double ln_ref,
+                                                   PsdSeg *seg, float4 *segf)
+{
+    int ok = 1;
+    for (int64_t j = threadIdx.x; j < nseg; j += blockDim.x) {
+        const double f0 = f[j], f1 = f[j + 1], s0 = S[j], s1 = S[j + 1];
+        ok &= f0 > 0.0 && f1 > f0 && isfinite(f1) && s0 > 0.0 && s1 > 0.0 && isfinite(s0) &&
+              isfinite(s1);
+    }
+    ok = __syncthreads_and(ok);
+    const double pw = is_asd ? 2.0 : 1.0;
+    for (int64_t j = threadIdx.x; j < nseg; j += blockDim.x) {
+        const double lf0 = log(f[j]), lf1 = log(f[j + 1]);
+        double ls0 = fma(pw, log(S[j]), ln_scale);
+        const double ls1 = fma(pw, log(S[j + 1]), ln_scale);
+        double slope = (ls1 - ls0) / (lf1 - lf0);
+        if (!ok) ls0 = slope = NAN;
+        seg[j] = PsdSeg{lf0, ls0, slope, lf1};
+        if (segf) {
+            const double rel = ls0 - ln_ref;
+            const float a = (float)lf0, b = (float)rel, c = (float)lf1;
+            segf[2 * j] = make_float4(a, (float)(lf0 - (double)a), b, (float)(rel - (double)b));
+            segf[2 * j + 1] = make_float4((float)slope, c, (float)(lf1 - (double)c), 0.0f);
+        }
+    }
+}
+
+cudaError_t launch_psd_table(const double *f, const double *S, int64_t nseg, int is_asd,
+                             double ln_scale, double ln_ref, PsdSeg *seg, float4 *segf,
+                             cudaStream_t s)
+{
+    if (nseg <= 0) return cudaSuccess;
+    k_psd_table<<<1, 256, 0, s>>>(f, S, nseg, is_asd, ln_scale, ln_ref, seg, segf);
+    return cudaGetLastError();
+}
+
 // detection gate (snr_th): flags, then order-preserving compaction after an
 // exclusive scan of the flags
 __global__ void k_flag_gt(const double *snr, int64_t n, double th, int64_t *flag)
