@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="do not time the FP64 path beside the mixed one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the six Fisher-pass tiles on this catalog (per precision and "
+                         "grid-length class, cached in a JSON file) before the arms")
     ap.add_argument("--eager", action="store_true",
                     help="launch the step call by call instead of replaying a CUDA graph")
     return ap.parse_args()
@@ -257,7 +260,7 @@ def aggregate(times_ms, n_events: int, steps: int, world: int, dist=None, device
     if world > 1 and dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     t = t.tolist()
-    rates = [n_events * steps / (x * 1e-3) for x in t]
+    rates = [n_events * steps / (x * 1e-3) if x > 0 else 0.0 for x in t]
     return t, rates
 
 
@@ -336,6 +339,33 @@ def golden_error(gw, refine_cond):
                      "pass_1e-3_frac": float(np.mean(rel_ok <= 1e-3)),
                      "refined_frac": nref / len(kappa),
                      "per_decade_[events,pass_1e-3,max_rel]": table}
+    return out
+
+
+def tune_tiles(gw, a, cat, net, order, prec):
+    """Autotuned Fisher-pass tiles of the arms: each precision on the step's
+    catalog and, for the mixed arm, the FP64 pass on the events its
+    refinement selects.  Returns, per pass, the chosen tile and (when timed
+    here rather than read from the cache) the time of every tile, the fixed
+    default 8x2 among them."""
+    import torch
+    from paper_2207_06910_gb300 import autotune
+
+    def entry(e):
+        return {"tile": f"{e['group']}x{e['blocks_per_sm']}", "cached": e["cached"],
+                "length_class": gw.LENGTH_CLASSES[e["length_class"]],
+                **({"ms": e["ms"]} if "ms" in e else {})}
+    out = {}
+    for p in order:
+        out["mixed" if p == gw.GW_MIXED else "fp64"] = entry(autotune.tune(cat, net, N_PAR, p))
+    if prec == gw.GW_MIXED:
+        F, snr, st = gw.gw_fisher(cat, net, N_PAR, gw.GW_MIXED)
+        inv = gw.gw_fisher_inverse(F, N_PAR)
+        flag = torch.zeros(cat.n, dtype=torch.uint8, device="cuda")
+        gw.gw_fisher_refine(cat, net, N_PAR, F, snr, st, inv, cond_th=a.refine_cond, refined=flag)
+        idx = torch.nonzero(flag).flatten()
+        if idx.numel() > 0:
+            out["fp64 refinement"] = entry(autotune.tune(cat.select(idx), net, N_PAR, gw.GW_FP64))
     return out
 
 
@@ -477,26 +507,35 @@ def run_ours(a):
         """Point-loop kernel durations from the library's CUDA events on the
         launching stream: the Fisher pass, and (mixed) the refinement's FP64 pass."""
         ms, ms_ref = [], []
+        pts_ref = 0
         gw.gw_set_profiling(True)
-        for _ in range(3):
+        for _ in range(4):
             flush.zero_()
-            out = forward(dev, p)
+            cat, F, snr, st, g, inv = forward(dev, p)
             ms.append(gw.gw_point_kernel_ms())
             if refine:
-                finish(out, p)
+                flag = torch.zeros(cat.n, dtype=torch.uint8, device="cuda")
+                gw.gw_fisher_refine(cat, net, N_PAR, F, snr, st, inv, grad_snr=grad_up[:cat.n],
+                                    grad_params=g, cond_th=a.refine_cond, refined=flag)
                 ms_ref.append(gw.gw_point_kernel_ms())
+                npts = cat.npts if cat.sel is None else cat.npts[cat.sel]
+                pts_ref = int(npts.to(torch.int64)[flag.bool()].sum().item())
         gw.gw_set_profiling(False)
         torch.cuda.synchronize()
-        return float(np.mean(ms)), (float(np.mean(ms_ref)) if ms_ref else 0.0)
+        # (the minimum: a first call can include one-time module loading)
+        return float(np.min(ms)), (float(np.min(ms_ref)) if ms_ref else 0.0), pts_ref
 
     # ---- the FP64 arm (same catalog, same launch), then the headline arm
     arms = {}
     order = [prec] if (a.no_fp64_arm or prec == gw.GW_FP64) else [gw.GW_FP64, prec]
+    tiles = None
+    if a.autotune:
+        tiles = tune_tiles(gw, a, gate(dev), net, order, prec)
     dev2 = {k: v.clone() for k, v in dev.items()}
     clocks = None
     for p in order:
         run = make_arm(p, [dev, dev2])
-        kern_ms, kern_ref_ms = point_kernel_ms(p, p == gw.GW_MIXED)
+        kern_ms, kern_ref_ms, pts_ref = point_kernel_ms(p, p == gw.GW_MIXED)
         clk = Clocks(local)
         if world > 1:
             dist.barrier()
@@ -507,7 +546,7 @@ def run_ours(a):
             dist.barrier()
         c = clk.stop()
         arms[p] = dict(run=run, total_ms=total_ms, out=out, nref=nref, kern_ms=kern_ms,
-                       kern_ref_ms=kern_ref_ms, clocks=c)
+                       kern_ref_ms=kern_ref_ms, pts_ref=pts_ref, clocks=c)
         if p == prec:
             clocks = c
         gw.gw_reserve(0, 0, 0)
@@ -605,7 +644,7 @@ def run_ours(a):
         refined_frac = n_refined / max(1, n_total)
         # points of one rank's launch of each point kernel
         pts_mixed = n_points if prec == gw.GW_MIXED else 0
-        pts_ref = int(round(n_points * refined_frac)) if prec == gw.GW_MIXED else n_points
+        pts_ref = head["pts_ref"] if prec == gw.GW_MIXED else n_points
         kernels = []
         if prec == gw.GW_MIXED:
             kernels.append({"kernel": "k_points_mixed (Fisher)", "ms": kern_ms, "points": pts_mixed,
@@ -715,6 +754,8 @@ def run_ours(a):
                       "oracle_sample_of_this_run": err_sample,
                       "oracle_stratified_1000_c3_events": golden},
         }
+        if tiles is not None:
+            line["tiles"] = tiles
         if fp64 is not None and prec == gw.GW_MIXED:
             line["fp64_arm"] = {"value": rates[4], "unit": "events/s", "ms_per_step": fp64_ms / a.steps,
                                 "point_kernel_ms": fp64_kern_ms, "clocks": fp64["clocks"]}

@@ -154,7 +154,7 @@ gw_status gw_create(gw_ctx **ctx, int device);
 gw_status gw_destroy(gw_ctx *ctx);
 /* Text of the last error on this context (static storage, never NULL). */
 const char *gw_last_error(const gw_ctx *ctx);
-/* ABI version of this header (incremented on any signature change or addition): 5. */
+/* ABI version of this header (incremented on any signature change or addition): 6. */
 int gw_abi_version(void);
 
 /* Reserve workspace for up to max_events events on up to max_sites detector
@@ -168,6 +168,29 @@ int gw_abi_version(void);
  * not allowed during capture and then fails with GW_ECUDA).  max_items = 0
  * returns to the synchronous default.  No counterpart in the paper. */
 gw_status gw_reserve(gw_ctx *ctx, int64_t max_events, int64_t max_items, int max_sites);
+
+/* Tiles of the Fisher pass (no counterpart in the paper).  The fused point
+ * kernels process work items of GW_ITEM_POINTS points with a group of `group`
+ * lanes each (4, 8 or 16; default 8) on a persistent grid of `blocks_per_sm`
+ * CTAs per SM (1 or 2; default 2).  The context keeps one tile per precision
+ * and grid-length class: class 0 = at most ~1.5 work items per event on
+ * average (grids up to ~380 points), 1 = up to 12 (~3000 points), 2 = longer;
+ * a call's class is its mean work items per event (after gw_reserve: the
+ * reservation's max_items / max_events).  Results do not depend on the tile
+ * (the reductions keep a fixed order per tile; different tiles sum in
+ * different orders, within rounding).
+ * gw_set_tile installs a tile; gw_autotune times every tile (group x
+ * blocks_per_sm, `reps` Fisher passes each after one warm-up, CUDA events
+ * around the point kernel) on the caller's catalog, installs the fastest for
+ * the catalog's class and precision, and returns the class, the tile and the
+ * six times in ms (ms_out [6]: group 4, 8, 16 x blocks 1, 2; or NULL).  It
+ * synchronises `stream` and must not run in the asynchronous mode of
+ * gw_reserve. */
+gw_status gw_set_tile(gw_ctx *ctx, gw_precision prec, int length_class, int group,
+                      int blocks_per_sm);
+gw_status gw_autotune(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
+                      gw_precision prec, int n_par, int reps, int32_t *length_class,
+                      int32_t *group, int32_t *blocks_per_sm, double *ms_out, void *stream);
 
 /* Measurement hook (no counterpart in the paper): when enabled, the context
  * records CUDA events on the call's stream around every point-loop kernel
@@ -275,13 +298,20 @@ gw_status gw_fisher_refine(gw_ctx *ctx, const gw_catalog *cat, const gw_network 
                            double *cov, double *cond, double *inv_err, int32_t *inv_status,
                            uint8_t *refined, int64_t *n_refined, void *stream);
 
-/* Vector-Jacobian product of the network SNR (derivatives w.r.t. the event's
- * n_par Fisher parameters, same order):
- *   grad_params[i * n + e] = grad_snr[e] * d SNR_e / d theta_i.
- * DEVICE in grad_snr [n]; DEVICE out grad_params [n_par][n]. */
+/* Vector-Jacobian product of the network SNR (Sec. 3.2, Eqs. 3.1-3.2)
+ * w.r.t. the event's n_par Fisher parameters (same order):
+ *   grad_params[i * n + e] = grad_snr[e] * d SNR_e / d theta_i,
+ * and, when grad_gamma is not NULL, w.r.t. the orientation angle gamma_d of
+ * every detector d of the network, summed over the events:
+ *   grad_gamma[d] = sum_e grad_snr[e] * d SNR_e / d gamma_d
+ * (dQ/dgamma follows from the pattern functions being linear in
+ * (sin 2 gamma, cos 2 gamma); a triangle's three arms turn together; events
+ * with a non-zero status are left out of the sum).
+ * DEVICE in grad_snr [n]; DEVICE out grad_params [n_par][n] and grad_gamma
+ * [n_det] (or NULL; overwritten).  No counterpart in the paper. */
 gw_status gw_snr_vjp(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
                      gw_precision prec, int n_par, const double *grad_snr,
-                     double *grad_params, void *stream);
+                     double *grad_params, double *grad_gamma, void *stream);
 
 /* Vector-Jacobian product of L = sum_e log det Gamma_e with respect to the
  * orientation angle gamma_d of every detector d of the network, by Jacobi's

@@ -62,7 +62,7 @@ EXPORTS = ("gw_create", "gw_destroy", "gw_last_error", "gw_abi_version", "gw_pre
            "gw_set_profiling", "gw_point_kernel_ms", "gw_fisher_noalloc", "gw_reserve",
            "gw_select_snr", "gw_fisher_eig", "gw_covariance", "gw_packed_submatrix",
            "gw_sky_area", "gw_strain", "gw_perturb_fisher", "gw_logdet_vjp_detangles_masked",
-           "gw_fma_rate", "gw_fisher_refine")
+           "gw_fma_rate", "gw_fisher_refine", "gw_set_tile", "gw_autotune")
 
 _lib = None
 
@@ -91,7 +91,7 @@ def load_library(path: str | None = None):
     lib.gw_snr.argtypes = [_P, C, N, ctypes.c_int, _P, _P, _P, _P]
     lib.gw_fisher.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P]
     lib.gw_fisher_inverse.argtypes = [_P, _P, i64, ctypes.c_int, d, _P, _P, _P, _P, _P]
-    lib.gw_snr_vjp.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+    lib.gw_snr_vjp.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
     lib.gw_logdet_vjp_detangles.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P, _P, _P]
     lib.gw_logdet_vjp_detangles_masked.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, _P,
                                                    ctypes.c_uint32, _P, _P]
@@ -112,6 +112,10 @@ def load_library(path: str | None = None):
                                 ctypes.c_int, _P, _P]
     lib.gw_fisher_refine.argtypes = [_P, C, N, ctypes.c_int, d, d] + [_P] * 10 + [
         ctypes.POINTER(i64), _P]
+    lib.gw_set_tile.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.gw_autotune.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                ctypes.POINTER(d), _P]
     lib.gw_fma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(d), ctypes.POINTER(d),
                                 ctypes.POINTER(d), _P]
     lib.gw_set_profiling.argtypes = [_P, ctypes.c_int]
@@ -165,6 +169,34 @@ def gw_set_profiling(enable: bool = True) -> None:
 def gw_point_kernel_ms() -> float:
     """Duration of the last point-loop kernel (ms), -1 if none recorded."""
     return load_library().gw_point_kernel_ms(context())
+
+
+LENGTH_CLASSES = ("short", "medium", "long")     # <= ~380, <= ~3000, longer grids
+TILES = [(g, b) for g in (4, 8, 16) for b in (1, 2)]
+
+
+def gw_set_tile(prec: int, length_class: int, group: int, blocks_per_sm: int) -> None:
+    """Fisher-pass tile (lanes per work item, CTAs per SM) of a precision and
+    grid-length class (0 short, 1 medium, 2 long) on the current device."""
+    ctx = context()
+    _check(load_library().gw_set_tile(ctx, int(prec), int(length_class), int(group),
+                                      int(blocks_per_sm)), ctx)
+
+
+def gw_autotune(cat: "Catalog", net: "Network", n_par: int, prec=GW_MIXED, reps: int = 3,
+                stream=None) -> dict:
+    """Time every tile of the Fisher pass on this catalog, install the fastest
+    for its grid-length class: {'length_class', 'group', 'blocks_per_sm',
+    'ms': {(group, blocks): ms}}."""
+    ctx = context()
+    c = cat.struct()
+    cls, g, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ms = (ctypes.c_double * 6)()
+    _check(load_library().gw_autotune(ctx, ctypes.byref(c), ctypes.byref(net.net), int(prec),
+                                      int(n_par), int(reps), ctypes.byref(cls), ctypes.byref(g),
+                                      ctypes.byref(b), ms, _stream(stream)), ctx)
+    return {"length_class": cls.value, "group": g.value, "blocks_per_sm": b.value,
+            "ms": {t: ms[i] for i, t in enumerate(TILES)}}
 
 
 def gw_fma_rate(fp64: bool, iters: int | None = None, stream=None) -> dict:
@@ -466,16 +498,19 @@ def gw_fisher_refine(cat: Catalog, net: Network, n_par: int, fisher, snr, status
 
 
 def gw_snr_vjp(cat: Catalog, net: Network, n_par: int, grad_snr: torch.Tensor, prec=GW_FP64,
-               stream=None, out=None):
-    """grad_params [n_par, n] = grad_snr * d SNR / d theta."""
+               stream=None, out=None, det_gamma=False):
+    """grad_params [n_par, n] = grad_snr * d SNR / d theta; with ``det_gamma``
+    also (grad_params, grad_gamma [n_det]) with grad_gamma[d] =
+    sum_e grad_snr[e] d SNR_e / d gamma_d (detector orientations)."""
     ctx = context()
     g = out if out is not None else torch.empty((n_par, cat.n), dtype=torch.float64,
                                                 device=grad_snr.device)
+    gg = torch.empty(net.n_det, dtype=torch.float64, device=grad_snr.device) if det_gamma else None
     c = cat.struct()
     st = load_library().gw_snr_vjp(ctx, ctypes.byref(c), ctypes.byref(net.net), int(prec), n_par,
-                                   _ptr(grad_snr.contiguous()), _ptr(g), _stream(stream))
+                                   _ptr(grad_snr.contiguous()), _ptr(g), _ptr(gg), _stream(stream))
     _check(st, ctx)
-    return g
+    return (g, gg) if det_gamma else g
 
 
 def gw_logdet_vjp_detangles(cat: Catalog, net: Network, n_par: int, cov: torch.Tensor,

@@ -42,12 +42,26 @@ struct gw_ctx {
     int32_t *ref_st = nullptr;    size_t ref_st_cap = 0;    // status, inverse status
     int64_t *h_total = nullptr;   // pinned
     int64_t item_cap = 0;       // > 0: asynchronous mode with this many work items
+    int64_t reserved_events = 0;
+    // Fisher-pass tile per precision and grid-length class (gw_set_tile,
+    // gw_autotune): lanes per work item and CTAs per SM
+    int tile_group[2][3] = {{GROUP, GROUP, GROUP}, {GROUP, GROUP, GROUP}};
+    int tile_bps[2][3] = {{2, 2, 2}, {2, 2, 2}};
     int profiling = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool ev_recorded = false;
 };
 
 namespace {
+
+// grid-length class of a call from its mean work items per event (items of
+// GW_ITEM_POINTS points): 0 up to ~380 points, 1 up to ~3000, 2 beyond
+int length_class(int64_t items, int64_t n)
+{
+    if (n <= 0) return 0;
+    const double m = (double)items / (double)n;
+    return m <= 1.5 ? 0 : (m <= 12.0 ? 1 : 2);
+}
 
 gw_status fail(gw_ctx *c, gw_status st, const char *fmt, ...)
 {
@@ -289,6 +303,8 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
         return fail(ctx, GW_EINVAL, "logdet_vjp: det_mask selects no detector of the network");
     if (n == 0) {
         if (mode == MODE_LOGDET) return logdet_zero(ctx, dn.n_det, det_mask, grad_gamma, s);
+        if (mode == MODE_SNRGRAD && grad_gamma)
+            CK(cudaMemsetAsync(grad_gamma, 0, sizeof(double) * dn.n_det, s));
         return GW_OK;
     }
     CK(cudaSetDevice(ctx->device));
@@ -305,6 +321,12 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
             if ((st = ensure(ctx, ctx->snr_tmp, ctx->snr_tmp_cap, (size_t)n))) return st;
             snr = ctx->snr_tmp;
         }
+    }
+    if (mode == MODE_SNRGRAD && grad_gamma) {
+        // per-event terms of the detector-orientation gradient, summed below
+        const size_t rows = dn.n_det > N_SNRGRAD_X ? dn.n_det : N_SNRGRAD_X;
+        if ((st = ensure(ctx, ctx->xsums, ctx->xsums_cap, rows * n))) return st;
+        xs = ctx->xsums;
     }
     if (mixed && (st = ensure(ctx, ctx->sitec_f, ctx->sitec_f_cap, (size_t)n * dn.n_site * SC_N)))
         return st;
@@ -352,6 +374,15 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     pa.nacc = nacc;
     pa.cov = cov;
     pa.det_mask = det_mask;
+    if (mode == MODE_FISHER) {
+        // the tile of this precision and grid-length class (asynchronous mode:
+        // the class of the reservation)
+        const int cls = ctx->item_cap > 0 ? length_class(ctx->item_cap, ctx->reserved_events)
+                                          : length_class(n_items, n);
+        const int pi = mixed ? 1 : 0;
+        pa.group = ctx->tile_group[pi][cls];
+        pa.blocks_per_sm = ctx->tile_bps[pi][cls];
+    }
     if (ctx->profiling) CK(cudaEventRecord(ctx->ev0, s));
     if (mixed) CK(launch_points_mixed(mode, np, dn.rotation, pa, s));
     else CK(launch_points_fp64(mode, np, dn.rotation, pa, s));
@@ -366,6 +397,7 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     if (fused_grad)
         CK(launch_snr_grad_from_fisher(n, np, mixed, dn.rotation, fisher, snr, xs, ctx->evc,
                                        status, grad_snr, grad_params, s));
+    if (mode == MODE_SNRGRAD && grad_gamma) CK(launch_sum_events(xs, n, dn.n_det, grad_gamma, s));
     return GW_OK;
 }
 
@@ -373,7 +405,7 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
 
 extern "C" {
 
-int gw_abi_version(void) { return 5; }
+int gw_abi_version(void) { return 6; }
 
 gw_status gw_create(gw_ctx **out, int device)
 {
@@ -452,6 +484,77 @@ gw_status gw_reserve(gw_ctx *ctx, int64_t max_events, int64_t max_items, int max
     if ((st = ensure(ctx, ctx->snr_tmp, ctx->snr_tmp_cap, n))) return st;
     if ((st = ensure(ctx, ctx->partial, ctx->partial_cap, (size_t)max_items * nacc_max))) return st;
     ctx->item_cap = max_items;
+    ctx->reserved_events = (int64_t)n;
+    return GW_OK;
+}
+
+gw_status gw_set_tile(gw_ctx *ctx, gw_precision prec, int length_class_, int group,
+                      int blocks_per_sm)
+{
+    if (!ctx) return GW_EINVAL;
+    if ((prec != GW_FP64 && prec != GW_MIXED) || length_class_ < 0 || length_class_ > 2 ||
+        (group != 4 && group != 8 && group != 16) || (blocks_per_sm != 1 && blocks_per_sm != 2))
+        return fail(ctx, GW_EINVAL, "set_tile: precision 0/1, class 0..2, group 4/8/16, "
+                    "blocks per SM 1/2");
+    ctx->tile_group[prec][length_class_] = group;
+    ctx->tile_bps[prec][length_class_] = blocks_per_sm;
+    return GW_OK;
+}
+
+gw_status gw_autotune(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
+                      gw_precision prec, int n_par, int reps, int32_t *length_class_out,
+                      int32_t *group_out, int32_t *bps_out, double *ms_out, void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (!cat || cat->n <= 0 || reps < 1 || reps > 100)
+        return fail(ctx, GW_EINVAL, "autotune: a non-empty catalog and 1 <= reps <= 100");
+    if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_EINVAL, "bad precision");
+    if (ctx->item_cap > 0) return fail(ctx, GW_EINVAL, "autotune: release gw_reserve first");
+    const int64_t n = cat->n;
+    const int npk = n_par * (n_par + 1) / 2;
+    gw_status st;
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure(ctx, ctx->ref_F, ctx->ref_F_cap, (size_t)npk * n))) return st;
+    if ((st = ensure(ctx, ctx->ref_v, ctx->ref_v_cap, (size_t)4 * n))) return st;
+    if ((st = ensure(ctx, ctx->ref_st, ctx->ref_st_cap, (size_t)2 * n))) return st;
+    // one pass for the work count (the grid-length class) and the workspace
+    if ((st = run_points(ctx, cat, net, prec, MODE_FISHER, n_par, ctx->ref_st, ctx->ref_v,
+                         nullptr, ctx->ref_F, nullptr, nullptr, nullptr, nullptr, stream)))
+        return st;
+    const int cls = length_class(*ctx->h_total, n);
+    const int pi = prec == GW_MIXED ? 1 : 0;
+    const int old_g = ctx->tile_group[pi][cls], old_b = ctx->tile_bps[pi][cls];
+    const int old_prof = ctx->profiling;
+    if ((st = gw_set_profiling(ctx, 1))) return st;
+    static const int G[3] = {4, 8, 16};
+    double best = 1e300;
+    int bg = old_g, bb = old_b;
+    for (int gi = 0; gi < 3; gi++)
+        for (int b = 1; b <= 2; b++) {
+            ctx->tile_group[pi][cls] = G[gi];
+            ctx->tile_bps[pi][cls] = b;
+            double tmin = 1e300;
+            for (int r = 0; r < reps + 1; r++) {   // the first run is a warm-up
+                if ((st = run_points(ctx, cat, net, prec, MODE_FISHER, n_par, ctx->ref_st,
+                                     ctx->ref_v, nullptr, ctx->ref_F, nullptr, nullptr, nullptr,
+                                     nullptr, stream)))
+                    return st;
+                const double ms = gw_point_kernel_ms(ctx);
+                if (r > 0 && ms >= 0.0 && ms < tmin) tmin = ms;
+            }
+            if (ms_out) ms_out[gi * 2 + (b - 1)] = tmin;
+            if (tmin < best) {
+                best = tmin;
+                bg = G[gi];
+                bb = b;
+            }
+        }
+    gw_set_profiling(ctx, old_prof);
+    ctx->tile_group[pi][cls] = bg;
+    ctx->tile_bps[pi][cls] = bb;
+    if (length_class_out) *length_class_out = cls;
+    if (group_out) *group_out = bg;
+    if (bps_out) *bps_out = bb;
     return GW_OK;
 }
 
@@ -783,14 +886,15 @@ gw_status gw_fisher_inverse(gw_ctx *ctx, const double *fisher, int64_t n, int n_
 }
 
 gw_status gw_snr_vjp(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, gw_precision prec,
-                     int n_par, const double *grad_snr, double *grad_params, void *stream)
+                     int n_par, const double *grad_snr, double *grad_params, double *grad_gamma,
+                     void *stream)
 {
     if (!ctx) return GW_EINVAL;
     if (!cat) return fail(ctx, GW_EINVAL, "catalog: null");
     if ((!grad_snr || !grad_params) && cat->n > 0)
         return fail(ctx, GW_EINVAL, "snr_vjp: null array");
     return run_points(ctx, cat, net, prec, MODE_SNRGRAD, n_par, nullptr, nullptr, nullptr,
-                      nullptr, grad_snr, grad_params, nullptr, nullptr, stream);
+                      nullptr, grad_snr, grad_params, nullptr, grad_gamma, stream);
 }
 
 gw_status gw_logdet_vjp_detangles(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,

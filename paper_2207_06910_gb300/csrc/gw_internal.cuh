@@ -104,9 +104,12 @@ enum EvSlot : int {
     EV_T0 = EV_P10 + 4,                 // 8: tau*                (basis B8, times v^-3)
     EV_TM = EV_T0 + 8,                  // 8: d tau*/d Mc
     EV_TE = EV_TM + 8,                  // 8: d tau*/d eta | Mc
-    EVC = EV_TE + 8
+    EV_COEF_END = EV_TE + 8,
+    EV_ADV = EV_COEF_END,               // 8: (rho, 1/rho, ln rho, amplitude ratio) of
+                                        // v over 4 points, then over 16 points
+    EVC = EV_ADV + 8
 };
-constexpr int NCOEF = EVC - EV_PM;   // polynomial coefficients of the point loop
+constexpr int NCOEF = EV_COEF_END - EV_PM;   // polynomial coefficients of the point loop
 constexpr int NSCAL = EV_INVDL - EV_WC0 + 1;   // scalar constants of the mixed point loop
 // B11 = (v^-5, v^-3, v^-2, v^-1, 1, v, v^2, v^5, v^7, ln v, v ln v)
 // B8  = (v^-5, v^-3, v^-2, v^-1, 1, v, v^2, v ln v)
@@ -130,13 +133,22 @@ template <int NP> struct Acc {
 enum Mode : int { MODE_SNR = 0, MODE_FISHER = 1, MODE_SNRGRAD = 2, MODE_LOGDET = 3 };
 
 // A work item is a contiguous run of at most CHUNK_MAX grid points of one
-// event, processed by a group of GROUP lanes (lane l takes points k0 + l,
-// k0 + l + GROUP, ...); a warp runs 32 / GROUP items at once.  Short items
-// (the 200-300-point grids of light catalogs) then give every lane ~30
-// points, which amortises the per-lane start and the per-item reduction.
+// event, processed by a group of G lanes (lane l takes points k0 + l,
+// k0 + l + G, ...); a warp runs 32 / G items at once.  G = 8 by default: short
+// items (the 200-300-point grids of light catalogs) then give every lane ~30
+// points, which amortises the per-lane start and the per-item reduction; the
+// Fisher point kernels are also built for G = 4 and 16 (the autotuner's choice).
 constexpr int GROUP = 8;
 constexpr int GROUPS_PER_WARP = 32 / GROUP;
-constexpr int PPL_MAX = 256 / GROUP;          // points per lane per work item (max)
-constexpr int CHUNK_MAX = GROUP * PPL_MAX;    // points per work item (max)
+constexpr int CHUNK_MAX = 256;                // points per work item (max)
+
+// slot of recurrence factor k (0: rho = v ratio, 1: 1/rho, 2: ln rho, 3: amplitude
+// ratio) over G points
+template <int G>
+__host__ __device__ constexpr int adv_slot(int k)
+{
+    return G == 8 ? (k == 0 ? EV_RHOG : k == 1 ? EV_RHOIG : k == 2 ? EV_LNRHOG : EV_RAG)
+                  : EV_ADV + (G == 4 ? 0 : 4) + k;
+}
 
 }  // namespace gw

@@ -72,6 +72,8 @@ struct PointArgs {
     const double *cov;        // logdet mode: covariance, packed, event-minor
     uint32_t det_mask = 0xffffffffu;   // logdet mode: detectors whose orientation
                                        // gradient is formed (bit d); other sites skipped
+    int group = GROUP;                 // Fisher pass: lanes per work item (4, 8 or 16)
+    int blocks_per_sm = 2;             // persistent grid: CTAs per SM (1 or 2)
 };
 
 // extra accumulators of the mixed Fisher kernel: phase-free SNR-gradient sums
@@ -85,7 +87,7 @@ inline int n_acc(int mode, int np, int n_det, bool mixed = false)
     switch (mode) {
     case MODE_SNR: return 1 + n_det;
     case MODE_FISHER: return 1 + np * (np + 1) / 2 + (mixed ? N_SNRGRAD_X : 0);
-    case MODE_SNRGRAD: return 1 + np;
+    case MODE_SNRGRAD: return 1 + np + n_det;
     default: return n_det;
     }
 }
@@ -176,6 +178,9 @@ cudaError_t launch_scatter_f64(int64_t m, int64_t n, int rows, const int64_t *po
                                double *out, cudaStream_t s);
 cudaError_t launch_scatter_i32(int64_t m, int64_t n, const int64_t *pos, const int32_t *in,
                                int32_t *out, cudaStream_t s);
+
+// out[r] = sum over e of x[r * n + e], r < rows (one block per row, fixed order)
+cudaError_t launch_sum_events(const double *x, int64_t n, int rows, double *out, cudaStream_t s);
 
 cudaError_t launch_invert(const double *fisher, int64_t n, int np, double cond_max, double *cov,
                           double *cond, double *inv_err, int32_t *status, cudaStream_t s);

@@ -193,6 +193,14 @@ k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec, float 
         E[EV_LNRHOG] = GROUP * lnr / 3.0;
         E[EV_A0] = SQRT_5_24 * PI_M23 * exp(5.0 / 6.0 * log(Mcs)) / (dL * GPC_S);
         E[EV_RAG] = exp(-7.0 / 6.0 * GROUP * lnr);
+        for (int g = 0; g < 2; g++) {        // the same over 4 and over 16 points
+            const double L = (g == 0 ? 4.0 : 16.0) * lnr;
+            const double rg = exp(L / 3.0);
+            E[EV_ADV + 4 * g] = rg;
+            E[EV_ADV + 4 * g + 1] = 1.0 / rg;
+            E[EV_ADV + 4 * g + 2] = L / 3.0;
+            E[EV_ADV + 4 * g + 3] = exp(-7.0 / 6.0 * L);
+        }
         double si, ci, s2p, c2p;
         sincos(io, &si, &ci);
         sincos(2.0 * ps, &s2p, &c2p);
@@ -278,6 +286,7 @@ k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec, float 
                 if (q > EV_INVDL && q < EV_PM) continue;
                 Ef[q] = split_f32(E[q]);
             }
+            for (int q = EV_ADV; q < EVC; q++) Ef[q] = split_f32(E[q]);
         }
     } else {
         // ---- tau*(f), 3.5PN (Buonanno et al. 2009 Eq. 3.8b), basis B8 times v^-3
@@ -310,7 +319,7 @@ k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec, float 
         }
 
         if (Ef)
-            for (int q = EV_T0; q < EVC; q++) Ef[q] = split_f32(E[q]);
+            for (int q = EV_T0; q < EV_COEF_END; q++) Ef[q] = split_f32(E[q]);
 
         // ---- per-site JKS coefficients (pattern functions as functions of the
         // hour-angle-like x = phi - lon - g) and Doppler factors.
@@ -521,8 +530,11 @@ __global__ void __launch_bounds__(FIN_BS) k_finish(int mode, int np, int n_det, 
             if (a > 0) {
                 const double s0 = fin_s[le];
                 // d SNR / d theta = sum W Re(Q* g) / SNR (zero when no arm is on)
-                grad_params[(int64_t)(a - 1) * n + e] =
-                    bad ? NAN : (s0 > 0.0 ? grad_snr[e] * s / sqrt(s0) : 0.0);
+                const double g = s0 > 0.0 ? grad_snr[e] * s / sqrt(s0) : 0.0;
+                if (a <= np) grad_params[(int64_t)(a - 1) * n + e] = bad ? NAN : g;
+                // detector orientations: the event's term of the sum over events
+                // (flagged events left out of the sum)
+                else if (xsums) xsums[(int64_t)(a - 1 - np) * n + e] = bad ? 0.0 : g;
             }
         }
     }
@@ -598,6 +610,29 @@ cudaError_t launch_select(const double *snr, int64_t n, double th, int64_t *flag
     if (e != cudaSuccess) return e;
     if ((e = launch_scan(flag, n, off, scan_tmp, s)) != cudaSuccess) return e;
     k_compact<<<nb, bs, 0, s>>>(snr, n, th, off, sel);
+    return cudaGetLastError();
+}
+
+// sum over events of each row of x [rows][n], fixed order
+__global__ void k_sum_events(const double *x, int64_t n, double *out)
+{
+    __shared__ double sh[256];
+    const int r = blockIdx.x;
+    double s = 0.0;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s += x[(int64_t)r * n + e];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r] = sh[0];
+}
+
+cudaError_t launch_sum_events(const double *x, int64_t n, int rows, double *out, cudaStream_t s)
+{
+    if (rows <= 0) return cudaSuccess;
+    k_sum_events<<<rows, 256, 0, s>>>(x, n, out);
     return cudaGetLastError();
 }
 

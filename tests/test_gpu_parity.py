@@ -403,3 +403,44 @@ def test_reserve_async_graph_and_overflow():
                            F4[:, ~torch.as_tensor(over, device="cuda")])
     finally:
         gw.gw_reserve(0, 0, 0)
+
+
+@pytest.mark.parametrize("masked", [False, True])
+def test_snr_vjp_detector_angles(masked):
+    """d(sum_e w_e SNR_e)/d gamma_d (gw_snr_vjp's detector-orientation output) on
+    the five-interferometer network against Richardson central differences of the
+    oracle's SNR over each detector's orientation; with a duty-factor mask that
+    switches one triangle arm off for one event the triangle's entry is no longer
+    zero (a closed triangle's SNR does not change when it turns in its plane)."""
+    cat, d, p = oracle_catalog("c4", 3, max_npts=300)
+    det, psd, rot = gwcat.network("c4")
+    mask = None
+    if masked:
+        mask = np.array([0b11110, 0b11111, 0b11111], dtype=np.uint32)   # arm 0 off, event 0
+        cat = oracle.Catalog(cat.ev, cat.pset, cat.fmin, cat.fmax, cat.npts, mask)
+    w = np.array([1.0, -2.0, 0.5])
+
+    def snr_at(k, gam):
+        dd = det.copy()
+        dd[k, 2] = gam
+        return oracle.snr(cat, dd, psd, rot)[0]
+
+    want = []
+    for k in range(len(det)):
+        g0, h = det[k, 2], 2e-3
+        dh = lambda hh: (snr_at(k, g0 + hh) - snr_at(k, g0 - hh)) / (2 * hh)
+        want.append(np.sum(w * (4 * dh(h / 2) - dh(h)) / 3))
+    want = np.array(want)
+    gcat = gw.Catalog.from_numpy(cat.ev, cat.pset, cat.fmin, cat.fmax, cat.npts, arm_mask=mask)
+    net = gw.Network(det, psd, rot)
+    wt = torch.tensor(w, dtype=torch.float64, device="cuda")
+    s0 = oracle.snr(cat, det, psd, rot)[0]
+    scale = np.sum(np.abs(w) * s0)              # d SNR / d gamma is O(SNR) per radian
+    for prec, tol in ((gw.GW_FP64, 1e-8), (gw.GW_MIXED, 2e-5)):
+        g, gg = gw.gw_snr_vjp(gcat, net, 11, wt, prec, det_gamma=True)
+        gg = gg.cpu().numpy()
+        assert np.all(np.abs(gg - want) <= tol * scale), (prec, gg, want)
+        if not masked:
+            assert abs(gg[0]) <= tol * scale and abs(want[0]) <= 1e-8 * scale
+        else:
+            assert abs(want[0]) > 1e-4 * scale

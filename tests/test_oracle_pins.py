@@ -268,6 +268,27 @@ def test_snr_geometric_series_closed_form(p_exp):
     assert abs(s[0] ** 2 - integral) <= 2e-7 * integral
 
 
+def test_closed_triangle_snr_does_not_depend_on_its_rotation():
+    """The three arms' detector tensors sum to zero and are spaced by 120 deg:
+    the sum of the arms' |h|^2 is invariant under a rotation of the triangle in
+    its plane, so the SNR does not depend on gamma_T (with every arm on); with
+    one arm off it does."""
+    ev, _ = _one_event("c1")
+    det = np.array([[0.7, 0.16, 0.0, math.pi / 3, 1, 0]])
+    psd = np.array([[10.0, 1e-49, 3, 1.0, 2.0, 2.0, 0, -4.0, 0.0, 2.0, 0]])
+    cat = oracle.Catalog(ev, 1, 2.0, 60.0, 120)
+    base = oracle.snr(cat, det, psd, 1)[0][0]
+    masked = oracle.Catalog(ev, 1, 2.0, 60.0, 120, np.uint32(0b110))
+    mbase = oracle.snr(masked, det, psd, 1)[0][0]
+    moved = []
+    for gam in (0.3, 1.1, 2.5):
+        d2 = det.copy()
+        d2[0, 2] = gam
+        assert abs(oracle.snr(cat, d2, psd, 1)[0][0] / base - 1) < 1e-13
+        moved.append(abs(oracle.snr(masked, d2, psd, 1)[0][0] / mbase - 1))
+    assert max(moved) > 1e-3
+
+
 # ---------------------------------------------------------------- tabulated PSD
 def test_psd_table_interpolation_pins():
     """Tabulated noise curves (Sec. 3.1, psd_path / is_ASD): log-log linear
