@@ -62,12 +62,24 @@ DRAM_BYTES_PER_POINT = {"mixed": (23.10528e6 + 11.52e3) / 4376070,
 GOLDEN = os.path.join(ROOT, "tests", "golden", "parity_oracle.npz")
 
 
+def _measured_peaks() -> dict:
+    """The measured copy bandwidth and bf16 GEMM rates of this machine's GPUs."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+MEASURED = _measured_peaks()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "dfloat"], default="mixed")
     ap.add_argument("--grid", choices=["literal", "stress"], default="literal")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--events", type=int, default=None, help="events per GPU")
@@ -81,6 +93,9 @@ def parse():
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="do not time the FP64 path beside the mixed one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-gram", choices=["tensor", "pipe"], default="tensor",
+                    help="Gram of the FP64 Fisher pass on the tensor cores (exact digit "
+                         "products) or on the FP64 pipe")
     ap.add_argument("--autotune", action="store_true",
                     help="time the six Fisher-pass tiles on this catalog (per precision and "
                          "grid-length class, cached in a JSON file) before the arms")
@@ -252,6 +267,21 @@ def flops_per_point(n_site: int, n_ifo: int, precision: str) -> float:
     return shared + 140 * n_site + 356 * n_ifo
 
 
+def fp64_gram_flops_per_point(n_ifo: int) -> float:
+    """The Gram update's share of the FP64 count above: 66 pairs x 2 products
+    (real and imaginary parts) x 2 flops per virtual interferometer, plus the
+    |Q|^2 sum (3 flops) that the Gram's (Phic, Phic) entry replaces."""
+    return 265.0 * n_ifo
+
+
+def tc_digit_flops_per_point(n_ifo: int, n_par: int = 11) -> float:
+    """Tensor-core work of the exact Gram per grid point: 2 K rows (real and
+    imaginary parts) per virtual interferometer, each entering one M = 128 by
+    N = 8 n_par (padded to 16) digit product, 2 flops per multiply-add."""
+    n = ((8 * n_par + 15) // 16) * 16
+    return 2.0 * n_ifo * 128 * n * 2
+
+
 def aggregate(times_ms, n_events: int, steps: int, world: int, dist=None, device="cpu"):
     """Max over ranks of each timed quantity (ms) and the whole-job rates:
     events/s = n_events (all ranks) * steps / max_time."""
@@ -299,8 +329,8 @@ KEYS = ("m1", "m2", "chi1", "chi2", "lam1", "lam2", "dL_Mpc", "tcoal", "fmin",
 
 
 def golden_error(gw, refine_cond):
-    """sqrt(diag C) error of the mixed path (with the FP64 refinement) and of
-    the FP64 path against the stored oracle results of 1000 stratified events
+    """sqrt(diag C) error of the mixed path (with the FP64 refinement), the
+    double-float path and the FP64 path against the stored oracle results of 1000 stratified events
     of the c3 catalog (tests/golden/parity_oracle.npz), per condition-number
     decade; worst = max of rel / max(1e-3, 1e-15 kappa) (pass: <= 1)."""
     import torch
@@ -318,7 +348,8 @@ def golden_error(gw, refine_cond):
     kappa = z["c3lit_kappa"]
     ok = (z["c3lit_inv_status"] & 33) == 0
     out = {"events": int(len(kappa)), "oracle_flagged": int((~ok).sum())}
-    for name, prec in (("mixed_refined", gw.GW_MIXED), ("fp64", gw.GW_FP64)):
+    for name, prec in (("mixed_refined", gw.GW_MIXED), ("dfloat", gw.GW_DFLOAT),
+                       ("fp64", gw.GW_FP64)):
         F, snr, st = gw.gw_fisher(cat, net, N_PAR, prec)
         inv = gw.gw_fisher_inverse(F, N_PAR)
         nref = gw.gw_fisher_refine(cat, net, N_PAR, F, snr, st, inv, cond_th=refine_cond) \
@@ -357,6 +388,8 @@ def tune_tiles(gw, a, cat, net, order, prec):
                 **({"ms": e["ms"]} if "ms" in e else {})}
     out = {}
     for p in order:
+        if p == gw.GW_DFLOAT:
+            continue     # one fixed shape (the tensor-core kernel)
         out["mixed" if p == gw.GW_MIXED else "fp64"] = entry(autotune.tune(cat, net, N_PAR, p))
     if prec == gw.GW_MIXED:
         F, snr, st = gw.gw_fisher(cat, net, N_PAR, gw.GW_MIXED)
@@ -382,7 +415,8 @@ def run_ours(a):
     import paper_2207_06910_gb300 as gw
     from paper_2207_06910_gb300 import shard
 
-    prec = gw.GW_MIXED if a.precision == "mixed" else gw.GW_FP64
+    prec = {"mixed": gw.GW_MIXED, "fp64": gw.GW_FP64, "dfloat": gw.GW_DFLOAT}[a.precision]
+    gw.gw_set_fp64_gram(a.fp64_gram == "tensor")
     gated = a.workload == "c3-gated"
     cfg = "c3" if gated else a.workload
     if gated:
@@ -646,6 +680,29 @@ def run_ours(a):
         pts_mixed = n_points if prec == gw.GW_MIXED else 0
         pts_ref = head["pts_ref"] if prec == gw.GW_MIXED else n_points
         kernels = []
+        # the FP64 Fisher pass runs the tensor-core Gram kernel for networks of at
+        # most two interferometers per point
+        tc_on = a.fp64_gram == "tensor" and n_ifo <= 2
+        fp64_name = "k_fisher_fp64_tc" if tc_on else "k_points_fp64"
+        fp64_pipe_fp = algo_fp - (fp64_gram_flops_per_point(n_ifo) if tc_on else 0.0)
+        peak_bf16 = MEASURED.get("bf16_tflops")
+
+        def fp64_entry(label, ms, points):
+            k = {"kernel": f"{fp64_name} ({label})", "ms": ms, "points": points, "bound": "alu",
+                 "peak": peak64, "executed_flops_per_point": fp64_pipe_fp,
+                 "pipe_flops_per_point": fp64_pipe_fp,
+                 "peak_basis": f"FP64 pipe: {sms} SMs x {FP64_FMA_PER_CLK_SM} FMA/clk "
+                               f"x 2 flops x {sm_mhz:.0f} MHz"}
+            if tc_on:
+                tfl = tc_digit_flops_per_point(n_ifo, N_PAR)
+                k["gram_on_tensor_cores"] = {
+                    "digit_flops_per_point": tfl,
+                    "achieved": tfl * points / (ms * 1e-3) / 1e12 if ms > 0 else None,
+                    "peak": peak_bf16, "unit": "TFLOP/s",
+                    "peak_basis": "measured cuBLAS bf16 (burst)",
+                    "note": f"the method's {fp64_gram_flops_per_point(n_ifo):.0f} Gram flops per "
+                            f"point as exact 7-bit digit products (8 digits per value)"}
+            return k
         if prec == gw.GW_MIXED:
             kernels.append({"kernel": "k_points_mixed (Fisher)", "ms": kern_ms, "points": pts_mixed,
                             "bound": "alu", "peak": peak32,
@@ -653,30 +710,46 @@ def run_ours(a):
                                           f"(packed FP32x2) x 2 flops x {sm_mhz:.0f} MHz",
                             "executed_flops_per_point": exec_fp})
             if kern_ref_ms > 0:
-                kernels.append({"kernel": "k_points_fp64 (refinement of the ill-conditioned events)",
-                                "ms": kern_ref_ms, "points": pts_ref, "bound": "alu",
-                                "peak": peak64, "executed_flops_per_point": algo_fp,
-                                "peak_basis": f"FP64 pipe: {sms} SMs x {FP64_FMA_PER_CLK_SM} FMA/clk "
-                                              f"x 2 flops x {sm_mhz:.0f} MHz"})
+                kernels.append(fp64_entry("refinement of the ill-conditioned events", kern_ref_ms,
+                                          pts_ref))
+        elif prec == gw.GW_DFLOAT and n_ifo <= 2:
+            tfl = tc_digit_flops_per_point(n_ifo, N_PAR)
+            kernels.append({
+                "kernel": "k_fisher_tc<double-float> (Fisher)", "ms": kern_ms, "points": n_points,
+                "bound": "alu", "peak": peak32,
+                "peak_basis": f"FP32 pipe: {sms} SMs x {FP32_FMA_PER_CLK_SM} FMA/clk "
+                              f"(packed FP32x2) x 2 flops x {sm_mhz:.0f} MHz",
+                "executed_flops_per_point": None,
+                "pipe_flops_per_point": algo_fp - fp64_gram_flops_per_point(n_ifo),
+                "gram_on_tensor_cores": {
+                    "digit_flops_per_point": tfl,
+                    "achieved": tfl * n_points / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None,
+                    "peak": peak_bf16, "unit": "TFLOP/s",
+                    "peak_basis": "measured cuBLAS bf16 (burst)"}})
         else:
-            kernels.append({"kernel": "k_points_fp64 (Fisher)", "ms": kern_ms, "points": n_points,
-                            "bound": "alu", "peak": peak64, "executed_flops_per_point": algo_fp,
-                            "peak_basis": f"FP64 pipe: {sms} SMs x {FP64_FMA_PER_CLK_SM} FMA/clk "
-                                          f"x 2 flops x {sm_mhz:.0f} MHz"})
+            kernels.append(fp64_entry("Fisher", kern_ms, n_points))
         for k in kernels:
-            k["achieved"] = algo_fp * k["points"] / (k["ms"] * 1e-3) / 1e12
+            # the flops of the kernel's bound pipe: the method's FP64 count, less the
+            # Gram where the tensor cores form it
+            k["achieved"] = k.get("pipe_flops_per_point", algo_fp) * k["points"] / (k["ms"] * 1e-3) / 1e12
             k["frac"] = k["achieved"] / k["peak"]
             k["algorithmic_flops_per_point"] = algo_fp
             k["unit"] = "TFLOP/s"
             is_mixed = k["kernel"].startswith("k_points_mixed")
-            k["traffic"] = (DRAM_BYTES_PER_POINT["mixed" if is_mixed else "fp64"] * k["points"]
-                            if a.grid == "literal" else None)
+            # DRAM bytes per point from ncu captures of the literal-grid workload
+            # (none yet for the tensor-core kernel)
+            is_tc = k["kernel"].startswith("k_fisher_")
+            per_pt = DRAM_BYTES_PER_POINT.get("mixed" if is_mixed else ("fp64_tc" if is_tc else "fp64"))
+            k["traffic"] = per_pt * k["points"] if (a.grid == "literal" and per_pt) else None
         dom = max(kernels, key=lambda k: k["ms"])
         roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
                     "unit": "TFLOP/s", "frac": dom["frac"], "traffic": dom["traffic"],
                     "kernel": dom["kernel"], "kernel_ms": dom["ms"],
                     "algorithmic_flops_per_point": algo_fp,
                     "executed_flops_per_point": dom["executed_flops_per_point"],
+                    "pipe_flops_per_point": dom.get("pipe_flops_per_point", algo_fp),
+                    **({"gram_on_tensor_cores": dom["gram_on_tensor_cores"]}
+                       if "gram_on_tensor_cores" in dom else {}),
                     "peak_basis": dom["peak_basis"] + " (median sampled SM clock)",
                     "kernels": kernels,
                     "measured_fma_per_clk_sm": {"fp64": rate64["fma_per_clk_sm"],
@@ -718,7 +791,9 @@ def run_ours(a):
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64 (mixed, FP64 refinement)" if a.precision == "mixed" else "f64",
+            "dtype": {"mixed": "f32+f64 (mixed, FP64 refinement)", "fp64": "f64",
+                      "dfloat": "double-float (f32 pairs) tangents, exact bf16-digit Gram, "
+                                "f64 combination"}[a.precision],
             "data": "synthetic (seeded, gwcat)",
             "config": {"workload": {"c3": WORKLOAD, "c4": WORKLOAD_C4,
                                     "c3-gated": WORKLOAD_GATED}[a.workload],
@@ -756,10 +831,10 @@ def run_ours(a):
         }
         if tiles is not None:
             line["tiles"] = tiles
-        if fp64 is not None and prec == gw.GW_MIXED:
+        if fp64 is not None and prec != gw.GW_FP64:
             line["fp64_arm"] = {"value": rates[4], "unit": "events/s", "ms_per_step": fp64_ms / a.steps,
                                 "point_kernel_ms": fp64_kern_ms, "clocks": fp64["clocks"]}
-            line["mixed_over_fp64"] = value / rates[4]
+            line[f"{a.precision}_over_fp64"] = value / rates[4]
         # launches per step: prepare 1; Fisher 7 (event setup, scan 3, point loop,
         # finish, SNR VJP); inversion 1; refinement (when it selects events) 22:
         # flag + scan 3 + compact, gather, FP64 Fisher 7, inversion, 8 scatters,

@@ -43,9 +43,18 @@ typedef enum {
 
 typedef enum {
     GW_FP64 = 0,   /* every operation in FP64                                  */
-    GW_MIXED = 1   /* FP64 grid, phase derivatives, tau*, Earth angle and
+    GW_MIXED = 1,  /* FP64 grid, phase derivatives, tau*, Earth angle and
                       accumulation; FP32 amplitude, patterns, tangents and
                       products with exactly compensated (double-float) sums  */
+    GW_DFLOAT = 2  /* Fisher pass of networks with at most two interferometers
+                      per grid point (one triangle, or up to two L-shaped
+                      detectors): every per-point quantity in double-float
+                      arithmetic (pairs of FP32, ~2^-48) on the FP32 pipe, the
+                      Gram matrix of the tangents exact on the tensor cores
+                      (see gw_set_fp64_gram), combined in FP64; results of the
+                      FP64 accuracy class.  Every other pass and wider networks
+                      run as GW_FP64.  Not accepted by gw_set_tile,
+                      gw_autotune or gw_fisher_noalloc. */
 } gw_precision;
 
 /* per-event status bits */
@@ -154,7 +163,7 @@ gw_status gw_create(gw_ctx **ctx, int device);
 gw_status gw_destroy(gw_ctx *ctx);
 /* Text of the last error on this context (static storage, never NULL). */
 const char *gw_last_error(const gw_ctx *ctx);
-/* ABI version of this header (incremented on any signature change or addition): 6. */
+/* ABI version of this header (incremented on any signature change or addition): 7. */
 int gw_abi_version(void);
 
 /* Reserve workspace for up to max_events events on up to max_sites detector
@@ -191,6 +200,29 @@ gw_status gw_set_tile(gw_ctx *ctx, gw_precision prec, int length_class, int grou
 gw_status gw_autotune(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
                       gw_precision prec, int n_par, int reps, int32_t *length_class,
                       int32_t *group, int32_t *blocks_per_sm, double *ms_out, void *stream);
+
+/* Gram accumulation of the FP64 Fisher pass (no counterpart in the paper).
+ * tensor = 1: for networks of at most two interferometers per
+ * grid point (one triangle, or up to two L-shaped detectors) the pass forms
+ * each work item's Gram matrix of tangents (Sec. 3.2, Eq. 3.3) on the tensor
+ * cores: every tangent is rounded to a 56-bit fixed-point number relative to
+ * the largest exponent of its column in the item, split into eight 7-bit
+ * digits, and the digit products are summed exactly (integers below 2^24 in
+ * the FP32 accumulator); the 64 digit-pair sums are combined in FP64.  The
+ * result is the FP64 Fisher matrix up to FP64 rounding of that combination.
+ * tensor = 0 (the default): every product on the FP64 pipe, as for wider
+ * networks and the other passes (measured slightly faster: without the Gram the
+ * FP64 pass is a chain of dependent FP64 operations per point).  GW_DFLOAT
+ * always forms its Gram on the tensor cores; the mixed path is not affected. */
+gw_status gw_set_fp64_gram(gw_ctx *ctx, int tensor);
+
+/* Kernel fault flag (no counterpart in the paper): the tensor-core kernel
+ * bounds every wait on its own MMAs (about a second); a wait that runs out
+ * writes NaN into the affected work item's sums, ends that CTA after freeing
+ * its tensor memory, and sets this context's flag.  gw_kernel_faults copies the
+ * flag (0 or 1) to *faults (HOST) and clears it when `reset` is nonzero;
+ * synchronous (waits for the device). */
+gw_status gw_kernel_faults(gw_ctx *ctx, int32_t *faults, int reset);
 
 /* Measurement hook (no counterpart in the paper): when enabled, the context
  * records CUDA events on the call's stream around every point-loop kernel

@@ -21,7 +21,7 @@ import torch
 
 from . import build as _build
 
-GW_FP64, GW_MIXED = 0, 1
+GW_FP64, GW_MIXED, GW_DFLOAT = 0, 1, 2
 ST_NOT_PD, ST_COND_GT_MAX, ST_NONFINITE, ST_EMPTY_GRID, ST_BAD_PARAM, ST_ILL_COND = 1, 2, 4, 8, 16, 32
 ST_OVERFLOW = 64
 ITEM_POINTS = 256          # grid points per work item (GW_ITEM_POINTS)
@@ -62,7 +62,8 @@ EXPORTS = ("gw_create", "gw_destroy", "gw_last_error", "gw_abi_version", "gw_pre
            "gw_set_profiling", "gw_point_kernel_ms", "gw_fisher_noalloc", "gw_reserve",
            "gw_select_snr", "gw_fisher_eig", "gw_covariance", "gw_packed_submatrix",
            "gw_sky_area", "gw_strain", "gw_perturb_fisher", "gw_logdet_vjp_detangles_masked",
-           "gw_fma_rate", "gw_fisher_refine", "gw_set_tile", "gw_autotune")
+           "gw_fma_rate", "gw_fisher_refine", "gw_set_tile", "gw_autotune", "gw_set_fp64_gram",
+           "gw_kernel_faults")
 
 _lib = None
 
@@ -113,6 +114,8 @@ def load_library(path: str | None = None):
     lib.gw_fisher_refine.argtypes = [_P, C, N, ctypes.c_int, d, d] + [_P] * 10 + [
         ctypes.POINTER(i64), _P]
     lib.gw_set_tile.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.gw_set_fp64_gram.argtypes = [_P, ctypes.c_int]
+    lib.gw_kernel_faults.argtypes = [_P, ctypes.POINTER(i32), ctypes.c_int]
     lib.gw_autotune.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                 ctypes.POINTER(d), _P]
@@ -181,6 +184,22 @@ def gw_set_tile(prec: int, length_class: int, group: int, blocks_per_sm: int) ->
     ctx = context()
     _check(load_library().gw_set_tile(ctx, int(prec), int(length_class), int(group),
                                       int(blocks_per_sm)), ctx)
+
+
+def gw_set_fp64_gram(tensor: bool) -> None:
+    """FP64 Fisher pass: Gram matrix of the tangents on the tensor cores (exact
+    digit products) or every product on the FP64 pipe (the default)."""
+    ctx = context()
+    _check(load_library().gw_set_fp64_gram(ctx, int(bool(tensor))), ctx)
+
+
+def gw_kernel_faults(reset: bool = True) -> int:
+    """1 if a kernel's bounded wait ran out since the last reset (its items'
+    sums are NaN), else 0; synchronises the device."""
+    ctx = context()
+    f = ctypes.c_int32(0)
+    _check(load_library().gw_kernel_faults(ctx, ctypes.byref(f), int(bool(reset))), ctx)
+    return int(f.value)
 
 
 def gw_autotune(cat: "Catalog", net: "Network", n_par: int, prec=GW_MIXED, reps: int = 3,

@@ -18,6 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgwfish.so")
 SOURCES = ["gw_api.cu", "gw_setup.cu", "gw_points_fp64.cu", "gw_points_fp64_fisher.cu",
+           "gw_points_fp64_tc.cu",
            "gw_points_mixed.cu", "gw_points_mixed_fisher.cu", "gw_noalloc.cu",
            "gw_covtools.cu", "gw_strain.cu", "gw_probe.cu",
            "gw_refine.cu"]

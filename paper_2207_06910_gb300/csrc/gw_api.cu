@@ -47,6 +47,8 @@ struct gw_ctx {
     // gw_autotune): lanes per work item and CTAs per SM
     int tile_group[2][3] = {{GROUP, GROUP, GROUP}, {GROUP, GROUP, GROUP}};
     int tile_bps[2][3] = {{2, 2, 2}, {2, 2, 2}};
+    int fp64_gram_tc = 0;       // FP64 Fisher pass: Gram on the tensor cores where supported
+    int32_t *kerr = nullptr;    // device flag: a kernel's bounded wait ran out
     int profiling = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool ev_recorded = false;
@@ -289,7 +291,8 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
     gw_status st = gwi_check_cat(ctx, cat, np);
     if (st) return st;
     if (np != 9 && np != 11) return fail(ctx, GW_EINVAL, "n_par must be 9 or 11 (got %d)", np);
-    if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_EINVAL, "bad precision");
+    if (prec != GW_FP64 && prec != GW_MIXED && prec != GW_DFLOAT)
+        return fail(ctx, GW_EINVAL, "bad precision");
     DevNet dn;
     if ((st = gwi_build_net(ctx, net, dn))) return st;
     dn.masked = cat->arm_mask != nullptr;
@@ -382,9 +385,13 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
         const int pi = mixed ? 1 : 0;
         pa.group = ctx->tile_group[pi][cls];
         pa.blocks_per_sm = ctx->tile_bps[pi][cls];
+        pa.gram_tc = ctx->fp64_gram_tc;
     }
+    pa.kerr = ctx->kerr;
     if (ctx->profiling) CK(cudaEventRecord(ctx->ev0, s));
     if (mixed) CK(launch_points_mixed(mode, np, dn.rotation, pa, s));
+    else if (prec == GW_DFLOAT && mode == MODE_FISHER && fisher_fp64_tc_supported(dn))
+        CK(launch_fisher_dfloat_tc(np, dn.rotation, pa, s));
     else CK(launch_points_fp64(mode, np, dn.rotation, pa, s));
     if (ctx->profiling) {
         CK(cudaEventRecord(ctx->ev1, s));
@@ -405,7 +412,7 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
 
 extern "C" {
 
-int gw_abi_version(void) { return 6; }
+int gw_abi_version(void) { return 7; }
 
 gw_status gw_create(gw_ctx **out, int device)
 {
@@ -415,8 +422,12 @@ gw_status gw_create(gw_ctx **out, int device)
     if (!ctx) return GW_ENOMEM;
     ctx->device = device;
     if (cudaSetDevice(device) != cudaSuccess ||
-        cudaMallocHost((void **)&ctx->h_total, sizeof(int64_t)) != cudaSuccess) {
+        cudaMallocHost((void **)&ctx->h_total, sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc((void **)&ctx->kerr, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(ctx->kerr, 0, sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
+        if (ctx->h_total) cudaFreeHost(ctx->h_total);
+        if (ctx->kerr) cudaFree(ctx->kerr);
         delete ctx;
         return GW_ECUDA;
     }
@@ -452,6 +463,7 @@ gw_status gw_destroy(gw_ctx *ctx)
     cudaFree(ctx->ref_v);
     cudaFree(ctx->ref_st);
     cudaFreeHost(ctx->h_total);
+    cudaFree(ctx->kerr);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -498,6 +510,23 @@ gw_status gw_set_tile(gw_ctx *ctx, gw_precision prec, int length_class_, int gro
                     "blocks per SM 1/2");
     ctx->tile_group[prec][length_class_] = group;
     ctx->tile_bps[prec][length_class_] = blocks_per_sm;
+    return GW_OK;
+}
+
+gw_status gw_set_fp64_gram(gw_ctx *ctx, int tensor)
+{
+    if (!ctx) return GW_EINVAL;
+    if (tensor != 0 && tensor != 1) return fail(ctx, GW_EINVAL, "set_fp64_gram: 0 or 1");
+    ctx->fp64_gram_tc = tensor;
+    return GW_OK;
+}
+
+gw_status gw_kernel_faults(gw_ctx *ctx, int32_t *faults, int reset)
+{
+    if (!ctx || !faults) return GW_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpy(faults, ctx->kerr, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (reset) CK(cudaMemset(ctx->kerr, 0, sizeof(int32_t)));
     return GW_OK;
 }
 
@@ -753,7 +782,8 @@ gw_status gw_strain(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, g
     if (!ctx) return GW_EINVAL;
     gw_status st = gwi_check_cat(ctx, cat, 9);
     if (st) return st;
-    if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_EINVAL, "strain: precision");
+    if (prec != GW_FP64 && prec != GW_MIXED && prec != GW_DFLOAT)
+        return fail(ctx, GW_EINVAL, "strain: precision");
     DevNet dn;
     if ((st = gwi_build_net(ctx, net, dn))) return st;
     const int64_t n = cat->n;

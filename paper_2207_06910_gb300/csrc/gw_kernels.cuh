@@ -74,6 +74,8 @@ struct PointArgs {
                                        // gradient is formed (bit d); other sites skipped
     int group = GROUP;                 // Fisher pass: lanes per work item (4, 8 or 16)
     int blocks_per_sm = 2;             // persistent grid: CTAs per SM (1 or 2)
+    int gram_tc = 0;                   // FP64 Fisher pass: Gram on the tensor cores
+    int32_t *kerr = nullptr;           // set to 1 by a kernel whose bounded wait ran out
 };
 
 // extra accumulators of the mixed Fisher kernel: phase-free SNR-gradient sums
@@ -113,6 +115,12 @@ cudaError_t launch_scan(const int64_t *counts, int64_t n, int64_t *off, int64_t 
                         cudaStream_t s);
 
 cudaError_t launch_points_fp64(int mode, int np, int rot, const PointArgs &a, cudaStream_t s);
+// FP64 Fisher pass with the Gram on the tensor cores (gw_points_fp64_tc.cu):
+// networks of at most two interferometers per grid point
+bool fisher_fp64_tc_supported(const DevNet &net);
+cudaError_t launch_fisher_fp64_tc(int np, int rot, const PointArgs &a, cudaStream_t s);
+// the same pass with the tangents in double-float on the FP32 pipe
+cudaError_t launch_fisher_dfloat_tc(int np, int rot, const PointArgs &a, cudaStream_t s);
 cudaError_t launch_points_mixed(int mode, int np, int rot, const PointArgs &a, cudaStream_t s);
 
 // partial sums of the items of each event -> outputs

@@ -1,6 +1,7 @@
 // gw_points_fp64.cu -- FP64 point loop: the SNR, SNR-gradient and log-det passes,
 // and the per-device launch facts (the Fisher pass is instantiated in
-// gw_points_fp64_fisher.cu, so the two compile in parallel).
+// gw_points_fp64_fisher.cu and, with its Gram on the tensor cores, in
+// gw_points_fp64_tc.cu, so the three compile in parallel).
 #include "gw_points_fp64.cuh"
 
 namespace gw {
@@ -28,7 +29,9 @@ cudaError_t launch_points_fp64(int mode, int np, int rot, const PointArgs &a, cu
 {
     switch (mode) {
     case MODE_SNR: return launch_mode<MODE_SNR>(np, rot, a, s);
-    case MODE_FISHER: return launch_points_fp64_fisher(np, rot, a, s);
+    case MODE_FISHER:
+        if (a.gram_tc && fisher_fp64_tc_supported(a.net)) return launch_fisher_fp64_tc(np, rot, a, s);
+        return launch_points_fp64_fisher(np, rot, a, s);
     case MODE_SNRGRAD: return launch_mode<MODE_SNRGRAD>(np, rot, a, s);
     default: return launch_mode<MODE_LOGDET>(np, rot, a, s);
     }

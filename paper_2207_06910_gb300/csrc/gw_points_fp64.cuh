@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "gw_kernels.cuh"
+#include "gw_dfloat.cuh"
 
 namespace gw {
 
@@ -66,18 +67,21 @@ struct NAccOf {
 };
 
 // per-IFO pattern values at one point
-struct Pat {
-    double fp, fx, fpT, fxT, fpX, fxX;
+// (T: double on the FP64 pipe, dfl in double-float on the FP32 pipe)
+template <typename T>
+struct PatT {
+    T fp, fx, fpT, fxT, fpX, fxX;
 };
+using Pat = PatT<double>;
 
-__device__ __forceinline__ Pat patterns(double s2g, double c2g, double P1, double P2,
-                                        const double (&J)[12])
+template <typename T>
+__device__ __forceinline__ PatT<T> patterns(T s2g, T c2g, T P1, T P2, const T (&J)[12])
 {
     // J = a_s, a_c, b_c, b_s, then theta- and x-derivatives of each
-    Pat p;
-    double a = s2g * J[0] + c2g * J[1], b = c2g * J[2] + s2g * J[3];
-    double aT = s2g * J[4] + c2g * J[5], bT = c2g * J[6] + s2g * J[7];
-    double aX = s2g * J[8] + c2g * J[9], bX = c2g * J[10] + s2g * J[11];
+    PatT<T> p;
+    T a = s2g * J[0] + c2g * J[1], b = c2g * J[2] + s2g * J[3];
+    T aT = s2g * J[4] + c2g * J[5], bT = c2g * J[6] + s2g * J[7];
+    T aX = s2g * J[8] + c2g * J[9], bX = c2g * J[10] + s2g * J[11];
     p.fp = P1 * a + P2 * b;
     p.fx = P1 * b - P2 * a;
     p.fpT = P1 * aT + P2 * bT;
@@ -88,22 +92,23 @@ __device__ __forceinline__ Pat patterns(double s2g, double c2g, double P1, doubl
 }
 
 // phase-derivative values common to all IFOs of one site at one point
-struct Phase {
-    double Mc, eta, th, ph, tc, p9, p10;   // d Phi / d theta_i
-    double tMc, teta;                      // Omega_E d tau*/d Mc, Omega_E d tau*/d eta
+template <typename T>
+struct PhaseT {
+    T Mc, eta, th, ph, tc, p9, p10;   // d Phi / d theta_i
+    T tMc, teta;                      // Omega_E d tau*/d Mc, Omega_E d tau*/d eta
 };
+using Phase = PhaseT<double>;
 
 // tangents of one IFO: real and imaginary parts
-template <int NP, bool ROT>
-__device__ __forceinline__ void tangents(const Pat &p, double Acp, double Acx, double Adcp,
-                                         double Adcx, double aMc, double invdL, const Phase &ph,
-                                         double (&gr)[NP], double (&gi)[NP], double &qr,
-                                         double &qi)
+template <int NP, bool ROT, typename T>
+__device__ __forceinline__ void tangents(const PatT<T> &p, T Acp, T Acx, T Adcp, T Adcx, T aMc,
+                                         T invdL, const PhaseT<T> &ph, T (&gr)[NP], T (&gi)[NP],
+                                         T &qr, T &qi)
 {
     qr = Acp * p.fp;
     qi = Acx * p.fx;
-    const double xr = Acp * p.fpX, xi = Acx * p.fxX;   // dQ/dx
-    const double tr = Acp * p.fpT, ti = Acx * p.fxT;   // dQ/dtheta
+    const T xr = Acp * p.fpX, xi = Acx * p.fxX;   // dQ/dx
+    const T tr = Acp * p.fpT, ti = Acx * p.fxT;   // dQ/dtheta
     // Mc
     gr[0] = aMc * qr - qi * ph.Mc;
     gi[0] = aMc * qi + qr * ph.Mc;
@@ -173,6 +178,151 @@ __device__ __forceinline__ double psd_table_lns(const DevNet &net, int p, double
     return fma(__ldg(&T[seg].slope), x - __ldg(&T[seg].lnf), __ldg(&T[seg].lns));
 }
 
+// PN terms at one grid point v = (pi M f)^(1/3): the frequency, the phase
+// derivatives d Psi/d Mc, d Psi/d eta (basis of 11 powers of v, ln v) and of
+// slots 9, 10, and (rotation) tau*(f) with its Mc and eta derivatives
+template <typename T>
+struct PnTermsT {
+    T f, vi3, dMc, dEt, d9, d10, tau, tMc, tEt;
+};
+using PnTerms = PnTermsT<double>;
+
+template <int NP, bool ROT, typename T>
+__device__ __forceinline__ PnTermsT<T> pn_terms(const T *E, T v, T vinv, T lnv)
+{
+    PnTermsT<T> t;
+    const T vi2 = vinv * vinv, vi3 = vi2 * vinv, vi5 = vi3 * vi2;
+    const T v2 = v * v, v5 = v2 * v2 * v, v7 = v5 * v2, vl = v * lnv;
+    t.vi3 = vi3;
+    t.f = v2 * v * E[EV_INV_PIM];
+    const T *PM = E + EV_PM, *PE = E + EV_PE;
+    T dMc = PM[8] * v7;
+    dMc = fma(PM[7], v5, dMc);
+    dMc = fma(PM[10], vl, dMc);
+    dMc = fma(PM[6], v2, dMc);
+    dMc = fma(PM[5], v, dMc);
+    dMc = PM[4] + dMc;
+    dMc = fma(PM[3], vinv, dMc);
+    dMc = fma(PM[2], vi2, dMc);
+    dMc = fma(PM[1], vi3, dMc);
+    dMc = fma(PM[0], vi5, dMc);
+    asm volatile("" ::: "memory");   // keep coefficient loads local (register pressure)
+    T dEt = PE[8] * v7;
+    dEt = fma(PE[7], v5, dEt);
+    dEt = fma(PE[10], vl, dEt);
+    dEt = fma(PE[9], lnv, dEt);
+    dEt = fma(PE[6], v2, dEt);
+    dEt = fma(PE[5], v, dEt);
+    dEt = PE[4] + dEt;
+    dEt = fma(PE[3], vinv, dEt);
+    dEt = fma(PE[2], vi2, dEt);
+    dEt = fma(PE[1], vi3, dEt);
+    dEt = fma(PE[0], vi5, dEt);
+    asm volatile("" ::: "memory");
+    t.dMc = dMc;
+    t.dEt = dEt;
+    t.d9 = t.d10 = T(0.0);
+    if (NP == 11) {
+        const T *P9 = E + EV_P9, *P10 = E + EV_P10;
+        t.d9 = fma(P9[0], vi2, fma(P9[1], vinv, fma(P9[2], v5, P9[3] * v7)));
+        t.d10 = fma(P10[0], vi2, fma(P10[1], vinv, fma(P10[2], v5, P10[3] * v7)));
+    }
+    // tau*(f) and its derivatives (rotation only)
+    t.tau = t.tMc = t.tEt = T(0.0);
+    if (ROT) {
+        const T *T0 = E + EV_T0, *TM = E + EV_TM, *TE = E + EV_TE;
+        const T b[8] = {vi5, vi3, vi2, vinv, T(1.0), v, v2, vl};
+        T s0 = T0[7] * b[7], s1 = TM[7] * b[7], s2 = TE[7] * b[7];
+#pragma unroll
+        for (int q = 6; q >= 0; q--) {
+            s0 = fma(T0[q], b[q], s0);
+            s1 = fma(TM[q], b[q], s1);
+            s2 = fma(TE[q], b[q], s2);
+        }
+        t.tau = s0 * vi3;
+        t.tMc = s1 * vi3;
+        t.tEt = s2 * vi3;
+        asm volatile("" ::: "memory");
+    }
+    return t;
+}
+
+// amplitude times the square root of the noise weight per PSD:
+// sigma_p = A sqrt(W_p), W_p = 4 w / S_p(f) at grid point k of weight w
+template <bool TAB>
+__device__ __forceinline__ void psd_sigma(const DevNet &net, const double *E, int k, double f,
+                                          double vi3, double w, double Aamp, int (&tseg)[MAX_PSD],
+                                          double (&Wp)[MAX_PSD])
+{
+#pragma unroll
+    for (int p = 0; p < MAX_PSD; p++) {
+        if (TAB && p < net.n_psd && net.psd_kind[p] == 1) {
+            // tabulated PSD: ln S on the log-log segment holding ln f
+            // (blind outside the table: zero weight)
+            const double lnf_k = fma((double)k, E[EV_LNR], E[EV_LNF0]);
+            const double lns = psd_table_lns(net, p, lnf_k, tseg[p]);
+            Wp[p] = Aamp * sqrt(4.0 * w) * exp(-0.5 * lns);
+        } else if (p < net.n_psd) {
+            const double x = f * net.psd_inv_f0[p];
+            const double xi = net.psd_f0[p] * E[EV_PIM] * vi3;
+            double S = 0.0;
+            for (int q = 0; q < net.psd_nterm[p]; q++) {
+                const int pw = net.psd_pow[p][q];
+                S = fma(net.psd_coef[p][q], pw >= 0 ? ipow(x, pw) : ipow(xi, -pw), S);
+            }
+            Wp[p] = Aamp * sqrt(4.0 * w * rcp64(S));
+        } else {
+            Wp[p] = 0.0;
+        }
+    }
+}
+
+// site terms at one grid point: the pattern-function coefficients J at the
+// Earth angle x = x0 + Omega_E tau* (rotation) and the phase derivatives,
+// including the Doppler phase, shared by the site's interferometers
+template <int MODE, bool ROT, typename T>
+__device__ __forceinline__ void site_terms(const T *S, const PnTermsT<T> &pn, T twopif,
+                                           T (&J)[12], PhaseT<T> &ph)
+{
+    const T x = ROT ? fma(T(OMEGA_E), pn.tau, S[SC_X0]) : S[SC_X0];
+    T sx, cxx;
+    sincos(x, &sx, &cxx);
+    const T c2x = fma(T(2.0) * cxx, cxx, T(-1.0)), s2x = T(2.0) * sx * cxx;
+    J[0] = fma(S[SC_A1], c2x, fma(S[SC_A2], cxx, S[SC_A3]));
+    J[1] = fma(S[SC_A4], s2x, S[SC_A5] * sx);
+    J[2] = fma(S[SC_B1], c2x, S[SC_B2] * cxx);
+    J[3] = fma(S[SC_B3], s2x, S[SC_B4] * sx);
+    J[4] = fma(S[SC_A1T], c2x, fma(S[SC_A2T], cxx, S[SC_A3T]));
+    J[5] = fma(S[SC_A4T], s2x, S[SC_A5T] * sx);
+    J[6] = fma(S[SC_B1T], c2x, S[SC_B2T] * cxx);
+    J[7] = fma(S[SC_B3T], s2x, S[SC_B4T] * sx);
+    J[8] = fma(-2.0 * S[SC_A1], s2x, -S[SC_A2] * sx);
+    J[9] = fma(2.0 * S[SC_A4], c2x, S[SC_A5] * cxx);
+    J[10] = fma(-2.0 * S[SC_B1], s2x, -S[SC_B2] * sx);
+    J[11] = fma(2.0 * S[SC_B3], c2x, S[SC_B4] * cxx);
+    const T dxPD = -twopif * S[SC_D1] * sx;
+    ph.th = twopif * fma(S[SC_D1T], cxx, S[SC_D2T]);
+    ph.ph = dxPD;
+    ph.Mc = pn.dMc;
+    ph.eta = pn.dEt;
+    ph.tc = twopif;
+    ph.p9 = pn.d9;
+    ph.p10 = pn.d10;
+    ph.tMc = T(0.0);
+    ph.teta = T(0.0);
+    if (ROT) {
+        // dx/dMc = Omega_E dtau*/dMc, dx/deta likewise, dx/dtc = -Omega_E
+        ph.tMc = T(OMEGA_E) * pn.tMc;
+        ph.teta = T(OMEGA_E) * pn.tEt;
+        ph.Mc = fma(dxPD, ph.tMc, pn.dMc);
+        ph.eta = fma(dxPD, ph.teta, pn.dEt);
+        ph.tc = fma(T(-OMEGA_E), dxPD, twopif);
+    }
+    if (MODE == MODE_SNRGRAD) {
+        ph.Mc = ph.eta = ph.th = ph.ph = ph.tc = ph.p9 = ph.p10 = T(0.0);
+    }
+}
+
 template <int MODE, int NP, bool ROT, bool TAB, int G>
 __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
 {
@@ -228,7 +378,6 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
             double Aamp = E[EV_A0] * exp(-7.0 / 6.0 * lnf);
             const double rho = E[adv_slot<G>(0)], rhoi = E[adv_slot<G>(1)];
             const double dlnv = E[adv_slot<G>(2)], rA = E[adv_slot<G>(3)];
-            const double inv_pim = E[EV_INV_PIM], pim = E[EV_PIM];
             const double wc0 = E[EV_WC0], wcm = E[EV_WCM], wcn = E[EV_WCN];
             const double cp = E[EV_CP], cx = E[EV_CX], dcp = E[EV_DCP], dcx = E[EV_DCX];
             const double c2p = E[EV_C2PSI], s2p = E[EV_S2PSI];
@@ -239,84 +388,14 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
 
 #pragma unroll 1
             for (; k < ke; k += G) {
-                // ---- grid point, weight, basis
-                const double vi2 = vinv * vinv, vi3 = vi2 * vinv, vi5 = vi3 * vi2;
-                const double v2 = v * v, v5 = v2 * v2 * v, v7 = v5 * v2, vl = v * lnv;
-                const double f = v2 * v * inv_pim;
-                const double w = f * (k == 0 ? wc0 : (k == N - 1 ? wcn : wcm));
-                const double twopif = TWO_PI * f;
-                // ---- phase derivatives of the PN phase (basis B11 dot products)
-                const double *PM = E + EV_PM, *PE = E + EV_PE;
-                double dMc = PM[8] * v7;
-                dMc = fma(PM[7], v5, dMc);
-                dMc = fma(PM[10], vl, dMc);
-                dMc = fma(PM[6], v2, dMc);
-                dMc = fma(PM[5], v, dMc);
-                dMc = fma(PM[4], 1.0, dMc);
-                dMc = fma(PM[3], vinv, dMc);
-                dMc = fma(PM[2], vi2, dMc);
-                dMc = fma(PM[1], vi3, dMc);
-                dMc = fma(PM[0], vi5, dMc);
-                asm volatile("" ::: "memory");   // keep coefficient loads local (register pressure)
-                double dEt = PE[8] * v7;
-                dEt = fma(PE[7], v5, dEt);
-                dEt = fma(PE[10], vl, dEt);
-                dEt = fma(PE[9], lnv, dEt);
-                dEt = fma(PE[6], v2, dEt);
-                dEt = fma(PE[5], v, dEt);
-                dEt = PE[4] + dEt;
-                dEt = fma(PE[3], vinv, dEt);
-                dEt = fma(PE[2], vi2, dEt);
-                dEt = fma(PE[1], vi3, dEt);
-                dEt = fma(PE[0], vi5, dEt);
-                asm volatile("" ::: "memory");
-                double d9 = 0.0, d10 = 0.0;
-                if (NP == 11) {
-                    const double *P9 = E + EV_P9, *P10 = E + EV_P10;
-                    d9 = fma(P9[0], vi2, fma(P9[1], vinv, fma(P9[2], v5, P9[3] * v7)));
-                    d10 = fma(P10[0], vi2, fma(P10[1], vinv, fma(P10[2], v5, P10[3] * v7)));
-                }
-                // ---- tau*(f) and its derivatives (rotation only)
-                double tau = 0.0, tMc = 0.0, tEt = 0.0;
-                if (ROT) {
-                    const double *T0 = E + EV_T0, *TM = E + EV_TM, *TE = E + EV_TE;
-                    double b[8] = {vi5, vi3, vi2, vinv, 1.0, v, v2, vl};
-                    double s0 = T0[7] * b[7], s1 = TM[7] * b[7], s2 = TE[7] * b[7];
-#pragma unroll
-                    for (int q = 6; q >= 0; q--) {
-                        s0 = fma(T0[q], b[q], s0);
-                        s1 = fma(TM[q], b[q], s1);
-                        s2 = fma(TE[q], b[q], s2);
-                    }
-                    tau = s0 * vi3;
-                    tMc = s1 * vi3;
-                    tEt = s2 * vi3;
-                    asm volatile("" ::: "memory");
-                }
+                // ---- grid point, weight, PN terms
+                const PnTerms pn = pn_terms<NP, ROT>(E, v, vinv, lnv);
+                const double w = pn.f * (k == 0 ? wc0 : (k == N - 1 ? wcn : wcm));
+                const double twopif = TWO_PI * pn.f;
                 // ---- amplitude times sqrt of the noise weight per PSD:
                 //      sigma = A sqrt(W), W = 4 w / S_n(f); tangents are scaled by it
                 double Wp[MAX_PSD];
-#pragma unroll
-                for (int p = 0; p < MAX_PSD; p++) {
-                    if (TAB && p < net.n_psd && net.psd_kind[p] == 1) {
-                        // tabulated PSD: ln S on the log-log segment holding ln f
-                        // (blind outside the table: zero weight)
-                        const double lnf_k = fma((double)k, lnr, E[EV_LNF0]);
-                        const double lns = psd_table_lns(net, p, lnf_k, tseg[p]);
-                        Wp[p] = Aamp * sqrt(4.0 * w) * exp(-0.5 * lns);
-                    } else if (p < net.n_psd) {
-                        const double x = f * net.psd_inv_f0[p];
-                        const double xi = net.psd_f0[p] * pim * vi3;
-                        double S = 0.0;
-                        for (int q = 0; q < net.psd_nterm[p]; q++) {
-                            const int pw = net.psd_pow[p][q];
-                            S = fma(net.psd_coef[p][q], pw >= 0 ? ipow(x, pw) : ipow(xi, -pw), S);
-                        }
-                        Wp[p] = Aamp * sqrt(4.0 * w * rcp64(S));
-                    } else {
-                        Wp[p] = 0.0;
-                    }
-                }
+                psd_sigma<TAB>(net, E, k, pn.f, pn.vi3, w, Aamp, tseg, Wp);
 
                 // ---- sites
 #pragma unroll 1
@@ -325,45 +404,9 @@ __global__ void __launch_bounds__(128) k_points_fp64(PointArgs A)
                     if (MODE == MODE_LOGDET && !((A.det_mask >> s) & 1u)) continue;
                     const double *S = A.sitec + (e * net.n_site + s) * (int64_t)SC_N;
                     if (net.masked && S[SC_SLOT0] < 0.0) continue;   // every arm of the site off
-                    const double x = ROT ? fma(OMEGA_E, tau, S[SC_X0]) : S[SC_X0];
-                    double sx, cxx;
-                    sincos(x, &sx, &cxx);
-                    const double c2x = fma(2.0 * cxx, cxx, -1.0), s2x = 2.0 * sx * cxx;
                     double J[12];
-                    J[0] = fma(S[SC_A1], c2x, fma(S[SC_A2], cxx, S[SC_A3]));
-                    J[1] = fma(S[SC_A4], s2x, S[SC_A5] * sx);
-                    J[2] = fma(S[SC_B1], c2x, S[SC_B2] * cxx);
-                    J[3] = fma(S[SC_B3], s2x, S[SC_B4] * sx);
-                    J[4] = fma(S[SC_A1T], c2x, fma(S[SC_A2T], cxx, S[SC_A3T]));
-                    J[5] = fma(S[SC_A4T], s2x, S[SC_A5T] * sx);
-                    J[6] = fma(S[SC_B1T], c2x, S[SC_B2T] * cxx);
-                    J[7] = fma(S[SC_B3T], s2x, S[SC_B4T] * sx);
-                    J[8] = fma(-2.0 * S[SC_A1], s2x, -S[SC_A2] * sx);
-                    J[9] = fma(2.0 * S[SC_A4], c2x, S[SC_A5] * cxx);
-                    J[10] = fma(-2.0 * S[SC_B1], s2x, -S[SC_B2] * sx);
-                    J[11] = fma(2.0 * S[SC_B3], c2x, S[SC_B4] * cxx);
                     Phase ph;
-                    const double dxPD = -twopif * S[SC_D1] * sx;
-                    ph.th = twopif * fma(S[SC_D1T], cxx, S[SC_D2T]);
-                    ph.ph = dxPD;
-                    ph.Mc = dMc;
-                    ph.eta = dEt;
-                    ph.tc = twopif;
-                    ph.p9 = d9;
-                    ph.p10 = d10;
-                    ph.tMc = 0.0;
-                    ph.teta = 0.0;
-                    if (ROT) {
-                        // dx/dMc = Omega_E dtau*/dMc, dx/deta likewise, dx/dtc = -Omega_E
-                        ph.tMc = OMEGA_E * tMc;
-                        ph.teta = OMEGA_E * tEt;
-                        ph.Mc = fma(dxPD, ph.tMc, dMc);
-                        ph.eta = fma(dxPD, ph.teta, dEt);
-                        ph.tc = fma(-OMEGA_E, dxPD, twopif);
-                    }
-                    if (MODE == MODE_SNRGRAD) {
-                        ph.Mc = ph.eta = ph.th = ph.ph = ph.tc = ph.p9 = ph.p10 = 0.0;
-                    }
+                    site_terms<MODE, ROT>(S, pn, twopif, J, ph);
 #pragma unroll 1
                     for (int slot = 0; slot < net.site_nslot[s]; slot++) {
                         // interferometer of this slot; an empty slot (duty factor)

@@ -1,0 +1,645 @@
+// gw_points_fp64_tc.cu -- the Fisher pass with its Gram accumulation on the
+// tensor cores (tcgen05), exactly, fed by tangents in FP64 or in double-float.
+//
+// The Fisher matrix of a work item is the Gram matrix of its tangent rows,
+//     Gamma_ij = sum_k y_ik y_jk,   y_.k = (Re g, Im g) of one interferometer at
+//     one grid point, tangents pre-scaled by sigma = A sqrt(4 w / S_n)
+// (Sec. 3.2, Eqs. 3.1-3.3).  Every tangent value is written, per item and
+// column, as a 56-bit fixed-point number relative to the column's largest
+// exponent, split into eight 7-bit digits (sign-magnitude, each exact in
+// bf16), and the tensor core forms all digit products with FP32 accumulation.
+// A digit product is below 2^14 and an item has at most 1024 rows (256 points
+// x 2 interferometers x real/imaginary), so every partial sum is an integer
+// below 2^24: the accumulation is exact.  The digit Gram D[(i,a),(j,b)] is then
+// combined in FP64,
+//     Gamma_ij = 2^(E_i + E_j - 2058) sum_ab 2^(-7(a + b)) D[(i,a),(j,b)],
+// so the item's Fisher matrix is the exact Gram of the tangents rounded to 56
+// bits (relative to the column maximum), summed in FP64 only over the 64 digit
+// pairs.
+//
+// The tangents come from the templated formulas of gw_points_fp64.cuh with
+// scalar type T:
+//  * T = double (GW_FP64 with the tensor-core Gram): the FP64 pass, every
+//    operation on the FP64 pipe except the Gram;
+//  * T = dfl (GW_DFLOAT): the same formulas in double-float arithmetic
+//    (gw_dfloat.cuh, ~2^-48) on the FP32 pipe.  An error of the tangents
+//    relative to their own scale is a perturbation of the Gram's vectors, which
+//    reaches the covariance only through the square root of the condition
+//    number, so double-float tangents with an exact Gram give FP64-class
+//    covariances at FP32-pipe speed.  The noise curve and the amplitude are
+//    carried relative to the network's reference PSD scale (FP32 range); a
+//    tabulated PSD's weight is taken in FP64 and converted.
+//
+// Shape.  128 threads (one grid point each, two rounds for items of more than
+// 128 points), two CTAs per SM, persistent over the items.  Each thread keeps
+// its point's values (columns x rows r = interferometer x {Re, Im}) in
+// registers; the first round of a two-round item is staged in shared memory
+// until the column maxima are known.  The digits go to shared memory in the
+// MN-major, no-swizzle operand layout (8 digits of one value = one 16-byte
+// row of a core matrix; K groups of 8 rows at stride KG, MN groups at 128
+// bytes), one K block of 128 rows per (round, r), double-buffered: one thread
+// issues the block's eight M=128 x N x K=16 MMAs (A = B = the block) into the
+// item's TMEM accumulator and commits them to the buffer's mbarrier, which the
+// writers of the buffer after next wait on.  After the item's last block the
+// four warps read their 32 TMEM lanes (rows (i, a)) and reduce over the digit
+// pairs.  Networks of at most two interferometers per point (one triangle or
+// up to two L-shaped detectors) take this kernel; wider networks, and the SNR,
+// SNR-gradient and log-det passes, run the FP64-pipe kernel.
+//
+// Every wait is bounded (about a second of wall time); a wait that runs out
+// sets *kerr, writes NaN into the item's sums and ends the CTA after freeing
+// its TMEM.
+#include <type_traits>
+
+#include "gw_points_fp64.cuh"
+
+namespace gw {
+
+namespace {
+
+constexpr int TC_T = 128;                 // threads = points per round
+constexpr int TC_KROWS = 128;             // K rows per block (one value per thread)
+constexpr int TC_MG = 128;                // bytes between MN groups (8 digits x 8 rows)
+constexpr int TC_PW = 104;                // power tables (96) and per-item bases (8)
+
+template <int NP>
+struct TcShape {
+    static constexpr int KG = NP * 128;                    // bytes between K groups
+    static constexpr int BLK = (TC_KROWS / 8) * KG;        // one K block
+    static constexpr int N = ((NP * 8 + 15) / 16) * 16;    // MMA N (digit rows used, padded)
+    // operand buffers, 1 KB slack after the second: an M = 128 read of the last
+    // MMA step of a block reaches 2047 - KG bytes past the block
+    static constexpr int OPS_BYTES = 2 * BLK + 1024;
+    static constexpr int STAGE_BYTES = NP * 4 * TC_T * 8;
+    // double-float copies: event constants, site constants, interferometer
+    // (s2g, c2g, amp) and PSD constants (inverse f0, f0, coefficients)
+    static constexpr int DF_WORDS = EVC + MAX_SITE * SC_N + 3 * MAX_IFO +
+                                    MAX_PSD * (2 + MAX_TERM) + TC_PW;
+    static constexpr size_t smem(bool df)
+    {
+        return (size_t)OPS_BYTES + STAGE_BYTES + (size_t)EVC * 8 + TC_PW * 8 + 16 * 4 + 2 * 8 +
+               16 + (df ? (size_t)DF_WORDS * 8 : 0);
+    }
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the completion of the mbarrier phase of the given parity, for at
+// most about a second
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t done = 0;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (globaltimer() - t0 > 1000000000ull) return false;
+    }
+}
+
+// shared-memory matrix descriptor, no swizzle: start, K-group stride (LBO),
+// MN-group stride (SBO), descriptor version 1
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t kstride, uint32_t mnstride)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((kstride >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((mnstride >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// the eight 7-bit digits of a 56-bit magnitude N as bf16 values with the given
+// sign, digit a (bits 49 - 7a .. 55 - 7a) in element a of the row
+__device__ __forceinline__ uint4 pack_digits(unsigned long long N, bool negative)
+{
+    const unsigned nh = (unsigned)(N >> 28), nl = (unsigned)N & 0x0FFFFFFFu;
+    // digit d as an FP32 number: the integer d below 2^23 in the mantissa of 2^23
+    auto fd = [](unsigned d) { return __float_as_uint(__uint_as_float(0x4B000000u | d) - 8388608.0f); };
+    uint4 r;
+    r.x = __byte_perm(fd((nh >> 21) & 127u), fd((nh >> 14) & 127u), 0x7632);
+    r.y = __byte_perm(fd((nh >> 7) & 127u), fd(nh & 127u), 0x7632);
+    r.z = __byte_perm(fd((nl >> 21) & 127u), fd((nl >> 14) & 127u), 0x7632);
+    r.w = __byte_perm(fd((nl >> 7) & 127u), fd(nl & 127u), 0x7632);
+    if (negative) {
+        r.x ^= 0x80008000u;
+        r.y ^= 0x80008000u;
+        r.z ^= 0x80008000u;
+        r.w ^= 0x80008000u;
+    }
+    return r;
+}
+
+// mant x 2^(-sh) rounded to nearest (sh >= -32 here, mant < 2^53), 0 when
+// shifted out
+__device__ __forceinline__ unsigned long long shift_round(unsigned long long mant, int sh)
+{
+    if (sh <= 0) return mant << (-sh);
+    if (sh >= 62) return 0ull;
+    return (mant + (1ull << (sh - 1))) >> sh;
+}
+
+// biased FP64 exponent of a value (FP32 exponents rebased; 0 for zero and
+// subnormals, 2047 for Inf and NaN)
+__device__ __forceinline__ unsigned expo(double y)
+{
+    return ((unsigned)__double2hiint(y) >> 20) & 0x7FFu;
+}
+__device__ __forceinline__ unsigned expo(dfl y)
+{
+    const unsigned e = (__float_as_uint(y.hi) >> 23) & 0xFFu;
+    return e == 0u ? 0u : (e == 255u ? 2047u : e + 896u);
+}
+
+// digits of |y| as a 56-bit fixed-point number relative to the column's
+// largest biased exponent ec: |y| ~ N 2^(ec - 1078), N < 2^56, rounded
+__device__ __forceinline__ uint4 digits8(double y, int ec)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+    const int e = (int)((b >> 52) & 0x7FFu);
+    unsigned long long N = 0;
+    if (e != 0) {
+        const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+        N = shift_round(mant, ec - e - 3);    // e <= ec: shift >= -3, N < 2^56
+    }
+    return pack_digits(N, (b >> 63) != 0);
+}
+
+// double-float y = hi + lo (|lo| <= ulp(hi) / 2): the pair's magnitude from
+// the two 24-bit mantissas (lo adds or subtracts by its sign)
+__device__ __forceinline__ uint4 digits8(dfl y, int ec)
+{
+    const unsigned bh = __float_as_uint(y.hi), bl = __float_as_uint(y.lo);
+    const int eh = (int)((bh >> 23) & 0xFFu), el = (int)((bl >> 23) & 0xFFu);
+    unsigned long long N = 0;
+    if (eh != 0) {
+        // |hi| = m 2^(eh - 150), in units of 2^(ec - 1078): shift by eh + 928 - ec (<= 32)
+        N = shift_round((unsigned long long)((bh & 0x7FFFFFu) | 0x800000u), ec - eh - 928);
+        if (el != 0) {
+            const unsigned long long nl =
+                shift_round((unsigned long long)((bl & 0x7FFFFFu) | 0x800000u), ec - el - 928);
+            N = ((bh ^ bl) >> 31) ? N - nl : N + nl;
+        }
+    }
+    return pack_digits(N, (bh >> 31) != 0);
+}
+
+// 2^x in FP64 (x an integer), NaN when a column held a non-finite value
+__device__ __forceinline__ double pow2_scale(int ei, int ej)
+{
+    if (ei == 2047 || ej == 2047) return __longlong_as_double(0x7FF8000000000000ll);
+    const int x = ei + ej - 2058;
+    const int be = x + 1023;
+    if (be >= 1 && be <= 2046) return __longlong_as_double((long long)be << 52);
+    return ldexp(1.0, x);
+}
+
+// double-float noise weights sigma_p = A sqrt(4 w / S_p) (A and S relative to
+// the reference scale); a tabulated PSD's factor is formed in FP64
+template <bool TAB>
+__device__ __forceinline__ void psd_sigma_df(const DevNet &net, const dfl *psd_d, const dfl *E,
+                                             const double *Ed, int k, dfl f, dfl vi3, dfl w,
+                                             dfl Aamp, int (&tseg)[MAX_PSD], dfl (&Wp)[MAX_PSD])
+{
+#pragma unroll
+    for (int p = 0; p < MAX_PSD; p++) {
+        const dfl *P = psd_d + p * (2 + MAX_TERM);   // inverse f0, f0, coefficients
+        if (TAB && p < net.n_psd && net.psd_kind[p] == 1) {
+            const double lnf_k = fma((double)k, Ed[EV_LNR], Ed[EV_LNF0]);
+            const double lns = psd_table_lns(net, p, lnf_k, tseg[p]);
+            const double wd = (double)w.hi + (double)w.lo;
+            Wp[p] = Aamp * dfl(sqrt(4.0 * wd) * exp(-0.5 * (lns - net.ln_scale_ref)));
+        } else if (p < net.n_psd) {
+            const dfl x = f * P[0];
+            const dfl xi = P[1] * E[EV_PIM] * vi3;
+            dfl S(0.0f, 0.0f);
+            for (int q = 0; q < net.psd_nterm[p]; q++) {
+                const int pw = net.psd_pow[p][q];
+                S = fma(P[2 + q], df_ipow(pw >= 0 ? x : xi, pw >= 0 ? pw : -pw), S);
+            }
+            Wp[p] = Aamp * df_sqrt(df_mul_f(w, 4.0f) * df_rcp(S));
+        } else {
+            Wp[p] = dfl(0.0f, 0.0f);
+        }
+    }
+}
+
+template <int NP, bool ROT, bool TAB, typename T>
+__global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
+{
+    using SH = TcShape<NP>;
+    constexpr bool DF = std::is_same<T, dfl>::value;
+    constexpr int KG = SH::KG, BLK = SH::BLK, NMMA = SH::N;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char *ops = tc_smem;
+    T *stage = reinterpret_cast<T *>(tc_smem + SH::OPS_BYTES);
+    double *cs = reinterpret_cast<double *>(stage + NP * 4 * TC_T);   // event constants
+    double *pw = cs + EVC;                   // [3][2][16] powers, then bases
+    unsigned *emax = reinterpret_cast<unsigned *>(pw + TC_PW);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(emax + 16);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
+    // double-float copies (T = dfl only)
+    dfl *Ed = reinterpret_cast<dfl *>(tmem_slot + 4);
+    dfl *Sd = Ed + EVC;                       // [MAX_SITE][SC_N]
+    dfl *Qd = Sd + MAX_SITE * SC_N;           // [MAX_IFO][3]: s2g, c2g, amp
+    dfl *Pd = Qd + 3 * MAX_IFO;               // [MAX_PSD][2 + MAX_TERM]
+    dfl *pwd = Pd + MAX_PSD * (2 + MAX_TERM);  // powers and bases
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const DevNet &net = A.net;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(tmem_slot)), "r"(128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(&mbar[1])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (DF) {
+        // network constants: interferometers, and the PSDs relative to the
+        // reference scale (S / scale_ref; the amplitude carries 1/sqrt(scale_ref))
+        const double inv_ref = net.inv_sqrt_scale_ref * net.inv_sqrt_scale_ref;
+        for (int q = t; q < net.n_ifo; q += TC_T) {
+            Qd[3 * q + 0] = dfl(net.ifo_s2g[q]);
+            Qd[3 * q + 1] = dfl(net.ifo_c2g[q]);
+            Qd[3 * q + 2] = dfl(net.ifo_amp[q]);
+        }
+        for (int i = t; i < net.n_psd * (2 + MAX_TERM); i += TC_T) {
+            const int p = i / (2 + MAX_TERM), j = i % (2 + MAX_TERM);
+            const double v = j == 0 ? net.psd_inv_f0[p]
+                           : j == 1 ? net.psd_f0[p]
+                           : (j - 2 < net.psd_nterm[p] ? net.psd_coef[p][j - 2] * inv_ref : 0.0);
+            Pd[i] = dfl(v);
+        }
+    }
+    // the operand slack and the digit rows past the stored ones are read by the
+    // MMAs (they only reach accumulator rows and columns that are not used):
+    // keep them finite
+    for (int i = t; i < SH::OPS_BYTES / 16; i += TC_T)
+        reinterpret_cast<uint4 *>(ops)[i] = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t ops_addr = smem_addr(ops);
+    // instruction descriptor: D FP32, A and B bf16, both MN-major, N, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                           ((uint32_t)(NMMA >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    uint32_t par0 = 0, par1 = 0;
+    bool pend0 = false, pend1 = false;
+    bool ok = true;
+
+    const int64_t n_total = A.item_off[A.n_ev];
+    const int64_t n_items = n_total < A.n_items ? n_total : A.n_items;
+
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int64_t e = find_event(A.item_off, A.n_ev, it);
+        const int64_t jit = it - A.item_off[e];
+        const int64_t nj = A.item_off[e + 1] - A.item_off[e];
+        const double *Eg = A.evc + e * (int64_t)EVC;
+        for (int q = t; q < EVC; q += TC_T) {
+            const double v = Eg[q];
+            cs[q] = v;
+            if (DF) Ed[q] = dfl(v);
+        }
+        if (DF) {
+            for (int i = t; i < net.n_site * SC_N; i += TC_T)
+                Sd[i] = dfl(A.sitec[e * net.n_site * (int64_t)SC_N + i]);
+        }
+        if (t < 16) emax[t] = 0u;
+        __syncthreads();
+        const int N = (int)cs[EV_NPTS];
+        const int kb = (int)((int64_t)N * jit / nj), ke = (int)((int64_t)N * (jit + 1) / nj);
+        const int rounds = ke - kb > TC_T ? 2 : 1;
+        const double lnr = cs[EV_LNR];
+        // powers of the per-point factors of v, 1/v and the amplitude (steps 1
+        // and 16 points) and their values at the item's first point
+        if (t < 6) {
+            const int q = t % 3, big = t / 3;
+            const double l = q == 0 ? lnr * (1.0 / 3.0) : (q == 1 ? -lnr * (1.0 / 3.0) : -7.0 / 6.0 * lnr);
+            const double fct = exp(big ? 16.0 * l : l);
+            double val = 1.0;
+            for (int i = 0; i < 16; i++) {
+                pw[(q * 2 + big) * 16 + i] = val;
+                if (DF) pwd[(q * 2 + big) * 16 + i] = dfl(val);
+                val *= fct;
+            }
+        } else if (t < 10) {
+            const double lnf0 = fma((double)kb, lnr, cs[EV_LNF0]);
+            const double lnv0 = (lnf0 + cs[EV_LNPIM]) * (1.0 / 3.0);
+            const int q = t - 6;
+            const double b = q == 0 ? exp(lnv0)
+                           : q == 1 ? exp(-lnv0)
+                           : q == 2 ? cs[EV_A0] * exp(-7.0 / 6.0 * lnf0)
+                                    : lnv0;
+            pw[96 + q] = b;
+            if (DF) {
+                // amplitude relative to sqrt(scale_ref); ln v step per point
+                pwd[96 + q] = dfl(q == 2 ? b * net.inv_sqrt_scale_ref : b);
+                if (q == 3) pwd[100] = dfl(lnr * (1.0 / 3.0));
+            }
+        }
+        __syncthreads();
+
+        // per-thread copies of the event's scalar constants
+        const T *E;
+        if constexpr (DF) E = Ed;
+        else E = cs;
+        const T wc0 = E[EV_WC0], wcm = E[EV_WCM], wcn = E[EV_WCN];
+        const T cp = E[EV_CP], cx = E[EV_CX], dcp = E[EV_DCP], dcx = E[EV_DCX];
+        const T c2p = E[EV_C2PSI], s2p = E[EV_S2PSI];
+        const T aMc = E[EV_AMC], invdL = E[EV_INVDL];
+        int tseg[MAX_PSD];
+#pragma unroll
+        for (int p = 0; p < MAX_PSD; p++) tseg[p] = -1;
+
+        // ---- tangents of this thread's point(s); rows r = 2 slot + {Re, Im}
+        T val[NP][4];
+        unsigned lmax[NP];
+#pragma unroll
+        for (int c = 0; c < NP; c++) lmax[c] = 0u;
+#pragma unroll 1
+        for (int rd = 0; rd < rounds; rd++) {
+#pragma unroll
+            for (int c = 0; c < NP; c++) val[c][0] = val[c][1] = val[c][2] = val[c][3] = T(0.0);
+            const int tt = rd * TC_T + t;
+            const int k = kb + tt;
+            if (k < ke) {
+                const int lo = tt & 15, hi = tt >> 4;
+                T v, vinv, Aamp, lnv;
+                if constexpr (DF) {
+                    v = pwd[96] * pwd[0 * 16 + lo] * pwd[1 * 16 + hi];
+                    vinv = pwd[97] * pwd[2 * 16 + lo] * pwd[3 * 16 + hi];
+                    Aamp = pwd[98] * pwd[4 * 16 + lo] * pwd[5 * 16 + hi];
+                    lnv = pwd[99] + df_mul_f(pwd[100], (float)tt);
+                } else {
+                    const double lnf = fma((double)k, lnr, cs[EV_LNF0]);
+                    lnv = (lnf + cs[EV_LNPIM]) * (1.0 / 3.0);
+                    v = pw[96] * pw[0 * 16 + lo] * pw[1 * 16 + hi];
+                    vinv = pw[97] * pw[2 * 16 + lo] * pw[3 * 16 + hi];
+                    Aamp = pw[98] * pw[4 * 16 + lo] * pw[5 * 16 + hi];
+                }
+                const PnTermsT<T> pn = pn_terms<NP, ROT>(E, v, vinv, lnv);
+                const T w = pn.f * (k == 0 ? wc0 : (k == N - 1 ? wcn : wcm));
+                const T twopif = T(TWO_PI) * pn.f;
+                T Wp[MAX_PSD];
+                if constexpr (DF)
+                    psd_sigma_df<TAB>(net, Pd, E, cs, k, pn.f, pn.vi3, w, Aamp, tseg, Wp);
+                else
+                    psd_sigma<TAB>(net, E, k, pn.f, pn.vi3, w, Aamp, tseg, Wp);
+                int L = 0;
+#pragma unroll 1
+                for (int s = 0; s < net.n_site; s++) {
+                    const double *Sg = A.sitec + (e * net.n_site + s) * (int64_t)SC_N;
+                    if (net.masked && Sg[SC_SLOT0] < 0.0) {   // every arm of the site off
+                        L += net.site_nslot[s];
+                        continue;
+                    }
+                    const T *S;
+                    if constexpr (DF) S = Sd + s * SC_N;
+                    else S = Sg;
+                    T J[12];
+                    PhaseT<T> ph;
+                    site_terms<MODE_FISHER, ROT>(S, pn, twopif, J, ph);
+#pragma unroll 1
+                    for (int slot = 0; slot < net.site_nslot[s]; slot++, L++) {
+                        int q = net.masked ? (int)Sg[SC_SLOT0 + slot] : net.site_ifo0[s] + slot;
+                        bool on = true;
+                        if (q < 0) {
+                            q = net.site_ifo0[s];
+                            on = false;
+                        }
+                        T s2g, c2g, amp;
+                        if constexpr (DF) {
+                            s2g = Qd[3 * q];
+                            c2g = Qd[3 * q + 1];
+                            amp = on ? Qd[3 * q + 2] : T(0.0);
+                        } else {
+                            s2g = net.ifo_s2g[q];
+                            c2g = net.ifo_c2g[q];
+                            amp = net.ifo_amp[q] * (on ? 1.0 : 0.0);
+                        }
+                        const PatT<T> pt = patterns(s2g, c2g, amp * c2p, amp * s2p, J);
+                        const T sg = Wp[net.ifo_psd[q]];
+                        T gr[NP], gi[NP], qr, qi;
+                        tangents<NP, ROT>(pt, sg * cp, sg * cx, sg * dcp, sg * dcx, aMc, invdL,
+                                          ph, gr, gi, qr, qi);
+                        if (L == 0) {
+#pragma unroll
+                            for (int c = 0; c < NP; c++) {
+                                val[c][0] = gr[c];
+                                val[c][1] = gi[c];
+                            }
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < NP; c++) {
+                                val[c][2] = gr[c];
+                                val[c][3] = gi[c];
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NP; c++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const unsigned ex = expo(val[c][r]);
+                    lmax[c] = ex > lmax[c] ? ex : lmax[c];
+                }
+            if (rounds == 2 && rd == 0) {
+#pragma unroll
+                for (int c = 0; c < NP; c++)
+#pragma unroll
+                    for (int r = 0; r < 4; r++) stage[(c * 4 + r) * TC_T + t] = val[c][r];
+            }
+        }
+        // ---- column maxima of the item's biased exponents
+#pragma unroll
+        for (int c = 0; c < NP; c++) {
+            const unsigned m = __reduce_max_sync(0xffffffffu, lmax[c]);
+            if (lane == 0) atomicMax(&emax[c], m);
+        }
+        __syncthreads();
+        int em[NP];
+#pragma unroll
+        for (int c = 0; c < NP; c++) em[c] = (int)emax[c];
+
+        // ---- digits into the operand buffers, one K block per (round, row)
+        int blk = 0;
+        const int krow = (t & 7) * 16 + (t >> 3) * KG;   // this thread's K row in a block
+#pragma unroll 1
+        for (int rd = 0; rd < rounds; rd++) {
+            const bool from_stage = rounds == 2 && rd == 0;
+#pragma unroll
+            for (int r = 0; r < 4; r++, blk++) {
+                const int buf = blk & 1;
+                // the MMAs that read this buffer two blocks ago must be done
+                if (buf == 0 ? pend0 : pend1) {
+                    const bool w = mbar_wait(smem_addr(&mbar[buf]), buf == 0 ? par0 : par1);
+                    ok = ok && w;
+                    if (buf == 0) {
+                        par0 ^= 1u;
+                        pend0 = false;
+                    } else {
+                        par1 ^= 1u;
+                        pend1 = false;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                }
+                unsigned char *B = ops + buf * BLK + krow;
+#pragma unroll
+                for (int c = 0; c < NP; c++) {
+                    const T y = from_stage ? stage[(c * 4 + r) * TC_T + t] : val[c][r];
+                    *reinterpret_cast<uint4 *>(B + c * TC_MG) = digits8(y, em[c]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncthreads();
+                if (t == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t b0 = ops_addr + buf * BLK;
+#pragma unroll
+                    for (int st = 0; st < TC_KROWS / 16; st++) {
+                        const uint64_t d = smem_desc(b0 + st * 2 * KG, KG, TC_MG);
+                        const uint32_t accum = (blk > 0 || st > 0) ? 1u : 0u;
+                        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                     :: "r"(tmem), "l"(d), "l"(d), "r"(idesc), "r"(accum));
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(smem_addr(&mbar[buf])));
+                }
+                if (buf == 0) pend0 = true;
+                else pend1 = true;
+            }
+        }
+        // ---- all of the item's MMAs complete
+        if (pend0) {
+            ok = ok && mbar_wait(smem_addr(&mbar[0]), par0);
+            par0 ^= 1u;
+            pend0 = false;
+        }
+        if (pend1) {
+            ok = ok && mbar_wait(smem_addr(&mbar[1]), par1);
+            par1 ^= 1u;
+            pend1 = false;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        double *out = A.partial + it * (int64_t)A.nacc;
+        if (__syncthreads_or(!ok)) {
+            for (int a = t; a < A.nacc; a += TC_T) out[a] = __longlong_as_double(0x7FF8000000000000ll);
+            if (t == 0 && A.kerr) atomicExch(A.kerr, 1);
+            break;
+        }
+
+        // ---- read the digit Gram: thread t holds row m = t = (i, a), i = t / 8,
+        // a = t % 8; columns (j, b) at 8 j + b.  Warp w holds rows of columns
+        // i >= 4 w, so it reads the column groups j >= 4 w.
+        const int i = t >> 3, a = t & 7;
+        const double sa = ldexp(1.0, -7 * a);
+#pragma unroll 1
+        for (int j = 4 * warp; j < NP; j++) {
+            uint32_t d[8];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 8);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]),
+                           "=r"(d[6]), "=r"(d[7])
+                         : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            // sum over b of 2^(-7 b) D[(i,a),(j,b)], then over a across the 8 lanes
+            double P = (double)__uint_as_float(d[7]);
+#pragma unroll
+            for (int b = 6; b >= 0; b--) P = fma(P, 0x1p-7, (double)__uint_as_float(d[b]));
+            P *= sa;
+            P += __shfl_xor_sync(0xffffffffu, P, 1);
+            P += __shfl_xor_sync(0xffffffffu, P, 2);
+            P += __shfl_xor_sync(0xffffffffu, P, 4);
+            if (a == 0 && i < NP && j >= i) {
+                const double g = P == 0.0 ? 0.0 : P * pow2_scale((int)emax[i], (int)emax[j]);
+                const int idx = 1 + i * NP - i * (i - 1) / 2 + (j - i);
+                if (idx < A.nacc) out[idx] = g;
+                // SNR^2 = sum |Q|^2 = the (Phic, Phic) entry: g_Phic = -i Q
+                if (i == 8 && j == 8) out[0] = g;
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();   // TMEM, emax and the buffers are free for the next item
+    }
+
+    // ---- teardown.  Normally every commit has been waited on.  After a wait
+    // that ran out, give the MMAs in flight one more bounded wait; then free
+    // the TMEM columns.
+    if (!ok) {
+        mbar_wait(smem_addr(&mbar[0]), par0 ^ 1u);
+        mbar_wait(smem_addr(&mbar[1]), par1 ^ 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(128));
+}
+
+template <int NP, bool ROT, bool TAB, typename T>
+cudaError_t launch_tc(const PointArgs &a, cudaStream_t s)
+{
+    const size_t smem = TcShape<NP>::smem(std::is_same<T, dfl>::value);
+    static PerDeviceOnce attr;
+    cudaError_t err = set_smem_once(attr, k_fisher_tc<NP, ROT, TAB, T>, smem);
+    if (err != cudaSuccess) return err;
+    if (a.n_items <= 0) return cudaSuccess;
+    k_fisher_tc<NP, ROT, TAB, T><<<points_grid_size(2), TC_T, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tc_t(int np, int rot, const PointArgs &a, cudaStream_t s)
+{
+    const bool tab = has_psd_table(a.net);
+    if (np == 9) {
+        if (rot) return tab ? launch_tc<9, true, true, T>(a, s) : launch_tc<9, true, false, T>(a, s);
+        return tab ? launch_tc<9, false, true, T>(a, s) : launch_tc<9, false, false, T>(a, s);
+    }
+    if (rot) return tab ? launch_tc<11, true, true, T>(a, s) : launch_tc<11, true, false, T>(a, s);
+    return tab ? launch_tc<11, false, true, T>(a, s) : launch_tc<11, false, false, T>(a, s);
+}
+
+}  // namespace
+
+bool fisher_fp64_tc_supported(const DevNet &net)
+{
+    int slots = 0;
+    for (int s = 0; s < net.n_site; s++) slots += net.site_nslot[s];
+    return slots <= 2;
+}
+
+cudaError_t launch_fisher_fp64_tc(int np, int rot, const PointArgs &a, cudaStream_t s)
+{
+    return launch_tc_t<double>(np, rot, a, s);
+}
+
+cudaError_t launch_fisher_dfloat_tc(int np, int rot, const PointArgs &a, cudaStream_t s)
+{
+    return launch_tc_t<dfl>(np, rot, a, s);
+}
+
+}  // namespace gw

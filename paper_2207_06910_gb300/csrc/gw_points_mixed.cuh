@@ -562,9 +562,9 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                                             sg * SC(EV_DCX).x, SC(EV_AMC).x, SC(EV_INVDL).x,
                                             ph, gr, gi, qr, qi, xr, xi, tr, ti);
                         // tangents as (real, imaginary) pairs
-                        float2 G[NP];
+                        float2 Gt[NP];
 #pragma unroll
-                        for (int i = 0; i < NP; i++) G[i] = make_float2(gr[i], gi[i]);
+                        for (int i = 0; i < NP; i++) Gt[i] = make_float2(gr[i], gi[i]);
                         const float2 Q = make_float2(qr, qi);
                         if (MODE == MODE_FISHER) {
                             // Gamma_ij: real and imaginary products summed separately
@@ -574,15 +574,15 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                             // Re(g_j Q^*) and the reduction scales them by -1/d_L;
                             // (d_L, d_L) and (d_L, Phic) follow from (Phic, Phic) and
                             // Re(Q (iQ)^*) = 0, so they are not summed.
-                            G[2] = Q;
+                            Gt[2] = Q;
                             int a = 1;
 #pragma unroll
                             for (int i = 0; i < NP; i++) {
-                                const float2 NGi = make_float2(-G[i].x, -G[i].y);
+                                const float2 NGi = make_float2(-Gt[i].x, -Gt[i].y);
 #pragma unroll
                                 for (int jj = i; jj < NP; jj++) {
                                     if (!(i == 2 && (jj == 2 || jj == 8)))
-                                        acc_pk(acc[a], mylo + a * LDS, G[jj], G[i], NGi);
+                                        acc_pk(acc[a], mylo + a * LDS, Gt[jj], Gt[i], NGi);
                                     a++;
                                 }
                                 if (i & 1) asm volatile("" ::: "memory");
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(128, 2) k_points_mixed(PointArgs A)
                             acc_pk(acc[0], mylo, Q, Q, NQ);
 #pragma unroll
                             for (int i = 0; i < 8; i++)
-                                acc_pk(acc[1 + i], mylo + (1 + i) * LDS, G[i], Q, NQ);
+                                acc_pk(acc[1 + i], mylo + (1 + i) * LDS, Gt[i], Q, NQ);
                             // the detector's orientation: dQ/dgamma is Q with
                             // (sin 2 gamma, cos 2 gamma) -> (2 cos 2 gamma, -2 sin 2 gamma)
                             const PatF pg = patterns_f(2.0f * (float)net.ifo_c2g[q],

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_null_context(lib):
-    assert lib.gw_abi_version() == 6
+    assert lib.gw_abi_version() == 7
     assert b"null" in lib.gw_last_error(None)
     assert lib.gw_fisher(None, None, None, 0, 11, None, None, None, None, None, None) == 1  # EINVAL
     assert lib.gw_destroy(None) == 0

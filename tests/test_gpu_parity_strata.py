@@ -9,15 +9,20 @@ of the five-interferometer c4 catalog are stored in tests/golden/parity_oracle.n
 The covariances of reference are the oracle's long-double inversion of its own
 Fisher matrices (Sec. 4.1).
 
-Arms: the FP64 path; the mixed path alone; and the mixed path followed by
-gw_fisher_refine (events whose mixed inversion fails or whose condition number
-exceeds 1e7 recomputed in FP64), which is the mixed path's result of record.
+Arms: the FP64 path with its Gram on the FP64 pipe and on the tensor cores
+(exact digit products); the double-float path (GW_DFLOAT: every per-point
+quantity in double-float on the FP32 pipe, the Gram exact on the tensor cores;
+the c4 network, four interferometers per point, runs it as FP64); the mixed
+path alone; and the mixed path followed by gw_fisher_refine (events whose mixed
+inversion fails or whose condition number exceeds 1e7 recomputed in FP64),
+which is the mixed path's result of record.
 
 Tolerances, per event:
-  SNR                FP64 1e-10 relative, mixed 1e-5.
-  Gamma_ij           FP64 1e-8 of sqrt(Gamma_ii Gamma_jj), mixed 2e-6.
+  SNR                FP64 and double-float 1e-10 relative, mixed 1e-5.
+  Gamma_ij           FP64 and double-float 1e-8 of sqrt(Gamma_ii Gamma_jj),
+                     mixed 2e-6.
   sqrt(diag C)       1e-3 relative, or the FP64 floor B * kappa where that is
-                     larger (FP64 and refined mixed arms).  kappa is the
+                     larger (FP64, double-float and refined mixed arms).  kappa is the
                      oracle's 2-norm condition number of the normalised Fisher
                      matrix.  Both Fisher matrices are FP64 arrays: rounding
                      each element of Gamma to FP64 (u = 2^-53, P = 11) moves
@@ -48,10 +53,10 @@ gw = pytest.importorskip("paper_2207_06910_gb300")
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "parity_oracle.npz")
 SETS = ("c3lit", "c3str", "long", "c4")
-ARMS = ("fp64", "mixed", "mixed_refined")
+ARMS = ("fp64", "fp64_tc", "dfloat", "mixed", "mixed_refined")
 B_COV = 1e-15
-TOL_SNR = {"fp64": 1e-10, "mixed": 1e-5, "mixed_refined": 1e-5}
-TOL_F = {"fp64": 1e-8, "mixed": 2e-6, "mixed_refined": 2e-6}
+TOL_SNR = {"fp64": 1e-10, "fp64_tc": 1e-10, "dfloat": 1e-10, "mixed": 1e-5, "mixed_refined": 1e-5}
+TOL_F = {"fp64": 1e-8, "fp64_tc": 1e-8, "dfloat": 1e-8, "mixed": 2e-6, "mixed_refined": 2e-6}
 
 
 @pytest.fixture(scope="module")
@@ -77,8 +82,12 @@ def _run(r, arm):
     det, psd, rot = gwcat.network(r["cfg"])
     net = gw.Network(det, psd, rot)
     cat = gw.Catalog.from_numpy(r["ev"], r["pset"], r["fmin"], r["fmax"], r["npts"])
-    prec = gw.GW_FP64 if arm == "fp64" else gw.GW_MIXED
-    F, snr, st = gw.gw_fisher(cat, net, 11, prec)
+    prec = {"fp64": gw.GW_FP64, "fp64_tc": gw.GW_FP64, "dfloat": gw.GW_DFLOAT}.get(arm, gw.GW_MIXED)
+    gw.gw_set_fp64_gram(arm == "fp64_tc")
+    try:
+        F, snr, st = gw.gw_fisher(cat, net, 11, prec)
+    finally:
+        gw.gw_set_fp64_gram(False)
     inv = gw.gw_fisher_inverse(F, 11)
     n_ref = 0
     if arm == "mixed_refined":
