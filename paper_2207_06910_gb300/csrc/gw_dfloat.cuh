@@ -160,6 +160,18 @@ constexpr float P2 = (float)P2D;
 constexpr float P3 = (float)(PIO2 - P1D - P2D);
 }  // namespace dfs
 
+// the coefficients as double-float pairs, fixed at compile time:
+// kTaylor[m] = (-1)^(m/2) / m!, m = 0..16
+#define GW_DFL_TAYLOR(m) {(float)dfs::taylor(m), (float)(dfs::taylor(m) - (double)(float)dfs::taylor(m))}
+__constant__ const float2 kTaylor[17] = {
+    GW_DFL_TAYLOR(0),  GW_DFL_TAYLOR(1),  GW_DFL_TAYLOR(2),  GW_DFL_TAYLOR(3),  GW_DFL_TAYLOR(4),
+    GW_DFL_TAYLOR(5),  GW_DFL_TAYLOR(6),  GW_DFL_TAYLOR(7),  GW_DFL_TAYLOR(8),  GW_DFL_TAYLOR(9),
+    GW_DFL_TAYLOR(10), GW_DFL_TAYLOR(11), GW_DFL_TAYLOR(12), GW_DFL_TAYLOR(13), GW_DFL_TAYLOR(14),
+    GW_DFL_TAYLOR(15), GW_DFL_TAYLOR(16)};
+#undef GW_DFL_TAYLOR
+
+__device__ __forceinline__ dfl taylor_coef(int m) { return dfl(kTaylor[m].x, kTaylor[m].y); }
+
 __device__ __forceinline__ void sincos(dfl x, dfl *sx, dfl *cx)
 {
     const float k = rintf(x.hi * 0.636619772f);          // nearest multiple of pi/2
@@ -168,13 +180,13 @@ __device__ __forceinline__ void sincos(dfl x, dfl *sx, dfl *cx)
     r = r + dfl(-k * dfs::P2, 0.0f);
     r = r + dfl(-k * dfs::P3, 0.0f);
     const dfl r2 = r * r;
-    dfl s = dfl(dfs::taylor(15));
+    dfl s = taylor_coef(15);
 #pragma unroll
-    for (int n = 6; n >= 0; n--) s = s * r2 + dfl(dfs::taylor(2 * n + 1));
+    for (int n = 6; n >= 0; n--) s = s * r2 + taylor_coef(2 * n + 1);
     s = s * r;
-    dfl c = dfl(dfs::taylor(16));
+    dfl c = taylor_coef(16);
 #pragma unroll
-    for (int n = 7; n >= 0; n--) c = c * r2 + dfl(dfs::taylor(2 * n));
+    for (int n = 7; n >= 0; n--) c = c * r2 + taylor_coef(2 * n);
     const int q = ((int)k) & 3;
     const dfl sn = (q == 0) ? s : (q == 1) ? c : (q == 2) ? -s : -c;
     const dfl cs = (q == 0) ? c : (q == 1) ? -s : (q == 2) ? -c : s;

@@ -5,14 +5,15 @@
 //     Gamma_ij = sum_k y_ik y_jk,   y_.k = (Re g, Im g) of one interferometer at
 //     one grid point, tangents pre-scaled by sigma = A sqrt(4 w / S_n)
 // (Sec. 3.2, Eqs. 3.1-3.3).  Every tangent value is written, per item and
-// column, as a 56-bit fixed-point number relative to the column's largest
-// exponent, split into eight 7-bit digits (sign-magnitude, each exact in
-// bf16), and the tensor core forms all digit products with FP32 accumulation.
-// A digit product is below 2^14 and an item has at most 1024 rows (256 points
-// x 2 interferometers x real/imaginary), so every partial sum is an integer
-// below 2^24: the accumulation is exact.  The digit Gram D[(i,a),(j,b)] is then
-// combined in FP64,
-//     Gamma_ij = 2^(E_i + E_j - 2058) sum_ab 2^(-7(a + b)) D[(i,a),(j,b)],
+// column, relative to the column's largest exponent E_i (y' = y 2^(1022 - E_i),
+// |y'| < 1) as eight digits: digit a is a multiple of q_a = 2^(-7(a+1)) of
+// magnitude at most 128 q_a, exact in bf16, the sum of the digits y' to 2^-57.
+// The tensor core forms all digit products with FP32 accumulation; a product
+// of digits a and b is a multiple of q_a q_b below 2^14 q_a q_b and an item has
+// at most 1024 rows (256 points x 2 interferometers x real/imaginary), so
+// every partial sum is such a multiple below 2^24 q_a q_b: the accumulation is
+// exact.  The digit Gram D[(i,a),(j,b)] is then summed in FP64,
+//     Gamma_ij = 2^(E_i + E_j - 2044) sum_ab D[(i,a),(j,b)],
 // so the item's Fisher matrix is the exact Gram of the tangents rounded to 56
 // bits (relative to the column maximum), summed in FP64 only over the 64 digit
 // pairs.
@@ -50,6 +51,8 @@
 // sets *kerr, writes NaN into the item's sums and ends the CTA after freeing
 // its TMEM.
 #include <type_traits>
+
+#include <cuda_bf16.h>
 
 #include "gw_points_fp64.cuh"
 
@@ -123,18 +126,29 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t kstride, 
     return d;
 }
 
-// the eight 7-bit digits of a 56-bit magnitude N as bf16 values with the given
-// sign, digit a (bits 49 - 7a .. 55 - 7a) in element a of the row
+// Digit a of a value y' in (-1, 1) (the value over 2^(ec - 1022), ec the
+// column's largest biased FP64 exponent) is a multiple of q_a = 2^(-7(a+1))
+// of magnitude <= 128 q_a; the row holds the eight digits as bf16 numbers in
+// these absolute units (digit a in element a), so the accumulator's sums are
+// exact multiples of q_a q_b below 2^24 q_a q_b and the item's Gram entry is
+// the plain sum over the digit pairs.
+
+// the eight 7-bit digits of a 56-bit magnitude N = |y'| 2^56 with the given
+// sign, digit a = bits 49 - 7a .. 55 - 7a of N, valued d q_a
 __device__ __forceinline__ uint4 pack_digits(unsigned long long N, bool negative)
 {
     const unsigned nh = (unsigned)(N >> 28), nl = (unsigned)N & 0x0FFFFFFFu;
-    // digit d as an FP32 number: the integer d below 2^23 in the mantissa of 2^23
-    auto fd = [](unsigned d) { return __float_as_uint(__uint_as_float(0x4B000000u | d) - 8388608.0f); };
+    // d q_a as an FP32 number: the integer d (< 2^23) in the mantissa of
+    // 2^(23 - 7(a+1)) (exponent field 150 - 7(a+1)), less that power of two
+    auto fd = [](unsigned d, int a) {
+        const unsigned e = (unsigned)(150 - 7 * (a + 1));
+        return __float_as_uint(__uint_as_float((e << 23) | d) - __uint_as_float(e << 23));
+    };
     uint4 r;
-    r.x = __byte_perm(fd((nh >> 21) & 127u), fd((nh >> 14) & 127u), 0x7632);
-    r.y = __byte_perm(fd((nh >> 7) & 127u), fd(nh & 127u), 0x7632);
-    r.z = __byte_perm(fd((nl >> 21) & 127u), fd((nl >> 14) & 127u), 0x7632);
-    r.w = __byte_perm(fd((nl >> 7) & 127u), fd(nl & 127u), 0x7632);
+    r.x = __byte_perm(fd((nh >> 21) & 127u, 0), fd((nh >> 14) & 127u, 1), 0x7632);
+    r.y = __byte_perm(fd((nh >> 7) & 127u, 2), fd(nh & 127u, 3), 0x7632);
+    r.z = __byte_perm(fd((nl >> 21) & 127u, 4), fd((nl >> 14) & 127u, 5), 0x7632);
+    r.w = __byte_perm(fd((nl >> 7) & 127u, 6), fd(nl & 127u, 7), 0x7632);
     if (negative) {
         r.x ^= 0x80008000u;
         r.y ^= 0x80008000u;
@@ -179,30 +193,41 @@ __device__ __forceinline__ uint4 digits8(double y, int ec)
     return pack_digits(N, (b >> 63) != 0);
 }
 
-// double-float y = hi + lo (|lo| <= ulp(hi) / 2): the pair's magnitude from
-// the two 24-bit mantissas (lo adds or subtracts by its sign)
+// double-float y = hi + lo: both parts scaled exactly to y' (a power of two),
+// then digit by digit, in both lanes of packed FP32x2 operations, rounded to
+// the multiple of q_a (adding and subtracting 1.5 2^(23 - 7(a+1)): round to
+// nearest) and the remainders kept exactly; digit a is the sum of the two
+// lanes' parts (for a >= 1 each is at most 64 q_a; lo has no part in digit 0)
 __device__ __forceinline__ uint4 digits8(dfl y, int ec)
 {
-    const unsigned bh = __float_as_uint(y.hi), bl = __float_as_uint(y.lo);
-    const int eh = (int)((bh >> 23) & 0xFFu), el = (int)((bl >> 23) & 0xFFu);
-    unsigned long long N = 0;
-    if (eh != 0) {
-        // |hi| = m 2^(eh - 150), in units of 2^(ec - 1078): shift by eh + 928 - ec (<= 32)
-        N = shift_round((unsigned long long)((bh & 0x7FFFFFu) | 0x800000u), ec - eh - 928);
-        if (el != 0) {
-            const unsigned long long nl =
-                shift_round((unsigned long long)((bl & 0x7FFFFFu) | 0x800000u), ec - el - 928);
-            N = ((bh ^ bl) >> 31) ? N - nl : N + nl;
-        }
+    if (ec == 0) return make_uint4(0u, 0u, 0u, 0u);      // a column of zeros
+    const int sf = 1149 - ec;                             // 2^(1022 - ec) as FP32
+    const float sc = __uint_as_float((unsigned)(sf > 0 ? sf : 1) << 23);
+    float2 r = __fmul2_rn(make_float2(y.hi, y.lo), make_float2(sc, sc));
+    float d[8];
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+        const float M = __uint_as_float(((unsigned)(143 - 7 * a) << 23) | 0x400000u);
+        const float2 t = __fadd2_rn(r, make_float2(M, M));
+        const float2 q = __fadd2_rn(t, make_float2(-M, -M));
+        r = __fadd2_rn(r, make_float2(-q.x, -q.y));
+        d[a] = q.x + q.y;
     }
-    return pack_digits(N, (bh >> 31) != 0);
+    uint4 o;
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(d[0], d[1]), p1 = __floats2bfloat162_rn(d[2], d[3]);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(d[4], d[5]), p3 = __floats2bfloat162_rn(d[6], d[7]);
+    o.x = *reinterpret_cast<unsigned *>(&p0);
+    o.y = *reinterpret_cast<unsigned *>(&p1);
+    o.z = *reinterpret_cast<unsigned *>(&p2);
+    o.w = *reinterpret_cast<unsigned *>(&p3);
+    return o;
 }
 
 // 2^x in FP64 (x an integer), NaN when a column held a non-finite value
 __device__ __forceinline__ double pow2_scale(int ei, int ej)
 {
     if (ei == 2047 || ej == 2047) return __longlong_as_double(0x7FF8000000000000ll);
-    const int x = ei + ej - 2058;
+    const int x = ei + ej - 2044;
     const int be = x + 1023;
     if (be >= 1 && be <= 2046) return __longlong_as_double((long long)be << 52);
     return ldexp(1.0, x);
@@ -336,11 +361,20 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
             const int q = t % 3, big = t / 3;
             const double l = q == 0 ? lnr * (1.0 / 3.0) : (q == 1 ? -lnr * (1.0 / 3.0) : -7.0 / 6.0 * lnr);
             const double fct = exp(big ? 16.0 * l : l);
-            double val = 1.0;
-            for (int i = 0; i < 16; i++) {
-                pw[(q * 2 + big) * 16 + i] = val;
-                if (DF) pwd[(q * 2 + big) * 16 + i] = dfl(val);
-                val *= fct;
+            if (DF) {
+                // the chain in double-float on the FP32 pipe (~16 x 2^-48)
+                const dfl f(fct);
+                dfl val(1.0f, 0.0f);
+                for (int i = 0; i < 16; i++) {
+                    pwd[(q * 2 + big) * 16 + i] = val;
+                    val = val * f;
+                }
+            } else {
+                double val = 1.0;
+                for (int i = 0; i < 16; i++) {
+                    pw[(q * 2 + big) * 16 + i] = val;
+                    val *= fct;
+                }
             }
         } else if (t < 10) {
             const double lnf0 = fma((double)kb, lnr, cs[EV_LNF0]);
@@ -420,7 +454,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
                     PhaseT<T> ph;
                     site_terms<MODE_FISHER, ROT>(S, pn, twopif, J, ph);
 #pragma unroll 1
-                    for (int slot = 0; slot < net.site_nslot[s]; slot++, L++) {
+                    for (int slot = 0; slot < net.site_nslot[s]; slot++) {
                         int q = net.masked ? (int)Sg[SC_SLOT0 + slot] : net.site_ifo0[s] + slot;
                         bool on = true;
                         if (q < 0) {
@@ -442,13 +476,13 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
                         T gr[NP], gi[NP], qr, qi;
                         tangents<NP, ROT>(pt, sg * cp, sg * cx, sg * dcp, sg * dcx, aMc, invdL,
                                           ph, gr, gi, qr, qi);
-                        if (L == 0) {
+                        if (L + slot == 0) {
 #pragma unroll
                             for (int c = 0; c < NP; c++) {
                                 val[c][0] = gr[c];
                                 val[c][1] = gi[c];
                             }
-                        } else {
+                        } else if (L + slot == 1) {
 #pragma unroll
                             for (int c = 0; c < NP; c++) {
                                 val[c][2] = gr[c];
@@ -456,6 +490,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
                             }
                         }
                     }
+                    L += net.site_nslot[s];
                 }
             }
 #pragma unroll
@@ -551,13 +586,24 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
             break;
         }
 
-        // ---- read the digit Gram: thread t holds row m = t = (i, a), i = t / 8,
-        // a = t % 8; columns (j, b) at 8 j + b.  Warp w holds rows of columns
-        // i >= 4 w, so it reads the column groups j >= 4 w.
+        // ---- read the digit Gram: thread t holds TMEM lane t = row (i, a),
+        // i = t / 8, a = t % 8; columns (j, b) at 8 j + b.  Row i forms the
+        // entries (i, j) for j = i .. i + H (mod P), H = (P - 1) / 2: every
+        // unordered pair once (P is odd), about P / 2 column groups per row, so
+        // warp w (rows i = 4w .. 4w + 3) reads the groups 4w .. 4w + 3 + H.
+        // The eight products D[(i,a),(j,b)] of a lane are exact multiples of
+        // q_a q_b below 2^24 q_a q_b: they are summed exactly as integers (b < 4
+        // in units of q_a q_3, b >= 4 in units of q_a q_7, both below 2^46),
+        // then the lane's sum goes to FP64 (two conversions, one FMA) and the
+        // eight lanes of row i are added with shuffles.
         const int i = t >> 3, a = t & 7;
-        const double sa = ldexp(1.0, -7 * a);
+        constexpr int H = (NP - 1) / 2;
+        // (a warp whose rows are all padding, 4w >= P, reads nothing)
+        const int jend = 4 * warp >= NP ? 0 : (4 * warp + 3 < NP - 1 ? 4 * warp + 3 : NP - 1) + H + 1;
+        const double ua = ldexp(1.0, -7 * (a + 5));     // unit of the b < 4 sum
 #pragma unroll 1
-        for (int j = 4 * warp; j < NP; j++) {
+        for (int jr = 4 * warp; jr < jend; jr++) {
+            const int j = jr < NP ? jr : jr - NP;
             uint32_t d[8];
             const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 8);
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -565,17 +611,24 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
                            "=r"(d[6]), "=r"(d[7])
                          : "r"(ta));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            // sum over b of 2^(-7 b) D[(i,a),(j,b)], then over a across the 8 lanes
-            double P = (double)__uint_as_float(d[7]);
+            long long hs = 0, ls = 0;
 #pragma unroll
-            for (int b = 6; b >= 0; b--) P = fma(P, 0x1p-7, (double)__uint_as_float(d[b]));
-            P *= sa;
+            for (int b = 0; b < 8; b++) {
+                // D / (q_a q_b): an integer below 2^24 (exact FP32 scaling by 2^(7(a+b+2)))
+                const float sb = __uint_as_float((unsigned)(127 + 7 * (a + b + 2)) << 23);
+                const long long n = (long long)__float2int_rn(__uint_as_float(d[b]) * sb);
+                if (b < 4) hs += n << (7 * (3 - b));
+                else ls += n << (7 * (7 - b));
+            }
+            double P = fma((double)ls, 0x1p-28, (double)hs) * ua;
             P += __shfl_xor_sync(0xffffffffu, P, 1);
             P += __shfl_xor_sync(0xffffffffu, P, 2);
             P += __shfl_xor_sync(0xffffffffu, P, 4);
-            if (a == 0 && i < NP && j >= i) {
+            const int dj = jr - i;   // j = i + dj (mod P)
+            if (a == 0 && i < NP && dj >= 0 && dj <= H) {
+                const int lo = i < j ? i : j, hi = i < j ? j : i;
                 const double g = P == 0.0 ? 0.0 : P * pow2_scale((int)emax[i], (int)emax[j]);
-                const int idx = 1 + i * NP - i * (i - 1) / 2 + (j - i);
+                const int idx = 1 + lo * NP - lo * (lo - 1) / 2 + (hi - lo);
                 if (idx < A.nacc) out[idx] = g;
                 // SNR^2 = sum |Q|^2 = the (Phic, Phic) entry: g_Phic = -i Q
                 if (i == 8 && j == 8) out[0] = g;
