@@ -73,8 +73,12 @@ enum {
 };
 
 /* A work item is a run of at most GW_ITEM_POINTS consecutive grid points of one
- * event: an event of npts points has ceil(npts / GW_ITEM_POINTS) items. */
+ * event: an event of npts points has ceil(npts / GW_ITEM_POINTS) items.  The
+ * Fisher pass with its Gram on the tensor cores (GW_DFLOAT, or GW_FP64 after
+ * gw_set_fp64_gram(ctx, 1), on networks of at most two interferometers per
+ * grid point) takes items of GW_TC_ITEM_POINTS points: ceil(npts / 128). */
 #define GW_ITEM_POINTS 256
+#define GW_TC_ITEM_POINTS 128
 
 /* Fisher parameter order (the fixed order of Sec. 3.2): slot 0..8 =
  *   Mc [Msun, detector frame], eta, dL [Gpc], theta, phi, iota, psi [rad],

@@ -25,6 +25,7 @@ GW_FP64, GW_MIXED, GW_DFLOAT = 0, 1, 2
 ST_NOT_PD, ST_COND_GT_MAX, ST_NONFINITE, ST_EMPTY_GRID, ST_BAD_PARAM, ST_ILL_COND = 1, 2, 4, 8, 16, 32
 ST_OVERFLOW = 64
 ITEM_POINTS = 256          # grid points per work item (GW_ITEM_POINTS)
+TC_ITEM_POINTS = 128       # the tensor-core Fisher pass (GW_TC_ITEM_POINTS)
 FISHER_PARAMS_9 = ("Mc", "eta", "dL", "theta", "phi", "iota", "psi", "tc", "Phic")
 
 _P = ctypes.c_void_p
@@ -157,10 +158,12 @@ def gw_reserve(max_events: int, max_items: int, max_sites: int = 1) -> None:
     _check(load_library().gw_reserve(ctx, int(max_events), int(max_items), int(max_sites)), ctx)
 
 
-def work_items(npts) -> int:
-    """Number of work items of a catalog with these grid lengths."""
+def work_items(npts, points_per_item: int | None = None) -> int:
+    """Number of work items of a catalog with these grid lengths (items of
+    ITEM_POINTS points, or TC_ITEM_POINTS for the tensor-core Fisher pass)."""
+    p = ITEM_POINTS if points_per_item is None else int(points_per_item)
     n = torch.as_tensor(npts).to(torch.int64)
-    return int(((n + ITEM_POINTS - 1) // ITEM_POINTS).sum().item())
+    return int(((n + p - 1) // p).sum().item())
 
 
 def gw_set_profiling(enable: bool = True) -> None:

@@ -348,8 +348,13 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
         CK(gwi_prep_psd(net, dn, ctx->psd_seg, ctx->psd_seg_f, s));
     }
     const DevCat dc = gwi_dev_cat(cat);
+    // the tensor-core Fisher pass (GW_DFLOAT, or GW_FP64 with the tensor-core
+    // Gram) takes work items of TC_CHUNK points
+    const bool tc = mode == MODE_FISHER && !mixed && fisher_fp64_tc_supported(dn) &&
+                    (prec == GW_DFLOAT || ctx->fp64_gram_tc);
     CK(launch_event_setup(dc, dn, np, ctx->evc, ctx->sitec, mixed ? ctx->sitec_f : nullptr,
-                          mixed ? ctx->evc_f : nullptr, status, ctx->counts, s));
+                          mixed ? ctx->evc_f : nullptr, status, ctx->counts, s,
+                          tc ? TC_CHUNK : CHUNK_MAX));
     CK(launch_scan(ctx->counts, n, ctx->off, ctx->scan, s));
     int64_t n_items;
     if (ctx->item_cap > 0) {
@@ -385,13 +390,12 @@ gw_status run_points(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, 
         const int pi = mixed ? 1 : 0;
         pa.group = ctx->tile_group[pi][cls];
         pa.blocks_per_sm = ctx->tile_bps[pi][cls];
-        pa.gram_tc = ctx->fp64_gram_tc;
     }
     pa.kerr = ctx->kerr;
     if (ctx->profiling) CK(cudaEventRecord(ctx->ev0, s));
     if (mixed) CK(launch_points_mixed(mode, np, dn.rotation, pa, s));
-    else if (prec == GW_DFLOAT && mode == MODE_FISHER && fisher_fp64_tc_supported(dn))
-        CK(launch_fisher_dfloat_tc(np, dn.rotation, pa, s));
+    else if (tc && prec == GW_DFLOAT) CK(launch_fisher_dfloat_tc(np, dn.rotation, pa, s));
+    else if (tc) CK(launch_fisher_fp64_tc(np, dn.rotation, pa, s));
     else CK(launch_points_fp64(mode, np, dn.rotation, pa, s));
     if (ctx->profiling) {
         CK(cudaEventRecord(ctx->ev1, s));

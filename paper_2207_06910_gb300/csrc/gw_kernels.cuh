@@ -74,7 +74,6 @@ struct PointArgs {
                                        // gradient is formed (bit d); other sites skipped
     int group = GROUP;                 // Fisher pass: lanes per work item (4, 8 or 16)
     int blocks_per_sm = 2;             // persistent grid: CTAs per SM (1 or 2)
-    int gram_tc = 0;                   // FP64 Fisher pass: Gram on the tensor cores
     int32_t *kerr = nullptr;           // set to 1 by a kernel whose bounded wait ran out
 };
 
@@ -103,10 +102,11 @@ cudaError_t launch_prepare(int64_t n, const double *m1, const double *m2, const 
                            double *dLamT, double *tc_s, double *fmax, int32_t *npts,
                            cudaStream_t s);
 
-// event constants, status, and work items per event
+// event constants, status, and work items per event (items of at most
+// `chunk` grid points: CHUNK_MAX, or TC_CHUNK for the tensor-core Fisher pass)
 cudaError_t launch_event_setup(const DevCat &cat, const DevNet &net, int np, double *evc,
                                double *sitec, float *sitec_f, float2 *evc_f, int32_t *status,
-                               int64_t *counts, cudaStream_t s);
+                               int64_t *counts, cudaStream_t s, int chunk = CHUNK_MAX);
 
 // exclusive scan of counts[0..n) into off[0..n], off[n] = total; tmp needs
 // scan_tmp_size(n) int64 elements
@@ -118,6 +118,7 @@ cudaError_t launch_points_fp64(int mode, int np, int rot, const PointArgs &a, cu
 // FP64 Fisher pass with the Gram on the tensor cores (gw_points_fp64_tc.cu):
 // networks of at most two interferometers per grid point
 bool fisher_fp64_tc_supported(const DevNet &net);
+constexpr int TC_CHUNK = 128;   // points per work item of the tensor-core Fisher pass
 cudaError_t launch_fisher_fp64_tc(int np, int rot, const PointArgs &a, cudaStream_t s);
 // the same pass with the tangents in double-float on the FP32 pipe
 cudaError_t launch_fisher_dfloat_tc(int np, int rot, const PointArgs &a, cudaStream_t s);

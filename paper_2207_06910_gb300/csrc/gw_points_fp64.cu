@@ -29,9 +29,7 @@ cudaError_t launch_points_fp64(int mode, int np, int rot, const PointArgs &a, cu
 {
     switch (mode) {
     case MODE_SNR: return launch_mode<MODE_SNR>(np, rot, a, s);
-    case MODE_FISHER:
-        if (a.gram_tc && fisher_fp64_tc_supported(a.net)) return launch_fisher_fp64_tc(np, rot, a, s);
-        return launch_points_fp64_fisher(np, rot, a, s);
+    case MODE_FISHER: return launch_points_fp64_fisher(np, rot, a, s);
     case MODE_SNRGRAD: return launch_mode<MODE_SNRGRAD>(np, rot, a, s);
     default: return launch_mode<MODE_LOGDET>(np, rot, a, s);
     }

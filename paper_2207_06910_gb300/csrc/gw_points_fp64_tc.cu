@@ -31,21 +31,24 @@
 //    carried relative to the network's reference PSD scale (FP32 range); a
 //    tabulated PSD's weight is taken in FP64 and converted.
 //
-// Shape.  128 threads (one grid point each, two rounds for items of more than
-// 128 points), two CTAs per SM, persistent over the items.  Each thread keeps
-// its point's values (columns x rows r = interferometer x {Re, Im}) in
-// registers; the first round of a two-round item is staged in shared memory
-// until the column maxima are known.  The digits go to shared memory in the
-// MN-major, no-swizzle operand layout (8 digits of one value = one 16-byte
-// row of a core matrix; K groups of 8 rows at stride KG, MN groups at 128
-// bytes), one K block of 128 rows per (round, r), double-buffered: one thread
-// issues the block's eight M=128 x N x K=16 MMAs (A = B = the block) into the
-// item's TMEM accumulator and commits them to the buffer's mbarrier, which the
-// writers of the buffer after next wait on.  After the item's last block the
-// four warps read their 32 TMEM lanes (rows (i, a)) and reduce over the digit
-// pairs.  Networks of at most two interferometers per point (one triangle or
-// up to two L-shaped detectors) take this kernel; wider networks, and the SNR,
-// SNR-gradient and log-det passes, run the FP64-pipe kernel.
+// Shape.  Work items of at most TC_CHUNK = 128 points (the event set-up splits
+// events accordingly), one grid point per thread of a 128-thread CTA, three
+// CTAs per SM, persistent over the items.  Each thread writes its point's
+// values (columns x rows r = interferometer x {Re, Im}) to shared memory as it
+// forms them (FP64 or double-float pairs, 8 bytes each), so that no value
+// stays in registers and the kernel fits three CTAs per SM (~168 registers);
+// the column maxima are reduced once the item's points are done.  The digits
+// go to shared memory in the MN-major, no-swizzle operand layout (8 digits of
+// one value = one 16-byte row of a core matrix; K groups of 8 rows at stride
+// KG, MN groups at 128 bytes), one K block of 128 rows per row r, in one
+// buffer: one thread issues the block's eight M=128 x N x K=16 MMAs (A = B =
+// the block) into the item's TMEM accumulator and commits them to the
+// mbarrier, which the writers of the next block wait on.  After the item's
+// last block the four warps read their 32 TMEM lanes (rows (i, a)) and reduce
+// over the digit pairs.  Networks of at most two interferometers per point
+// (one triangle or up to two L-shaped detectors) take this kernel; wider
+// networks, and the SNR, SNR-gradient and log-det passes, run the FP64-pipe
+// kernel.
 //
 // Every wait is bounded (about a second of wall time); a wait that runs out
 // sets *kerr, writes NaN into the item's sums and ends the CTA after freeing
@@ -65,24 +68,28 @@ constexpr int TC_KROWS = 128;             // K rows per block (one value per thr
 constexpr int TC_MG = 128;                // bytes between MN groups (8 digits x 8 rows)
 constexpr int TC_PW = 104;                // power tables (96) and per-item bases (8)
 
+constexpr int TC_CTAS = 3;                // CTAs per SM (registers, shared memory, TMEM)
+constexpr int TC_SITES = 2;               // sites of a supported network (<= 2 interferometers)
+
 template <int NP>
 struct TcShape {
     static constexpr int KG = NP * 128;                    // bytes between K groups
-    static constexpr int BLK = (TC_KROWS / 8) * KG;        // one K block
+    static constexpr int BLK = (TC_KROWS / 8) * KG;        // one K block (the operand buffer)
     static constexpr int N = ((NP * 8 + 15) / 16) * 16;    // MMA N (digit rows used, padded)
-    // operand buffers, 1 KB slack after the second: an M = 128 read of the last
-    // MMA step of a block reaches 2047 - KG bytes past the block
-    static constexpr int OPS_BYTES = 2 * BLK + 1024;
+    // The staged values follow the operand buffer: an M = 128 read of the
+    // last MMA step of a block reaches 2047 - KG bytes past the block, into
+    // them (finite data, only for accumulator rows and columns never read).
     static constexpr int STAGE_BYTES = NP * 4 * TC_T * 8;
     // double-float copies: event constants, site constants, interferometer
     // (s2g, c2g, amp) and PSD constants (inverse f0, f0, coefficients)
-    static constexpr int DF_WORDS = EVC + MAX_SITE * SC_N + 3 * MAX_IFO +
+    static constexpr int DF_WORDS = EVC + TC_SITES * SC_N + 3 * MAX_IFO +
                                     MAX_PSD * (2 + MAX_TERM) + TC_PW;
     static constexpr size_t smem(bool df)
     {
-        return (size_t)OPS_BYTES + STAGE_BYTES + (size_t)EVC * 8 + TC_PW * 8 + 16 * 4 + 2 * 8 +
-               16 + (df ? (size_t)DF_WORDS * 8 : 0);
+        return (size_t)BLK + STAGE_BYTES + (size_t)EVC * 8 + TC_PW * 8 + 16 * 4 + 8 + 8 + 16 +
+               (df ? (size_t)DF_WORDS * 8 : 0);
     }
+    static_assert(2047 - KG <= STAGE_BYTES, "operand over-read stays in shared memory");
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -264,14 +271,14 @@ __device__ __forceinline__ void psd_sigma_df(const DevNet &net, const dfl *psd_d
 }
 
 template <int NP, bool ROT, bool TAB, typename T>
-__global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
+__global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
 {
     using SH = TcShape<NP>;
     constexpr bool DF = std::is_same<T, dfl>::value;
-    constexpr int KG = SH::KG, BLK = SH::BLK, NMMA = SH::N;
+    constexpr int KG = SH::KG, NMMA = SH::N;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char *ops = tc_smem;
-    T *stage = reinterpret_cast<T *>(tc_smem + SH::OPS_BYTES);
+    T *stage = reinterpret_cast<T *>(tc_smem + SH::BLK);   // [NP][4][TC_T] values
     double *cs = reinterpret_cast<double *>(stage + NP * 4 * TC_T);   // event constants
     double *pw = cs + EVC;                   // [3][2][16] powers, then bases
     unsigned *emax = reinterpret_cast<unsigned *>(pw + TC_PW);
@@ -279,8 +286,8 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
     // double-float copies (T = dfl only)
     dfl *Ed = reinterpret_cast<dfl *>(tmem_slot + 4);
-    dfl *Sd = Ed + EVC;                       // [MAX_SITE][SC_N]
-    dfl *Qd = Sd + MAX_SITE * SC_N;           // [MAX_IFO][3]: s2g, c2g, amp
+    dfl *Sd = Ed + EVC;                       // [TC_SITES][SC_N]
+    dfl *Qd = Sd + TC_SITES * SC_N;           // [MAX_IFO][3]: s2g, c2g, amp
     dfl *Pd = Qd + 3 * MAX_IFO;               // [MAX_PSD][2 + MAX_TERM]
     dfl *pwd = Pd + MAX_PSD * (2 + MAX_TERM);  // powers and bases
 
@@ -294,7 +301,6 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
     }
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(&mbar[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(&mbar[1])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (DF) {
@@ -314,10 +320,9 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
             Pd[i] = dfl(v);
         }
     }
-    // the operand slack and the digit rows past the stored ones are read by the
-    // MMAs (they only reach accumulator rows and columns that are not used):
-    // keep them finite
-    for (int i = t; i < SH::OPS_BYTES / 16; i += TC_T)
+    // the staged values are read past the operand buffer (see TcShape): keep
+    // them finite from the start
+    for (int i = t; i < (SH::BLK + SH::STAGE_BYTES) / 16; i += TC_T)
         reinterpret_cast<uint4 *>(ops)[i] = make_uint4(0, 0, 0, 0);
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -328,8 +333,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
     // instruction descriptor: D FP32, A and B bf16, both MN-major, N, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
                            ((uint32_t)(NMMA >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    uint32_t par0 = 0, par1 = 0;
-    bool pend0 = false, pend1 = false;
+    uint32_t par = 0;        // parity of the mbarrier phase of the next commit
     bool ok = true;
 
     const int64_t n_total = A.item_off[A.n_ev];
@@ -353,7 +357,6 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
         __syncthreads();
         const int N = (int)cs[EV_NPTS];
         const int kb = (int)((int64_t)N * jit / nj), ke = (int)((int64_t)N * (jit + 1) / nj);
-        const int rounds = ke - kb > TC_T ? 2 : 1;
         const double lnr = cs[EV_LNR];
         // powers of the per-point factors of v, 1/v and the amplitude (steps 1
         // and 16 points) and their values at the item's first point
@@ -397,116 +400,101 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
         const T *E;
         if constexpr (DF) E = Ed;
         else E = cs;
-        const T wc0 = E[EV_WC0], wcm = E[EV_WCM], wcn = E[EV_WCN];
-        const T cp = E[EV_CP], cx = E[EV_CX], dcp = E[EV_DCP], dcx = E[EV_DCX];
-        const T c2p = E[EV_C2PSI], s2p = E[EV_S2PSI];
-        const T aMc = E[EV_AMC], invdL = E[EV_INVDL];
         int tseg[MAX_PSD];
 #pragma unroll
         for (int p = 0; p < MAX_PSD; p++) tseg[p] = -1;
 
-        // ---- tangents of this thread's point(s); rows r = 2 slot + {Re, Im}
-        T val[NP][4];
+        // ---- tangents of this thread's point, staged as they are formed:
+        // rows r = 2 L + {Re, Im} of interferometer slot L (0 or 1)
         unsigned lmax[NP];
 #pragma unroll
         for (int c = 0; c < NP; c++) lmax[c] = 0u;
-#pragma unroll 1
-        for (int rd = 0; rd < rounds; rd++) {
-#pragma unroll
-            for (int c = 0; c < NP; c++) val[c][0] = val[c][1] = val[c][2] = val[c][3] = T(0.0);
-            const int tt = rd * TC_T + t;
-            const int k = kb + tt;
-            if (k < ke) {
-                const int lo = tt & 15, hi = tt >> 4;
-                T v, vinv, Aamp, lnv;
-                if constexpr (DF) {
-                    v = pwd[96] * pwd[0 * 16 + lo] * pwd[1 * 16 + hi];
-                    vinv = pwd[97] * pwd[2 * 16 + lo] * pwd[3 * 16 + hi];
-                    Aamp = pwd[98] * pwd[4 * 16 + lo] * pwd[5 * 16 + hi];
-                    lnv = pwd[99] + df_mul_f(pwd[100], (float)tt);
-                } else {
-                    const double lnf = fma((double)k, lnr, cs[EV_LNF0]);
-                    lnv = (lnf + cs[EV_LNPIM]) * (1.0 / 3.0);
-                    v = pw[96] * pw[0 * 16 + lo] * pw[1 * 16 + hi];
-                    vinv = pw[97] * pw[2 * 16 + lo] * pw[3 * 16 + hi];
-                    Aamp = pw[98] * pw[4 * 16 + lo] * pw[5 * 16 + hi];
-                }
-                const PnTermsT<T> pn = pn_terms<NP, ROT>(E, v, vinv, lnv);
-                const T w = pn.f * (k == 0 ? wc0 : (k == N - 1 ? wcn : wcm));
-                const T twopif = T(TWO_PI) * pn.f;
-                T Wp[MAX_PSD];
-                if constexpr (DF)
-                    psd_sigma_df<TAB>(net, Pd, E, cs, k, pn.f, pn.vi3, w, Aamp, tseg, Wp);
-                else
-                    psd_sigma<TAB>(net, E, k, pn.f, pn.vi3, w, Aamp, tseg, Wp);
-                int L = 0;
-#pragma unroll 1
-                for (int s = 0; s < net.n_site; s++) {
-                    const double *Sg = A.sitec + (e * net.n_site + s) * (int64_t)SC_N;
-                    if (net.masked && Sg[SC_SLOT0] < 0.0) {   // every arm of the site off
-                        L += net.site_nslot[s];
-                        continue;
-                    }
-                    const T *S;
-                    if constexpr (DF) S = Sd + s * SC_N;
-                    else S = Sg;
-                    T J[12];
-                    PhaseT<T> ph;
-                    site_terms<MODE_FISHER, ROT>(S, pn, twopif, J, ph);
-#pragma unroll 1
-                    for (int slot = 0; slot < net.site_nslot[s]; slot++) {
-                        int q = net.masked ? (int)Sg[SC_SLOT0 + slot] : net.site_ifo0[s] + slot;
-                        bool on = true;
-                        if (q < 0) {
-                            q = net.site_ifo0[s];
-                            on = false;
-                        }
-                        T s2g, c2g, amp;
-                        if constexpr (DF) {
-                            s2g = Qd[3 * q];
-                            c2g = Qd[3 * q + 1];
-                            amp = on ? Qd[3 * q + 2] : T(0.0);
-                        } else {
-                            s2g = net.ifo_s2g[q];
-                            c2g = net.ifo_c2g[q];
-                            amp = net.ifo_amp[q] * (on ? 1.0 : 0.0);
-                        }
-                        const PatT<T> pt = patterns(s2g, c2g, amp * c2p, amp * s2p, J);
-                        const T sg = Wp[net.ifo_psd[q]];
-                        T gr[NP], gi[NP], qr, qi;
-                        tangents<NP, ROT>(pt, sg * cp, sg * cx, sg * dcp, sg * dcx, aMc, invdL,
-                                          ph, gr, gi, qr, qi);
-                        if (L + slot == 0) {
-#pragma unroll
-                            for (int c = 0; c < NP; c++) {
-                                val[c][0] = gr[c];
-                                val[c][1] = gi[c];
-                            }
-                        } else if (L + slot == 1) {
-#pragma unroll
-                            for (int c = 0; c < NP; c++) {
-                                val[c][2] = gr[c];
-                                val[c][3] = gi[c];
-                            }
-                        }
-                    }
-                    L += net.site_nslot[s];
-                }
+        unsigned written = 0u;
+        const int k = kb + t;
+        if (k < ke) {
+            const int lo = t & 15, hi = t >> 4;
+            T v, vinv, Aamp, lnv;
+            if constexpr (DF) {
+                v = pwd[96] * pwd[0 * 16 + lo] * pwd[1 * 16 + hi];
+                vinv = pwd[97] * pwd[2 * 16 + lo] * pwd[3 * 16 + hi];
+                Aamp = pwd[98] * pwd[4 * 16 + lo] * pwd[5 * 16 + hi];
+                lnv = pwd[99] + df_mul_f(pwd[100], (float)t);
+            } else {
+                const double lnf = fma((double)k, lnr, cs[EV_LNF0]);
+                lnv = (lnf + cs[EV_LNPIM]) * (1.0 / 3.0);
+                v = pw[96] * pw[0 * 16 + lo] * pw[1 * 16 + hi];
+                vinv = pw[97] * pw[2 * 16 + lo] * pw[3 * 16 + hi];
+                Aamp = pw[98] * pw[4 * 16 + lo] * pw[5 * 16 + hi];
             }
-#pragma unroll
-            for (int c = 0; c < NP; c++)
-#pragma unroll
-                for (int r = 0; r < 4; r++) {
-                    const unsigned ex = expo(val[c][r]);
-                    lmax[c] = ex > lmax[c] ? ex : lmax[c];
+            const PnTermsT<T> pn = pn_terms<NP, ROT>(E, v, vinv, lnv);
+            const T w = pn.f * (k == 0 ? E[EV_WC0] : (k == N - 1 ? E[EV_WCN] : E[EV_WCM]));
+            const T twopif = T(TWO_PI) * pn.f;
+            T Wp[MAX_PSD];
+            if constexpr (DF)
+                psd_sigma_df<TAB>(net, Pd, E, cs, k, pn.f, pn.vi3, w, Aamp, tseg, Wp);
+            else
+                psd_sigma<TAB>(net, E, k, pn.f, pn.vi3, w, Aamp, tseg, Wp);
+            int L = 0;
+#pragma unroll 1
+            for (int s = 0; s < net.n_site; s++) {
+                const double *Sg = A.sitec + (e * net.n_site + s) * (int64_t)SC_N;
+                if (net.masked && Sg[SC_SLOT0] < 0.0) {   // every arm of the site off
+                    L += net.site_nslot[s];
+                    continue;
                 }
-            if (rounds == 2 && rd == 0) {
+                const T *S;
+                if constexpr (DF) S = Sd + s * SC_N;
+                else S = Sg;
+                T J[12];
+                PhaseT<T> ph;
+                site_terms<MODE_FISHER, ROT>(S, pn, twopif, J, ph);
+#pragma unroll 1
+                for (int slot = 0; slot < net.site_nslot[s]; slot++, L++) {
+                    int q = net.masked ? (int)Sg[SC_SLOT0 + slot] : net.site_ifo0[s] + slot;
+                    bool on = true;
+                    if (q < 0) {
+                        q = net.site_ifo0[s];
+                        on = false;
+                    }
+                    T s2g, c2g, amp;
+                    if constexpr (DF) {
+                        s2g = Qd[3 * q];
+                        c2g = Qd[3 * q + 1];
+                        amp = on ? Qd[3 * q + 2] : T(0.0);
+                    } else {
+                        s2g = net.ifo_s2g[q];
+                        c2g = net.ifo_c2g[q];
+                        amp = net.ifo_amp[q] * (on ? 1.0 : 0.0);
+                    }
+                    const PatT<T> pt = patterns(s2g, c2g, amp * E[EV_C2PSI], amp * E[EV_S2PSI], J);
+                    const T sg = Wp[net.ifo_psd[q]];
+                    T gr[NP], gi[NP], qr, qi;
+                    tangents<NP, ROT>(pt, sg * E[EV_CP], sg * E[EV_CX], sg * E[EV_DCP],
+                                      sg * E[EV_DCX], E[EV_AMC], E[EV_INVDL], ph, gr, gi, qr, qi);
+                    T *row = stage + (2 * L) * TC_T + t;
 #pragma unroll
-                for (int c = 0; c < NP; c++)
-#pragma unroll
-                    for (int r = 0; r < 4; r++) stage[(c * 4 + r) * TC_T + t] = val[c][r];
+                    for (int c = 0; c < NP; c++) {
+                        row[(c * 4) * TC_T] = gr[c];
+                        row[(c * 4 + 1) * TC_T] = gi[c];
+                        const unsigned er = expo(gr[c]), ei = expo(gi[c]);
+                        const unsigned em2 = er > ei ? er : ei;
+                        lmax[c] = em2 > lmax[c] ? em2 : lmax[c];
+                    }
+                    written |= 1u << L;
+                }
             }
         }
+        // rows of slots this point did not fill (absent or switched-off
+        // interferometers, points past the item) are zero
+#pragma unroll
+        for (int L = 0; L < 2; L++)
+            if (!((written >> L) & 1u)) {
+#pragma unroll
+                for (int c = 0; c < NP; c++) {
+                    stage[(c * 4 + 2 * L) * TC_T + t] = T(0.0);
+                    stage[(c * 4 + 2 * L + 1) * TC_T + t] = T(0.0);
+                }
+            }
         // ---- column maxima of the item's biased exponents
 #pragma unroll
         for (int c = 0; c < NP; c++) {
@@ -518,72 +506,47 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
 #pragma unroll
         for (int c = 0; c < NP; c++) em[c] = (int)emax[c];
 
-        // ---- digits into the operand buffers, one K block per (round, row)
-        int blk = 0;
-        const int krow = (t & 7) * 16 + (t >> 3) * KG;   // this thread's K row in a block
-#pragma unroll 1
-        for (int rd = 0; rd < rounds; rd++) {
-            const bool from_stage = rounds == 2 && rd == 0;
+        // ---- digits into the operand buffer, one K block per row r; the
+        // block's MMAs must be done before the next block overwrites it
+        unsigned char *B = ops + (t & 7) * 16 + (t >> 3) * KG;   // this thread's K row
 #pragma unroll
-            for (int r = 0; r < 4; r++, blk++) {
-                const int buf = blk & 1;
-                // the MMAs that read this buffer two blocks ago must be done
-                if (buf == 0 ? pend0 : pend1) {
-                    const bool w = mbar_wait(smem_addr(&mbar[buf]), buf == 0 ? par0 : par1);
-                    ok = ok && w;
-                    if (buf == 0) {
-                        par0 ^= 1u;
-                        pend0 = false;
-                    } else {
-                        par1 ^= 1u;
-                        pend1 = false;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                }
-                unsigned char *B = ops + buf * BLK + krow;
+        for (int r = 0; r < 4; r++) {
+            if (r > 0) {
+                ok = mbar_wait(smem_addr(&mbar[0]), par) && ok;
+                par ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+            }
 #pragma unroll
-                for (int c = 0; c < NP; c++) {
-                    const T y = from_stage ? stage[(c * 4 + r) * TC_T + t] : val[c][r];
-                    *reinterpret_cast<uint4 *>(B + c * TC_MG) = digits8(y, em[c]);
-                }
-                asm volatile("fence.proxy.async.shared::cta;");
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncthreads();
-                if (t == 0) {
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t b0 = ops_addr + buf * BLK;
+            for (int c = 0; c < NP; c++)
+                *reinterpret_cast<uint4 *>(B + c * TC_MG) = digits8(stage[(c * 4 + r) * TC_T + t], em[c]);
+            asm volatile("fence.proxy.async.shared::cta;");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            if (t == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-                    for (int st = 0; st < TC_KROWS / 16; st++) {
-                        const uint64_t d = smem_desc(b0 + st * 2 * KG, KG, TC_MG);
-                        const uint32_t accum = (blk > 0 || st > 0) ? 1u : 0u;
-                        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                                     :: "r"(tmem), "l"(d), "l"(d), "r"(idesc), "r"(accum));
-                    }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                                 :: "r"(smem_addr(&mbar[buf])));
+                for (int st = 0; st < TC_KROWS / 16; st++) {
+                    const uint64_t d = smem_desc(ops_addr + st * 2 * KG, KG, TC_MG);
+                    const uint32_t accum = (r > 0 || st > 0) ? 1u : 0u;
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                 :: "r"(tmem), "l"(d), "l"(d), "r"(idesc), "r"(accum));
                 }
-                if (buf == 0) pend0 = true;
-                else pend1 = true;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_addr(&mbar[0])));
             }
         }
-        // ---- all of the item's MMAs complete
-        if (pend0) {
-            ok = ok && mbar_wait(smem_addr(&mbar[0]), par0);
-            par0 ^= 1u;
-            pend0 = false;
-        }
-        if (pend1) {
-            ok = ok && mbar_wait(smem_addr(&mbar[1]), par1);
-            par1 ^= 1u;
-            pend1 = false;
-        }
+        ok = mbar_wait(smem_addr(&mbar[0]), par) && ok;
+        par ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
         double *out = A.partial + it * (int64_t)A.nacc;
-        if (__syncthreads_or(!ok)) {
+        if (__syncthreads_or(!ok || ke - kb > TC_T)) {
+            // a wait that ran out, or an item longer than the kernel's round
             for (int a = t; a < A.nacc; a += TC_T) out[a] = __longlong_as_double(0x7FF8000000000000ll);
             if (t == 0 && A.kerr) atomicExch(A.kerr, 1);
-            break;
+            if (!ok) break;
+            __syncthreads();
+            continue;
         }
 
         // ---- read the digit Gram: thread t holds TMEM lane t = row (i, a),
@@ -641,10 +604,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_fisher_tc(PointArgs A)
     // ---- teardown.  Normally every commit has been waited on.  After a wait
     // that ran out, give the MMAs in flight one more bounded wait; then free
     // the TMEM columns.
-    if (!ok) {
-        mbar_wait(smem_addr(&mbar[0]), par0 ^ 1u);
-        mbar_wait(smem_addr(&mbar[1]), par1 ^ 1u);
-    }
+    if (!ok) mbar_wait(smem_addr(&mbar[0]), par ^ 1u);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -660,7 +620,7 @@ cudaError_t launch_tc(const PointArgs &a, cudaStream_t s)
     cudaError_t err = set_smem_once(attr, k_fisher_tc<NP, ROT, TAB, T>, smem);
     if (err != cudaSuccess) return err;
     if (a.n_items <= 0) return cudaSuccess;
-    k_fisher_tc<NP, ROT, TAB, T><<<points_grid_size(2), TC_T, smem, s>>>(a);
+    k_fisher_tc<NP, ROT, TAB, T><<<points_grid_size(TC_CTAS), TC_T, smem, s>>>(a);
     return cudaGetLastError();
 }
 

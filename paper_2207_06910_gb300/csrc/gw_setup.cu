@@ -119,7 +119,7 @@ constexpr int SETUP_BS = 128;   // threads per block: two warps per 32 events
 
 __global__ void __launch_bounds__(SETUP_BS)
 k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec, float *sitec_f,
-              float2 *evc_f, int32_t *status, int64_t *counts)
+              float2 *evc_f, int32_t *status, int64_t *counts, int chunk)
 {
     // two warps per 32 events (the set-up is a long chain of dependent FP64
     // operations: twice the warps hide twice the latency): the even warp of a
@@ -156,7 +156,7 @@ k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec, float 
     if (part == 0) {
         status[e] = st;
         // no work items when no interferometer is in use (zero SNR and Fisher)
-        counts[e] = (st || !ifo_on) ? 0 : (int64_t)((N + CHUNK_MAX - 1) / CHUNK_MAX);
+        counts[e] = (st || !ifo_on) ? 0 : (int64_t)((N + chunk - 1) / chunk);
     }
     if (st) return;
 
@@ -385,13 +385,13 @@ k_event_setup(DevCat cat, DevNet net, int np, double *evc, double *sitec, float 
 
 cudaError_t launch_event_setup(const DevCat &cat, const DevNet &net, int np, double *evc,
                                double *sitec, float *sitec_f, float2 *evc_f, int32_t *status,
-                               int64_t *counts, cudaStream_t s)
+                               int64_t *counts, cudaStream_t s, int chunk)
 {
     if (cat.n <= 0) return cudaSuccess;
     const int64_t per_block = SETUP_BS / 2;       // events per block
     const int64_t nb = (cat.n + per_block - 1) / per_block;
     k_event_setup<<<(unsigned)nb, SETUP_BS, 0, s>>>(cat, net, np, evc, sitec, sitec_f, evc_f,
-                                                   status, counts);
+                                                   status, counts, chunk);
     return cudaGetLastError();
 }
 
