@@ -101,6 +101,10 @@ def parse():
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="do not time the FP64 path beside the mixed one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--psd", choices=["power", "table"], default="power",
+                    help="noise curves as the configuration's power sums, or as tables of "
+                         "2000 log-spaced (f, S_n) points read by log-log interpolation "
+                         "(Sec. 3.1 psd_path)")
     ap.add_argument("--fp64-gram", choices=["tensor", "pipe"], default="pipe",
                     help="Gram of the FP64 Fisher pass on the tensor cores (exact digit "
                          "products) or on the FP64 pipe")
@@ -112,12 +116,23 @@ def parse():
     return ap.parse_args()
 
 
+def bench_network(cfg: str, kind: str):
+    """Detector table, PSD rows, rotation flag and PSD tables (None for power
+    sums) of a workload."""
+    if kind == "table":
+        return gwcat.network_tabulated(cfg)
+    det, psd, rot = gwcat.network(cfg)
+    return det, psd, rot, None
+
+
 # ------------------------------------------------------------------ oracle leg
 def _oracle_event_step(args):
     """Every row of the step for one event, on the CPU oracle; returns the
     event's packed Fisher matrix, SNR, covariance and condition number."""
     import oracle
-    raw, rule, det, psd, rot = args
+    raw, rule, det, psd, rot, tables = args
+    if tables:
+        oracle.set_psd_tables(tables)
     p = oracle.prepare(raw["m1"], raw["m2"], raw["chi1"], raw["chi2"], raw["lam1"], raw["lam2"],
                        raw["dL_Mpc"], raw["zflag"], raw["tcoal"])
     if rule[0] == "efold":
@@ -142,23 +157,23 @@ def _sample(raw, idx):
     return out
 
 
-def oracle_timing(raw, cfg, cores, budget_s=20.0):
+def oracle_timing(raw, cfg, cores, budget_s=20.0, psd_kind="power"):
     """Time the oracle on a bounded random sample of the workload (spawn
     pool, one event per process); returns the rate and the sampled events'
     rows and oracle results."""
     import multiprocessing as mp
     import oracle
     oracle.build()
-    det, psd, rot = gwcat.network(cfg)
+    det, psd, rot, tables = bench_network(cfg, psd_kind)
     rule = raw["npts_rule"]
     rng = np.random.default_rng(1)
     rows, res = [], []
     with mp.get_context("spawn").Pool(cores) as pool:
-        pool.map(_oracle_event_step, [(_sample(raw, [0]), rule, det, psd, rot)])   # warm
+        pool.map(_oracle_event_step, [(_sample(raw, [0]), rule, det, psd, rot, tables)])   # warm
         t0 = time.time()
         while True:
             idx = rng.choice(len(raw["m1"]), cores, replace=False)
-            res += pool.map(_oracle_event_step, [(_sample(raw, [i]), rule, det, psd, rot)
+            res += pool.map(_oracle_event_step, [(_sample(raw, [i]), rule, det, psd, rot, tables)
                                                  for i in idx])
             rows += list(idx)
             el = time.time() - t0
@@ -172,7 +187,7 @@ def run_reference(a):
         return
     raw = gwcat.draw("c3", a.events, grid=a.grid)
     cores = os.cpu_count() or 1
-    det, psd, rot = gwcat.network("c3")
+    det, psd, rot, tables = bench_network("c3", a.psd)
     import multiprocessing as mp
     import oracle
     oracle.build()
@@ -181,7 +196,7 @@ def run_reference(a):
     with mp.get_context("spawn").Pool(cores) as pool:
         for i in range(a.warmup + a.steps):
             idx = rng.choice(len(raw["m1"]), cores, replace=False)
-            tasks = [(_sample(raw, [j]), raw["npts_rule"], det, psd, rot) for j in idx]
+            tasks = [(_sample(raw, [j]), raw["npts_rule"], det, psd, rot, tables) for j in idx]
             t0 = time.time()
             pool.map(_oracle_event_step, tasks)
             if i >= a.warmup:
@@ -431,8 +446,8 @@ def run_ours(a):
         a.eager = True      # the gate reads its count back: no single-graph step
     with_logdet = a.workload == "c4"
     n_per_gpu = a.events or gwcat.SIZES[cfg]
-    det, psd, rot = gwcat.network(cfg)
-    net = gw.Network(det, psd, rot)
+    det, psd, rot, tables = bench_network(cfg, a.psd)
+    net = gw.Network(det, psd, rot, tables)
     n_arms = sum(1 if int(r[4]) == 0 else 3 for r in det)
     n_site = net.n_det
     n_ifo = sum(1 if int(r[4]) == 0 else 2 for r in det)
@@ -777,7 +792,7 @@ def run_ours(a):
         err_sample = None
         if not a.no_cpu_baseline:
             cores = os.cpu_count() or 1
-            v, rows, ores, el = oracle_timing(raw, cfg, cores, budget_s=20.0)
+            v, rows, ores, el = oracle_timing(raw, cfg, cores, budget_s=20.0, psd_kind=a.psd)
             cpu = {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
                    "sample": f"{len(rows)} random events of this rank's catalog in {el:.1f} s "
                              f"(prepare + SNR + Fisher + inversion + SNR gradient), "
@@ -805,7 +820,9 @@ def run_ours(a):
                               "sqrt_diag_cov_max_rel": float(np.nanmax(relC[okd])) if okd.any() else None,
                               "sqrt_diag_cov_worst_over_bound": float(np.nanmax(
                                   relC[okd] / np.maximum(1e-3, 1e-15 * ko[okd]))) if okd.any() else None}
-        golden = golden_error(gw, a.refine_cond) if (cfg == "c3" and not gated) else None
+        # (the stored oracle results use the power-sum noise curve)
+        golden = golden_error(gw, a.refine_cond) if (cfg == "c3" and not gated and a.psd == "power") \
+            else None
         line = {
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
@@ -817,7 +834,7 @@ def run_ours(a):
             "config": {"workload": {"c3": WORKLOAD, "c4": WORKLOAD_C4,
                                     "c3-gated": WORKLOAD_GATED}[a.workload],
                        "n_events_total": n_total, "n_events_per_gpu": n_per_gpu,
-                       "grid": a.grid, "points_per_step_rank0": n_points + (n_points_all if gated else 0),
+                       "grid": a.grid, "psd": a.psd, "points_per_step_rank0": n_points + (n_points_all if gated else 0),
                        "precision": a.precision, "n_par": N_PAR,
                        "step": ("prepare + SNR pass + gate + " if gated else "prepare + ")
                                + "SNR/Fisher with fused SNR VJP + Cholesky inversion"
