@@ -12,11 +12,11 @@
 // of digits a and b is a multiple of q_a q_b below 2^14 q_a q_b and an item has
 // at most 1024 rows (256 points x 2 interferometers x real/imaginary), so
 // every partial sum is such a multiple below 2^24 q_a q_b: the accumulation is
-// exact.  The digit Gram D[(i,a),(j,b)] is then summed in FP64,
+// exact.  The digit Gram D[(i,a),(j,b)] is then summed exactly (integers) and
+// rounded once to FP64,
 //     Gamma_ij = 2^(E_i + E_j - 2044) sum_ab D[(i,a),(j,b)],
 // so the item's Fisher matrix is the exact Gram of the tangents rounded to 56
-// bits (relative to the column maximum), summed in FP64 only over the 64 digit
-// pairs.
+// bits (relative to the column maximum), rounded once to FP64.
 //
 // The tangents come from the templated formulas of gw_points_fp64.cuh with
 // scalar type T:
@@ -33,22 +33,28 @@
 //
 // Shape.  Work items of at most TC_CHUNK = 128 points (the event set-up splits
 // events accordingly), one grid point per thread of a 128-thread CTA, three
-// CTAs per SM, persistent over the items.  Each thread writes its point's
-// values (columns x rows r = interferometer x {Re, Im}) to shared memory as it
-// forms them (FP64 or double-float pairs, 8 bytes each), so that no value
-// stays in registers and the kernel fits three CTAs per SM (~168 registers);
-// the column maxima are reduced once the item's points are done.  The digits
-// go to shared memory in the MN-major, no-swizzle operand layout (8 digits of
-// one value = one 16-byte row of a core matrix; K groups of 8 rows at stride
-// KG, MN groups at 128 bytes), one K block of 128 rows per row r, in one
-// buffer: one thread issues the block's eight M=128 x N x K=16 MMAs (A = B =
-// the block) into the item's TMEM accumulator and commits them to the
-// mbarrier, which the writers of the next block wait on.  After the item's
-// last block the four warps read their 32 TMEM lanes (rows (i, a)) and reduce
-// over the digit pairs.  Networks of at most two interferometers per point
-// (one triangle or up to two L-shaped detectors) take this kernel; wider
-// networks, and the SNR, SNR-gradient and log-det passes, run the FP64-pipe
-// kernel.
+// CTAs per SM, persistent: each CTA takes a contiguous range of items, finds
+// the event of its first item by bisection and then walks forward, and loads
+// an event's constants (and builds its power tables) once for the event's
+// consecutive items.  Each thread writes its point's values (rows r =
+// interferometer x {Re, Im}, then columns) to shared memory as it forms them
+// (FP64 or double-float pairs, 8 bytes each), so that no value stays in
+// registers and the kernel fits three CTAs per SM (~168 registers); the column
+// maxima are reduced once the item's points are done.  The digits go to shared
+// memory in the MN-major, no-swizzle operand layout (8 digits of one value =
+// one 16-byte row of a core matrix; K groups of 8 rows at stride KG, MN groups
+// at 128 bytes), one K block of 128 rows per row r, alternating between two
+// operand buffers: a dedicated one and the staged rows 0 and 1, which are free
+// once they have been turned into digits.  One thread issues a block's eight
+// M=128 x N x K=16 MMAs (A = B = the block) into the item's TMEM accumulator and
+// commits them to the buffer's mbarrier; the digits of the next block are
+// formed meanwhile, and a buffer is rewritten only after its previous MMAs are
+// done.  After the item's last block the four warps read their 32 TMEM lanes
+// (rows (i, a)) and reduce over the digit pairs in 128-bit integer arithmetic,
+// one rounding to FP64 per Fisher entry.  Networks of at most two
+// interferometers per point (one triangle or up to two L-shaped detectors) take
+// this kernel; wider networks, and the SNR, SNR-gradient and log-det passes,
+// run the FP64-pipe kernel.
 //
 // Every wait is bounded (about a second of wall time); a wait that runs out
 // sets *kerr, writes NaN into the item's sums and ends the CTA after freeing
@@ -76,9 +82,11 @@ struct TcShape {
     static constexpr int KG = NP * 128;                    // bytes between K groups
     static constexpr int BLK = (TC_KROWS / 8) * KG;        // one K block (the operand buffer)
     static constexpr int N = ((NP * 8 + 15) / 16) * 16;    // MMA N (digit rows used, padded)
-    // The staged values follow the operand buffer: an M = 128 read of the
-    // last MMA step of a block reaches 2047 - KG bytes past the block, into
-    // them (finite data, only for accumulator rows and columns never read).
+    // The staged values follow operand buffer 0, and their rows 0 and 1 (one
+    // block: 2 x NP x TC_T values of 8 bytes) are operand buffer 1: an M = 128
+    // read of the last MMA step of a block reaches 2047 - KG bytes past the
+    // block, into the staged values (finite data, only for accumulator rows
+    // and columns never read).
     static constexpr int STAGE_BYTES = NP * 4 * TC_T * 8;
     // double-float copies: event constants, site constants, interferometer
     // (s2g, c2g, amp) and PSD constants (inverse f0, f0, coefficients)
@@ -89,7 +97,8 @@ struct TcShape {
         return (size_t)BLK + STAGE_BYTES + (size_t)EVC * 8 + TC_PW * 8 + 16 * 4 + 8 + 8 + 16 +
                (df ? (size_t)DF_WORDS * 8 : 0);
     }
-    static_assert(2047 - KG <= STAGE_BYTES, "operand over-read stays in shared memory");
+    static_assert(2 * BLK == STAGE_BYTES, "staged rows 0 and 1 hold one operand block");
+    static_assert(2047 - KG <= STAGE_BYTES - BLK, "operand over-read stays in shared memory");
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -277,12 +286,16 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
     constexpr bool DF = std::is_same<T, dfl>::value;
     constexpr int KG = SH::KG, NMMA = SH::N;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    unsigned char *ops = tc_smem;
-    T *stage = reinterpret_cast<T *>(tc_smem + SH::BLK);   // [NP][4][TC_T] values
+    // operand buffer 0, then the staged values [4 rows r][NP columns][TC_T
+    // points]; the first two rows' values (2 x NP x TC_T x 8 bytes = one operand
+    // block) become operand buffer 1 once they have been turned into digits
+    unsigned char *ops0 = tc_smem;
+    T *stage = reinterpret_cast<T *>(tc_smem + SH::BLK);
+    unsigned char *ops1 = reinterpret_cast<unsigned char *>(stage);
     double *cs = reinterpret_cast<double *>(stage + NP * 4 * TC_T);   // event constants
     double *pw = cs + EVC;                   // [3][2][16] powers, then bases
     unsigned *emax = reinterpret_cast<unsigned *>(pw + TC_PW);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(emax + 16);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(emax + 16);   // one per operand buffer
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
     // double-float copies (T = dfl only)
     dfl *Ed = reinterpret_cast<dfl *>(tmem_slot + 4);
@@ -301,6 +314,7 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
     }
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(&mbar[1])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (DF) {
@@ -320,38 +334,54 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
             Pd[i] = dfl(v);
         }
     }
-    // the staged values are read past the operand buffer (see TcShape): keep
-    // them finite from the start
+    // the staged values are read past either operand buffer (see TcShape):
+    // keep them finite from the start
     for (int i = t; i < (SH::BLK + SH::STAGE_BYTES) / 16; i += TC_T)
-        reinterpret_cast<uint4 *>(ops)[i] = make_uint4(0, 0, 0, 0);
+        reinterpret_cast<uint4 *>(ops0)[i] = make_uint4(0, 0, 0, 0);
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t ops_addr = smem_addr(ops);
+    const uint32_t ops_addr[2] = {smem_addr(ops0), smem_addr(ops1)};
     // instruction descriptor: D FP32, A and B bf16, both MN-major, N, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
                            ((uint32_t)(NMMA >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    uint32_t par = 0;        // parity of the mbarrier phase of the next commit
+    uint32_t par[2] = {0u, 0u};   // parity of the next mbarrier phase of each buffer
     bool ok = true;
 
+    // this CTA's contiguous range of work items: consecutive items mostly
+    // belong to one event, whose constants then stay in shared memory
     const int64_t n_total = A.item_off[A.n_ev];
     const int64_t n_items = n_total < A.n_items ? n_total : A.n_items;
+    const int64_t it_begin = n_items * blockIdx.x / gridDim.x;
+    const int64_t it_end = n_items * (blockIdx.x + 1) / gridDim.x;
+    int64_t e = -1;
 
-    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int64_t e = find_event(A.item_off, A.n_ev, it);
-        const int64_t jit = it - A.item_off[e];
-        const int64_t nj = A.item_off[e + 1] - A.item_off[e];
-        const double *Eg = A.evc + e * (int64_t)EVC;
-        for (int q = t; q < EVC; q += TC_T) {
-            const double v = Eg[q];
-            cs[q] = v;
-            if (DF) Ed[q] = dfl(v);
+    for (int64_t it = it_begin; it < it_end; it++) {
+        // event of the item: a search for the range's first item, then forward
+        int64_t en;
+        if (e < 0) {
+            en = find_event(A.item_off, A.n_ev, it);
+        } else {
+            en = e;
+            while (__ldg(A.item_off + en + 1) <= it) en++;
         }
-        if (DF) {
-            for (int i = t; i < net.n_site * SC_N; i += TC_T)
-                Sd[i] = dfl(A.sitec[e * net.n_site * (int64_t)SC_N + i]);
+        const bool new_event = en != e;
+        e = en;
+        const int64_t jit = it - __ldg(A.item_off + e);
+        const int64_t nj = __ldg(A.item_off + e + 1) - __ldg(A.item_off + e);
+        if (new_event) {
+            const double *Eg = A.evc + e * (int64_t)EVC;
+            for (int q = t; q < EVC; q += TC_T) {
+                const double v = Eg[q];
+                cs[q] = v;
+                if (DF) Ed[q] = dfl(v);
+            }
+            if (DF) {
+                for (int i = t; i < net.n_site * SC_N; i += TC_T)
+                    Sd[i] = dfl(A.sitec[e * net.n_site * (int64_t)SC_N + i]);
+            }
         }
         if (t < 16) emax[t] = 0u;
         __syncthreads();
@@ -359,8 +389,9 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
         const int kb = (int)((int64_t)N * jit / nj), ke = (int)((int64_t)N * (jit + 1) / nj);
         const double lnr = cs[EV_LNR];
         // powers of the per-point factors of v, 1/v and the amplitude (steps 1
-        // and 16 points) and their values at the item's first point
-        if (t < 6) {
+        // and 16 points; warp 0, once per event) and their values at the item's
+        // first point (warp 1, every item)
+        if (new_event && t < 6) {
             const int q = t % 3, big = t / 3;
             const double l = q == 0 ? lnr * (1.0 / 3.0) : (q == 1 ? -lnr * (1.0 / 3.0) : -7.0 / 6.0 * lnr);
             const double fct = exp(big ? 16.0 * l : l);
@@ -379,10 +410,10 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
                     val *= fct;
                 }
             }
-        } else if (t < 10) {
+        } else if (t >= 32 && t < 36) {
             const double lnf0 = fma((double)kb, lnr, cs[EV_LNF0]);
             const double lnv0 = (lnf0 + cs[EV_LNPIM]) * (1.0 / 3.0);
-            const int q = t - 6;
+            const int q = t - 32;
             const double b = q == 0 ? exp(lnv0)
                            : q == 1 ? exp(-lnv0)
                            : q == 2 ? cs[EV_A0] * exp(-7.0 / 6.0 * lnf0)
@@ -471,11 +502,11 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
                     T gr[NP], gi[NP], qr, qi;
                     tangents<NP, ROT>(pt, sg * E[EV_CP], sg * E[EV_CX], sg * E[EV_DCP],
                                       sg * E[EV_DCX], E[EV_AMC], E[EV_INVDL], ph, gr, gi, qr, qi);
-                    T *row = stage + (2 * L) * TC_T + t;
+                    T *row = stage + (2 * L) * NP * TC_T + t;
 #pragma unroll
                     for (int c = 0; c < NP; c++) {
-                        row[(c * 4) * TC_T] = gr[c];
-                        row[(c * 4 + 1) * TC_T] = gi[c];
+                        row[c * TC_T] = gr[c];
+                        row[(NP + c) * TC_T] = gi[c];
                         const unsigned er = expo(gr[c]), ei = expo(gi[c]);
                         const unsigned em2 = er > ei ? er : ei;
                         lmax[c] = em2 > lmax[c] ? em2 : lmax[c];
@@ -491,8 +522,8 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
             if (!((written >> L) & 1u)) {
 #pragma unroll
                 for (int c = 0; c < NP; c++) {
-                    stage[(c * 4 + 2 * L) * TC_T + t] = T(0.0);
-                    stage[(c * 4 + 2 * L + 1) * TC_T + t] = T(0.0);
+                    stage[(2 * L * NP + c) * TC_T + t] = T(0.0);
+                    stage[((2 * L + 1) * NP + c) * TC_T + t] = T(0.0);
                 }
             }
         // ---- column maxima of the item's biased exponents
@@ -506,19 +537,27 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
 #pragma unroll
         for (int c = 0; c < NP; c++) em[c] = (int)emax[c];
 
-        // ---- digits into the operand buffer, one K block per row r; the
-        // block's MMAs must be done before the next block overwrites it
-        unsigned char *B = ops + (t & 7) * 16 + (t >> 3) * KG;   // this thread's K row
+        // ---- digits of row r into operand buffer r % 2; buffer 1 overlays the
+        // staged rows 0 and 1, so it is written only after every thread has read
+        // them, and each buffer's previous MMAs must be done before it is
+        // rewritten.  The digits of the next row are formed while the tensor
+        // core works on the previous one.
+        const int koff = (t & 7) * 16 + (t >> 3) * KG;   // this thread's K row in a buffer
 #pragma unroll
         for (int r = 0; r < 4; r++) {
-            if (r > 0) {
-                ok = mbar_wait(smem_addr(&mbar[0]), par) && ok;
-                par ^= 1u;
+            uint4 dg[NP];
+#pragma unroll
+            for (int c = 0; c < NP; c++) dg[c] = digits8(stage[(r * NP + c) * TC_T + t], em[c]);
+            const int b = r & 1;
+            if (r == 1) __syncthreads();   // staged rows 0 and 1 read by every thread
+            if (r >= 2) {
+                ok = mbar_wait(smem_addr(&mbar[b]), par[b]) && ok;
+                par[b] ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;");
             }
+            unsigned char *B = (b ? ops1 : ops0) + koff;
 #pragma unroll
-            for (int c = 0; c < NP; c++)
-                *reinterpret_cast<uint4 *>(B + c * TC_MG) = digits8(stage[(c * 4 + r) * TC_T + t], em[c]);
+            for (int c = 0; c < NP; c++) *reinterpret_cast<uint4 *>(B + c * TC_MG) = dg[c];
             asm volatile("fence.proxy.async.shared::cta;");
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
@@ -526,18 +565,21 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
                 asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
                 for (int st = 0; st < TC_KROWS / 16; st++) {
-                    const uint64_t d = smem_desc(ops_addr + st * 2 * KG, KG, TC_MG);
+                    const uint64_t d = smem_desc(ops_addr[b] + st * 2 * KG, KG, TC_MG);
                     const uint32_t accum = (r > 0 || st > 0) ? 1u : 0u;
                     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
                                  :: "r"(tmem), "l"(d), "l"(d), "r"(idesc), "r"(accum));
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(smem_addr(&mbar[0])));
+                             :: "r"(smem_addr(&mbar[b])));
             }
         }
-        ok = mbar_wait(smem_addr(&mbar[0]), par) && ok;
-        par ^= 1u;
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            ok = mbar_wait(smem_addr(&mbar[b]), par[b]) && ok;
+            par[b] ^= 1u;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;");
         double *out = A.partial + it * (int64_t)A.nacc;
         if (__syncthreads_or(!ok || ke - kb > TC_T)) {
@@ -552,49 +594,79 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
         // ---- read the digit Gram: thread t holds TMEM lane t = row (i, a),
         // i = t / 8, a = t % 8; columns (j, b) at 8 j + b.  Row i forms the
         // entries (i, j) for j = i .. i + H (mod P), H = (P - 1) / 2: every
-        // unordered pair once (P is odd), about P / 2 column groups per row, so
-        // warp w (rows i = 4w .. 4w + 3) reads the groups 4w .. 4w + 3 + H.
-        // The eight products D[(i,a),(j,b)] of a lane are exact multiples of
-        // q_a q_b below 2^24 q_a q_b: they are summed exactly as integers (b < 4
-        // in units of q_a q_3, b >= 4 in units of q_a q_7, both below 2^46),
-        // then the lane's sum goes to FP64 (two conversions, one FMA) and the
-        // eight lanes of row i are added with shuffles.
+        // unordered pair once (P is odd), so warp w (rows i = 4w .. 4w + 3)
+        // reads the column groups 4w .. 4w + 3 + H, all loads issued before one
+        // wait.  The products D[(i,a),(j,b)] are exact multiples of q_a q_b
+        // below 2^24 q_a q_b: with n_ab = D / (q_a q_b), the entry is
+        //     sum_ab D = 2^-112 I,   I = sum_a 2^(7 (7 - a)) sum_b 2^(7 (7 - b)) n_ab,
+        // an integer below 2^123 in magnitude, formed exactly in 128-bit
+        // integer arithmetic (per lane over b, across the row's eight lanes with
+        // shuffles) and rounded once to FP64.
         const int i = t >> 3, a = t & 7;
         constexpr int H = (NP - 1) / 2;
+        constexpr int NGRP = 4 + H;   // column groups read per warp (at most)
         // (a warp whose rows are all padding, 4w >= P, reads nothing)
         const int jend = 4 * warp >= NP ? 0 : (4 * warp + 3 < NP - 1 ? 4 * warp + 3 : NP - 1) + H + 1;
-        const double ua = ldexp(1.0, -7 * (a + 5));     // unit of the b < 4 sum
+        constexpr int GB = 3;          // column groups per batch of TMEM loads
 #pragma unroll 1
-        for (int jr = 4 * warp; jr < jend; jr++) {
-            const int j = jr < NP ? jr : jr - NP;
-            uint32_t d[8];
-            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 8);
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]),
-                           "=r"(d[6]), "=r"(d[7])
-                         : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            long long hs = 0, ls = 0;
+        for (int g0 = 0; g0 < NGRP; g0 += GB) {
+            if (4 * warp + g0 >= jend) break;
+            uint32_t dd[GB][8];
 #pragma unroll
-            for (int b = 0; b < 8; b++) {
-                // D / (q_a q_b): an integer below 2^24 (exact FP32 scaling by 2^(7(a+b+2)))
-                const float sb = __uint_as_float((unsigned)(127 + 7 * (a + b + 2)) << 23);
-                const long long n = (long long)__float2int_rn(__uint_as_float(d[b]) * sb);
-                if (b < 4) hs += n << (7 * (3 - b));
-                else ls += n << (7 * (7 - b));
+            for (int g = 0; g < GB; g++) {
+                const int jr = 4 * warp + g0 + g;
+                if (jr < jend) {
+                    const int j = jr < NP ? jr : jr - NP;
+                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 8);
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(dd[g][0]), "=r"(dd[g][1]), "=r"(dd[g][2]), "=r"(dd[g][3]),
+                                   "=r"(dd[g][4]), "=r"(dd[g][5]), "=r"(dd[g][6]), "=r"(dd[g][7])
+                                 : "r"(ta));
+                }
             }
-            double P = fma((double)ls, 0x1p-28, (double)hs) * ua;
-            P += __shfl_xor_sync(0xffffffffu, P, 1);
-            P += __shfl_xor_sync(0xffffffffu, P, 2);
-            P += __shfl_xor_sync(0xffffffffu, P, 4);
-            const int dj = jr - i;   // j = i + dj (mod P)
-            if (a == 0 && i < NP && dj >= 0 && dj <= H) {
-                const int lo = i < j ? i : j, hi = i < j ? j : i;
-                const double g = P == 0.0 ? 0.0 : P * pow2_scale((int)emax[i], (int)emax[j]);
-                const int idx = 1 + lo * NP - lo * (lo - 1) / 2 + (hi - lo);
-                if (idx < A.nacc) out[idx] = g;
-                // SNR^2 = sum |Q|^2 = the (Phic, Phic) entry: g_Phic = -i Q
-                if (i == 8 && j == 8) out[0] = g;
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int g = 0; g < GB; g++) {
+                const int jr = 4 * warp + g0 + g;
+                if (jr >= jend) break;
+                const int j = jr < NP ? jr : jr - NP;
+                // W = sum_b 2^(7 (7 - b)) n_ab (|W| < 2^74), as hs 2^28 + ls
+                long long hs = 0, ls = 0;
+#pragma unroll
+                for (int b = 0; b < 8; b++) {
+                    // D / (q_a q_b): an integer below 2^24 (exact FP32 scaling by 2^(7(a+b+2)))
+                    const float sb = __uint_as_float((unsigned)(127 + 7 * (a + b + 2)) << 23);
+                    const long long n = (long long)__float2int_rn(__uint_as_float(dd[g][b]) * sb);
+                    if (b < 4) hs += n << (7 * (3 - b));
+                    else ls += n << (7 * (7 - b));
+                }
+                // X = W 2^(7 (7 - a)) as a 128-bit two's-complement integer, summed
+                // over the row's eight lanes
+                using u128 = unsigned __int128;
+                u128 X = (((u128)(__int128)hs << 28) + (u128)(__int128)ls) << (7 * (7 - a));
+#pragma unroll
+                for (int m = 1; m < 8; m <<= 1) {
+                    const unsigned long long yl = __shfl_xor_sync(0xffffffffu, (unsigned long long)X, m);
+                    const unsigned long long yh =
+                        __shfl_xor_sync(0xffffffffu, (unsigned long long)(X >> 64), m);
+                    X += ((u128)yh << 64) | (u128)yl;
+                }
+                const int dj = jr - i;   // j = i + dj (mod P)
+                if (a == 0 && i < NP && dj >= 0 && dj <= H) {
+                    const int lo = i < j ? i : j, hi = i < j ? j : i;
+                    // |I| rounded to FP64 (high word, exact below 2^53, times 2^64
+                    // plus the low word), the sign, then the scale 2^-112 (exact)
+                    const bool neg = (long long)(unsigned long long)(X >> 64) < 0;
+                    const u128 M = neg ? (u128)0 - X : X;
+                    const double mag = fma((double)(unsigned long long)(M >> 64), 0x1p64,
+                                           (double)(unsigned long long)M);
+                    const double P = (neg ? -mag : mag) * 0x1p-112;
+                    const double gv = P == 0.0 ? 0.0 : P * pow2_scale((int)emax[i], (int)emax[j]);
+                    const int idx = 1 + lo * NP - lo * (lo - 1) / 2 + (hi - lo);
+                    if (idx < A.nacc) out[idx] = gv;
+                    // SNR^2 = sum |Q|^2 = the (Phic, Phic) entry: g_Phic = -i Q
+                    if (i == 8 && j == 8) out[0] = gv;
+                }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -604,7 +676,11 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
     // ---- teardown.  Normally every commit has been waited on.  After a wait
     // that ran out, give the MMAs in flight one more bounded wait; then free
     // the TMEM columns.
-    if (!ok) mbar_wait(smem_addr(&mbar[0]), par ^ 1u);
+    if (!ok) {
+        // (each wait flipped its parity: par ^ 1 is the phase last waited for)
+        mbar_wait(smem_addr(&mbar[0]), par[0] ^ 1u);
+        mbar_wait(smem_addr(&mbar[1]), par[1] ^ 1u);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
