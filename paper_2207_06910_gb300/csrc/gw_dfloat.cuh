@@ -180,13 +180,16 @@ __device__ __forceinline__ void sincos(dfl x, dfl *sx, dfl *cx)
     r = r + dfl(-k * dfs::P2, 0.0f);
     r = r + dfl(-k * dfs::P3, 0.0f);
     const dfl r2 = r * r;
+    // both series in one rolled loop (two independent chains per iteration;
+    // rolled to keep the callers' code small)
     dfl s = taylor_coef(15);
-#pragma unroll
-    for (int n = 6; n >= 0; n--) s = s * r2 + taylor_coef(2 * n + 1);
+    dfl c = taylor_coef(16) * r2 + taylor_coef(14);
+#pragma unroll 1
+    for (int n = 6; n >= 0; n--) {
+        s = s * r2 + taylor_coef(2 * n + 1);
+        c = c * r2 + taylor_coef(2 * n);
+    }
     s = s * r;
-    dfl c = taylor_coef(16);
-#pragma unroll
-    for (int n = 7; n >= 0; n--) c = c * r2 + taylor_coef(2 * n);
     const int q = ((int)k) & 3;
     const dfl sn = (q == 0) ? s : (q == 1) ? c : (q == 2) ? -s : -c;
     const dfl cs = (q == 0) ? c : (q == 1) ? -s : (q == 2) ? -c : s;

@@ -343,11 +343,11 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t ops_addr[2] = {smem_addr(ops0), smem_addr(ops1)};
+    const uint32_t ops_addr0 = smem_addr(ops0), ops_addr1 = smem_addr(ops1);
     // instruction descriptor: D FP32, A and B bf16, both MN-major, N, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
                            ((uint32_t)(NMMA >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    uint32_t par[2] = {0u, 0u};   // parity of the next mbarrier phase of each buffer
+    uint32_t par = 0u;   // bit b: parity of the next mbarrier phase of buffer b
     bool ok = true;
 
     // this CTA's contiguous range of work items: consecutive items mostly
@@ -543,7 +543,8 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
         // rewritten.  The digits of the next row are formed while the tensor
         // core works on the previous one.
         const int koff = (t & 7) * 16 + (t >> 3) * KG;   // this thread's K row in a buffer
-#pragma unroll
+        // (a rolled loop: the kernel's code size is what limits instruction fetch)
+#pragma unroll 1
         for (int r = 0; r < 4; r++) {
             uint4 dg[NP];
 #pragma unroll
@@ -551,8 +552,8 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
             const int b = r & 1;
             if (r == 1) __syncthreads();   // staged rows 0 and 1 read by every thread
             if (r >= 2) {
-                ok = mbar_wait(smem_addr(&mbar[b]), par[b]) && ok;
-                par[b] ^= 1u;
+                ok = mbar_wait(smem_addr(&mbar[b]), (par >> b) & 1u) && ok;
+                par ^= 1u << b;
                 asm volatile("tcgen05.fence::after_thread_sync;");
             }
             unsigned char *B = (b ? ops1 : ops0) + koff;
@@ -565,7 +566,7 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
                 asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
                 for (int st = 0; st < TC_KROWS / 16; st++) {
-                    const uint64_t d = smem_desc(ops_addr[b] + st * 2 * KG, KG, TC_MG);
+                    const uint64_t d = smem_desc((b ? ops_addr1 : ops_addr0) + st * 2 * KG, KG, TC_MG);
                     const uint32_t accum = (r > 0 || st > 0) ? 1u : 0u;
                     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
@@ -577,8 +578,8 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
         }
 #pragma unroll
         for (int b = 0; b < 2; b++) {
-            ok = mbar_wait(smem_addr(&mbar[b]), par[b]) && ok;
-            par[b] ^= 1u;
+            ok = mbar_wait(smem_addr(&mbar[b]), (par >> b) & 1u) && ok;
+            par ^= 1u << b;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         double *out = A.partial + it * (int64_t)A.nacc;
@@ -678,8 +679,8 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
     // the TMEM columns.
     if (!ok) {
         // (each wait flipped its parity: par ^ 1 is the phase last waited for)
-        mbar_wait(smem_addr(&mbar[0]), par[0] ^ 1u);
-        mbar_wait(smem_addr(&mbar[1]), par[1] ^ 1u);
+        mbar_wait(smem_addr(&mbar[0]), (par & 1u) ^ 1u);
+        mbar_wait(smem_addr(&mbar[1]), ((par >> 1) & 1u) ^ 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
