@@ -36,7 +36,10 @@
 // CTAs per SM, persistent: each CTA takes a contiguous range of items, finds
 // the event of its first item by bisection and then walks forward, and loads
 // an event's constants (and builds its power tables) once for the event's
-// consecutive items.  Each thread writes its point's values (rows r =
+// consecutive items.  An event's items take the even share of its points
+// rounded up to whole warps (the last item the rest), and warp 3, whose TMEM
+// lanes hold no Gram rows, prepares the next item while warps 0-2 read the
+// current one's Gram.  Each thread writes its point's values (rows r =
 // interferometer x {Re, Im}, then columns) to shared memory as it forms them
 // (FP64 or double-float pairs, 8 bytes each), so that no value stays in
 // registers and the kernel fits three CTAs per SM (~168 registers); the column
@@ -94,7 +97,7 @@ struct TcShape {
                                     MAX_PSD * (2 + MAX_TERM) + TC_PW;
     static constexpr size_t smem(bool df)
     {
-        return (size_t)BLK + STAGE_BYTES + (size_t)EVC * 8 + TC_PW * 8 + 16 * 4 + 8 + 8 + 16 +
+        return (size_t)BLK + STAGE_BYTES + (size_t)EVC * 8 + TC_PW * 8 + 32 * 4 + 8 + 8 + 16 + 32 +
                (df ? (size_t)DF_WORDS * 8 : 0);
     }
     static_assert(2 * BLK == STAGE_BYTES, "staged rows 0 and 1 hold one operand block");
@@ -216,7 +219,8 @@ __device__ __forceinline__ uint4 digits8(double y, int ec)
 // lanes' parts (for a >= 1 each is at most 64 q_a; lo has no part in digit 0)
 __device__ __forceinline__ uint4 digits8(dfl y, int ec)
 {
-    if (ec == 0) return make_uint4(0u, 0u, 0u, 0u);      // a column of zeros
+    // a column of zeros, or a zero value (rows of idle points, slots switched off)
+    if (ec == 0 || y.hi == 0.0f) return make_uint4(0u, 0u, 0u, 0u);
     const int sf = 1149 - ec;                             // 2^(1022 - ec) as FP32
     const float sc = __uint_as_float((unsigned)(sf > 0 ? sf : 1) << 23);
     float2 r = __fmul2_rn(make_float2(y.hi, y.lo), make_float2(sc, sc));
@@ -279,6 +283,13 @@ __device__ __forceinline__ void psd_sigma_df(const DevNet &net, const dfl *psd_d
     }
 }
 
+// a work item as the preparing warp leaves it for the CTA
+struct __align__(16) TcItem {
+    long long e;       // event
+    int n, kb, ke;     // the event's grid length, the item's points [kb, ke)
+    int pad[3];
+};
+
 template <int NP, bool ROT, bool TAB, typename T>
 __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
 {
@@ -294,11 +305,12 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
     unsigned char *ops1 = reinterpret_cast<unsigned char *>(stage);
     double *cs = reinterpret_cast<double *>(stage + NP * 4 * TC_T);   // event constants
     double *pw = cs + EVC;                   // [3][2][16] powers, then bases
-    unsigned *emax = reinterpret_cast<unsigned *>(pw + TC_PW);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(emax + 16);   // one per operand buffer
+    unsigned *emax = reinterpret_cast<unsigned *>(pw + TC_PW);   // [2][16]: column maxima
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(emax + 32);   // one per operand buffer
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
+    TcItem *item = reinterpret_cast<TcItem *>(tmem_slot + 4);   // the next item to run
     // double-float copies (T = dfl only)
-    dfl *Ed = reinterpret_cast<dfl *>(tmem_slot + 4);
+    dfl *Ed = reinterpret_cast<dfl *>(item + 1);
     dfl *Sd = Ed + EVC;                       // [TC_SITES][SC_N]
     dfl *Qd = Sd + TC_SITES * SC_N;           // [MAX_IFO][3]: s2g, c2g, amp
     dfl *Pd = Qd + 3 * MAX_IFO;               // [MAX_PSD][2 + MAX_TERM]
@@ -356,52 +368,61 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
     const int64_t n_items = n_total < A.n_items ? n_total : A.n_items;
     const int64_t it_begin = n_items * blockIdx.x / gridDim.x;
     const int64_t it_end = n_items * (blockIdx.x + 1) / gridDim.x;
-    int64_t e = -1;
-
-    for (int64_t it = it_begin; it < it_end; it++) {
-        // event of the item: a search for the range's first item, then forward
+    // Warp 3 prepares each item: the event (a search for the range's first
+    // item, then forward), the event's constants and power tables when the
+    // event changes, the item's starting values, a cleared column-maximum
+    // buffer and the item descriptor.  It does so for the next item while
+    // warps 0-2 read the current item's Gram out of TMEM (TMEM rows 96-127,
+    // warp 3's lanes, hold no Gram rows), so only the range's first item waits
+    // for it.
+    int64_t e_w = -1;   // warp 3: the event of the last prepared item
+    auto prepare = [&](int64_t itp, unsigned *emx_next) {
         int64_t en;
-        if (e < 0) {
-            en = find_event(A.item_off, A.n_ev, it);
+        if (e_w < 0) {
+            en = find_event(A.item_off, A.n_ev, itp);
         } else {
-            en = e;
-            while (__ldg(A.item_off + en + 1) <= it) en++;
+            en = e_w;
+            while (__ldg(A.item_off + en + 1) <= itp) en++;
         }
-        const bool new_event = en != e;
-        e = en;
-        const int64_t jit = it - __ldg(A.item_off + e);
-        const int64_t nj = __ldg(A.item_off + e + 1) - __ldg(A.item_off + e);
+        const bool new_event = en != e_w;
+        e_w = en;
+        const int64_t off0 = __ldg(A.item_off + en);
+        const int64_t jit = itp - off0, nj = __ldg(A.item_off + en + 1) - off0;
         if (new_event) {
-            const double *Eg = A.evc + e * (int64_t)EVC;
-            for (int q = t; q < EVC; q += TC_T) {
+            const double *Eg = A.evc + en * (int64_t)EVC;
+            for (int q = lane; q < EVC; q += 32) {
                 const double v = Eg[q];
                 cs[q] = v;
                 if (DF) Ed[q] = dfl(v);
             }
             if (DF) {
-                for (int i = t; i < net.n_site * SC_N; i += TC_T)
-                    Sd[i] = dfl(A.sitec[e * net.n_site * (int64_t)SC_N + i]);
+                for (int i = lane; i < net.n_site * SC_N; i += 32)
+                    Sd[i] = dfl(A.sitec[en * net.n_site * (int64_t)SC_N + i]);
             }
         }
-        if (t < 16) emax[t] = 0u;
-        __syncthreads();
+        __syncwarp();
         const int N = (int)cs[EV_NPTS];
-        const int kb = (int)((int64_t)N * jit / nj), ke = (int)((int64_t)N * (jit + 1) / nj);
+        // the event's nj = ceil(N / 128) items take isz points each, isz the
+        // even share rounded up to whole warps (<= 128), the last item the rest:
+        // fewer partly filled warps than an even split ((nj - 1) isz < N holds
+        // because N > 128 (nj - 1))
+        const int isz = (int)(((N + nj - 1) / nj + 31) & ~31);
+        const int kb = (int)jit * isz, ke = min(N, kb + isz);
         const double lnr = cs[EV_LNR];
         // powers of the per-point factors of v, 1/v and the amplitude (steps 1
-        // and 16 points; warp 0, once per event) and their values at the item's
-        // first point (warp 1, every item)
-        if (new_event && t < 6) {
-            const int q = t % 3, big = t / 3;
+        // and 16 points; lanes 0-5, once per event) and their values at the
+        // item's first point (lanes 8-11, every item)
+        if (new_event && lane < 6) {
+            const int q = lane % 3, big = lane / 3;
             const double l = q == 0 ? lnr * (1.0 / 3.0) : (q == 1 ? -lnr * (1.0 / 3.0) : -7.0 / 6.0 * lnr);
             const double fct = exp(big ? 16.0 * l : l);
             if (DF) {
                 // the chain in double-float on the FP32 pipe (~16 x 2^-48)
-                const dfl f(fct);
+                const dfl fc(fct);
                 dfl val(1.0f, 0.0f);
                 for (int i = 0; i < 16; i++) {
                     pwd[(q * 2 + big) * 16 + i] = val;
-                    val = val * f;
+                    val = val * fc;
                 }
             } else {
                 double val = 1.0;
@@ -410,22 +431,41 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
                     val *= fct;
                 }
             }
-        } else if (t >= 32 && t < 36) {
+        } else if (lane >= 8 && lane < 12) {
             const double lnf0 = fma((double)kb, lnr, cs[EV_LNF0]);
             const double lnv0 = (lnf0 + cs[EV_LNPIM]) * (1.0 / 3.0);
-            const int q = t - 32;
-            const double b = q == 0 ? exp(lnv0)
-                           : q == 1 ? exp(-lnv0)
-                           : q == 2 ? cs[EV_A0] * exp(-7.0 / 6.0 * lnf0)
-                                    : lnv0;
-            pw[96 + q] = b;
+            const int q = lane - 8;
+            const double bv = q == 0 ? exp(lnv0)
+                            : q == 1 ? exp(-lnv0)
+                            : q == 2 ? cs[EV_A0] * exp(-7.0 / 6.0 * lnf0)
+                                     : lnv0;
+            pw[96 + q] = bv;
             if (DF) {
                 // amplitude relative to sqrt(scale_ref); ln v step per point
-                pwd[96 + q] = dfl(q == 2 ? b * net.inv_sqrt_scale_ref : b);
+                pwd[96 + q] = dfl(q == 2 ? bv * net.inv_sqrt_scale_ref : bv);
                 if (q == 3) pwd[100] = dfl(lnr * (1.0 / 3.0));
             }
         }
-        __syncthreads();
+        if (lane < 16) emx_next[lane] = 0u;
+        if (lane == 0) {
+            item->e = en;
+            item->n = N;
+            item->kb = kb;
+            item->ke = ke;
+        }
+        __syncwarp();
+    };
+    int cur = 1;   // column-maximum buffer of the current item
+    // (the first pass, it = it_begin - 1, only prepares the range's first item:
+    // one call site keeps the kernel's code small)
+    for (int64_t it = it_begin - 1; it < it_end; it++) {
+      unsigned *emx = emax + 16 * cur;
+      double *out = A.partial + (it < 0 ? 0 : it) * (int64_t)A.nacc;   // the item's row
+      bool bad = false;
+      if (it >= it_begin) {
+        const int64_t e = item->e;
+        const int N = item->n, kb = item->kb, ke = item->ke;
+        const double lnr = cs[EV_LNR];
 
         // per-thread copies of the event's scalar constants
         const T *E;
@@ -530,12 +570,12 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
 #pragma unroll
         for (int c = 0; c < NP; c++) {
             const unsigned m = __reduce_max_sync(0xffffffffu, lmax[c]);
-            if (lane == 0) atomicMax(&emax[c], m);
+            if (lane == 0) atomicMax(&emx[c], m);
         }
         __syncthreads();
         int em[NP];
 #pragma unroll
-        for (int c = 0; c < NP; c++) em[c] = (int)emax[c];
+        for (int c = 0; c < NP; c++) em[c] = (int)emx[c];
 
         // ---- digits of row r into operand buffer r % 2; buffer 1 overlays the
         // staged rows 0 and 1, so it is written only after every thread has read
@@ -582,16 +622,18 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
             par ^= 1u << b;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        double *out = A.partial + it * (int64_t)A.nacc;
-        if (__syncthreads_or(!ok || ke - kb > TC_T)) {
+        bad = __syncthreads_or(!ok || ke - kb > TC_T);
+        if (bad) {
             // a wait that ran out, or an item longer than the kernel's round
             for (int a = t; a < A.nacc; a += TC_T) out[a] = __longlong_as_double(0x7FF8000000000000ll);
             if (t == 0 && A.kerr) atomicExch(A.kerr, 1);
             if (!ok) break;
-            __syncthreads();
-            continue;
         }
-
+      }
+        if (warp == 3) {
+            // the next item's set-up (warp 3 holds no Gram rows)
+            if (it + 1 < it_end) prepare(it + 1, emax + 16 * (cur ^ 1));
+        } else if (it >= it_begin && !bad) {
         // ---- read the digit Gram: thread t holds TMEM lane t = row (i, a),
         // i = t / 8, a = t % 8; columns (j, b) at 8 j + b.  Row i forms the
         // entries (i, j) for j = i .. i + H (mod P), H = (P - 1) / 2: every
@@ -662,7 +704,7 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
                     const double mag = fma((double)(unsigned long long)(M >> 64), 0x1p64,
                                            (double)(unsigned long long)M);
                     const double P = (neg ? -mag : mag) * 0x1p-112;
-                    const double gv = P == 0.0 ? 0.0 : P * pow2_scale((int)emax[i], (int)emax[j]);
+                    const double gv = P == 0.0 ? 0.0 : P * pow2_scale((int)emx[i], (int)emx[j]);
                     const int idx = 1 + lo * NP - lo * (lo - 1) / 2 + (hi - lo);
                     if (idx < A.nacc) out[idx] = gv;
                     // SNR^2 = sum |Q|^2 = the (Phic, Phic) entry: g_Phic = -i Q
@@ -670,8 +712,10 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
                 }
             }
         }
+        }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();   // TMEM, emax and the buffers are free for the next item
+        cur ^= 1;
     }
 
     // ---- teardown.  Normally every commit has been waited on.  After a wait
