@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cmath>
+#include <type_traits>
 
 #include "gw_kernels.cuh"
 #include "gw_dfloat.cuh"
@@ -232,16 +233,35 @@ __device__ __forceinline__ PnTermsT<T> pn_terms(const T *E, T v, T vinv, T lnv)
     if (ROT) {
         const T *T0 = E + EV_T0, *TM = E + EV_TM, *TE = E + EV_TE;
         const T b[8] = {vi5, vi3, vi2, vinv, T(1.0), v, v2, vl};
-        T s0 = T0[7] * b[7], s1 = TM[7] * b[7], s2 = TE[7] * b[7];
+        T s0 = T0[7] * b[7];
 #pragma unroll
-        for (int q = 6; q >= 0; q--) {
-            s0 = fma(T0[q], b[q], s0);
-            s1 = fma(TM[q], b[q], s1);
-            s2 = fma(TE[q], b[q], s2);
-        }
+        for (int q = 6; q >= 0; q--) s0 = fma(T0[q], b[q], s0);
         t.tau = s0 * vi3;
-        t.tMc = s1 * vi3;
-        t.tEt = s2 * vi3;
+        if constexpr (std::is_same<T, dfl>::value) {
+            // double-float pass: the Mc and eta derivatives of tau* in FP32.
+            // They enter only the Earth-rotation parts of the Mc and eta
+            // tangents, Omega_E dtau*/dtheta dQ/dx, about Omega_E / (2 pi f)
+            // (< 1e-5) of those tangents, so an FP32 rounding there is ~1e-12
+            // of the tangent, below the double-float arithmetic's own error
+            // amplified through the Gram
+            float s1 = TM[7].hi * b[7].hi, s2 = TE[7].hi * b[7].hi;
+#pragma unroll
+            for (int q = 6; q >= 0; q--) {
+                s1 = fmaf(TM[q].hi, b[q].hi, s1);
+                s2 = fmaf(TE[q].hi, b[q].hi, s2);
+            }
+            t.tMc = dfl(s1 * vi3.hi, 0.0f);
+            t.tEt = dfl(s2 * vi3.hi, 0.0f);
+        } else {
+            T s1 = TM[7] * b[7], s2 = TE[7] * b[7];
+#pragma unroll
+            for (int q = 6; q >= 0; q--) {
+                s1 = fma(TM[q], b[q], s1);
+                s2 = fma(TE[q], b[q], s2);
+            }
+            t.tMc = s1 * vi3;
+            t.tEt = s2 * vi3;
+        }
         asm volatile("" ::: "memory");
     }
     return t;
