@@ -62,7 +62,13 @@ FP64_FMA_PER_CLK_SM = 2
 # ncu capture of the 2e4-event c3 catalog (4,376,070 points; profiles/
 # k_points_*_fisher_c3.md), scaled by points to a full launch
 DRAM_BYTES_PER_POINT = {"mixed": (23.10528e6 + 11.52e3) / 4376070,
-                        "fp64": (19.284224e6 + 91.136e3) / 4376070}
+                        "fp64": (19.284224e6 + 91.136e3) / 4376070,
+                        "dfloat_tc": (20.601856e6 + 60.928e3) / 4376070}
+# executed warp instructions per grid point of the double-float tensor-core
+# kernel (the same capture, profiles/k_fisher_tc_dfloat_c3.md): the kernel is
+# latency-bound, so its issue rate against the schedulers' peak (4 per SM and
+# clock) is the roofline that explains its time
+ISSUE_WARP_INSTR_PER_POINT = {"dfloat_tc": 1.3201526e9 / 4376070}
 GOLDEN = os.path.join(ROOT, "tests", "golden", "parity_oracle.npz")
 
 
@@ -755,6 +761,14 @@ def run_ours(a):
                               f"the tensor cores)",
                 "executed_flops_per_point": None,
                 "pipe_flops_per_point": algo_fp,
+                "issue": {
+                    "warp_instructions_per_point": ISSUE_WARP_INSTR_PER_POINT["dfloat_tc"],
+                    "achieved": ISSUE_WARP_INSTR_PER_POINT["dfloat_tc"] * n_points /
+                                (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else None,
+                    "peak": sms * 4 * sm_mhz * 1e6 / 1e9, "unit": "G warp instructions/s",
+                    "peak_basis": f"{sms} SMs x 4 schedulers x 1 instruction/clk x {sm_mhz:.0f} MHz",
+                    "source": "instructions per point from one ncu capture of the 2e4-event "
+                              "literal-grid catalog, scaled by this launch's points"},
                 "gram_on_tensor_cores": {
                     "digit_flops_per_point": tfl,
                     "achieved": tfl * n_points / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None,
@@ -771,9 +785,13 @@ def run_ours(a):
             k["unit"] = "TFLOP/s"
             is_mixed = k["kernel"].startswith("k_points_mixed")
             # DRAM bytes per point from ncu captures of the literal-grid workload
-            # (none yet for the tensor-core kernel)
+            # (none for the FP64 tensor-core variant)
+            is_df = k["kernel"].startswith("k_fisher_tc<double-float>")
             is_tc = k["kernel"].startswith("k_fisher_")
-            per_pt = DRAM_BYTES_PER_POINT.get("mixed" if is_mixed else ("fp64_tc" if is_tc else "fp64"))
+            per_pt = DRAM_BYTES_PER_POINT.get("mixed" if is_mixed else (
+                "dfloat_tc" if is_df else ("fp64_tc" if is_tc else "fp64")))
+            if "issue" in k and k["issue"]["achieved"] is not None:
+                k["issue"]["frac"] = k["issue"]["achieved"] / k["issue"]["peak"]
             k["traffic"] = per_pt * k["points"] if (a.grid == "literal" and per_pt) else None
         dom = max(kernels, key=lambda k: k["ms"])
         roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
@@ -784,6 +802,7 @@ def run_ours(a):
                     "pipe_flops_per_point": dom.get("pipe_flops_per_point", algo_fp),
                     **({"gram_on_tensor_cores": dom["gram_on_tensor_cores"]}
                        if "gram_on_tensor_cores" in dom else {}),
+                    **({"issue": dom["issue"]} if "issue" in dom else {}),
                     "peak_basis": dom["peak_basis"] + " (median sampled SM clock)",
                     "kernels": kernels,
                     "measured_fma_per_clk_sm": {"fp64": rate64["fma_per_clk_sm"],

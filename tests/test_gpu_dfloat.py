@@ -64,6 +64,32 @@ def test_dfloat_matches_fp64(name):
     assert gw.gw_kernel_faults() == 0
 
 
+def test_dfloat_item_split_edges():
+    """Grid lengths around the tensor-core pass's work-item shapes: an event's
+    ceil(N/128) items take the even share rounded up to whole warps (32 points),
+    the last item the rest.  Lengths at and next to the warp and item edges,
+    on the rotating triangle (11 parameters) and one L-shaped detector
+    without rotation (9 parameters), against the FP64 pass."""
+    lens = [2, 3, 31, 32, 33, 95, 96, 97, 127, 128, 129, 160, 200, 255, 256, 257,
+            288, 289, 384, 385, 513]
+    for cfg, np_ in (("c3", 11), ("c0", 9)):
+        cat, d, p = oracle_catalog(cfg, len(lens), seed=20220714 + 45)
+        npts = np.array(lens, dtype=np.int32)
+        gcat = gw.Catalog.from_numpy(cat.ev, cat.pset, cat.fmin, cat.fmax, npts)
+        net = gw.Network(*gwcat.network(cfg))
+        F1, s1, st1 = gw.gw_fisher(gcat, net, np_, gw.GW_DFLOAT)
+        F2, s2, st2 = gw.gw_fisher(gcat, net, np_, gw.GW_FP64)
+        assert torch.equal(st1, st2)
+        ok = (st1 == 0).cpu().numpy()
+        assert ok.sum() >= len(lens) - 2          # (N = 2, 3 may be degenerate)
+        F1n, F2n = F1.cpu().numpy()[:, ok], F2.cpu().numpy()[:, ok]
+        r = _rel(torch.as_tensor(F1n), torch.as_tensor(F2n), np_)
+        rs = float(np.max(np.abs(s1.cpu().numpy()[ok] / s2.cpu().numpy()[ok] - 1)))
+        print(f"\n{cfg} split edges: max |dGamma| / sqrt(Gii Gjj) = {r:.2e}, SNR {rs:.2e}")
+        assert r < 1e-10 and rs < 1e-12
+    assert gw.gw_kernel_faults() == 0
+
+
 def test_dfloat_against_oracle():
     cat, d, p = oracle_catalog("c3", 24, seed=20220714 + 43)
     det, psd, rot = gwcat.network("c3")
