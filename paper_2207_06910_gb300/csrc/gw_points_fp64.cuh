@@ -75,6 +75,21 @@ struct PatT {
 };
 using Pat = PatT<double>;
 
+// the pattern functions and their theta- and x-derivatives from the JKS
+// coefficients a, b of one interferometer and P1, P2 = amp (cos 2psi, sin 2psi)
+template <typename T>
+__device__ __forceinline__ PatT<T> patterns_ab(T P1, T P2, T a, T b, T aT, T bT, T aX, T bX)
+{
+    PatT<T> p;
+    p.fp = P1 * a + P2 * b;
+    p.fx = P1 * b - P2 * a;
+    p.fpT = P1 * aT + P2 * bT;
+    p.fxT = P1 * bT - P2 * aT;
+    p.fpX = P1 * aX + P2 * bX;
+    p.fxX = P1 * bX - P2 * aX;
+    return p;
+}
+
 template <typename T>
 __device__ __forceinline__ PatT<T> patterns(T s2g, T c2g, T P1, T P2, const T (&J)[12])
 {

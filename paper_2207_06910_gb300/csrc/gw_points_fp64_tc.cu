@@ -537,7 +537,21 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
                         c2g = net.ifo_c2g[q];
                         amp = net.ifo_amp[q] * (on ? 1.0 : 0.0);
                     }
-                    const PatT<T> pt = patterns(s2g, c2g, amp * E[EV_C2PSI], amp * E[EV_S2PSI], J);
+                    // A triangle's two virtual interferometers (at gamma_T and
+                    // gamma_T + 45 deg, same amplitude and noise) enter the
+                    // patterns through (sin 2g, cos 2g) and (cos 2g, -sin 2g): an
+                    // orthogonal pair, so the sum over the two of the outer
+                    // products of anything linear in the patterns is unchanged
+                    // with (1, 0) and (0, 1) in their place -- the pair's Gram
+                    // is that of the unrotated coefficients, 18 operations less
+                    // per slot and point
+                    const int L1 = q - net.site_ifo0[s];
+                    const PatT<T> pt =
+                        (net.site_nslot[s] == 2 && L1 >= 0 && L1 < 2)
+                            ? patterns_ab(amp * E[EV_C2PSI], amp * E[EV_S2PSI], L1 ? J[1] : J[0],
+                                          L1 ? J[2] : J[3], L1 ? J[5] : J[4], L1 ? J[6] : J[7],
+                                          L1 ? J[9] : J[8], L1 ? J[10] : J[11])
+                            : patterns(s2g, c2g, amp * E[EV_C2PSI], amp * E[EV_S2PSI], J);
                     const T sg = Wp[net.ifo_psd[q]];
                     T gr[NP], gi[NP], qr, qi;
                     tangents<NP, ROT>(pt, sg * E[EV_CP], sg * E[EV_CX], sg * E[EV_DCP],
