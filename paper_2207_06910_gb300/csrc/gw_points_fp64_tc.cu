@@ -7,7 +7,8 @@
 // (Sec. 3.2, Eqs. 3.1-3.3).  Every tangent value is written, per item and
 // column, relative to the column's largest exponent E_i (y' = y 2^(1022 - E_i),
 // |y'| < 1) as eight digits: digit a is a multiple of q_a = 2^(-7(a+1)) of
-// magnitude at most 128 q_a, exact in bf16, the sum of the digits y' to 2^-57.
+// magnitude at most 128 q_a, exact in bf16, the sum of the digits y' to 2^-57
+// (FP64 values; double-float values use seven digits, y' to 2^-50).
 // The tensor core forms all digit products with FP32 accumulation; a product
 // of digits a and b is a multiple of q_a q_b below 2^14 q_a q_b and an item has
 // at most 1024 rows (256 points x 2 interferometers x real/imaginary), so
@@ -216,7 +217,10 @@ __device__ __forceinline__ uint4 digits8(double y, int ec)
 // then digit by digit, in both lanes of packed FP32x2 operations, rounded to
 // the multiple of q_a (adding and subtracting 1.5 2^(23 - 7(a+1)): round to
 // nearest) and the remainders kept exactly; digit a is the sum of the two
-// lanes' parts (for a >= 1 each is at most 64 q_a; lo has no part in digit 0)
+// lanes' parts (for a >= 1 each is at most 64 q_a; lo has no part in digit 0).
+// Seven digits (49 bits; digit 7 is zero): the value is rounded to 2^-49 of
+// the column's scale, below the double-float tangents' own error (~2^-48 of
+// their size), so the eighth digit would only carry rounding noise.
 __device__ __forceinline__ uint4 digits8(dfl y, int ec)
 {
     // a column of zeros, or a zero value (rows of idle points, slots switched off)
@@ -225,8 +229,9 @@ __device__ __forceinline__ uint4 digits8(dfl y, int ec)
     const float sc = __uint_as_float((unsigned)(sf > 0 ? sf : 1) << 23);
     float2 r = __fmul2_rn(make_float2(y.hi, y.lo), make_float2(sc, sc));
     float d[8];
+    d[7] = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 8; a++) {
+    for (int a = 0; a < 7; a++) {
         const float M = __uint_as_float(((unsigned)(143 - 7 * a) << 23) | 0x400000u);
         const float2 t = __fadd2_rn(r, make_float2(M, M));
         const float2 q = __fadd2_rn(t, make_float2(-M, -M));
