@@ -134,6 +134,74 @@ __device__ __forceinline__ dfl df_ipow(dfl x, int p)
     return r;
 }
 
+// Two double-float numbers computed together with the packed FP32x2
+// instructions (FADD2, FMUL2, FFMA2): lane x holds one number, lane y the
+// other.  Each operation is the double-float operation above applied to both
+// lanes (the packed instructions round each lane as the scalar ones do), in
+// half the instructions.  Used for quantities that come in pairs: the real and
+// imaginary parts of a tangent, the pattern functions F+ and Fx, sine and
+// cosine.
+struct dfl2 {
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ dfl2 d2_make(dfl x, dfl y)
+{
+    return dfl2{make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)};
+}
+__device__ __forceinline__ dfl2 d2_bcast(dfl s)
+{
+    return dfl2{make_float2(s.hi, s.hi), make_float2(s.lo, s.lo)};
+}
+__device__ __forceinline__ dfl d2_x(const dfl2 &a) { return dfl(a.hi.x, a.lo.x); }
+__device__ __forceinline__ dfl d2_y(const dfl2 &a) { return dfl(a.hi.y, a.lo.y); }
+
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// (x, y) -> (-y, x): the pair times i, read as (Re, Im)
+__device__ __forceinline__ dfl2 d2_mul_i(const dfl2 &a)
+{
+    return dfl2{make_float2(-a.hi.y, a.hi.x), make_float2(-a.lo.y, a.lo.x)};
+}
+
+__device__ __forceinline__ dfl2 d2_fast_two_sum(float2 a, float2 b)   // |a| >= |b| per lane
+{
+    const float2 s = __fadd2_rn(a, b);
+    return dfl2{s, __fadd2_rn(b, f2neg(__fadd2_rn(s, f2neg(a))))};
+}
+
+__device__ __forceinline__ dfl2 operator+(const dfl2 &a, const dfl2 &b)
+{
+    // two-sum of the high parts, low parts added, renormalised
+    const float2 s = __fadd2_rn(a.hi, b.hi);
+    const float2 bb = __fadd2_rn(s, f2neg(a.hi));
+    const float2 e = __fadd2_rn(__fadd2_rn(a.hi, f2neg(__fadd2_rn(s, f2neg(bb)))),
+                                __fadd2_rn(b.hi, f2neg(bb)));
+    return d2_fast_two_sum(s, __fadd2_rn(e, __fadd2_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ dfl2 operator-(const dfl2 &a)
+{
+    return dfl2{f2neg(a.hi), f2neg(a.lo)};
+}
+__device__ __forceinline__ dfl2 operator-(const dfl2 &a, const dfl2 &b) { return a + (-b); }
+
+__device__ __forceinline__ dfl2 operator*(const dfl2 &a, const dfl2 &b)
+{
+    const float2 p = __fmul2_rn(a.hi, b.hi);
+    float2 e = __ffma2_rn(a.hi, b.hi, f2neg(p));
+    e = __ffma2_rn(a.hi, b.lo, e);
+    e = __ffma2_rn(a.lo, b.hi, e);
+    return d2_fast_two_sum(p, e);
+}
+
+// a * s + c with a double-float scalar s in both lanes
+__device__ __forceinline__ dfl2 d2_fma(const dfl2 &a, dfl s, const dfl2 &c)
+{
+    return a * d2_bcast(s) + c;
+}
+
+
 // Overloads with the names the templated formulas call.
 __device__ __forceinline__ dfl sqrt(dfl a) { return df_sqrt(a); }
 
@@ -180,16 +248,13 @@ __device__ __forceinline__ void sincos(dfl x, dfl *sx, dfl *cx)
     r = r + dfl(-k * dfs::P2, 0.0f);
     r = r + dfl(-k * dfs::P3, 0.0f);
     const dfl r2 = r * r;
-    // both series in one rolled loop (two independent chains per iteration;
-    // rolled to keep the callers' code small)
-    dfl s = taylor_coef(15);
-    dfl c = taylor_coef(16) * r2 + taylor_coef(14);
+    // both series in one rolled loop, as one packed pair (sine in lane x,
+    // cosine in lane y; rolled to keep the callers' code small)
+    const dfl2 R2 = d2_bcast(r2);
+    dfl2 sc = d2_make(taylor_coef(15), taylor_coef(16) * r2 + taylor_coef(14));
 #pragma unroll 1
-    for (int n = 6; n >= 0; n--) {
-        s = s * r2 + taylor_coef(2 * n + 1);
-        c = c * r2 + taylor_coef(2 * n);
-    }
-    s = s * r;
+    for (int n = 6; n >= 0; n--) sc = sc * R2 + d2_make(taylor_coef(2 * n + 1), taylor_coef(2 * n));
+    const dfl s = d2_x(sc) * r, c = d2_y(sc);
     const int q = ((int)k) & 3;
     const dfl sn = (q == 0) ? s : (q == 1) ? c : (q == 2) ? -s : -c;
     const dfl cs = (q == 0) ? c : (q == 1) ? -s : (q == 2) ? -c : s;

@@ -212,36 +212,64 @@ __device__ __forceinline__ PnTermsT<T> pn_terms(const T *E, T v, T vinv, T lnv)
     t.vi3 = vi3;
     t.f = v2 * v * E[EV_INV_PIM];
     const T *PM = E + EV_PM, *PE = E + EV_PE;
-    T dMc = PM[8] * v7;
-    dMc = fma(PM[7], v5, dMc);
-    dMc = fma(PM[10], vl, dMc);
-    dMc = fma(PM[6], v2, dMc);
-    dMc = fma(PM[5], v, dMc);
-    dMc = PM[4] + dMc;
-    dMc = fma(PM[3], vinv, dMc);
-    dMc = fma(PM[2], vi2, dMc);
-    dMc = fma(PM[1], vi3, dMc);
-    dMc = fma(PM[0], vi5, dMc);
-    asm volatile("" ::: "memory");   // keep coefficient loads local (register pressure)
-    T dEt = PE[8] * v7;
-    dEt = fma(PE[7], v5, dEt);
-    dEt = fma(PE[10], vl, dEt);
-    dEt = fma(PE[9], lnv, dEt);
-    dEt = fma(PE[6], v2, dEt);
-    dEt = fma(PE[5], v, dEt);
-    dEt = PE[4] + dEt;
-    dEt = fma(PE[3], vinv, dEt);
-    dEt = fma(PE[2], vi2, dEt);
-    dEt = fma(PE[1], vi3, dEt);
-    dEt = fma(PE[0], vi5, dEt);
-    asm volatile("" ::: "memory");
-    t.dMc = dMc;
-    t.dEt = dEt;
-    t.d9 = t.d10 = T(0.0);
-    if (NP == 11) {
-        const T *P9 = E + EV_P9, *P10 = E + EV_P10;
-        t.d9 = fma(P9[0], vi2, fma(P9[1], vinv, fma(P9[2], v5, P9[3] * v7)));
-        t.d10 = fma(P10[0], vi2, fma(P10[1], vinv, fma(P10[2], v5, P10[3] * v7)));
+    if constexpr (std::is_same<T, dfl>::value) {
+        // d Psi/d Mc and d Psi/d eta together on the packed FP32x2 instructions
+        // (the Mc polynomial's ln v coefficient is zero: adding its term is exact)
+        auto pr = [&](int q) { return d2_make(PM[q], PE[q]); };
+        dfl2 d = pr(8) * d2_bcast(v7);
+        d = pr(7) * d2_bcast(v5) + d;
+        d = pr(10) * d2_bcast(vl) + d;
+        d = pr(9) * d2_bcast(lnv) + d;
+        d = pr(6) * d2_bcast(v2) + d;
+        d = pr(5) * d2_bcast(v) + d;
+        d = pr(4) + d;
+        d = pr(3) * d2_bcast(vinv) + d;
+        d = pr(2) * d2_bcast(vi2) + d;
+        d = pr(1) * d2_bcast(vi3) + d;
+        d = pr(0) * d2_bcast(vi5) + d;
+        t.dMc = d2_x(d);
+        t.dEt = d2_y(d);
+        t.d9 = t.d10 = T(0.0);
+        if (NP == 11) {
+            const T *P9 = E + EV_P9, *P10 = E + EV_P10;
+            auto p9 = [&](int q) { return d2_make(P9[q], P10[q]); };
+            const dfl2 e = p9(0) * d2_bcast(vi2) +
+                           (p9(1) * d2_bcast(vinv) + (p9(2) * d2_bcast(v5) + p9(3) * d2_bcast(v7)));
+            t.d9 = d2_x(e);
+            t.d10 = d2_y(e);
+        }
+    } else {
+        T dMc = PM[8] * v7;
+        dMc = fma(PM[7], v5, dMc);
+        dMc = fma(PM[10], vl, dMc);
+        dMc = fma(PM[6], v2, dMc);
+        dMc = fma(PM[5], v, dMc);
+        dMc = PM[4] + dMc;
+        dMc = fma(PM[3], vinv, dMc);
+        dMc = fma(PM[2], vi2, dMc);
+        dMc = fma(PM[1], vi3, dMc);
+        dMc = fma(PM[0], vi5, dMc);
+        asm volatile("" ::: "memory");   // keep coefficient loads local (register pressure)
+        T dEt = PE[8] * v7;
+        dEt = fma(PE[7], v5, dEt);
+        dEt = fma(PE[10], vl, dEt);
+        dEt = fma(PE[9], lnv, dEt);
+        dEt = fma(PE[6], v2, dEt);
+        dEt = fma(PE[5], v, dEt);
+        dEt = PE[4] + dEt;
+        dEt = fma(PE[3], vinv, dEt);
+        dEt = fma(PE[2], vi2, dEt);
+        dEt = fma(PE[1], vi3, dEt);
+        dEt = fma(PE[0], vi5, dEt);
+        asm volatile("" ::: "memory");
+        t.dMc = dMc;
+        t.dEt = dEt;
+        t.d9 = t.d10 = T(0.0);
+        if (NP == 11) {
+            const T *P9 = E + EV_P9, *P10 = E + EV_P10;
+            t.d9 = fma(P9[0], vi2, fma(P9[1], vinv, fma(P9[2], v5, P9[3] * v7)));
+            t.d10 = fma(P10[0], vi2, fma(P10[1], vinv, fma(P10[2], v5, P10[3] * v7)));
+        }
     }
     // tau*(f) and its derivatives (rotation only)
     t.tau = t.tMc = t.tEt = T(0.0);
@@ -323,18 +351,41 @@ __device__ __forceinline__ void site_terms(const T *S, const PnTermsT<T> &pn, T 
     T sx, cxx;
     sincos(x, &sx, &cxx);
     const T c2x = fma(T(2.0) * cxx, cxx, T(-1.0)), s2x = T(2.0) * sx * cxx;
-    J[0] = fma(S[SC_A1], c2x, fma(S[SC_A2], cxx, S[SC_A3]));
-    J[1] = fma(S[SC_A4], s2x, S[SC_A5] * sx);
-    J[2] = fma(S[SC_B1], c2x, S[SC_B2] * cxx);
-    J[3] = fma(S[SC_B3], s2x, S[SC_B4] * sx);
-    J[4] = fma(S[SC_A1T], c2x, fma(S[SC_A2T], cxx, S[SC_A3T]));
-    J[5] = fma(S[SC_A4T], s2x, S[SC_A5T] * sx);
-    J[6] = fma(S[SC_B1T], c2x, S[SC_B2T] * cxx);
-    J[7] = fma(S[SC_B3T], s2x, S[SC_B4T] * sx);
-    J[8] = fma(-2.0 * S[SC_A1], s2x, -S[SC_A2] * sx);
-    J[9] = fma(2.0 * S[SC_A4], c2x, S[SC_A5] * cxx);
-    J[10] = fma(-2.0 * S[SC_B1], s2x, -S[SC_B2] * sx);
-    J[11] = fma(2.0 * S[SC_B3], c2x, S[SC_B4] * cxx);
+    if constexpr (std::is_same<T, dfl>::value) {
+        // the same operations, two coefficients at a time on the packed FP32x2
+        // instructions (the pairs share their structure a u + b w [+ c])
+        auto two = [](dfl a) { return dfl(2.0f * a.hi, 2.0f * a.lo); };   // exact
+        const dfl2 sc2 = d2_make(s2x, c2x);
+        const dfl2 cc = d2_bcast(c2x), ss = d2_bcast(s2x), cx = d2_bcast(cxx), sq = d2_bcast(sx);
+        const dfl2 xc = d2_make(sx, cxx);
+        dfl2 p;
+        p = d2_make(S[SC_A1], S[SC_A1T]) * cc +
+            (d2_make(S[SC_A2], S[SC_A2T]) * cx + d2_make(S[SC_A3], S[SC_A3T]));
+        J[0] = d2_x(p), J[4] = d2_y(p);
+        p = d2_make(S[SC_A4], S[SC_B1]) * sc2 + d2_make(S[SC_A5], S[SC_B2]) * xc;
+        J[1] = d2_x(p), J[2] = d2_y(p);
+        p = d2_make(S[SC_B3], S[SC_B1T]) * sc2 + d2_make(S[SC_B4], S[SC_B2T]) * xc;
+        J[3] = d2_x(p), J[6] = d2_y(p);
+        p = d2_make(S[SC_A4T], S[SC_B3T]) * ss + d2_make(S[SC_A5T], S[SC_B4T]) * sq;
+        J[5] = d2_x(p), J[7] = d2_y(p);
+        p = d2_make(-two(S[SC_A1]), two(S[SC_A4])) * sc2 + d2_make(-S[SC_A2], S[SC_A5]) * xc;
+        J[8] = d2_x(p), J[9] = d2_y(p);
+        p = d2_make(-two(S[SC_B1]), two(S[SC_B3])) * sc2 + d2_make(-S[SC_B2], S[SC_B4]) * xc;
+        J[10] = d2_x(p), J[11] = d2_y(p);
+    } else {
+        J[0] = fma(S[SC_A1], c2x, fma(S[SC_A2], cxx, S[SC_A3]));
+        J[1] = fma(S[SC_A4], s2x, S[SC_A5] * sx);
+        J[2] = fma(S[SC_B1], c2x, S[SC_B2] * cxx);
+        J[3] = fma(S[SC_B3], s2x, S[SC_B4] * sx);
+        J[4] = fma(S[SC_A1T], c2x, fma(S[SC_A2T], cxx, S[SC_A3T]));
+        J[5] = fma(S[SC_A4T], s2x, S[SC_A5T] * sx);
+        J[6] = fma(S[SC_B1T], c2x, S[SC_B2T] * cxx);
+        J[7] = fma(S[SC_B3T], s2x, S[SC_B4T] * sx);
+        J[8] = fma(-2.0 * S[SC_A1], s2x, -S[SC_A2] * sx);
+        J[9] = fma(2.0 * S[SC_A4], c2x, S[SC_A5] * cxx);
+        J[10] = fma(-2.0 * S[SC_B1], s2x, -S[SC_B2] * sx);
+        J[11] = fma(2.0 * S[SC_B3], c2x, S[SC_B4] * cxx);
+    }
     const T dxPD = -twopif * S[SC_D1] * sx;
     ph.th = twopif * fma(S[SC_D1T], cxx, S[SC_D2T]);
     ph.ph = dxPD;

@@ -295,6 +295,49 @@ struct __align__(16) TcItem {
     int pad[3];
 };
 
+// The tangents of one interferometer as (Re, Im) pairs of double-float
+// numbers, the operations of tangents() (gw_points_fp64.cuh) on both parts at
+// once: with Q = (qr, qi) and iQ = (-qi, qr),
+//   g_Mc = aMc Q + dPhi/dMc iQ [+ Omega dtau*/dMc dQ/dx],  g_eta, g_theta,
+//   g_phi, g_tc, g_9, g_10 likewise, g_dL = -Q/d_L, g_iota = dQ/diota,
+//   g_psi = 2 (Acp Fx, -Acx F+), g_Phic = -iQ.
+// F = (F+, Fx), FT, FX their theta- and x-derivatives; A = (Acp, Acx),
+// Ad = (Adcp, Adcx) the amplitudes times the noise weight.
+template <int NP, bool ROT>
+__device__ __forceinline__ void tangents2(const dfl2 &F, const dfl2 &FT, const dfl2 &FX,
+                                          const dfl2 &A, const dfl2 &Ad, dfl aMc, dfl invdL,
+                                          const PhaseT<dfl> &ph, dfl2 (&g)[NP])
+{
+    const dfl2 Q = A * F, X = A * FX, Tt = A * FT;
+    const dfl2 iQ = d2_mul_i(Q);
+    g[0] = Q * d2_bcast(aMc) + iQ * d2_bcast(ph.Mc);
+    g[1] = iQ * d2_bcast(ph.eta);
+    if (ROT) {
+        g[0] = d2_fma(X, ph.tMc, g[0]);
+        g[1] = d2_fma(X, ph.teta, g[1]);
+    }
+    g[2] = Q * d2_bcast(-invdL);
+    g[3] = Tt + iQ * d2_bcast(ph.th);
+    g[4] = X + iQ * d2_bcast(ph.ph);
+    g[5] = Ad * F;
+    // psi: dF+/dpsi = 2 Fx, dFx/dpsi = -2 F+
+    g[6] = dfl2{make_float2(2.0f * A.hi.x, -2.0f * A.hi.y), make_float2(2.0f * A.lo.x, -2.0f * A.lo.y)} *
+           dfl2{make_float2(F.hi.y, F.hi.x), make_float2(F.lo.y, F.lo.x)};
+    g[7] = iQ * d2_bcast(ph.tc);
+    if (ROT) g[7] = d2_fma(X, dfl(-OMEGA_E), g[7]);
+    g[8] = -iQ;
+    if (NP == 11) {
+        g[NP - 2] = iQ * d2_bcast(ph.p9);
+        g[NP - 1] = iQ * d2_bcast(ph.p10);
+    }
+}
+
+// (F+, Fx) = P1 (a, b) + P2 (b, -a): one pattern pair from the JKS coefficients
+__device__ __forceinline__ dfl2 pattern_pair(dfl a, dfl b, const dfl2 &P1, const dfl2 &P2)
+{
+    return d2_make(a, b) * P1 + d2_make(b, -a) * P2;
+}
+
 template <int NP, bool ROT, bool TAB, typename T>
 __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
 {
@@ -551,24 +594,54 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
                     // is that of the unrotated coefficients, 18 operations less
                     // per slot and point
                     const int L1 = q - net.site_ifo0[s];
-                    const PatT<T> pt =
-                        (net.site_nslot[s] == 2 && L1 >= 0 && L1 < 2)
-                            ? patterns_ab(amp * E[EV_C2PSI], amp * E[EV_S2PSI], L1 ? J[1] : J[0],
-                                          L1 ? J[2] : J[3], L1 ? J[5] : J[4], L1 ? J[6] : J[7],
-                                          L1 ? J[9] : J[8], L1 ? J[10] : J[11])
-                            : patterns(s2g, c2g, amp * E[EV_C2PSI], amp * E[EV_S2PSI], J);
+                    const bool unit = net.site_nslot[s] == 2 && L1 >= 0 && L1 < 2;
                     const T sg = Wp[net.ifo_psd[q]];
-                    T gr[NP], gi[NP], qr, qi;
-                    tangents<NP, ROT>(pt, sg * E[EV_CP], sg * E[EV_CX], sg * E[EV_DCP],
-                                      sg * E[EV_DCX], E[EV_AMC], E[EV_INVDL], ph, gr, gi, qr, qi);
                     T *row = stage + (2 * L) * NP * TC_T + t;
+                    if constexpr (DF) {
+                        // (Re, Im) pairs on the packed FP32x2 instructions
+                        const dfl2 P1 = d2_bcast(amp * E[EV_C2PSI]), P2 = d2_bcast(amp * E[EV_S2PSI]);
+                        dfl2 F, FT, FX;
+                        if (unit) {
+                            F = pattern_pair(L1 ? J[1] : J[0], L1 ? J[2] : J[3], P1, P2);
+                            FT = pattern_pair(L1 ? J[5] : J[4], L1 ? J[6] : J[7], P1, P2);
+                            FX = pattern_pair(L1 ? J[9] : J[8], L1 ? J[10] : J[11], P1, P2);
+                        } else {
+                            const PatT<T> pt = patterns(s2g, c2g, amp * E[EV_C2PSI], amp * E[EV_S2PSI], J);
+                            F = d2_make(pt.fp, pt.fx);
+                            FT = d2_make(pt.fpT, pt.fxT);
+                            FX = d2_make(pt.fpX, pt.fxX);
+                        }
+                        const dfl2 sg2 = d2_bcast(sg);
+                        dfl2 g[NP];
+                        tangents2<NP, ROT>(F, FT, FX, sg2 * d2_make(E[EV_CP], E[EV_CX]),
+                                           sg2 * d2_make(E[EV_DCP], E[EV_DCX]), E[EV_AMC],
+                                           E[EV_INVDL], ph, g);
 #pragma unroll
-                    for (int c = 0; c < NP; c++) {
-                        row[c * TC_T] = gr[c];
-                        row[(NP + c) * TC_T] = gi[c];
-                        const unsigned er = expo(gr[c]), ei = expo(gi[c]);
-                        const unsigned em2 = er > ei ? er : ei;
-                        lmax[c] = em2 > lmax[c] ? em2 : lmax[c];
+                        for (int c = 0; c < NP; c++) {
+                            const dfl gr = d2_x(g[c]), gi = d2_y(g[c]);
+                            row[c * TC_T] = gr;
+                            row[(NP + c) * TC_T] = gi;
+                            const unsigned er = expo(gr), ei = expo(gi);
+                            const unsigned em2 = er > ei ? er : ei;
+                            lmax[c] = em2 > lmax[c] ? em2 : lmax[c];
+                        }
+                    } else {
+                        const PatT<T> pt =
+                            unit ? patterns_ab(amp * E[EV_C2PSI], amp * E[EV_S2PSI], L1 ? J[1] : J[0],
+                                               L1 ? J[2] : J[3], L1 ? J[5] : J[4], L1 ? J[6] : J[7],
+                                               L1 ? J[9] : J[8], L1 ? J[10] : J[11])
+                                 : patterns(s2g, c2g, amp * E[EV_C2PSI], amp * E[EV_S2PSI], J);
+                        T gr[NP], gi[NP], qr, qi;
+                        tangents<NP, ROT>(pt, sg * E[EV_CP], sg * E[EV_CX], sg * E[EV_DCP],
+                                          sg * E[EV_DCX], E[EV_AMC], E[EV_INVDL], ph, gr, gi, qr, qi);
+#pragma unroll
+                        for (int c = 0; c < NP; c++) {
+                            row[c * TC_T] = gr[c];
+                            row[(NP + c) * TC_T] = gi[c];
+                            const unsigned er = expo(gr[c]), ei = expo(gi[c]);
+                            const unsigned em2 = er > ei ? er : ei;
+                            lmax[c] = em2 > lmax[c] ? em2 : lmax[c];
+                        }
                     }
                     written |= 1u << L;
                 }
