@@ -248,6 +248,47 @@ __device__ __forceinline__ uint4 digits8(dfl y, int ec)
     return o;
 }
 
+// Two double-float values at once (the digits of digits8(dfl) above, the same
+// roundings): the high parts of both run as one packed pair, the low parts as
+// another.  A low part is below 2^-24 of the column's scale (|lo| <= ulp(hi)/2
+// and |hi| < 2^(ec - 1022)), so its rounded parts in digits 0-2 (multiples of
+// 2^-7, 2^-14, 2^-21) are zero and those steps are left out for it.
+__device__ __forceinline__ void digits8x2(dfl y1, int ec1, dfl y2, int ec2, uint4 &o1, uint4 &o2)
+{
+    if (y1.hi == 0.0f && y2.hi == 0.0f) {
+        o1 = o2 = make_uint4(0u, 0u, 0u, 0u);
+        return;
+    }
+    auto scale = [](int ec) {                               // 2^(1022 - ec); 0 for a zero column
+        const int sf = 1149 - ec;
+        return ec == 0 ? 0.0f : __uint_as_float((unsigned)(sf > 0 ? sf : 1) << 23);
+    };
+    const float2 sc = make_float2(scale(ec1), scale(ec2));
+    float2 rh = __fmul2_rn(make_float2(y1.hi, y2.hi), sc);
+    float2 rl = __fmul2_rn(make_float2(y1.lo, y2.lo), sc);
+    float2 d[7];
+#pragma unroll
+    for (int a = 0; a < 7; a++) {
+        const float M = __uint_as_float(((unsigned)(143 - 7 * a) << 23) | 0x400000u);
+        const float2 th = __fadd2_rn(rh, make_float2(M, M));
+        const float2 qh = __fadd2_rn(th, make_float2(-M, -M));
+        rh = __fadd2_rn(rh, make_float2(-qh.x, -qh.y));
+        if (a >= 3) {
+            const float2 tl = __fadd2_rn(rl, make_float2(M, M));
+            const float2 ql = __fadd2_rn(tl, make_float2(-M, -M));
+            rl = __fadd2_rn(rl, make_float2(-ql.x, -ql.y));
+            d[a] = __fadd2_rn(qh, ql);
+        } else {
+            d[a] = qh;
+        }
+    }
+    // a digit has at most 8 significant bits: its bf16 form is the upper half
+    // of its FP32 bits
+    auto b2 = [](float lo, float hi) { return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632); };
+    o1 = make_uint4(b2(d[0].x, d[1].x), b2(d[2].x, d[3].x), b2(d[4].x, d[5].x), b2(d[6].x, 0.0f));
+    o2 = make_uint4(b2(d[0].y, d[1].y), b2(d[2].y, d[3].y), b2(d[4].y, d[5].y), b2(d[6].y, 0.0f));
+}
+
 // 2^x in FP64 (x an integer), NaN when a column held a non-finite value
 __device__ __forceinline__ double pow2_scale(int ei, int ej)
 {
@@ -679,8 +720,16 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
 #pragma unroll 1
         for (int r = 0; r < 4; r++) {
             uint4 dg[NP];
+            if constexpr (DF) {
 #pragma unroll
-            for (int c = 0; c < NP; c++) dg[c] = digits8(stage[(r * NP + c) * TC_T + t], em[c]);
+                for (int c = 0; c + 1 < NP; c += 2)
+                    digits8x2(stage[(r * NP + c) * TC_T + t], em[c], stage[(r * NP + c + 1) * TC_T + t],
+                              em[c + 1], dg[c], dg[c + 1]);
+                if (NP & 1) dg[NP - 1] = digits8(stage[(r * NP + NP - 1) * TC_T + t], em[NP - 1]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < NP; c++) dg[c] = digits8(stage[(r * NP + c) * TC_T + t], em[c]);
+            }
             const int b = r & 1;
             if (r == 1) __syncthreads();   // staged rows 0 and 1 read by every thread
             if (r >= 2) {
