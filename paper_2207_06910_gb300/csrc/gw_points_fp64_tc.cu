@@ -776,31 +776,35 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
             if (it + 1 < it_end) prepare(it + 1, emax + 16 * (cur ^ 1));
         } else if (it >= it_begin && !bad) {
         // ---- read the digit Gram: thread t holds TMEM lane t = row (i, a),
-        // i = t / 8, a = t % 8; columns (j, b) at 8 j + b.  Row i forms the
-        // entries (i, j) for j = i .. i + H (mod P), H = (P - 1) / 2: every
-        // unordered pair once (P is odd), so warp w (rows i = 4w .. 4w + 3)
-        // reads the column groups 4w .. 4w + 3 + H, all loads issued before one
-        // wait.  The products D[(i,a),(j,b)] are exact multiples of q_a q_b
+        // i = t / 8, a = t % 8; columns (j, b) at 8 j + b.  The rows sit in
+        // warps 0-2 (rows 4w .. 4w + 3); warp w reads its own four column
+        // groups (entries (i, j), i <= j, of its own rows) and the next warp's
+        // (w + 1 mod 3: every (i, j) of its rows with them), so each unordered
+        // pair is formed once and a warp reads at most 8 groups, three per
+        // batch of TMEM loads.  The products D[(i,a),(j,b)] are exact multiples of q_a q_b
         // below 2^24 q_a q_b: with n_ab = D / (q_a q_b), the entry is
         //     sum_ab D = 2^-112 I,   I = sum_a 2^(7 (7 - a)) sum_b 2^(7 (7 - b)) n_ab,
         // an integer below 2^123 in magnitude, formed exactly in 128-bit
         // integer arithmetic (per lane over b, across the row's eight lanes with
         // shuffles) and rounded once to FP64.
         const int i = t >> 3, a = t & 7;
-        constexpr int H = (NP - 1) / 2;
-        constexpr int NGRP = 4 + H;   // column groups read per warp (at most)
+        static_assert(NP <= 12, "Gram rows in warps 0-2");
+        constexpr int NGRP = 8;       // column groups read per warp (at most)
+        const int nxt = warp == 2 ? 0 : warp + 1;
+        const int own_n = NP - 4 * warp < 4 ? NP - 4 * warp : 4;
+        const int nxt_n = NP - 4 * nxt < 4 ? NP - 4 * nxt : 4;
         // (a warp whose rows are all padding, 4w >= P, reads nothing)
-        const int jend = 4 * warp >= NP ? 0 : (4 * warp + 3 < NP - 1 ? 4 * warp + 3 : NP - 1) + H + 1;
+        const int ngrp = 4 * warp >= NP ? 0 : own_n + nxt_n;
+        auto col_of = [&](int g) { return g < own_n ? 4 * warp + g : 4 * nxt + (g - own_n); };
         constexpr int GB = 3;          // column groups per batch of TMEM loads
 #pragma unroll 1
         for (int g0 = 0; g0 < NGRP; g0 += GB) {
-            if (4 * warp + g0 >= jend) break;
+            if (g0 >= ngrp) break;
             uint32_t dd[GB][8];
 #pragma unroll
             for (int g = 0; g < GB; g++) {
-                const int jr = 4 * warp + g0 + g;
-                if (jr < jend) {
-                    const int j = jr < NP ? jr : jr - NP;
+                if (g0 + g < ngrp) {
+                    const int j = col_of(g0 + g);
                     const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 8);
                     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                                  : "=r"(dd[g][0]), "=r"(dd[g][1]), "=r"(dd[g][2]), "=r"(dd[g][3]),
@@ -811,9 +815,8 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int g = 0; g < GB; g++) {
-                const int jr = 4 * warp + g0 + g;
-                if (jr >= jend) break;
-                const int j = jr < NP ? jr : jr - NP;
+                if (g0 + g >= ngrp) break;
+                const int j = col_of(g0 + g);
                 // W = sum_b 2^(7 (7 - b)) n_ab (|W| < 2^74), as hs 2^28 + ls
                 long long hs = 0, ls = 0;
 #pragma unroll
@@ -835,8 +838,8 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS) k_fisher_tc(PointArgs A)
                         __shfl_xor_sync(0xffffffffu, (unsigned long long)(X >> 64), m);
                     X += ((u128)yh << 64) | (u128)yl;
                 }
-                const int dj = jr - i;   // j = i + dj (mod P)
-                if (a == 0 && i < NP && dj >= 0 && dj <= H) {
+                // own groups: the pairs i <= j; the next warp's: every pair
+                if (a == 0 && i < NP && (g0 + g >= own_n || i <= j)) {
                     const int lo = i < j ? i : j, hi = i < j ? j : i;
                     // |I| rounded to FP64 (high word, exact below 2^53, times 2^64
                     // plus the low word), the sign, then the scale 2^-112 (exact)
