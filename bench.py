@@ -63,12 +63,12 @@ FP64_FMA_PER_CLK_SM = 2
 # k_points_*_fisher_c3.md), scaled by points to a full launch
 DRAM_BYTES_PER_POINT = {"mixed": (23.10528e6 + 11.52e3) / 4376070,
                         "fp64": (19.284224e6 + 91.136e3) / 4376070,
-                        "dfloat_tc": (20.601856e6 + 60.928e3) / 4376070}
+                        "dfloat_tc": (20.592128e6 + 70.656e3) / 4376070}
 # executed warp instructions per grid point of the double-float tensor-core
 # kernel (the same capture, profiles/k_fisher_tc_dfloat_c3.md): the kernel is
 # latency-bound, so its issue rate against the schedulers' peak (4 per SM and
 # clock) is the roofline that explains its time
-ISSUE_WARP_INSTR_PER_POINT = {"dfloat_tc": 1.3201526e9 / 4376070}
+ISSUE_WARP_INSTR_PER_POINT = {"dfloat_tc": 1.028082637e9 / 4376070}
 GOLDEN = os.path.join(ROOT, "tests", "golden", "parity_oracle.npz")
 
 
