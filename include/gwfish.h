@@ -50,9 +50,10 @@ typedef enum {
                       per grid point (one triangle, or up to two L-shaped
                       detectors): every per-point quantity in double-float
                       arithmetic (pairs of FP32, ~2^-48) on the FP32 pipe, the
-                      Gram matrix of the tangents exact on the tensor cores
-                      (see gw_set_fp64_gram), combined in FP64; results of the
-                      FP64 accuracy class.  Every other pass and wider networks
+                      Gram matrix of the tangents (rounded to 49 bits relative
+                      to their column's largest value, seven digits) exact on
+                      the tensor cores (see gw_set_fp64_gram), rounded once to
+                      FP64; results of the FP64 accuracy class.  Every other pass and wider networks
                       run as GW_FP64.  Not accepted by gw_set_tile,
                       gw_autotune or gw_fisher_noalloc. */
 } gw_precision;
@@ -212,8 +213,9 @@ gw_status gw_autotune(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net,
  * cores: every tangent is rounded to a 56-bit fixed-point number relative to
  * the largest exponent of its column in the item, split into eight 7-bit
  * digits, and the digit products are summed exactly (integers below 2^24 in
- * the FP32 accumulator); the 64 digit-pair sums are combined in FP64.  The
- * result is the FP64 Fisher matrix up to FP64 rounding of that combination.
+ * the FP32 accumulator, then the 64 digit-pair sums as 128-bit integers) and
+ * rounded once to FP64.  The result is the FP64 Fisher matrix up to that
+ * rounding.
  * tensor = 0 (the default): every product on the FP64 pipe, as for wider
  * networks and the other passes (measured slightly faster: without the Gram the
  * FP64 pass is a chain of dependent FP64 operations per point).  GW_DFLOAT

@@ -4,13 +4,13 @@ oracle.
 
 Both forms compute the Fisher matrix of Sec. 3.2 (Eqs. 3.1-3.3) in FP64; they
 differ only in rounding: the tensor-core form is the exact Gram of the tangents
-rounded to 56 bits relative to each column's maximum, combined in FP64 over the
-digit pairs, the FP64-pipe form rounds every one of its fused multiply-adds,
+rounded to 56 bits relative to each column's maximum, summed exactly over the
+digit pairs and rounded once to FP64, the FP64-pipe form rounds every one of its fused multiply-adds,
 and the two evaluate the grid powers of v in different orders.  Elementwise
 they agree to ~1e-14 of sqrt(Gamma_ii Gamma_jj); the bound below is 1e-12.
 
 Cases cover one- and two-round work items (grids of 200 to 20000 points, items
-of up to 256 points), both parameter counts (9: one L-shaped detector without
+of up to 128 points), both parameter counts (9: one L-shaped detector without
 Earth rotation; 11: the triangle with rotation), a tabulated PSD, duty-factor
 arm masks (empty interferometer slots), and a network wider than two
 interferometers per point (which keeps the FP64-pipe kernel: the two settings
