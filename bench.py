@@ -6,16 +6,19 @@ batched FP64 Cholesky inversion with the conditioning check, and, in the mixed
 path, the precision refinement (events whose mixed inversion fails or whose
 condition number exceeds 1e7 are recomputed in FP64).  The default workload is
 the 1e5-event uneven catalog (70 % BBH / 30 % tidal BNS, rotating triangle,
-per-event log grid from 2 Hz to f_ISCO).  The headline is the double-float path
-(every per-point quantity in double-float arithmetic on the FP32 pipe, the
-Fisher matrix the exact Gram of the tangents on the tensor cores: FP64-class
-errors in one pass, no refinement); the FP64 path is timed on the same catalog
-as the second arm, and the stored oracle results of 1000 stratified events
-give the error of the FP64, mixed (with refinement) and double-float paths.
+per-event log grid from 2 Hz to f_ISCO).  The headline is the routed step
+(gw_fisher_routed: the precision chosen per event -- the double-float path,
+every per-point quantity in double-float arithmetic on the FP32 pipe and the
+Fisher matrix the exact Gram of the tangents on the tensor cores, for the BBH,
+whose two spins make their Fisher matrices ill-conditioned; the mixed path for
+the rest, with a double-float recomputation of any event whose condition
+number exceeds 1e7); the FP64 path is timed on the same catalog as the second
+arm, and the stored oracle results of 1000 stratified events give the error of
+the FP64, mixed (with refinement), double-float and routed paths.
 Inputs are resident in HBM before the timed region; L2 is flushed (256 MiB
 write) before every timed step.
 
-  python bench.py [--gpus N --steps K --warmup W] [--precision dfloat|mixed|fp64]
+  python bench.py [--gpus N --steps K --warmup W] [--precision routed|dfloat|mixed|fp64]
                   [--grid literal|stress] [--workload c3|c4|c3-gated]
                   [--impl ours|reference]
 
@@ -89,8 +92,12 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", choices=["mixed", "fp64", "dfloat"], default="dfloat",
-                    help="dfloat: double-float tangents on the FP32 pipe with the exact "
+    ap.add_argument("--precision", choices=["routed", "mixed", "fp64", "dfloat"],
+                    default="routed",
+                    help="routed: precision chosen per event (gw_fisher_routed: double-float "
+                         "for the BBH, whose two spins make them ill-conditioned, mixed for the "
+                         "rest with a double-float recomputation of any ill-conditioned one); "
+                         "dfloat: double-float tangents on the FP32 pipe with the exact "
                          "tensor-core Gram (FP64-class results in one pass); mixed: FP32 "
                          "tangents with compensated sums and FP64 refinement of the "
                          "ill-conditioned events; fp64: every operation in FP64")
@@ -378,11 +385,16 @@ def golden_error(gw, refine_cond):
     ok = (z["c3lit_inv_status"] & 33) == 0
     out = {"events": int(len(kappa)), "oracle_flagged": int((~ok).sum())}
     for name, prec in (("mixed_refined", gw.GW_MIXED), ("dfloat", gw.GW_DFLOAT),
-                       ("fp64", gw.GW_FP64)):
-        F, snr, st = gw.gw_fisher(cat, net, N_PAR, prec)
-        inv = gw.gw_fisher_inverse(F, N_PAR)
-        nref = gw.gw_fisher_refine(cat, net, N_PAR, F, snr, st, inv, cond_th=refine_cond) \
-            if prec == gw.GW_MIXED else 0
+                       ("fp64", gw.GW_FP64), ("routed", None)):
+        if prec is None:
+            # double-float for the BBH (pset 1), mixed + FP64 refinement for the rest
+            r = gw.gw_fisher_routed(cat, net, N_PAR, 1 << 1, cond_th=refine_cond)
+            inv, nref = r[3:7], r[-1]
+        else:
+            F, snr, st = gw.gw_fisher(cat, net, N_PAR, prec)
+            inv = gw.gw_fisher_inverse(F, N_PAR)
+            nref = gw.gw_fisher_refine(cat, net, N_PAR, F, snr, st, inv, cond_th=refine_cond) \
+                if prec == gw.GW_MIXED else 0
         torch.cuda.synchronize()
         C = inv[0].cpu().numpy()
         sg = np.sqrt(np.abs(C[diag].T))
@@ -417,6 +429,8 @@ def tune_tiles(gw, a, cat, net, order, prec):
                 **({"ms": e["ms"]} if "ms" in e else {})}
     out = {}
     for p in order:
+        if p < 0:
+            continue        # the routed step: its passes are tuned as themselves
         if p == gw.GW_DFLOAT:
             continue     # one fixed shape (the tensor-core kernel)
         out["mixed" if p == gw.GW_MIXED else "fp64"] = entry(autotune.tune(cat, net, N_PAR, p))
@@ -444,7 +458,10 @@ def run_ours(a):
     import paper_2207_06910_gb300 as gw
     from paper_2207_06910_gb300 import shard
 
-    prec = {"mixed": gw.GW_MIXED, "fp64": gw.GW_FP64, "dfloat": gw.GW_DFLOAT}[a.precision]
+    ROUTED = -1          # the routed step (not a library precision)
+    prec = {"mixed": gw.GW_MIXED, "fp64": gw.GW_FP64, "dfloat": gw.GW_DFLOAT,
+            "routed": ROUTED}[a.precision]
+    routed_counts = {"dfloat": 0, "recomputed": 0}
     gw.gw_set_fp64_gram(a.fp64_gram == "tensor")
     gated = a.workload == "c3-gated"
     cfg = "c3" if gated else a.workload
@@ -495,7 +512,7 @@ def run_ours(a):
     def item_points(p):
         """Points per work item of the Fisher pass at precision p (the
         tensor-core pass takes shorter items)."""
-        tc = p == gw.GW_DFLOAT or (p == gw.GW_FP64 and a.fp64_gram == "tensor")
+        tc = p in (gw.GW_DFLOAT, ROUTED) or (p == gw.GW_FP64 and a.fp64_gram == "tensor")
         return gw.TC_ITEM_POINTS if (tc and n_ifo <= 2) else gw.ITEM_POINTS
 
     def gate(d):
@@ -510,17 +527,28 @@ def run_ours(a):
 
     def forward(d, p):
         """The capturable part of the step: prepare, Fisher with fused SNR VJP,
-        inversion (and the gate for the gated workload)."""
+        inversion (and the gate for the gated workload); the routed step
+        captures only the preparation."""
         cat = gate(d)
+        if p == ROUTED:
+            return [cat, None, None, None, None, None]
         F, snr, st, g = gw.gw_fisher(cat, net, N_PAR, p, grad_snr=grad_up[:cat.n])
         inv = gw.gw_fisher_inverse(F, N_PAR)
         return [cat, F, snr, st, g, inv]
 
     def finish(out, p):
-        """The rest of the step: FP64 refinement of the mixed events (reads back
-        its count), log-det VJP (c4) and its sum over ranks."""
-        cat, F, snr, st, g, inv = out
+        """The rest of the step: the routed Fisher pass and inversion (reads back
+        its split and count), FP64 refinement of the mixed path's events (reads
+        back its count), log-det VJP (c4) and its sum over ranks."""
         nref = 0
+        if p == ROUTED:
+            cr = out[0]
+            r = gw.gw_fisher_routed(cr, net, N_PAR, 1 << 1, grad_snr=grad_up[:cr.n],
+                                    cond_th=a.refine_cond)
+            out[1:6] = [r[0], r[1], r[2], r[7], tuple(r[3:7])]
+            routed_counts["dfloat"], routed_counts["recomputed"] = r[8], r[9]
+            nref = r[9]
+        cat, F, snr, st, g, inv = out
         if p == gw.GW_MIXED:
             nref = gw.gw_fisher_refine(cat, net, N_PAR, F, snr, st, inv, grad_snr=grad_up[:cat.n],
                                        grad_params=g, cond_th=a.refine_cond)
@@ -578,6 +606,20 @@ def run_ours(a):
         ms, ms_ref = [], []
         pts_ref = 0
         gw.gw_set_profiling(True)
+        if p == ROUTED:
+            # the routed step's dominant kernel: the double-float pass over its
+            # BBH (pset 1) events, timed on its own (measurement only)
+            cr = gate(dev)
+            ps = cr.pset[cr.sel] if cr.sel is not None else cr.pset
+            sub = cr.select(torch.nonzero(ps == 1).flatten())
+            routed_counts["points_df"] = int(sub.npts[sub.sel].to(torch.int64).sum().item())
+            for _ in range(4):
+                flush.zero_()
+                gw.gw_fisher(sub, net, N_PAR, gw.GW_DFLOAT, grad_snr=grad_up[:sub.n])
+                ms.append(gw.gw_point_kernel_ms())
+            gw.gw_set_profiling(False)
+            torch.cuda.synchronize()
+            return float(np.min(ms)), 0.0, 0
         for _ in range(4):
             flush.zero_()
             cat, F, snr, st, g, inv = forward(dev, p)
@@ -619,6 +661,35 @@ def run_ours(a):
         if p == prec:
             clocks = c
         gw.gw_reserve(0, 0, 0)
+    # ---- the routed step beside the double-float headline (gw_fisher_routed:
+    # double-float for the BBH, mixed for the rest with a double-float
+    # recomputation of its ill-conditioned events; host synchronisations
+    # inside, so launched call by call), same catalog and timing; one GPU
+    routed = None
+    if prec == gw.GW_DFLOAT and not a.no_fp64_arm and not gated and not with_logdet \
+            and n_ifo <= 2 and world == 1:
+        def run_routed():
+            cr = gate(dev)
+            return cr.n, gw.gw_fisher_routed(cr, net, N_PAR, 1 << 1, grad_snr=grad_up[:cr.n],
+                                             cond_th=a.refine_cond)
+        for _ in range(a.warmup):
+            run_routed()
+        torch.cuda.synchronize()
+        rev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(a.steps)]
+        for i in range(a.steps):
+            flush.zero_()
+            rev[i][0].record(stream)
+            nr, rr = run_routed()
+            rev[i][1].record(stream)
+        torch.cuda.synchronize()
+        r_ms = float(sum(x.elapsed_time(y) for x, y in rev)) / a.steps
+        routed = {"value": nr / (r_ms * 1e-3), "unit": "events/s", "ms_per_step": r_ms,
+                  "events_dfloat": rr[-2], "events_recomputed": rr[-1],
+                  "step": "prepare + gw_fisher_routed (split by parameter set, double-float "
+                          "Fisher for the BBH, mixed Fisher + inversion check + double-float "
+                          "recomputation of the ill-conditioned others, inversion, fused SNR "
+                          "VJP), launched call by call"}
     head = arms[prec]
     cat, F, snr, st, g, inv = head["out"]
     assert int((st != 0).sum()) == 0, "events flagged in the benchmark catalog"
@@ -747,13 +818,17 @@ def run_ours(a):
             if kern_ref_ms > 0:
                 kernels.append(fp64_entry("refinement of the ill-conditioned events", kern_ref_ms,
                                           pts_ref))
-        elif prec == gw.GW_DFLOAT and n_ifo <= 2:
+        elif prec in (gw.GW_DFLOAT, ROUTED) and n_ifo <= 2:
             # the method's FP64-class arithmetic against the FP64 pipe's peak:
             # the kernel runs it as double-float on the FP32 pipe and as exact
             # digit products on the tensor cores, so it can exceed that peak
+            # (the routed step: the double-float pass over its BBH events)
             tfl = tc_digit_flops_per_point(n_ifo, N_PAR)
+            pts_df = routed_counts["points_df"] if prec == ROUTED else n_points
             kernels.append({
-                "kernel": "k_fisher_tc<double-float> (Fisher)", "ms": kern_ms, "points": n_points,
+                "kernel": "k_fisher_tc<double-float> (Fisher" +
+                          (", the routed step's BBH events)" if prec == ROUTED else ")"),
+                "ms": kern_ms, "points": pts_df,
                 "bound": "alu", "peak": peak64,
                 "peak_basis": f"FP64 pipe: {sms} SMs x {FP64_FMA_PER_CLK_SM} FMA/clk x 2 flops "
                               f"x {sm_mhz:.0f} MHz (the method's arithmetic in FP64; executed as "
@@ -763,7 +838,7 @@ def run_ours(a):
                 "pipe_flops_per_point": algo_fp,
                 "issue": {
                     "warp_instructions_per_point": ISSUE_WARP_INSTR_PER_POINT["dfloat_tc"],
-                    "achieved": ISSUE_WARP_INSTR_PER_POINT["dfloat_tc"] * n_points /
+                    "achieved": ISSUE_WARP_INSTR_PER_POINT["dfloat_tc"] * pts_df /
                                 (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else None,
                     "peak": sms * 4 * sm_mhz * 1e6 / 1e9, "unit": "G warp instructions/s",
                     "peak_basis": f"{sms} SMs x 4 schedulers x 1 instruction/clk x {sm_mhz:.0f} MHz",
@@ -771,11 +846,12 @@ def run_ours(a):
                               "literal-grid catalog, scaled by this launch's points"},
                 "gram_on_tensor_cores": {
                     "digit_flops_per_point": tfl,
-                    "achieved": tfl * n_points / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None,
+                    "achieved": tfl * pts_df / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None,
                     "peak": peak_bf16, "unit": "TFLOP/s",
                     "peak_basis": "measured cuBLAS bf16 (burst)"}})
         else:
-            kernels.append(fp64_entry("Fisher", kern_ms, n_points))
+            kernels.append(fp64_entry("Fisher", kern_ms,
+                                      routed_counts["points_df"] if prec == ROUTED else n_points))
         for k in kernels:
             # the flops of the kernel's bound pipe: the method's FP64 count, less the
             # Gram where the tensor cores form it
@@ -848,7 +924,10 @@ def run_ours(a):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"mixed": "f32+f64 (mixed, FP64 refinement)", "fp64": "f64",
                       "dfloat": "double-float (f32 pairs) tangents, exact bf16-digit Gram, "
-                                "f64 combination"}[a.precision],
+                                "f64 combination",
+                      "routed": "per event: double-float (f32 pairs) + exact bf16-digit Gram "
+                                "for the BBH, f32+f64 mixed for the rest (double-float "
+                                "recomputation above kappa 1e7)"}[a.precision],
             "data": "synthetic (seeded, gwcat)",
             "config": {"workload": {"c3": WORKLOAD, "c4": WORKLOAD_C4,
                                     "c3-gated": WORKLOAD_GATED}[a.workload],
@@ -864,14 +943,16 @@ def run_ours(a):
                        **({"selected_events_rank0": n_sel, "fisher_points_rank0": n_points}
                           if gated else {}),
                        "l2": "flushed before every timed step (256 MiB write)",
-                       "launch": "eager calls" if a.eager else
-                                 "one CUDA graph replay per step + the refinement's calls",
+                       "launch": "eager calls" if a.eager else (
+                                 "the preparation as a CUDA graph replay + gw_fisher_routed "
+                                 "called per step (it reads back its split)" if prec == ROUTED
+                                 else "one CUDA graph replay per step + the refinement's calls"),
                        "parallelism": f"one catalog split into {world} cost-balanced contiguous "
                                       f"ranges, one per GPU" + (
                                           "; log-det gradient all-reduced (SUM) per step"
                                           if with_logdet and world > 1 else "; no collective")},
             "clocks": clocks,
-            "refined_fraction": refined_frac if prec == gw.GW_MIXED else None,
+            "refined_fraction": refined_frac if prec in (gw.GW_MIXED, ROUTED) else None,
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "copies": "pinned host buffers, on a copy stream overlapping the "
@@ -890,11 +971,20 @@ def run_ours(a):
             line["fp64_arm"] = {"value": rates[4], "unit": "events/s", "ms_per_step": fp64_ms / a.steps,
                                 "point_kernel_ms": fp64_kern_ms, "clocks": fp64["clocks"]}
             line[f"{a.precision}_over_fp64"] = value / rates[4]
+            if routed is not None:
+                line["routed_arm"] = routed
+                line["routed_over_fp64"] = routed["value"] / rates[4]
         # launches per step: prepare 1; Fisher 7 (event setup, scan 3, point loop,
         # finish, SNR VJP); inversion 1; refinement (when it selects events) 22:
         # flag + scan 3 + compact, gather, FP64 Fisher 7, inversion, 8 scatters,
         # else 5; log-det VJP 6; gated: SNR pass 6 and gate 5
         per_step = 1 + 7 + 1 + (6 if with_logdet else 0) + (11 if gated else 0)
+        if prec == ROUTED:
+            # prepare 1; split 9 (flag, two scans of 3, two compactions); per
+            # part: gather, Fisher 7, inversion, 8 scatters; the mixed part's
+            # refinement 22 when it selects events, else 5
+            per_step = 1 + 9 + 2 * 17 + (6 if with_logdet else 0) + (11 if gated else 0)
+            per_step += 22 if n_refined > 0 else 5
         if prec == gw.GW_MIXED:
             per_step += 22 if n_refined > 0 else 5
         line["gpu_launches"] = per_step * a.steps

@@ -64,7 +64,7 @@ EXPORTS = ("gw_create", "gw_destroy", "gw_last_error", "gw_abi_version", "gw_pre
            "gw_select_snr", "gw_fisher_eig", "gw_covariance", "gw_packed_submatrix",
            "gw_sky_area", "gw_strain", "gw_perturb_fisher", "gw_logdet_vjp_detangles_masked",
            "gw_fma_rate", "gw_fisher_refine", "gw_set_tile", "gw_autotune", "gw_set_fp64_gram",
-           "gw_kernel_faults")
+           "gw_kernel_faults", "gw_fisher_routed")
 
 _lib = None
 
@@ -114,6 +114,8 @@ def load_library(path: str | None = None):
                                 ctypes.c_int, _P, _P]
     lib.gw_fisher_refine.argtypes = [_P, C, N, ctypes.c_int, d, d] + [_P] * 10 + [
         ctypes.POINTER(i64), _P]
+    lib.gw_fisher_routed.argtypes = [_P, C, N, ctypes.c_int, ctypes.c_uint32, d, d] + [_P] * 9 + [
+        ctypes.POINTER(i64), ctypes.POINTER(i64), _P]
     lib.gw_set_tile.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.gw_set_fp64_gram.argtypes = [_P, ctypes.c_int]
     lib.gw_kernel_faults.argtypes = [_P, ctypes.POINTER(i32), ctypes.c_int]
@@ -517,6 +519,39 @@ def gw_fisher_refine(cat: Catalog, net: Network, n_par: int, fisher, snr, status
         _stream(stream))
     _check(st, ctx)
     return int(cnt.value)
+
+
+def gw_fisher_routed(cat: Catalog, net: Network, n_par: int, dfloat_psets: int = 1 << 1,
+                     grad_snr: torch.Tensor | None = None, cond_th=REFINE_COND, cond_max=1e50,
+                     stream=None, out=None):
+    """Fisher pass and inversion with the precision chosen per event: parameter
+    sets with their bit in ``dfloat_psets`` in double-float, the others mixed
+    with the FP64 refinement of ill-conditioned events.  Returns (fisher, snr,
+    status, cov, cond, inv_err, inv_status[, grad_params], n_dfloat,
+    n_refined)."""
+    ctx = context()
+    dev = cat.t["Mc"].device
+    n, npk = cat.n, n_packed(n_par)
+    if out is None:
+        f64 = dict(dtype=torch.float64, device=dev)
+        fisher, snr = torch.empty((npk, n), **f64), torch.empty(n, **f64)
+        status = torch.empty(n, dtype=torch.int32, device=dev)
+        cov, cond, err = torch.empty((npk, n), **f64), torch.empty(n, **f64), torch.empty(n, **f64)
+        sti = torch.empty(n, dtype=torch.int32, device=dev)
+        gp = torch.empty((n_par, n), **f64) if grad_snr is not None else None
+    else:
+        fisher, snr, status, cov, cond, err, sti = out[:7]
+        gp = out[7] if len(out) > 7 else None
+    c = cat.struct()
+    n_df, n_ref = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = load_library().gw_fisher_routed(
+        ctx, ctypes.byref(c), ctypes.byref(net.net), n_par, int(dfloat_psets), float(cond_th),
+        float(cond_max), _ptr(fisher), _ptr(snr), _ptr(status),
+        _ptr(grad_snr.contiguous() if grad_snr is not None else None), _ptr(gp), _ptr(cov),
+        _ptr(cond), _ptr(err), _ptr(sti), ctypes.byref(n_df), ctypes.byref(n_ref), _stream(stream))
+    _check(st, ctx)
+    res = (fisher, snr, status, cov, cond, err, sti) + ((gp,) if grad_snr is not None else ())
+    return res + (int(n_df.value), int(n_ref.value))
 
 
 def gw_snr_vjp(cat: Catalog, net: Network, n_par: int, grad_snr: torch.Tensor, prec=GW_FP64,

@@ -40,6 +40,17 @@ struct gw_ctx {
     double *ref_g = nullptr;      size_t ref_g_cap = 0;
     double *ref_v = nullptr;      size_t ref_v_cap = 0;     // snr, grad_snr, cond, inv_err
     int32_t *ref_st = nullptr;    size_t ref_st_cap = 0;    // status, inverse status
+    // gw_fisher_routed: the split by parameter set and both parts' results
+    int64_t *rt_flag = nullptr;   size_t rt_flag_cap = 0;
+    int64_t *rt_off = nullptr;    size_t rt_off_cap = 0;
+    int64_t *rt_scan = nullptr;   size_t rt_scan_cap = 0;
+    int64_t *rt_pos = nullptr;    size_t rt_pos_cap = 0;
+    int64_t *rt_rows = nullptr;   size_t rt_rows_cap = 0;
+    double *rt_F = nullptr;       size_t rt_F_cap = 0;
+    double *rt_C = nullptr;       size_t rt_C_cap = 0;
+    double *rt_g = nullptr;       size_t rt_g_cap = 0;
+    double *rt_v = nullptr;       size_t rt_v_cap = 0;      // snr, grad_snr, cond, inv_err
+    int32_t *rt_st = nullptr;     size_t rt_st_cap = 0;     // status, inverse status
     int64_t *h_total = nullptr;   // pinned
     int64_t item_cap = 0;       // > 0: asynchronous mode with this many work items
     int64_t reserved_events = 0;
@@ -466,6 +477,16 @@ gw_status gw_destroy(gw_ctx *ctx)
     cudaFree(ctx->ref_g);
     cudaFree(ctx->ref_v);
     cudaFree(ctx->ref_st);
+    cudaFree(ctx->rt_flag);
+    cudaFree(ctx->rt_off);
+    cudaFree(ctx->rt_scan);
+    cudaFree(ctx->rt_pos);
+    cudaFree(ctx->rt_rows);
+    cudaFree(ctx->rt_F);
+    cudaFree(ctx->rt_C);
+    cudaFree(ctx->rt_g);
+    cudaFree(ctx->rt_v);
+    cudaFree(ctx->rt_st);
     cudaFreeHost(ctx->h_total);
     cudaFree(ctx->kerr);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -834,11 +855,14 @@ gw_status gw_fisher(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, g
                       grad_snr, grad_params, nullptr, nullptr, stream);
 }
 
-gw_status gw_fisher_refine(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, int n_par,
-                           double cond_th, double cond_max, double *fisher, double *snr,
-                           int32_t *status, const double *grad_snr, double *grad_params,
-                           double *cov, double *cond, double *inv_err, int32_t *inv_status,
-                           uint8_t *refined, int64_t *n_refined, void *stream)
+// the refinement with the recomputing pass's precision as a parameter:
+// gw_fisher_refine recomputes in FP64, gw_fisher_routed in double-float
+static gw_status refine_with(gw_precision rprec, gw_ctx *ctx, const gw_catalog *cat,
+                             const gw_network *net, int n_par, double cond_th, double cond_max,
+                             double *fisher, double *snr, int32_t *status, const double *grad_snr,
+                             double *grad_params, double *cov, double *cond, double *inv_err,
+                             int32_t *inv_status, uint8_t *refined, int64_t *n_refined,
+                             void *stream)
 {
     if (!ctx) return GW_EINVAL;
     if (n_refined) *n_refined = 0;
@@ -881,7 +905,7 @@ gw_status gw_fisher_refine(gw_ctx *ctx, const gw_catalog *cat, const gw_network 
     sub.n = m;
     sub.sel = ctx->ref_rows;
     if (grad_snr) CK(launch_gather(m, ctx->ref_pos, grad_snr, r_gin, s));
-    if ((st = run_points(ctx, &sub, net, GW_FP64, MODE_FISHER, n_par, r_st, r_snr, nullptr,
+    if ((st = run_points(ctx, &sub, net, rprec, MODE_FISHER, n_par, r_st, r_snr, nullptr,
                          ctx->ref_F, grad_snr ? r_gin : nullptr, grad_snr ? ctx->ref_g : nullptr,
                          nullptr, nullptr, stream)))
         return st;
@@ -896,6 +920,93 @@ gw_status gw_fisher_refine(gw_ctx *ctx, const gw_catalog *cat, const gw_network 
     if (grad_params) CK(launch_scatter_f64(m, n, n_par, pos, ctx->ref_g, grad_params, s));
     CK(launch_scatter_i32(m, n, pos, r_st, status, s));
     CK(launch_scatter_i32(m, n, pos, r_sti, inv_status, s));
+    return GW_OK;
+}
+
+gw_status gw_fisher_refine(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, int n_par,
+                           double cond_th, double cond_max, double *fisher, double *snr,
+                           int32_t *status, const double *grad_snr, double *grad_params,
+                           double *cov, double *cond, double *inv_err, int32_t *inv_status,
+                           uint8_t *refined, int64_t *n_refined, void *stream)
+{
+    return refine_with(GW_FP64, ctx, cat, net, n_par, cond_th, cond_max, fisher, snr, status,
+                       grad_snr, grad_params, cov, cond, inv_err, inv_status, refined, n_refined,
+                       stream);
+}
+
+gw_status gw_fisher_routed(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, int n_par,
+                           uint32_t dfloat_psets, double cond_th, double cond_max, double *fisher,
+                           double *snr, int32_t *status, const double *grad_snr,
+                           double *grad_params, double *cov, double *cond, double *inv_err,
+                           int32_t *inv_status, int64_t *n_dfloat, int64_t *n_refined,
+                           void *stream)
+{
+    if (!ctx) return GW_EINVAL;
+    if (n_dfloat) *n_dfloat = 0;
+    if (n_refined) *n_refined = 0;
+    if (!cat) return fail(ctx, GW_EINVAL, "catalog: null");
+    if (n_par != 9 && n_par != 11) return fail(ctx, GW_EINVAL, "n_par must be 9 or 11");
+    if (std::isnan(cond_th)) return fail(ctx, GW_EINVAL, "routed: cond_th is NaN");
+    const int64_t n = cat->n;
+    if (n == 0) return GW_OK;
+    if (!fisher || !status || !cov || !cond || !inv_status)
+        return fail(ctx, GW_EINVAL, "routed: fisher, status, cov, cond and inv_status are required");
+    if ((grad_params != nullptr) != (grad_snr != nullptr))
+        return fail(ctx, GW_EINVAL, "routed: grad_params and grad_snr go together");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    gw_status st;
+    if ((st = ensure(ctx, ctx->rt_flag, ctx->rt_flag_cap, (size_t)2 * n))) return st;
+    if ((st = ensure(ctx, ctx->rt_off, ctx->rt_off_cap, (size_t)2 * n + 2))) return st;
+    if ((st = ensure(ctx, ctx->rt_scan, ctx->rt_scan_cap, scan_tmp_size(n)))) return st;
+    if ((st = ensure(ctx, ctx->rt_pos, ctx->rt_pos_cap, (size_t)2 * n))) return st;
+    if ((st = ensure(ctx, ctx->rt_rows, ctx->rt_rows_cap, (size_t)2 * n))) return st;
+    CK(launch_split_pset(n, cat->pset, cat->sel, dfloat_psets, ctx->rt_flag, ctx->rt_off,
+                         ctx->rt_scan, ctx->rt_pos, ctx->rt_rows, s));
+    CK(cudaMemcpyAsync(ctx->h_total, ctx->rt_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t m_df = *ctx->h_total, m_mx = n - m_df;
+    if (n_dfloat) *n_dfloat = m_df;
+    const int npk = n_par * (n_par + 1) / 2;
+    if ((st = ensure(ctx, ctx->rt_F, ctx->rt_F_cap, (size_t)npk * n))) return st;
+    if ((st = ensure(ctx, ctx->rt_C, ctx->rt_C_cap, (size_t)npk * n))) return st;
+    if (grad_snr && (st = ensure(ctx, ctx->rt_g, ctx->rt_g_cap, (size_t)n_par * n))) return st;
+    if ((st = ensure(ctx, ctx->rt_v, ctx->rt_v_cap, (size_t)4 * n))) return st;
+    if ((st = ensure(ctx, ctx->rt_st, ctx->rt_st_cap, (size_t)2 * n))) return st;
+    // part 0: the double-float events, part 1: the mixed ones; each part's
+    // results event-minor and contiguous in the temporaries, at offset base
+    for (int part = 0; part < 2; part++) {
+        const int64_t m = part ? m_mx : m_df, base = part ? m_df : 0;
+        if (m == 0) continue;
+        const int64_t *pos = ctx->rt_pos + part * n;
+        gw_catalog sub = *cat;
+        sub.n = m;
+        sub.sel = ctx->rt_rows + part * n;
+        double *F = ctx->rt_F + npk * base, *C = ctx->rt_C + npk * base;
+        double *g = grad_snr ? ctx->rt_g + n_par * base : nullptr;
+        double *v_snr = ctx->rt_v + base, *v_gin = ctx->rt_v + n + base,
+               *v_cond = ctx->rt_v + 2 * n + base, *v_err = ctx->rt_v + 3 * n + base;
+        int32_t *v_st = ctx->rt_st + base, *v_sti = ctx->rt_st + n + base;
+        if (grad_snr) CK(launch_gather(m, pos, grad_snr, v_gin, s));
+        if ((st = run_points(ctx, &sub, net, part ? GW_MIXED : GW_DFLOAT, MODE_FISHER, n_par, v_st,
+                             v_snr, nullptr, F, grad_snr ? v_gin : nullptr, g, nullptr, nullptr,
+                             stream)))
+            return st;
+        CK(launch_invert(F, m, n_par, cond_max, C, v_cond, v_err, v_sti, s));
+        if (part == 1 &&
+            (st = refine_with(GW_DFLOAT, ctx, &sub, net, n_par, cond_th, cond_max, F, v_snr, v_st,
+                              grad_snr ? v_gin : nullptr, g, C, v_cond, v_err, v_sti, nullptr,
+                              n_refined, stream)))
+            return st;
+        CK(launch_scatter_f64(m, n, npk, pos, F, fisher, s));
+        CK(launch_scatter_f64(m, n, npk, pos, C, cov, s));
+        CK(launch_scatter_f64(m, n, 1, pos, v_snr, snr, s));
+        CK(launch_scatter_f64(m, n, 1, pos, v_cond, cond, s));
+        CK(launch_scatter_f64(m, n, 1, pos, v_err, inv_err, s));
+        if (grad_params) CK(launch_scatter_f64(m, n, n_par, pos, g, grad_params, s));
+        CK(launch_scatter_i32(m, n, pos, v_st, status, s));
+        CK(launch_scatter_i32(m, n, pos, v_sti, inv_status, s));
+    }
     return GW_OK;
 }
 

@@ -181,6 +181,12 @@ cudaError_t launch_refine_select(int64_t n, double cond_th, const int32_t *statu
                                  const int32_t *inv_status, const double *cond, const int64_t *sel,
                                  int64_t *flag, int64_t *off, int64_t *scan_tmp, int64_t *pos,
                                  int64_t *rows, uint8_t *refined, cudaStream_t s);
+// the call's events split by parameter set (bit pset of mask: part a, else b):
+// order-preserving positions and catalog rows of each part; flag, pos, rows
+// [2n], off [2(n + 1)] (part b at offset n, its count at off[2n + 1])
+cudaError_t launch_split_pset(int64_t n, const int8_t *pset, const int64_t *sel, uint32_t mask,
+                              int64_t *flag, int64_t *off, int64_t *scan_tmp, int64_t *pos,
+                              int64_t *rows, cudaStream_t s);
 cudaError_t launch_gather(int64_t m, const int64_t *pos, const double *in, double *out,
                           cudaStream_t s);
 cudaError_t launch_scatter_f64(int64_t m, int64_t n, int rows, const int64_t *pos, const double *in,

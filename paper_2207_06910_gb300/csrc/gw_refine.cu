@@ -43,6 +43,19 @@ __global__ void k_compact_flagged(int64_t n, const int64_t *flag, const int64_t 
     rows[j] = sel ? sel[i] : i;
 }
 
+// the call's events by parameter set: flag_a[i] = 1 when bit pset of mask is
+// set for event i's row, flag_b[i] the complement
+__global__ void k_flag_pset(int64_t n, const int8_t *pset, const int64_t *sel, uint32_t mask,
+                            int64_t *flag_a, int64_t *flag_b)
+{
+    const int64_t i = blockIdx.x * (int64_t)BS + threadIdx.x;
+    if (i >= n) return;
+    const int p = pset ? (int)pset[sel ? sel[i] : i] : 0;
+    const bool a = p >= 0 && p < 32 && ((mask >> p) & 1u);
+    flag_a[i] = a ? 1 : 0;
+    flag_b[i] = a ? 0 : 1;
+}
+
 __global__ void k_gather(int64_t m, const int64_t *pos, const double *in, double *out)
 {
     const int64_t j = blockIdx.x * (int64_t)BS + threadIdx.x;
@@ -75,6 +88,24 @@ cudaError_t launch_refine_select(int64_t n, double cond_th, const int32_t *statu
     if ((e = launch_scan(flag, n, off, scan_tmp, s)) != cudaSuccess) return e;
     k_compact_flagged<<<blocks(n), BS, 0, s>>>(n, flag, off, sel, pos, rows);
     return cudaGetLastError();
+}
+
+cudaError_t launch_split_pset(int64_t n, const int8_t *pset, const int64_t *sel, uint32_t mask,
+                              int64_t *flag, int64_t *off, int64_t *scan_tmp, int64_t *pos,
+                              int64_t *rows, cudaStream_t s)
+{
+    // flag, pos, rows: [2n]; off: [2(n + 1)]; part a first, part b at offset n
+    if (n <= 0) return cudaSuccess;
+    k_flag_pset<<<blocks(n), BS, 0, s>>>(n, pset, sel, mask, flag, flag + n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int part = 0; part < 2; part++) {
+        int64_t *fl = flag + part * n, *of = off + part * (n + 1);
+        if ((e = launch_scan(fl, n, of, scan_tmp, s)) != cudaSuccess) return e;
+        k_compact_flagged<<<blocks(n), BS, 0, s>>>(n, fl, of, sel, pos + part * n, rows + part * n);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_gather(int64_t m, const int64_t *pos, const double *in, double *out,
