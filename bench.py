@@ -975,18 +975,18 @@ def run_ours(a):
                 line["routed_arm"] = routed
                 line["routed_over_fp64"] = routed["value"] / rates[4]
         # launches per step: prepare 1; Fisher 7 (event setup, scan 3, point loop,
-        # finish, SNR VJP); inversion 1; refinement (when it selects events) 22:
-        # flag + scan 3 + compact, gather, FP64 Fisher 7, inversion, 8 scatters,
-        # else 5; log-det VJP 6; gated: SNR pass 6 and gate 5
+        # finish, SNR VJP); inversion 1; refinement (when it selects events) 15:
+        # flag + scan 3 + compact, gather, Fisher 7, inversion, one scatter of
+        # every result, else 5; log-det VJP 6; gated: SNR pass 6 and gate 5
         per_step = 1 + 7 + 1 + (6 if with_logdet else 0) + (11 if gated else 0)
         if prec == ROUTED:
             # prepare 1; split 9 (flag, two scans of 3, two compactions); per
-            # part: gather, Fisher 7, inversion, 8 scatters; the mixed part's
-            # refinement 22 when it selects events, else 5
-            per_step = 1 + 9 + 2 * 17 + (6 if with_logdet else 0) + (11 if gated else 0)
-            per_step += 22 if n_refined > 0 else 5
+            # part: gather, Fisher 7, inversion, one scatter; the mixed part's
+            # recomputation 15 when it selects events, else 5
+            per_step = 1 + 9 + 2 * 10 + (6 if with_logdet else 0) + (11 if gated else 0)
+            per_step += 15 if n_refined > 0 else 5
         if prec == gw.GW_MIXED:
-            per_step += 22 if n_refined > 0 else 5
+            per_step += 15 if n_refined > 0 else 5
         line["gpu_launches"] = per_step * a.steps
         print(json.dumps(line), flush=True)
     if world > 1:

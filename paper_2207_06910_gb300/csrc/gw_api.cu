@@ -912,14 +912,16 @@ static gw_status refine_with(gw_precision rprec, gw_ctx *ctx, const gw_catalog *
     CK(launch_invert(ctx->ref_F, m, n_par, cond_max, ctx->ref_C, r_cond, r_err, r_sti, s));
     // written back in place, at the call's indices of the flagged events
     const int64_t *pos = ctx->ref_pos;
-    CK(launch_scatter_f64(m, n, npk, pos, ctx->ref_F, fisher, s));
-    CK(launch_scatter_f64(m, n, npk, pos, ctx->ref_C, cov, s));
-    CK(launch_scatter_f64(m, n, 1, pos, r_snr, snr, s));
-    CK(launch_scatter_f64(m, n, 1, pos, r_cond, cond, s));
-    CK(launch_scatter_f64(m, n, 1, pos, r_err, inv_err, s));
-    if (grad_params) CK(launch_scatter_f64(m, n, n_par, pos, ctx->ref_g, grad_params, s));
-    CK(launch_scatter_i32(m, n, pos, r_st, status, s));
-    CK(launch_scatter_i32(m, n, pos, r_sti, inv_status, s));
+    ScatterSet set;
+    set.add(ctx->ref_F, fisher, npk, 8);
+    set.add(ctx->ref_C, cov, npk, 8);
+    set.add(r_snr, snr, 1, 8);
+    set.add(r_cond, cond, 1, 8);
+    set.add(r_err, inv_err, 1, 8);
+    if (grad_params) set.add(ctx->ref_g, grad_params, n_par, 8);
+    set.add(r_st, status, 1, 4);
+    set.add(r_sti, inv_status, 1, 4);
+    CK(launch_scatter_set(m, n, pos, set, s));
     return GW_OK;
 }
 
@@ -998,14 +1000,16 @@ gw_status gw_fisher_routed(gw_ctx *ctx, const gw_catalog *cat, const gw_network 
                               grad_snr ? v_gin : nullptr, g, C, v_cond, v_err, v_sti, nullptr,
                               n_refined, stream)))
             return st;
-        CK(launch_scatter_f64(m, n, npk, pos, F, fisher, s));
-        CK(launch_scatter_f64(m, n, npk, pos, C, cov, s));
-        CK(launch_scatter_f64(m, n, 1, pos, v_snr, snr, s));
-        CK(launch_scatter_f64(m, n, 1, pos, v_cond, cond, s));
-        CK(launch_scatter_f64(m, n, 1, pos, v_err, inv_err, s));
-        if (grad_params) CK(launch_scatter_f64(m, n, n_par, pos, g, grad_params, s));
-        CK(launch_scatter_i32(m, n, pos, v_st, status, s));
-        CK(launch_scatter_i32(m, n, pos, v_sti, inv_status, s));
+        ScatterSet set;
+        set.add(F, fisher, npk, 8);
+        set.add(C, cov, npk, 8);
+        set.add(v_snr, snr, 1, 8);
+        set.add(v_cond, cond, 1, 8);
+        set.add(v_err, inv_err, 1, 8);
+        if (grad_params) set.add(g, grad_params, n_par, 8);
+        set.add(v_st, status, 1, 4);
+        set.add(v_sti, inv_status, 1, 4);
+        CK(launch_scatter_set(m, n, pos, set, s));
     }
     return GW_OK;
 }

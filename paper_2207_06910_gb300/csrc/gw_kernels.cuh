@@ -189,10 +189,21 @@ cudaError_t launch_split_pset(int64_t n, const int8_t *pset, const int64_t *sel,
                               int64_t *rows, cudaStream_t s);
 cudaError_t launch_gather(int64_t m, const int64_t *pos, const double *in, double *out,
                           cudaStream_t s);
-cudaError_t launch_scatter_f64(int64_t m, int64_t n, int rows, const int64_t *pos, const double *in,
-                               double *out, cudaStream_t s);
-cudaError_t launch_scatter_i32(int64_t m, int64_t n, const int64_t *pos, const int32_t *in,
-                               int32_t *out, cudaStream_t s);
+// event-minor arrays written back at positions pos of an n-event call: for
+// each array of the set, out[k * n + pos[j]] = in[k * m + j], k < its rows,
+// j < m; one launch for the whole set (elements of 8 or 4 bytes; an array
+// with a null destination is left out)
+struct ScatterSet {
+    static constexpr int MAX = 8;
+    int na = 0;
+    int row0[MAX + 1] = {0};      // first row of each array in the set's rows
+    int esz[MAX] = {0};
+    const void *in[MAX] = {nullptr};
+    void *out[MAX] = {nullptr};
+    void add(const void *src, void *dst, int rows, int elem_bytes);
+};
+cudaError_t launch_scatter_set(int64_t m, int64_t n, const int64_t *pos, const ScatterSet &set,
+                               cudaStream_t s);
 
 // out[r] = sum over e of x[r * n + e], r < rows (one block per row, fixed order)
 cudaError_t launch_sum_events(const double *x, int64_t n, int rows, double *out, cudaStream_t s);

@@ -62,14 +62,25 @@ __global__ void k_gather(int64_t m, const int64_t *pos, const double *in, double
     if (j < m) out[j] = in[pos[j]];
 }
 
-// out[k * n + pos[j]] = in[k * m + j] for k < rows (event-minor arrays)
-template <typename T>
-__global__ void k_scatter(int64_t m, int64_t n, int rows, const int64_t *pos, const T *in, T *out)
+// out_a[k * n + pos[j]] = in_a[k * m + j] for every array a of the set and
+// k < its rows (event-minor arrays): one thread per (row of the set, event),
+// so that the loads of a warp are independent and coalesced
+__global__ void k_scatter_set(int64_t m, int64_t n, const int64_t *__restrict__ pos,
+                              ScatterSet set)
 {
     const int64_t j = blockIdx.x * (int64_t)BS + threadIdx.x;
     if (j >= m) return;
+    const int r = blockIdx.y;
+    int a = 0;
+    while (a + 1 < set.na && r >= set.row0[a + 1]) a++;
+    const int64_t k = r - set.row0[a];
     const int64_t i = pos[j];
-    for (int k = 0; k < rows; k++) out[(int64_t)k * n + i] = in[(int64_t)k * m + j];
+    if (set.esz[a] == 8)
+        static_cast<double *>(set.out[a])[k * n + i] =
+            static_cast<const double *>(set.in[a])[k * m + j];
+    else
+        static_cast<int32_t *>(set.out[a])[k * n + i] =
+            static_cast<const int32_t *>(set.in[a])[k * m + j];
 }
 
 unsigned blocks(int64_t n) { return (unsigned)((n + BS - 1) / BS); }
@@ -116,19 +127,22 @@ cudaError_t launch_gather(int64_t m, const int64_t *pos, const double *in, doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_f64(int64_t m, int64_t n, int rows, const int64_t *pos, const double *in,
-                               double *out, cudaStream_t s)
+void ScatterSet::add(const void *src, void *dst, int rows, int elem_bytes)
 {
-    if (m <= 0 || !out) return cudaSuccess;
-    k_scatter<double><<<blocks(m), BS, 0, s>>>(m, n, rows, pos, in, out);
-    return cudaGetLastError();
+    if (!dst || rows <= 0 || na >= MAX) return;
+    in[na] = src;
+    out[na] = dst;
+    esz[na] = elem_bytes;
+    row0[na + 1] = row0[na] + rows;
+    na++;
 }
 
-cudaError_t launch_scatter_i32(int64_t m, int64_t n, const int64_t *pos, const int32_t *in,
-                               int32_t *out, cudaStream_t s)
+cudaError_t launch_scatter_set(int64_t m, int64_t n, const int64_t *pos, const ScatterSet &set,
+                               cudaStream_t s)
 {
-    if (m <= 0 || !out) return cudaSuccess;
-    k_scatter<int32_t><<<blocks(m), BS, 0, s>>>(m, n, 1, pos, in, out);
+    if (m <= 0 || set.na == 0) return cudaSuccess;
+    const dim3 grid(blocks(m), (unsigned)set.row0[set.na]);
+    k_scatter_set<<<grid, BS, 0, s>>>(m, n, pos, set);
     return cudaGetLastError();
 }
 

@@ -910,7 +910,10 @@ cudaError_t launch_invert(const double *fisher, int64_t n, int np, double cond_m
                           double *cond, double *inv_err, int32_t *status, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    int bs = 64;
+    // one warp per block: at ~255 registers a thread, eight warps fit an SM
+    // either way, and a small call (the events a refinement recomputes)
+    // spreads over twice as many SMs as with blocks of two warps
+    int bs = 32;
     unsigned nb = (unsigned)((n + bs - 1) / bs);
     if (np == 9)
         k_invert<9><<<nb, bs, 0, s>>>(fisher, n, cond_max, cov, cond, inv_err, status);
