@@ -981,10 +981,9 @@ def run_ours(a):
         per_step = 1 + 7 + 1 + (6 if with_logdet else 0) + (11 if gated else 0)
         if prec == ROUTED:
             # prepare 1; split 9 (flag, two scans of 3, two compactions); per
-            # part: gather, Fisher 7, inversion, one scatter; the mixed part's
-            # recomputation 15 when it selects events, else 5
-            per_step = 1 + 9 + 2 * 10 + (6 if with_logdet else 0) + (11 if gated else 0)
-            per_step += 15 if n_refined > 0 else 5
+            # part: gather, Fisher 7, inversion, one scatter; after the mixed
+            # part the marking of its events to recompute, scan 3 and compaction
+            per_step = 1 + 9 + 2 * 10 + 5 + (6 if with_logdet else 0) + (11 if gated else 0)
         if prec == gw.GW_MIXED:
             per_step += 15 if n_refined > 0 else 5
         line["gpu_launches"] = per_step * a.steps

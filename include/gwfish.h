@@ -340,11 +340,11 @@ gw_status gw_fisher_refine(gw_ctx *ctx, const gw_catalog *cat, const gw_network 
  * counterpart in the paper; the passes compute Sec. 3.2, Eqs. 3.1-3.3, and the
  * inversion of Sec. 4.1).  Events whose parameter set p has bit p of
  * dfloat_psets set run the double-float pass (GW_DFLOAT); the others run the
- * mixed pass (GW_MIXED) and then gw_fisher_refine's check: those with a failed
- * inversion or a condition number above cond_th are recomputed by the
- * double-float pass (FP64 accuracy class; FP64 for networks it does not
- * take).  Every
- * event is inverted with cond_max.  The precision is a per-event property: an
+ * mixed pass (GW_MIXED) first, then gw_fisher_refine's check: those with a
+ * clean point-loop status and a failed inversion or a condition number above
+ * cond_th join the double-float events in one double-float pass (FP64
+ * accuracy class; FP64 for networks it does not take), whose results are
+ * written over their mixed ones.  Every event is inverted with cond_max.  The precision is a per-event property: an
  * event's results equal those of the pass it was routed to (plus, for the
  * mixed events, the double-float recomputation), in the call's event order.  Use it where one
  * class of events is known to be ill-conditioned (here the BBH, whose two spins
@@ -355,8 +355,8 @@ gw_status gw_fisher_refine(gw_ctx *ctx, const gw_catalog *cat, const gw_network 
  * grad_params [n_par][n] with DEVICE in grad_snr [n] (both or neither: the
  * fused SNR VJP).  HOST out: *n_dfloat, the events routed to the double-float
  * pass, and *n_refined, the mixed events recomputed (either may be
- * NULL).  Reads back the split and the refinement's count (synchronisations
- * of `stream`).  Errors as gw_fisher; GW_EINVAL for a NaN cond_th or missing
+ * NULL).  Reads back the split and the double-float pass's event count
+ * (synchronisations of `stream`).  Errors as gw_fisher; GW_EINVAL for a NaN cond_th or missing
  * required outputs. */
 gw_status gw_fisher_routed(gw_ctx *ctx, const gw_catalog *cat, const gw_network *net, int n_par,
                            uint32_t dfloat_psets, double cond_th, double cond_max, double *fisher,

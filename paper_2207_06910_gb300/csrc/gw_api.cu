@@ -975,31 +975,31 @@ gw_status gw_fisher_routed(gw_ctx *ctx, const gw_catalog *cat, const gw_network 
     if (grad_snr && (st = ensure(ctx, ctx->rt_g, ctx->rt_g_cap, (size_t)n_par * n))) return st;
     if ((st = ensure(ctx, ctx->rt_v, ctx->rt_v_cap, (size_t)4 * n))) return st;
     if ((st = ensure(ctx, ctx->rt_st, ctx->rt_st_cap, (size_t)2 * n))) return st;
-    // part 0: the double-float events, part 1: the mixed ones; each part's
-    // results event-minor and contiguous in the temporaries, at offset base
-    for (int part = 0; part < 2; part++) {
-        const int64_t m = part ? m_mx : m_df, base = part ? m_df : 0;
-        if (m == 0) continue;
-        const int64_t *pos = ctx->rt_pos + part * n;
+    // part b (the mixed events) first: its Fisher pass and inversion, its
+    // results written to the call's outputs, and the events that fail the
+    // conditioning check marked for part a; then part a (the double-float
+    // events and the marked ones) in one pass, written over them.  Each
+    // part's results are event-minor in the temporaries, from offset 0.
+    auto run_part = [&](gw_precision prec, int64_t m, const int64_t *pos,
+                        const int64_t *rows) -> gw_status {
         gw_catalog sub = *cat;
         sub.n = m;
-        sub.sel = ctx->rt_rows + part * n;
-        double *F = ctx->rt_F + npk * base, *C = ctx->rt_C + npk * base;
-        double *g = grad_snr ? ctx->rt_g + n_par * base : nullptr;
-        double *v_snr = ctx->rt_v + base, *v_gin = ctx->rt_v + n + base,
-               *v_cond = ctx->rt_v + 2 * n + base, *v_err = ctx->rt_v + 3 * n + base;
-        int32_t *v_st = ctx->rt_st + base, *v_sti = ctx->rt_st + n + base;
+        sub.sel = rows;
+        double *F = ctx->rt_F, *C = ctx->rt_C;
+        double *g = grad_snr ? ctx->rt_g : nullptr;
+        double *v_snr = ctx->rt_v, *v_gin = ctx->rt_v + n, *v_cond = ctx->rt_v + 2 * n,
+               *v_err = ctx->rt_v + 3 * n;
+        int32_t *v_st = ctx->rt_st, *v_sti = ctx->rt_st + n;
+        gw_status e;
         if (grad_snr) CK(launch_gather(m, pos, grad_snr, v_gin, s));
-        if ((st = run_points(ctx, &sub, net, part ? GW_MIXED : GW_DFLOAT, MODE_FISHER, n_par, v_st,
-                             v_snr, nullptr, F, grad_snr ? v_gin : nullptr, g, nullptr, nullptr,
-                             stream)))
-            return st;
+        if ((e = run_points(ctx, &sub, net, prec, MODE_FISHER, n_par, v_st, v_snr, nullptr, F,
+                            grad_snr ? v_gin : nullptr, g, nullptr, nullptr, stream)))
+            return e;
         CK(launch_invert(F, m, n_par, cond_max, C, v_cond, v_err, v_sti, s));
-        if (part == 1 &&
-            (st = refine_with(GW_DFLOAT, ctx, &sub, net, n_par, cond_th, cond_max, F, v_snr, v_st,
-                              grad_snr ? v_gin : nullptr, g, C, v_cond, v_err, v_sti, nullptr,
-                              n_refined, stream)))
-            return st;
+        if (prec == GW_MIXED)
+            CK(launch_route_recompute(m, cond_th, v_st, v_sti, v_cond, pos, n, cat->sel,
+                                      ctx->rt_flag, ctx->rt_off, ctx->rt_scan, ctx->rt_pos,
+                                      ctx->rt_rows, s));
         ScatterSet set;
         set.add(F, fisher, npk, 8);
         set.add(C, cov, npk, 8);
@@ -1010,7 +1010,18 @@ gw_status gw_fisher_routed(gw_ctx *ctx, const gw_catalog *cat, const gw_network 
         set.add(v_st, status, 1, 4);
         set.add(v_sti, inv_status, 1, 4);
         CK(launch_scatter_set(m, n, pos, set, s));
+        return GW_OK;
+    };
+    int64_t m_a = m_df;
+    if (m_mx > 0) {
+        if ((st = run_part(GW_MIXED, m_mx, ctx->rt_pos + n, ctx->rt_rows + n))) return st;
+        CK(cudaMemcpyAsync(ctx->h_total, ctx->rt_off + n, sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        m_a = *ctx->h_total;
+        if (n_refined) *n_refined = m_a - m_df;
     }
+    if (m_a > 0 && (st = run_part(GW_DFLOAT, m_a, ctx->rt_pos, ctx->rt_rows))) return st;
     return GW_OK;
 }
 

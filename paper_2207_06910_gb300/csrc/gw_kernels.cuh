@@ -187,6 +187,14 @@ cudaError_t launch_refine_select(int64_t n, double cond_th, const int32_t *statu
 cudaError_t launch_split_pset(int64_t n, const int8_t *pset, const int64_t *sel, uint32_t mask,
                               int64_t *flag, int64_t *off, int64_t *scan_tmp, int64_t *pos,
                               int64_t *rows, cudaStream_t s);
+// part b's events to recompute with part a (k_flag_refine's rule on part b's
+// m results, pos_b their call indices) marked in part a's flags, then part a
+// compacted again: off_a [n + 1] (its new count at off_a[n]), pos_a, rows_a [n]
+cudaError_t launch_route_recompute(int64_t m, double cond_th, const int32_t *status,
+                                   const int32_t *inv_status, const double *cond,
+                                   const int64_t *pos_b, int64_t n, const int64_t *sel,
+                                   int64_t *flag_a, int64_t *off_a, int64_t *scan_tmp,
+                                   int64_t *pos_a, int64_t *rows_a, cudaStream_t s);
 cudaError_t launch_gather(int64_t m, const int64_t *pos, const double *in, double *out,
                           cudaStream_t s);
 // event-minor arrays written back at positions pos of an n-event call: for

@@ -43,6 +43,19 @@ __global__ void k_compact_flagged(int64_t n, const int64_t *flag, const int64_t 
     rows[j] = sel ? sel[i] : i;
 }
 
+// the recomputation rule of k_flag_refine on the m events of a part, marked
+// in the other part's flags at the call's indices pos[j]: flag[pos[j]] = 1
+// for each event to recompute (the other entries are left as they are)
+__global__ void k_mark_refine(int64_t m, double cond_th, const int32_t *status,
+                              const int32_t *inv_status, const double *cond, const int64_t *pos,
+                              int64_t *flag)
+{
+    const int64_t j = blockIdx.x * (int64_t)BS + threadIdx.x;
+    if (j >= m) return;
+    const bool inv_bad = (inv_status[j] & (1 | 4)) != 0;   // NOT_PD, NONFINITE
+    if (status[j] == 0 && (inv_bad || !(cond[j] <= cond_th))) flag[pos[j]] = 1;
+}
+
 // the call's events by parameter set: flag_a[i] = 1 when bit pset of mask is
 // set for event i's row, flag_b[i] the complement
 __global__ void k_flag_pset(int64_t n, const int8_t *pset, const int64_t *sel, uint32_t mask,
@@ -98,6 +111,24 @@ cudaError_t launch_refine_select(int64_t n, double cond_th, const int32_t *statu
     if (e != cudaSuccess) return e;
     if ((e = launch_scan(flag, n, off, scan_tmp, s)) != cudaSuccess) return e;
     k_compact_flagged<<<blocks(n), BS, 0, s>>>(n, flag, off, sel, pos, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_route_recompute(int64_t m, double cond_th, const int32_t *status,
+                                   const int32_t *inv_status, const double *cond,
+                                   const int64_t *pos_b, int64_t n, const int64_t *sel,
+                                   int64_t *flag_a, int64_t *off_a, int64_t *scan_tmp,
+                                   int64_t *pos_a, int64_t *rows_a, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e;
+    if (m > 0) {
+        k_mark_refine<<<blocks(m), BS, 0, s>>>(m, cond_th, status, inv_status, cond, pos_b,
+                                               flag_a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = launch_scan(flag_a, n, off_a, scan_tmp, s)) != cudaSuccess) return e;
+    k_compact_flagged<<<blocks(n), BS, 0, s>>>(n, flag_a, off_a, sel, pos_a, rows_a);
     return cudaGetLastError();
 }
 
