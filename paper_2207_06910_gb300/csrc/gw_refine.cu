@@ -1,7 +1,9 @@
-// gw_refine.cu -- kernels of gw_fisher_refine: the events whose mixed-precision
-// covariance is not determined to the mixed path's tolerance are selected by
-// their condition number (Sec. 4.1: the conditioning check of the inversion),
-// recomputed by the FP64 path, and written back in place.
+// gw_refine.cu -- kernels of gw_fisher_refine and gw_fisher_routed: the
+// events whose mixed-precision covariance is not determined to the mixed
+// path's tolerance are selected by their condition number (Sec. 4.1: the
+// conditioning check of the inversion), recomputed by the FP64 path
+// (gw_fisher_refine) or the double-float path (gw_fisher_routed, which also
+// splits a call's events by parameter set), and written back in place.
 //
 // Why a condition-number test: the mixed path's Fisher matrix carries an
 // elementwise error of ~1e-7 of sqrt(Gamma_ii Gamma_jj) (FP32 patterns,
