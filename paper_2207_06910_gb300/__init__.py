@@ -525,10 +525,11 @@ def gw_fisher_routed(cat: Catalog, net: Network, n_par: int, dfloat_psets: int =
                      grad_snr: torch.Tensor | None = None, cond_th=REFINE_COND, cond_max=1e50,
                      stream=None, out=None):
     """Fisher pass and inversion with the precision chosen per event: parameter
-    sets with their bit in ``dfloat_psets`` in double-float, the others mixed
-    with the FP64 refinement of ill-conditioned events.  Returns (fisher, snr,
-    status, cov, cond, inv_err, inv_status[, grad_params], n_dfloat,
-    n_refined)."""
+    sets with their bit in ``dfloat_psets`` in double-float, the others mixed,
+    those of them with a failed inversion or a condition number above
+    ``cond_th`` recomputed in double-float.  Returns (fisher, snr, status, cov,
+    cond, inv_err, inv_status[, grad_params], n_dfloat, n_refined), n_refined
+    the mixed events recomputed."""
     ctx = context()
     dev = cat.t["Mc"].device
     n, npk = cat.n, n_packed(n_par)
